@@ -1,0 +1,369 @@
+"""FP64 CPU oracle of the differentiable tile rasterizer (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
+import this package. It wraps ``lobe_oracle.c`` (plain C, double precision, compiled
+with ``-ffp-contract=off``) through ctypes and shares no code with the CUDA library.
+
+Every function takes float64 numpy arrays (float32 inputs are widened exactly) and
+returns float64 / int32 arrays. One call handles one (Gaussian set, camera) item; a
+batch of items is a Python loop over items.
+
+Parity-unpinned parts: none of the functions below is unpinned; the pins live in
+``tests/test_oracle_*.py`` (closed forms, library routines, invariants, brute force and
+central finite differences).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lobe_oracle.c")
+_LIB = os.path.join(_HERE, "liblobe_oracle.so")
+
+# margin order: rel (alpha/T/clamp), px (rect edges), rad (3 sqrt(lambda) near integer),
+# col (colour clamp), sig (sigma near 0), guard (fov guard, relative)
+MARGINS_NONE = np.zeros(6)
+# same float32 inputs on both sides: only the renderer's float32 arithmetic differs
+MARGINS_STAGE = np.array([2e-5, 1e-4, 2e-6, 1e-6, 1e-5, 1e-6])
+# end to end: the GPU's float32 projection feeds its renderer
+MARGINS_E2E = np.array([5e-4, 2e-3, 2e-5, 2e-5, 1e-4, 2e-5])
+
+F_GUARD, F_RADIUS, F_RECT, F_COLOR = 1, 2, 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile lobe_oracle.c into liblobe_oracle.so (gcc, -O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", _LIB, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _lib.orc_bin.restype = ctypes.c_int64
+        _lib.orc_depth_key.restype = ctypes.c_uint32
+        _lib.orc_depth_key.argtypes = [ctypes.c_double]
+        _lib.orc_round_f32.restype = ctypes.c_float
+        _lib.orc_round_f32.argtypes = [ctypes.c_double]
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _u8(a):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cam_vector(cam) -> np.ndarray:
+    """[viewmat(16), fx, fy, cx, cy, width, height, near, far] as float64 (from float32 values)."""
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    v = np.empty(24)
+    v[:16] = np.asarray(c["viewmat"], np.float32).astype(np.float64).reshape(16)
+    v[16:20] = np.float32([c["fx"], c["fy"], c["cx"], c["cy"]]).astype(np.float64)
+    v[20], v[21] = c["width"], c["height"]
+    v[22], v[23] = np.float32(c["near"]), np.float32(c["far"])
+    return v
+
+
+@dataclass
+class Projection:
+    mean2d: np.ndarray
+    conic: np.ndarray
+    color: np.ndarray
+    opacity: np.ndarray
+    depth: np.ndarray
+    radius: np.ndarray
+    rect: np.ndarray
+    flags: np.ndarray
+    radius_all: np.ndarray
+
+    @property
+    def n(self):
+        return self.radius.shape[0]
+
+    def rounded(self) -> "Projection":
+        """The same projection with every float rounded to float32 (what a float32 stage sees)."""
+        r = lambda a: a.astype(np.float32).astype(np.float64)
+        return Projection(r(self.mean2d), r(self.conic), r(self.color), r(self.opacity),
+                          self.depth.copy(), self.radius.copy(), self.rect.copy(), self.flags.copy(),
+                          self.radius_all.copy())
+
+
+def project(g, cam, tile=(16, 16), sh_degree=3, crop=None, margins=MARGINS_NONE) -> Projection:
+    L = lib()
+    n = g["means"].shape[0]
+    means, pm = _d(g["means"])
+    ls, pls = _d(g["log_scales"])
+    q, pq = _d(g["quats"])
+    lo, plo = _d(g["opacity_logits"])
+    sh, psh = _d(g["sh"])
+    cr, pcr = _u8(crop)
+    cv, pcv = _d(cam_vector(cam))
+    mg, pmg = _d(margins)
+    out = Projection(np.zeros((n, 2)), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n), np.zeros(n),
+                     np.zeros(n, np.int32), np.zeros((n, 4), np.int32), np.zeros(n, np.int32),
+                     np.zeros(n, np.int32))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    L.orc_project(ctypes.c_int64(n), pm, pls, pq, plo, psh, ctypes.c_int(sh_degree), pcr, pcv,
+                  ctypes.c_int(tile[0]), ctypes.c_int(tile[1]), pmg,
+                  ptr(out.mean2d), ptr(out.conic), ptr(out.color), ptr(out.opacity), ptr(out.depth),
+                  ptr(out.radius), ptr(out.rect), ptr(out.flags), ptr(out.radius_all))
+    return out
+
+
+def grid(cam, tile):
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    return (c["width"] + tile[0] - 1) // tile[0], (c["height"] + tile[1] - 1) // tile[1]
+
+
+def bin_sort(p: Projection, cam, tile=(16, 16)):
+    """(ids, tile_start): Gaussian index of every pair in (tile, depth, index) order, and the
+    first pair of every tile (n_tiles + 1 entries)."""
+    L = lib()
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    m2, pm2 = _d(p.mean2d)
+    rad, pr = _i(p.radius)
+    dep, pd = _d(p.depth)
+    total = L.orc_bin(ctypes.c_int64(p.n), pm2, pr, pd, W, H, tile[0], tile[1], None, None)
+    gx, gy = grid(c, tile)
+    ids = np.zeros(max(total, 1), np.int32)
+    ts = np.zeros(gx * gy + 1, np.int32)
+    L.orc_bin(ctypes.c_int64(p.n), pm2, pr, pd, W, H, tile[0], tile[1],
+              ids.ctypes.data_as(ctypes.c_void_p), ts.ctypes.data_as(ctypes.c_void_p))
+    return ids[:total], ts
+
+
+def flag_pixels(p: Projection, cam, tile=(16, 16)) -> np.ndarray:
+    """int32 [H*W]: pixels a marginal Gaussian decision could change."""
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    pxf = np.zeros(W * H, np.int32)
+    fl, pfl = _i(p.flags)
+    m2, pm2 = _d(p.mean2d)
+    r, pr = _i(p.radius)
+    ra, pra = _i(p.radius_all)
+    lib().orc_flag_marginal_gaussians(ctypes.c_int64(p.n), pfl, pm2, pr, pra, W, H, tile[0], tile[1],
+                                      pxf.ctypes.data_as(ctypes.c_void_p))
+    return pxf
+
+
+@dataclass
+class Image:
+    rgb: np.ndarray       # [3,H,W]
+    T_final: np.ndarray   # [H,W]
+    n_contrib: np.ndarray  # [H,W] int32
+    flags: np.ndarray     # [H,W] int32, 1 = some decision on this pixel is marginal
+    wsum: np.ndarray      # [H,W] sum_i alpha_i T_i
+
+
+def render_fwd(p: Projection, ids, tile_start, cam, tile=(16, 16), bg=(0.0, 0.0, 0.0),
+               margins=MARGINS_NONE, pixel_flags=None) -> Image:
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    rgb = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    nc = np.zeros((H, W), np.int32)
+    fl = np.zeros((H, W), np.int32) if pixel_flags is None else \
+        np.ascontiguousarray(pixel_flags, np.int32).reshape(H, W).copy()
+    ws = np.zeros((H, W))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m2, _ = _d(p.mean2d)
+    cn, _ = _d(p.conic)
+    co, _ = _d(p.color)
+    op, _ = _d(p.opacity)
+    ids_, _ = _i(ids if len(ids) else np.zeros(1, np.int32))
+    ts, _ = _i(tile_start)
+    bgv, _ = _d(np.asarray(bg, np.float64))
+    mg, _ = _d(margins)
+    lib().orc_render_fwd(W, H, tile[0], tile[1], ptr(m2), ptr(cn), ptr(co), ptr(op), ptr(ids_), ptr(ts),
+                         ptr(bgv), ptr(mg), ptr(rgb), ptr(T), ptr(nc), ptr(fl), ptr(ws))
+    return Image(rgb, T, nc, fl, ws)
+
+
+def render_untiled(p: Projection, cam, tile=(16, 16), respect_rect=True, bg=(0.0, 0.0, 0.0),
+                   margins=MARGINS_NONE):
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    rgb = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    fl = np.zeros((H, W), np.int32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m2, _ = _d(p.mean2d)
+    cn, _ = _d(p.conic)
+    co, _ = _d(p.color)
+    op, _ = _d(p.opacity)
+    r, _ = _i(p.radius)
+    dp, _ = _d(p.depth)
+    bgv, _ = _d(np.asarray(bg, np.float64))
+    mg, _ = _d(margins)
+    lib().orc_render_untiled(ctypes.c_int64(p.n), W, H, tile[0], tile[1], ptr(m2), ptr(cn), ptr(co),
+                             ptr(op), ptr(r), ptr(dp), int(respect_rect), ptr(bgv), ptr(mg), ptr(rgb),
+                             ptr(T), ptr(fl))
+    return rgb, T, fl
+
+
+@dataclass
+class Grad2D:
+    mean2d: np.ndarray
+    conic: np.ndarray
+    color: np.ndarray
+    opacity: np.ndarray
+
+
+def render_bwd(p: Projection, ids, tile_start, cam, dL_drgb, tile=(16, 16), bg=(0.0, 0.0, 0.0)) -> Grad2D:
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    n = p.n
+    out = Grad2D(np.zeros((n, 2)), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m2, _ = _d(p.mean2d)
+    cn, _ = _d(p.conic)
+    co, _ = _d(p.color)
+    op, _ = _d(p.opacity)
+    ids_, _ = _i(ids if len(ids) else np.zeros(1, np.int32))
+    ts, _ = _i(tile_start)
+    bgv, _ = _d(np.asarray(bg, np.float64))
+    gr, _ = _d(np.asarray(dL_drgb).reshape(3, H, W))
+    lib().orc_render_bwd(W, H, tile[0], tile[1], ptr(m2), ptr(cn), ptr(co), ptr(op), ptr(ids_), ptr(ts),
+                         ptr(bgv), ptr(gr), ptr(out.mean2d), ptr(out.conic), ptr(out.color),
+                         ptr(out.opacity))
+    return out
+
+
+@dataclass
+class ParamGrads:
+    means: np.ndarray
+    log_scales: np.ndarray
+    quats: np.ndarray
+    opacity_logits: np.ndarray
+    sh: np.ndarray
+    sd_acc: np.ndarray
+    sd_cnt: np.ndarray
+
+
+def zero_param_grads(n) -> ParamGrads:
+    return ParamGrads(np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros(n),
+                      np.zeros((n, 16, 3)), np.zeros(n), np.zeros(n, np.int32))
+
+
+def project_bwd(g, cam, g2d: Grad2D, tile=(16, 16), sh_degree=3, crop=None, aabb=None,
+                out: ParamGrads | None = None) -> ParamGrads:
+    L = lib()
+    n = g["means"].shape[0]
+    out = zero_param_grads(n) if out is None else out
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    means, _ = _d(g["means"])
+    ls, _ = _d(g["log_scales"])
+    q, _ = _d(g["quats"])
+    lo, _ = _d(g["opacity_logits"])
+    sh, _ = _d(g["sh"])
+    cr, pcr = _u8(crop)
+    cv, _ = _d(cam_vector(cam))
+    if aabb is None:
+        box = np.array([-np.inf, -np.inf, -np.inf, np.inf, np.inf, np.inf])
+    else:
+        box = np.array(list(aabb.lo) + list(aabb.hi), np.float64)
+    box = box.astype(np.float32).astype(np.float64)
+    dm, _ = _d(g2d.mean2d)
+    dc, _ = _d(g2d.conic)
+    dcol, _ = _d(g2d.color)
+    dop, _ = _d(g2d.opacity)
+    L.orc_project_bwd(ctypes.c_int64(n), ptr(means), ptr(ls), ptr(q), ptr(lo), ptr(sh), sh_degree, pcr,
+                      ptr(cv), tile[0], tile[1], ptr(box), ptr(dm), ptr(dc), ptr(dcol), ptr(dop),
+                      ptr(out.means), ptr(out.log_scales), ptr(out.quats), ptr(out.opacity_logits),
+                      ptr(out.sh), ptr(out.sd_acc), ptr(out.sd_cnt))
+    return out
+
+
+def visibility_crop(g, cams, tile=(16, 16), sh_degree=3) -> np.ndarray:
+    """uint8 mask: 1 where the Gaussian is visible from at least one of ``cams`` (Sec. 3.3)."""
+    L = lib()
+    n = g["means"].shape[0]
+    mask = np.zeros(n, np.uint8)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    means, _ = _d(g["means"])
+    ls, _ = _d(g["log_scales"])
+    q, _ = _d(g["quats"])
+    lo, _ = _d(g["opacity_logits"])
+    sh, _ = _d(g["sh"])
+    for cam in cams:
+        cv, _ = _d(cam_vector(cam))
+        L.orc_visibility_crop(ctypes.c_int64(n), ptr(means), ptr(ls), ptr(q), ptr(lo), ptr(sh), sh_degree,
+                              ptr(cv), tile[0], tile[1], ptr(mask))
+    return mask
+
+
+def sh_basis(dirs, degree=3):
+    """Real SH basis [n,16] and its derivative [n,16,3] for each row of ``dirs``."""
+    L = lib()
+    dirs = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+    Y = np.zeros((dirs.shape[0], 16))
+    dY = np.zeros((dirs.shape[0], 16, 3))
+    for i in range(dirs.shape[0]):
+        L.orc_sh_basis(degree, dirs[i].ctypes.data_as(ctypes.c_void_p),
+                       Y[i].ctypes.data_as(ctypes.c_void_p), dY[i].ctypes.data_as(ctypes.c_void_p))
+    return Y, dY
+
+
+def depth_key(z: float) -> int:
+    return int(lib().orc_depth_key(float(z)))
+
+
+# ----------------------------------------------------------------------------- pipelines
+
+@dataclass
+class Forward:
+    proj: Projection
+    ids: np.ndarray
+    tile_start: np.ndarray
+    image: Image
+    pixel_flags: np.ndarray  # [H,W] int32: union of pixel and Gaussian marginal flags
+
+
+def forward(g, cam, tile=(16, 16), sh_degree=3, crop=None, bg=(0.0, 0.0, 0.0), margins=MARGINS_NONE,
+            proj: Projection | None = None) -> Forward:
+    """Full forward of one item: project -> bin/sort -> composite."""
+    p = project(g, cam, tile, sh_degree, crop, margins) if proj is None else proj
+    ids, ts = bin_sort(p, cam, tile)
+    pxf = flag_pixels(p, cam, tile)
+    img = render_fwd(p, ids, ts, cam, tile, bg, margins, pxf)
+    return Forward(p, ids, ts, img, img.flags)
+
+
+def backward(g, cam, fwd: Forward, dL_drgb, tile=(16, 16), sh_degree=3, crop=None, aabb=None,
+             bg=(0.0, 0.0, 0.0)):
+    g2d = render_bwd(fwd.proj, fwd.ids, fwd.tile_start, cam, dL_drgb, tile, bg)
+    pg = project_bwd(g, cam, g2d, tile, sh_degree, crop, aabb)
+    return g2d, pg
+
+
+def set_dict(gs) -> dict:
+    """Widen a scenes.GaussianSet (or dict of float32 arrays) to float64 arrays."""
+    if hasattr(gs, "arrays"):
+        gs = gs.arrays()
+    return {k: np.asarray(v, np.float64) for k, v in gs.items()}

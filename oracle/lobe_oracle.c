@@ -1,0 +1,856 @@
+/*
+ * lobe_oracle.c -- plain, slow FP64 reference of the differentiable tile rasterizer.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or call this
+ * file; only tests/, the smoke check and bench.py's CPU-baseline leg use it. It shares
+ * no code, header, table or constant with the CUDA library.
+ *
+ * What it computes (the 3DGS rasterizer the paper builds on; "vanilla 3DGS procedure"
+ * of the appendix "3DGS Training", differentiable rasterization of Sec. 2.1, frustum
+ * culling of Sec. 3.3, visibility cropping and selective densification of Sec. 3.3, and
+ * the alpha-blending equation of Sec. 3.2 with colour in place of depth):
+ *
+ *   project   : EWA splatting of each 3D Gaussian into a 2D conic, a 3-sigma radius,
+ *               a tile rectangle and a view-dependent colour from real SH (degree <= 3).
+ *   bin       : (tile, depth) keys for every (Gaussian, tile-in-rect) pair, sorted by
+ *               (tile, fp32 depth bits, Gaussian index).
+ *   render    : per pixel front-to-back compositing of its tile's list with the
+ *               alpha >= 1/255 skip, the 0.99 alpha clamp and the T < 1e-4 stop.
+ *   backward  : the textbook reverse-order adjoint of the composite, then the chain
+ *               rule back to means, log-scales, quaternions, opacity logits and SH.
+ *
+ * Every floating-point quantity is double. Inputs that the GPU sees as float32 are
+ * passed in already widened, so both sides start from the same values.
+ *
+ * Readings of points the paper leaves open (each is listed in the design doc):
+ *   - camera space is OpenCV (x right, y down, +z forward); pixel (i,j) has centre
+ *     (i+0.5, j+0.5); u = fx*x/z + cx, v = fy*y/z + cy.
+ *   - cull when z < near or z > far, when |x/z| > 1.3*W/(2fx) or |y/z| > 1.3*H/(2fy),
+ *     when det(cov2d) <= 0, or when the tile rectangle is empty; crop_mask[g] == 0
+ *     (visibility cropping) culls as well.
+ *   - cov2d = J W Sigma W^T J^T + 0.3 I ; radius = ceil(3 sqrt(lambda_max)) with
+ *     lambda_max = mid + sqrt(max(0.1, mid^2 - det)).
+ *   - tile rectangle = [floor((u-r)/tw), ceil((u+r)/tw)) x [floor((v-r)/th), ceil((v+r)/th))
+ *     clamped to the tile grid.
+ *   - depth = camera-space z evaluated as ((V20*x + V21*y) + V22*z) + V23 in double,
+ *     rounded to float32 for the sort key.
+ *   - colour = max(0, sum_k sh_k Y_k(normalize(mu - campos)) + 0.5); opacity = sigmoid(logit).
+ *   - alpha = min(0.99, o exp(-sigma)); skip sigma < 0 and alpha < 1/255; stop, before
+ *     adding, once T (1 - alpha) < 1e-4; C = sum c_i alpha_i T_i + T_final * bg.
+ *   - selective-densification statistic: for a Gaussian with radius > 0 whose mean lies
+ *     in the block box (lo <= mu < hi per axis), add |(dL/du * W/2, dL/dv * H/2)| and 1.
+ *
+ * "Marginal" decisions: a decision that float32 arithmetic could take the other way is
+ * flagged so that tests can leave it out (per pixel and per Gaussian). The margins are
+ * inputs; see orc_margins below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* margins[]: relative margin on alpha/T/clamp decisions, absolute margin (pixels) on
+ * rectangle edges, relative margin on 3*sqrt(lambda) near an integer, absolute margin on
+ * the colour clamp, absolute margin on sigma near 0, relative margin on the fov guard. */
+enum { M_REL = 0, M_PX = 1, M_RAD = 2, M_COL = 3, M_SIG = 4, M_GUARD = 5, M_COUNT = 6 };
+
+/* per-Gaussian flag bits */
+enum {
+    F_GUARD = 1,   /* fov-guard decision marginal */
+    F_RADIUS = 2,  /* ceil(3 sqrt(lambda)) marginal */
+    F_RECT = 4,    /* a rectangle edge within M_PX of a tile boundary */
+    F_COLOR = 8,   /* colour clamp marginal (gradient mask) */
+};
+
+/* ------------------------------------------------------------------ small helpers */
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+static float to_f32(double x) { return (float)x; }
+
+static uint32_t f32_bits(double x)
+{
+    float f = (float)x;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return b;
+}
+
+/* ------------------------------------------------------------------ real spherical harmonics
+ *
+ * Real SH with the Condon-Shortley phase, ordered (l, m = -l..l), l <= 3:
+ *   Y_l^0  = K_l^0 P_l(z)
+ *   Y_l^m  = sqrt(2) K_l^m (-1)^m Q_l^m(z) Re((x+iy)^m)      m > 0
+ *   Y_l^-m = sqrt(2) K_l^m (-1)^m Q_l^m(z) Im((x+iy)^m)      m > 0
+ * with K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), Q_l^m = d^m P_l / dz^m and P_l from
+ * Rodrigues' formula P_l(z) = 1/(2^l l!) d^l/dz^l (z^2-1)^l. On the unit sphere
+ * (1-z^2)^{m/2} cos(m phi) = Re((x+iy)^m), so this equals the spherical-coordinate form
+ * (associated Legendre P_l^m = (-1)^m (1-z^2)^{m/2} Q_l^m). Derivatives are taken of this
+ * polynomial in (x,y,z); the chain rule through the normalisation removes the radial part.
+ */
+
+static double factorial(int k)
+{
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return f;
+}
+
+static double binom(int n, int k) { return factorial(n) / (factorial(k) * factorial(n - k)); }
+
+/* coefficients c[k] of z^k in d^m/dz^m P_l(z) */
+static void legendre_deriv_coeffs(int l, int m, double c[8])
+{
+    double p[16] = {0};
+    /* (z^2-1)^l = sum_j binom(l,j) z^{2j} (-1)^{l-j} */
+    for (int j = 0; j <= l; ++j) p[2 * j] = binom(l, j) * (((l - j) & 1) ? -1.0 : 1.0);
+    /* differentiate l + m times */
+    for (int d = 0; d < l + m; ++d)
+        for (int k = 0; k < 15; ++k) p[k] = p[k + 1] * (k + 1);
+    double s = 1.0 / (pow(2.0, l) * factorial(l));
+    for (int k = 0; k < 8; ++k) c[k] = p[k] * s;
+}
+
+static double poly_eval(const double c[8], double z, double *dz)
+{
+    double v = 0.0, d = 0.0;
+    for (int k = 7; k >= 0; --k) v = v * z + c[k];
+    for (int k = 7; k >= 1; --k) d = d * z + k * c[k];
+    if (dz) *dz = d;
+    return v;
+}
+
+/* (x+iy)^m as (re, im) together with its x,y derivatives */
+static void cpow_xy(double x, double y, int m, double *re, double *im,
+                    double *dre_dx, double *dre_dy, double *dim_dx, double *dim_dy)
+{
+    double r = 1.0, i = 0.0, rm1 = 1.0, im1 = 0.0; /* w^m and w^(m-1) */
+    for (int k = 0; k < m; ++k) {
+        rm1 = r;
+        im1 = i;
+        double nr = r * x - i * y;
+        double ni = r * y + i * x;
+        r = nr;
+        i = ni;
+    }
+    *re = r;
+    *im = i;
+    if (m == 0) {
+        *dre_dx = *dre_dy = *dim_dx = *dim_dy = 0.0;
+    } else {
+        /* d/dx w^m = m w^(m-1);  d/dy w^m = i m w^(m-1) */
+        *dre_dx = m * rm1;
+        *dim_dx = m * im1;
+        *dre_dy = -m * im1;
+        *dim_dy = m * rm1;
+    }
+}
+
+/* Y[16] and dY/d(x,y,z)[16][3] of the polynomial form at (x,y,z). */
+void orc_sh_basis(int degree, const double dir[3], double *Y, double *dY)
+{
+    int k = 0;
+    for (int l = 0; l <= degree; ++l) {
+        for (int mm = -l; mm <= l; ++mm, ++k) {
+            int m = mm < 0 ? -mm : mm;
+            double c[8];
+            legendre_deriv_coeffs(l, m, c);
+            double K = sqrt((2 * l + 1) / (4.0 * ORC_PI) * factorial(l - m) / factorial(l + m));
+            double dq;
+            double q = poly_eval(c, dir[2], &dq);
+            double re, im, drx, dry, dix, diy;
+            cpow_xy(dir[0], dir[1], m, &re, &im, &drx, &dry, &dix, &diy);
+            double A, dAx, dAy, pre;
+            if (mm == 0) {
+                A = 1.0; dAx = dAy = 0.0; pre = K;
+            } else if (mm > 0) {
+                A = re; dAx = drx; dAy = dry; pre = sqrt(2.0) * K * ((m & 1) ? -1.0 : 1.0);
+            } else {
+                A = im; dAx = dix; dAy = diy; pre = sqrt(2.0) * K * ((m & 1) ? -1.0 : 1.0);
+            }
+            Y[k] = pre * q * A;
+            if (dY) {
+                dY[3 * k + 0] = pre * q * dAx;
+                dY[3 * k + 1] = pre * q * dAy;
+                dY[3 * k + 2] = pre * dq * A;
+            }
+        }
+    }
+    for (; k < 16; ++k) {
+        Y[k] = 0.0;
+        if (dY) dY[3 * k] = dY[3 * k + 1] = dY[3 * k + 2] = 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------ camera */
+
+typedef struct {
+    double V[16];
+    double fx, fy, cx, cy;
+    int W, H;
+    double near_plane, far_plane;
+    double campos[3];
+} cam_t;
+
+/* cam[]: viewmat (16, row-major world->camera), fx, fy, cx, cy, width, height, near, far */
+static void load_cam(const double *c, cam_t *k)
+{
+    memcpy(k->V, c, 16 * sizeof(double));
+    k->fx = c[16]; k->fy = c[17]; k->cx = c[18]; k->cy = c[19];
+    k->W = (int)c[20]; k->H = (int)c[21];
+    k->near_plane = c[22]; k->far_plane = c[23];
+    /* camera centre of a rigid transform [R|t]: -R^T t */
+    for (int i = 0; i < 3; ++i)
+        k->campos[i] = -(k->V[0 + i] * k->V[3] + k->V[4 + i] * k->V[7] + k->V[8 + i] * k->V[11]);
+}
+
+/* ------------------------------------------------------------------ 3x3 helpers */
+
+static void quat_to_rot(const double q[4], double R[9])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* dR/dq_c for c in {w,x,y,z}: out[c][9] */
+static void quat_to_rot_grad(const double q[4], double dR[4][9])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double Dw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    double Dx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    double Dy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    double Dz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    memcpy(dR[0], Dw, sizeof Dw);
+    memcpy(dR[1], Dx, sizeof Dx);
+    memcpy(dR[2], Dy, sizeof Dy);
+    memcpy(dR[3], Dz, sizeof Dz);
+}
+
+static void mat3_mul(const double A[9], const double B[9], double C[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+
+static void mat3_transpose(const double A[9], double T[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) T[3 * i + j] = A[3 * j + i];
+}
+
+/* ------------------------------------------------------------------ projection of one Gaussian */
+
+typedef struct {
+    int visible;
+    int flags;
+    double pc[3];       /* camera-space mean */
+    double depth;       /* z as evaluated for the key */
+    double mean2d[2];
+    double cov2d[3];    /* a, b, c of the dilated 2x2 covariance */
+    double conic[3];
+    int radius;
+    int rect[4];        /* xmin, ymin, xmax, ymax (tiles, max exclusive) */
+    double color[3];
+    double color_raw[3];
+    double opacity;
+    double R[9], s[3], qn[3 + 1], qnorm;
+    double Sigma[9], Sigma_c[9], J[6];
+    double dir[3], dirlen, n[3];
+    double Y[16];
+} proj_t;
+
+static int near_integer(double x, double margin)
+{
+    return fabs(x - floor(x + 0.5)) < margin;
+}
+
+static void tile_rect(double u, double v, int r, int tw, int th, int gx, int gy, int rect[4])
+{
+    rect[0] = (int)clampd(floor((u - r) / tw), 0, gx);
+    rect[1] = (int)clampd(floor((v - r) / th), 0, gy);
+    rect[2] = (int)clampd(ceil((u + r) / tw), 0, gx);
+    rect[3] = (int)clampd(ceil((v + r) / th), 0, gy);
+}
+
+static void project_one(const double *mu, const double *ls, const double *q, double logit,
+                        const double *sh, int degree, int cropped, const cam_t *k,
+                        int tw, int th, const double *mg, proj_t *P)
+{
+    memset(P, 0, sizeof *P);
+    if (cropped) return;
+    const double *V = k->V;
+    /* camera-space mean; each component as ((V0*x + V1*y) + V2*z) + V3 */
+    for (int i = 0; i < 3; ++i)
+        P->pc[i] = ((V[4 * i + 0] * mu[0] + V[4 * i + 1] * mu[1]) + V[4 * i + 2] * mu[2]) + V[4 * i + 3];
+    double x = P->pc[0], y = P->pc[1], z = P->pc[2];
+    P->depth = z;
+    if (!(z >= k->near_plane && z <= k->far_plane)) return;
+    double limx = 1.3 * (0.5 * k->W) / k->fx, limy = 1.3 * (0.5 * k->H) / k->fy;
+    double txz = x / z, tyz = y / z;
+    if (fabs(fabs(txz) - limx) < mg[M_GUARD] * limx || fabs(fabs(tyz) - limy) < mg[M_GUARD] * limy)
+        P->flags |= F_GUARD;
+    /* the guard decision is applied at the end so that a culled Gaussian still carries
+     * the radius and rectangle it would have had (used to flag marginal pixels) */
+    int guard_out = fabs(txz) > limx || fabs(tyz) > limy;
+
+    /* 3D covariance Sigma = R S S^T R^T */
+    P->qnorm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) P->qn[i] = q[i] / P->qnorm;
+    quat_to_rot(P->qn, P->R);
+    for (int i = 0; i < 3; ++i) P->s[i] = exp(ls[i]);
+    double M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = P->R[3 * i + j] * P->s[j];
+    double Mt[9];
+    mat3_transpose(M, Mt);
+    mat3_mul(M, Mt, P->Sigma);
+    /* camera-frame covariance W Sigma W^T */
+    double W[9] = {V[0], V[1], V[2], V[4], V[5], V[6], V[8], V[9], V[10]}, Wt[9], T1[9];
+    mat3_transpose(W, Wt);
+    mat3_mul(W, P->Sigma, T1);
+    mat3_mul(T1, Wt, P->Sigma_c);
+    /* perspective Jacobian */
+    double *J = P->J;
+    J[0] = k->fx / z; J[1] = 0.0;       J[2] = -k->fx * x / (z * z);
+    J[3] = 0.0;       J[4] = k->fy / z; J[5] = -k->fy * y / (z * z);
+    double JS[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int t = 0; t < 3; ++t) s += J[3 * i + t] * P->Sigma_c[3 * t + j];
+            JS[3 * i + j] = s;
+        }
+    double c00 = 0, c01 = 0, c11 = 0;
+    for (int t = 0; t < 3; ++t) {
+        c00 += JS[t] * J[t];
+        c01 += JS[t] * J[3 + t];
+        c11 += JS[3 + t] * J[3 + t];
+    }
+    c00 += 0.3;
+    c11 += 0.3;
+    P->cov2d[0] = c00; P->cov2d[1] = c01; P->cov2d[2] = c11;
+    double det = c00 * c11 - c01 * c01;
+    if (!(det > 0.0)) return;
+    P->conic[0] = c11 / det;
+    P->conic[1] = -c01 / det;
+    P->conic[2] = c00 / det;
+    double mid = 0.5 * (c00 + c11);
+    double lam = mid + sqrt(fmax(0.1, mid * mid - det));
+    double r3 = 3.0 * sqrt(lam);
+    if (near_integer(r3, mg[M_RAD] * r3 + 1e-12)) P->flags |= F_RADIUS;
+    P->radius = (int)ceil(r3);
+    P->mean2d[0] = k->fx * x / z + k->cx;
+    P->mean2d[1] = k->fy * y / z + k->cy;
+    int gx = (k->W + tw - 1) / tw, gy = (k->H + th - 1) / th;
+    tile_rect(P->mean2d[0], P->mean2d[1], P->radius, tw, th, gx, gy, P->rect);
+    {
+        double e[4] = {P->mean2d[0] - P->radius, P->mean2d[0] + P->radius,
+                       P->mean2d[1] - P->radius, P->mean2d[1] + P->radius};
+        double t[4] = {tw, tw, th, th};
+        double gmax[4] = {gx, gx, gy, gy};
+        for (int i = 0; i < 4; ++i) {
+            double kk = floor(e[i] / t[i] + 0.5);
+            if (kk >= 0 && kk <= gmax[i] && fabs(e[i] - kk * t[i]) < mg[M_PX]) P->flags |= F_RECT;
+        }
+    }
+    if (guard_out || P->rect[2] <= P->rect[0] || P->rect[3] <= P->rect[1]) return;
+    /* view-dependent colour */
+    for (int i = 0; i < 3; ++i) P->dir[i] = mu[i] - k->campos[i];
+    P->dirlen = sqrt(P->dir[0] * P->dir[0] + P->dir[1] * P->dir[1] + P->dir[2] * P->dir[2]);
+    for (int i = 0; i < 3; ++i) P->n[i] = P->dir[i] / P->dirlen;
+    orc_sh_basis(degree, P->n, P->Y, NULL);
+    int nb = (degree + 1) * (degree + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += sh[3 * b + ch] * P->Y[b];
+        P->color_raw[ch] = s + 0.5;
+        P->color[ch] = P->color_raw[ch] < 0.0 ? 0.0 : P->color_raw[ch];
+        if (fabs(P->color_raw[ch]) < mg[M_COL]) P->flags |= F_COLOR;
+    }
+    P->opacity = 1.0 / (1.0 + exp(-logit));
+    P->visible = 1;
+}
+
+/* ------------------------------------------------------------------ public: project */
+
+int orc_project(int64_t n, const double *means, const double *log_scales, const double *quats,
+                const double *logits, const double *sh, int degree, const uint8_t *crop,
+                const double *camv, int tw, int th, const double *margins,
+                double *mean2d, double *conic, double *color, double *opacity, double *depth,
+                int32_t *radius, int32_t *rect, int32_t *flags, int32_t *radius_all)
+{
+    cam_t k;
+    load_cam(camv, &k);
+    for (int64_t g = 0; g < n; ++g) {
+        proj_t P;
+        project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], sh + 48 * g, degree,
+                    crop ? crop[g] == 0 : 0, &k, tw, th, margins, &P);
+        mean2d[2 * g] = P.mean2d[0];
+        mean2d[2 * g + 1] = P.mean2d[1];
+        for (int i = 0; i < 3; ++i) {
+            conic[3 * g + i] = P.conic[i];
+            color[3 * g + i] = P.color[i];
+        }
+        opacity[g] = P.opacity;
+        depth[g] = P.depth;
+        radius[g] = P.visible ? P.radius : 0;
+        for (int i = 0; i < 4; ++i) rect[4 * g + i] = P.visible ? P.rect[i] : 0;
+        flags[g] = P.flags;
+        if (radius_all) radius_all[g] = P.radius;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ public: bin + sort */
+
+typedef struct {
+    uint32_t tile;
+    uint32_t dbits;
+    int32_t g;
+} pair_t;
+
+static int pair_cmp(const void *a, const void *b)
+{
+    const pair_t *p = a, *q = b;
+    if (p->tile != q->tile) return p->tile < q->tile ? -1 : 1;
+    if (p->dbits != q->dbits) return p->dbits < q->dbits ? -1 : 1;
+    return p->g < q->g ? -1 : (p->g > q->g);
+}
+
+/* Returns the number of (Gaussian, tile) pairs. When ids/tile_start are non-NULL they
+ * receive the Gaussian index of every pair in (tile, depth, index) order and, for every
+ * tile t, the first pair index whose tile is >= t (n_tiles + 1 entries). */
+int64_t orc_bin(int64_t n, const double *mean2d, const int32_t *radius, const double *depth,
+                int W, int H, int tw, int th, int32_t *ids, int32_t *tile_start)
+{
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int64_t total = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        if (radius[g] <= 0) continue;
+        int r[4];
+        tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, r);
+        total += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
+    }
+    if (!ids) return total;
+    pair_t *pairs = malloc(sizeof(pair_t) * (total ? total : 1));
+    int64_t k = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        if (radius[g] <= 0) continue;
+        int r[4];
+        tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, r);
+        for (int ty = r[1]; ty < r[3]; ++ty)
+            for (int tx = r[0]; tx < r[2]; ++tx) {
+                pairs[k].tile = (uint32_t)(ty * gx + tx);
+                pairs[k].dbits = f32_bits(depth[g]);
+                pairs[k].g = (int32_t)g;
+                ++k;
+            }
+    }
+    qsort(pairs, total, sizeof(pair_t), pair_cmp);
+    for (int64_t i = 0; i < total; ++i) ids[i] = pairs[i].g;
+    int64_t i = 0;
+    for (int t = 0; t <= gx * gy; ++t) {
+        while (i < total && pairs[i].tile < (uint32_t)t) ++i;
+        tile_start[t] = (int32_t)i;
+    }
+    free(pairs);
+    return total;
+}
+
+/* ------------------------------------------------------------------ compositing of one pixel */
+
+typedef struct {
+    int32_t g;
+    double alpha, T, G, dx, dy, sigma;
+    int clamped;
+} contrib_t;
+
+/* Walks `list` front to back for pixel (px,py). Writes C[3] (without background), the
+ * final T, n_contrib, a marginal flag and (optionally) the contributors. */
+static void composite_pixel(int px, int py, const int32_t *list, int64_t len,
+                            const double *mean2d, const double *conic, const double *color,
+                            const double *opacity, const double *mg,
+                            double C[3], double *T_out, int32_t *ncontrib, int *marginal,
+                            contrib_t *rec, int64_t *nrec, double *wsum)
+{
+    double T = 1.0, ws = 0.0;
+    C[0] = C[1] = C[2] = 0.0;
+    int32_t last = 0;
+    int marg = 0;
+    int64_t nr = 0;
+    double pxc = px + 0.5, pyc = py + 0.5;
+    for (int64_t i = 0; i < len; ++i) {
+        int32_t g = list[i];
+        double dx = mean2d[2 * g] - pxc, dy = mean2d[2 * g + 1] - pyc;
+        const double *cn = conic + 3 * g;
+        double sigma = 0.5 * (cn[0] * dx * dx + cn[2] * dy * dy) + cn[1] * dx * dy;
+        if (fabs(sigma) < mg[M_SIG]) marg = 1;
+        if (sigma < 0.0) continue;
+        double G = exp(-sigma);
+        double araw = opacity[g] * G;
+        if (fabs(araw - 0.99) < mg[M_REL] * 0.99) marg = 1;
+        int clamped = araw >= 0.99;
+        double alpha = clamped ? 0.99 : araw;
+        if (fabs(alpha * 255.0 - 1.0) < mg[M_REL]) marg = 1;
+        if (alpha < 1.0 / 255.0) continue;
+        double Tn = T * (1.0 - alpha);
+        if (fabs(Tn - 1e-4) < mg[M_REL] * 1e-4) marg = 1;
+        if (Tn < 1e-4) break;
+        double w = alpha * T;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += color[3 * g + ch] * w;
+        ws += w;
+        if (rec) {
+            rec[nr].g = g; rec[nr].alpha = alpha; rec[nr].T = T; rec[nr].G = G;
+            rec[nr].dx = dx; rec[nr].dy = dy; rec[nr].sigma = sigma; rec[nr].clamped = clamped;
+        }
+        ++nr;
+        T = Tn;
+        last = (int32_t)(i + 1);
+    }
+    *T_out = T;
+    *ncontrib = last;
+    *marginal = marg;
+    if (nrec) *nrec = nr;
+    if (wsum) *wsum = ws;
+}
+
+/* Flags every pixel of the tiles that a marginal Gaussian might or might not cover.
+ * Any rectangle reachable by flipping the marginal decision lies between the rectangle of
+ * radius r-1 ("inner") and that of radius r+1 ("outer"); the band outer \ inner is
+ * flagged. A Gaussian whose culling decision is marginal flags its whole outer rectangle.
+ * radius_all[g] is the radius the projection computed whether or not it culled g. */
+int orc_flag_marginal_gaussians(int64_t n, const int32_t *gflags, const double *mean2d,
+                                const int32_t *radius, const int32_t *radius_all, int W, int H,
+                                int tw, int th, int32_t *pxf)
+{
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    for (int64_t g = 0; g < n; ++g) {
+        if (!(gflags[g] & (F_GUARD | F_RADIUS | F_RECT))) continue;
+        if (radius_all[g] <= 0) continue;
+        int outer[4], inner[4] = {0, 0, 0, 0};
+        tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g] + 1, tw, th, gx, gy, outer);
+        int whole = (gflags[g] & F_GUARD) || radius[g] <= 0;
+        if (!whole && radius_all[g] > 1)
+            tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g] - 1, tw, th, gx, gy, inner);
+        for (int ty = outer[1]; ty < outer[3]; ++ty)
+            for (int tx = outer[0]; tx < outer[2]; ++tx) {
+                if (tx >= inner[0] && tx < inner[2] && ty >= inner[1] && ty < inner[3]) continue;
+                for (int y = ty * th; y < (ty + 1) * th && y < H; ++y)
+                    for (int x = tx * tw; x < (tx + 1) * tw && x < W; ++x) pxf[(int64_t)y * W + x] = 1;
+            }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ public: render forward */
+
+int orc_render_fwd(int W, int H, int tw, int th, const double *mean2d, const double *conic,
+                   const double *color, const double *opacity, const int32_t *ids,
+                   const int32_t *tile_start, const double *bg, const double *margins,
+                   double *rgb, double *T_final, int32_t *n_contrib, int32_t *pxflags, double *wsum)
+{
+    int gx = (W + tw - 1) / tw;
+    int64_t HW = (int64_t)W * H;
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            int t = (py / th) * gx + px / tw;
+            double C[3], T, ws;
+            int32_t nc;
+            int marg;
+            composite_pixel(px, py, ids + tile_start[t], tile_start[t + 1] - tile_start[t], mean2d, conic,
+                            color, opacity, margins, C, &T, &nc, &marg, NULL, NULL, &ws);
+            int64_t p = (int64_t)py * W + px;
+            for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + p] = C[ch] + T * bg[ch];
+            T_final[p] = T;
+            n_contrib[p] = nc;
+            if (pxflags) pxflags[p] |= marg;
+            if (wsum) wsum[p] = ws;
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ public: untiled renders */
+
+typedef struct {
+    uint32_t dbits;
+    int32_t g;
+} dk_t;
+
+static int dk_cmp(const void *a, const void *b)
+{
+    const dk_t *p = a, *q = b;
+    if (p->dbits != q->dbits) return p->dbits < q->dbits ? -1 : 1;
+    return p->g < q->g ? -1 : (p->g > q->g);
+}
+
+/* Per pixel: every Gaussian with radius > 0 (and, if respect_rect, whose tile rectangle
+ * holds the pixel's tile), sorted by (fp32 depth, index), composited with the same rules.
+ * No key duplication, no global sort, no tile ranges. */
+int orc_render_untiled(int64_t n, int W, int H, int tw, int th, const double *mean2d,
+                       const double *conic, const double *color, const double *opacity,
+                       const int32_t *radius, const double *depth, int respect_rect,
+                       const double *bg, const double *margins, double *rgb, double *T_final,
+                       int32_t *pxflags)
+{
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    dk_t *all = malloc(sizeof(dk_t) * (n ? n : 1));
+    int32_t *list = malloc(sizeof(int32_t) * (n ? n : 1));
+    int64_t m = 0;
+    for (int64_t g = 0; g < n; ++g)
+        if (radius[g] > 0) {
+            all[m].dbits = f32_bits(depth[g]);
+            all[m].g = (int32_t)g;
+            ++m;
+        }
+    qsort(all, m, sizeof(dk_t), dk_cmp);
+    int64_t HW = (int64_t)W * H;
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            int tx = px / tw, ty = py / th;
+            int64_t len = 0;
+            for (int64_t i = 0; i < m; ++i) {
+                int32_t g = all[i].g;
+                if (respect_rect) {
+                    int r[4];
+                    tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, r);
+                    if (tx < r[0] || tx >= r[2] || ty < r[1] || ty >= r[3]) continue;
+                }
+                list[len++] = g;
+            }
+            double C[3], T;
+            int32_t nc;
+            int marg;
+            composite_pixel(px, py, list, len, mean2d, conic, color, opacity, margins, C, &T, &nc,
+                            &marg, NULL, NULL, NULL);
+            int64_t p = (int64_t)py * W + px;
+            for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + p] = C[ch] + T * bg[ch];
+            T_final[p] = T;
+            if (pxflags) pxflags[p] |= marg;
+        }
+    free(all);
+    free(list);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ public: render backward
+ *
+ * Textbook reverse-order adjoint of C = sum_i c_i alpha_i T_i + T_N bg. Walking back from
+ * the last contributor with B = colour seen behind Gaussian i (B starts as bg):
+ *   dL/dc_i     = alpha_i T_i dL/dC
+ *   dL/dalpha_i = T_i (c_i - B) . dL/dC,         B <- alpha_i c_i + (1 - alpha_i) B
+ *   alpha = o G, G = exp(-sigma) (unclamped): dL/do = dL/dalpha G, dL/dsigma = -dL/dalpha alpha
+ *   sigma = 0.5 (a dx^2 + c dy^2) + b dx dy, dx = u - (px + 0.5), dy = v - (py + 0.5)
+ * Gradients accumulate (+=) into per-Gaussian arrays.
+ */
+int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const double *conic,
+                   const double *color, const double *opacity, const int32_t *ids,
+                   const int32_t *tile_start, const double *bg, const double *dL_drgb,
+                   double *d_mean2d, double *d_conic, double *d_color, double *d_opacity)
+{
+    int gx = (W + tw - 1) / tw;
+    int64_t HW = (int64_t)W * H;
+    double mg[M_COUNT] = {0, 0, 0, 0, 0, 0};
+    int64_t maxlen = 0;
+    for (int t = 0; t < gx * ((H + th - 1) / th); ++t)
+        if (tile_start[t + 1] - tile_start[t] > maxlen) maxlen = tile_start[t + 1] - tile_start[t];
+    contrib_t *rec = malloc(sizeof(contrib_t) * (maxlen ? maxlen : 1));
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            int64_t p = (int64_t)py * W + px;
+            double gC[3] = {dL_drgb[p], dL_drgb[HW + p], dL_drgb[2 * HW + p]};
+            if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;
+            int t = (py / th) * gx + px / tw;
+            double C[3], T;
+            int32_t nc;
+            int marg;
+            int64_t nr;
+            composite_pixel(px, py, ids + tile_start[t], tile_start[t + 1] - tile_start[t], mean2d,
+                            conic, color, opacity, mg, C, &T, &nc, &marg, rec, &nr, NULL);
+            double B[3] = {bg[0], bg[1], bg[2]};
+            for (int64_t i = nr - 1; i >= 0; --i) {
+                const contrib_t *r = rec + i;
+                int32_t g = r->g;
+                const double *c = color + 3 * g;
+                double dalpha = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    d_color[3 * g + ch] += r->alpha * r->T * gC[ch];
+                    dalpha += r->T * (c[ch] - B[ch]) * gC[ch];
+                    B[ch] = r->alpha * c[ch] + (1.0 - r->alpha) * B[ch];
+                }
+                if (r->clamped) continue;
+                d_opacity[g] += dalpha * r->G;
+                double dsig = -dalpha * r->alpha;
+                const double *cn = conic + 3 * g;
+                d_conic[3 * g + 0] += dsig * 0.5 * r->dx * r->dx;
+                d_conic[3 * g + 1] += dsig * r->dx * r->dy;
+                d_conic[3 * g + 2] += dsig * 0.5 * r->dy * r->dy;
+                d_mean2d[2 * g + 0] += dsig * (cn[0] * r->dx + cn[1] * r->dy);
+                d_mean2d[2 * g + 1] += dsig * (cn[1] * r->dx + cn[2] * r->dy);
+            }
+        }
+    free(rec);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ public: projection backward
+ *
+ * Chain rule from dL/d(mean2d, conic, colour, opacity) of one view to the raw parameters.
+ * Adds into g_* (+=). sd_acc/sd_cnt receive the selective-densification statistic.
+ */
+int orc_project_bwd(int64_t n, const double *means, const double *log_scales, const double *quats,
+                    const double *logits, const double *sh, int degree, const uint8_t *crop,
+                    const double *camv, int tw, int th, const double *aabb,
+                    const double *d_mean2d, const double *d_conic, const double *d_color,
+                    const double *d_opacity, double *g_means, double *g_log_scales,
+                    double *g_quats, double *g_logits, double *g_sh, double *sd_acc, int32_t *sd_cnt)
+{
+    cam_t k;
+    load_cam(camv, &k);
+    double mg[M_COUNT] = {0, 0, 0, 0, 0, 0};
+    const double *V = k.V;
+    double W[9] = {V[0], V[1], V[2], V[4], V[5], V[6], V[8], V[9], V[10]};
+    for (int64_t g = 0; g < n; ++g) {
+        proj_t P;
+        const double *mu = means + 3 * g;
+        project_one(mu, log_scales + 3 * g, quats + 4 * g, logits[g], sh + 48 * g, degree,
+                    crop ? crop[g] == 0 : 0, &k, tw, th, mg, &P);
+        if (!P.visible) continue;
+        double gmu[3] = {0, 0, 0};
+        /* opacity */
+        g_logits[g] += d_opacity[g] * P.opacity * (1.0 - P.opacity);
+        /* colour -> SH and view direction */
+        int nb = (degree + 1) * (degree + 1);
+        double Y[16], dY[48];
+        orc_sh_basis(degree, P.n, Y, dY);
+        double dn[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ++ch) {
+            if (P.color_raw[ch] < 0.0) continue;
+            double dc = d_color[3 * g + ch];
+            for (int b = 0; b < nb; ++b) {
+                g_sh[48 * g + 3 * b + ch] += Y[b] * dc;
+                for (int i = 0; i < 3; ++i) dn[i] += sh[48 * g + 3 * b + ch] * dY[3 * b + i] * dc;
+            }
+        }
+        /* n = dir/|dir|: dn/ddir = (I - n n^T)/|dir| */
+        double ndn = P.n[0] * dn[0] + P.n[1] * dn[1] + P.n[2] * dn[2];
+        for (int i = 0; i < 3; ++i) gmu[i] += (dn[i] - P.n[i] * ndn) / P.dirlen;
+
+        /* conic = inverse(cov2d): dL/dcov2d = -C Gs C with Gs = [[da, db/2],[db/2, dc]] */
+        double C2[4] = {P.conic[0], P.conic[1], P.conic[1], P.conic[2]};
+        double Gs[4] = {d_conic[3 * g], 0.5 * d_conic[3 * g + 1], 0.5 * d_conic[3 * g + 1], d_conic[3 * g + 2]};
+        double CG[4], H2[4];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) CG[2 * i + j] = C2[2 * i] * Gs[j] + C2[2 * i + 1] * Gs[2 + j];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) H2[2 * i + j] = -(CG[2 * i] * C2[j] + CG[2 * i + 1] * C2[2 + j]);
+        /* cov2d = J Sigma_c J^T + 0.3 I:  dL/dSigma_c = J^T H J,  dL/dJ = 2 H J Sigma_c */
+        const double *J = P.J;
+        double dSc[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0;
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) s += J[3 * i + a] * H2[2 * i + j] * J[3 * j + b];
+                dSc[3 * a + b] = s;
+            }
+        double dJ[6];
+        for (int i = 0; i < 2; ++i)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0;
+                for (int j = 0; j < 2; ++j)
+                    for (int a = 0; a < 3; ++a) s += H2[2 * i + j] * J[3 * j + a] * P.Sigma_c[3 * a + b];
+                dJ[3 * i + b] = 2.0 * s;
+            }
+        /* J and (u,v) as functions of the camera-space mean */
+        double x = P.pc[0], y = P.pc[1], z = P.pc[2];
+        double fx = k.fx, fy = k.fy;
+        double dpc[3] = {0, 0, 0};
+        double du = d_mean2d[2 * g], dv = d_mean2d[2 * g + 1];
+        dpc[0] += du * fx / z;
+        dpc[1] += dv * fy / z;
+        dpc[2] += -du * fx * x / (z * z) - dv * fy * y / (z * z);
+        /* J00 = fx/z, J02 = -fx x/z^2, J11 = fy/z, J12 = -fy y/z^2 */
+        dpc[0] += dJ[2] * (-fx / (z * z));
+        dpc[1] += dJ[5] * (-fy / (z * z));
+        dpc[2] += dJ[0] * (-fx / (z * z)) + dJ[2] * (2.0 * fx * x / (z * z * z)) +
+                  dJ[4] * (-fy / (z * z)) + dJ[5] * (2.0 * fy * y / (z * z * z));
+        /* pc = W mu + t */
+        for (int i = 0; i < 3; ++i) gmu[i] += W[0 + i] * dpc[0] + W[3 + i] * dpc[1] + W[6 + i] * dpc[2];
+        /* Sigma_c = W Sigma W^T -> dL/dSigma = W^T dSc W */
+        double Wt[9], T1[9], dS[9];
+        mat3_transpose(W, Wt);
+        mat3_mul(Wt, dSc, T1);
+        mat3_mul(T1, W, dS);
+        /* Sigma = M M^T, M = R diag(s): dL/dM = (dS + dS^T) M */
+        double M[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[3 * i + j] = P.R[3 * i + j] * P.s[j];
+        double dSsym[9], dM[9];
+        for (int i = 0; i < 9; ++i) dSsym[i] = dS[i] + dS[3 * (i % 3) + i / 3];
+        mat3_mul(dSsym, M, dM);
+        double dR[9];
+        for (int j = 0; j < 3; ++j) {
+            double ds = 0;
+            for (int i = 0; i < 3; ++i) {
+                ds += dM[3 * i + j] * P.R[3 * i + j];
+                dR[3 * i + j] = dM[3 * i + j] * P.s[j];
+            }
+            g_log_scales[3 * g + j] += ds * P.s[j];
+        }
+        double dRq[4][9];
+        quat_to_rot_grad(P.qn, dRq);
+        double dqn[4];
+        for (int c = 0; c < 4; ++c) {
+            double s = 0;
+            for (int i = 0; i < 9; ++i) s += dR[i] * dRq[c][i];
+            dqn[c] = s;
+        }
+        double qd = 0;
+        for (int c = 0; c < 4; ++c) qd += P.qn[c] * dqn[c];
+        for (int c = 0; c < 4; ++c) g_quats[4 * g + c] += (dqn[c] - P.qn[c] * qd) / P.qnorm;
+        for (int i = 0; i < 3; ++i) g_means[3 * g + i] += gmu[i];
+        /* selective densification statistic */
+        if (aabb && sd_acc) {
+            int inside = 1;
+            for (int i = 0; i < 3; ++i)
+                if (!(mu[i] >= aabb[i] && mu[i] < aabb[3 + i])) inside = 0;
+            if (inside) {
+                double a = du * 0.5 * k.W, b = dv * 0.5 * k.H;
+                sd_acc[g] += sqrt(a * a + b * b);
+                sd_cnt[g] += 1;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ public: visibility crop
+ * Sec. 3.3: keep a Gaussian if it is visible (radius > 0 under the culling rules above)
+ * from at least one of the block's cameras. mask[g] |= visible. */
+int orc_visibility_crop(int64_t n, const double *means, const double *log_scales, const double *quats,
+                        const double *logits, const double *sh, int degree, const double *camv,
+                        int tw, int th, uint8_t *mask)
+{
+    cam_t k;
+    load_cam(camv, &k);
+    double mg[M_COUNT] = {0, 0, 0, 0, 0, 0};
+    for (int64_t g = 0; g < n; ++g) {
+        proj_t P;
+        project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], sh + 48 * g, degree, 0,
+                    &k, tw, th, mg, &P);
+        if (P.visible) mask[g] = 1;
+    }
+    return 0;
+}
+
+/* float32 rounding helper exported for tests that need the key the GPU sees */
+uint32_t orc_depth_key(double z) { return f32_bits(z); }
+float orc_round_f32(double x) { return to_f32(x); }
