@@ -1,0 +1,226 @@
+/*
+ * lobe.h -- C ABI of the B300 (sm_103a) differentiable tile rasterizer used by the
+ * per-block fine-training step of LoBE-GS (arXiv 2510.01767).
+ *
+ * The paper trains each KD-tree block with the vanilla 3DGS procedure (appendix,
+ * "3DGS Training"): differentiable rasterization of 3D Gaussians (Sec. 2.1), frustum
+ * culling during rasterization (Sec. 3.3), front-to-back alpha blending (the blending
+ * equation of Sec. 3.2, with colour in place of depth), visibility cropping and
+ * selective densification (Sec. 3.3). This library implements that rasterizer as four
+ * stages plus their adjoints:
+ *
+ *   lobe_project      Gaussians -> 2D splats (mean, conic, colour, opacity, depth, radius)
+ *   lobe_bin_sort     splats -> per-tile lists ordered by (tile, depth, index)
+ *   lobe_render_fwd   per-tile front-to-back compositing
+ *   lobe_render_bwd   adjoint of the composite -> per-splat 2D gradients
+ *   lobe_project_bwd  adjoint of the projection -> parameter gradients + SD statistics
+ *
+ * A "batch" is a list of items (Gaussian set, camera, block); one call processes every
+ * item of the batch in one launch per stage. The plain single-view path is a batch of one.
+ *
+ * Conventions (all calls):
+ *  - Every pointer inside the structs below is a DEVICE pointer allocated and owned by the
+ *    caller, except the struct arrays themselves (lobe_batch members), which are HOST
+ *    memory read during the call only. The library never frees caller memory.
+ *  - Every call is asynchronous on the context's CUDA stream and returns after enqueueing,
+ *    except where a host output pointer is given (then it synchronises that stream).
+ *  - Argument errors are reported synchronously (LOBE_ERR_ARG) and nothing is enqueued.
+ *  - Errors found on the device (intersection count above capacity) are latched in a
+ *    device status word; lobe_get_status() reads and clears it.
+ *  - All floating-point data is float32, little-endian, C-contiguous.
+ *  - The calls are safe to capture in a CUDA graph when no host output pointer is passed
+ *    and lobe_ctx_reserve() was called beforehand.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef LOBE_H
+#define LOBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOBE_ABI_VERSION 1
+#define LOBE_MAX_SETS 16
+#define LOBE_MAX_ITEMS 64
+#define LOBE_SH_COEFFS 16
+
+typedef enum {
+    LOBE_OK = 0,
+    LOBE_ERR_ARG = -1,      /* invalid argument; nothing was enqueued */
+    LOBE_ERR_CAPACITY = -2, /* more (Gaussian, tile) pairs than the bins' capacity */
+    LOBE_ERR_CUDA = -3,     /* a CUDA runtime call failed; see lobe_last_error() */
+    LOBE_ERR_TIMEOUT = -4,  /* a bounded device-side wait expired */
+    LOBE_ERR_OOM = -5,      /* device allocation of context scratch failed */
+    LOBE_ERR_STATE = -6     /* call order violated (e.g. scratch not reserved) */
+} lobe_status;
+
+typedef struct lobe_ctx lobe_ctx;
+
+/* One set of 3D Gaussians, structure of arrays (device memory, caller-owned, read only).
+ * Parameterisation (Sec. 3.2 "opacity determined by covariance and opacity"): log-scales,
+ * a quaternion (w,x,y,z) that need not be normalised, an opacity logit and real SH
+ * coefficients (band-major, DC first, 16 x RGB). crop_mask (nullable) is the visibility
+ * crop of Sec. 3.3: a Gaussian with crop_mask[g] == 0 is culled. */
+typedef struct {
+    const float *means;          /* [n][3] */
+    const float *log_scales;     /* [n][3] */
+    const float *quats;          /* [n][4], 16-byte aligned */
+    const float *opacity_logits; /* [n]    */
+    const float *sh;             /* [n][16][3], 16-byte aligned */
+    const uint8_t *crop_mask;    /* [n] or NULL */
+    int64_t n;
+} lobe_gaussians;
+
+/* Pinhole camera (host struct). viewmat is the row-major 4x4 world->camera rigid transform
+ * in OpenCV axes (x right, y down, +z forward); pixel (i,j) has centre (i+0.5, j+0.5). */
+typedef struct {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_plane, far_plane;
+} lobe_camera;
+
+/* Block box B^(b) of the KD partition (Sec. 3.1). A mean is inside when lo <= mu < hi on
+ * every axis; +-INFINITY bounds are allowed (the partition splits only x and y). */
+typedef struct {
+    float lo[3];
+    float hi[3];
+} lobe_aabb;
+
+/* One render item: Gaussian set index, camera index, block index (-1: unbounded box). */
+typedef struct {
+    int32_t set;
+    int32_t camera;
+    int32_t block;
+} lobe_item;
+
+/* Host description of a batch. Items of the same set must share the set's parameters. */
+typedef struct {
+    const lobe_gaussians *sets;
+    int32_t n_sets;
+    const lobe_camera *cameras;
+    int32_t n_cameras;
+    const lobe_aabb *blocks; /* may be NULL when n_blocks == 0 */
+    int32_t n_blocks;
+    const lobe_item *items;
+    int32_t n_items;
+} lobe_batch;
+
+/* Context configuration. tile_w x tile_h must be one of 8x8, 16x16, 32x16. */
+typedef struct {
+    int32_t tile_w, tile_h;
+    int32_t sh_degree;  /* active SH degree, 0..3 */
+    float bg[3];        /* background colour */
+    int32_t recompute_T; /* 1: render_bwd re-derives the per-pixel state (T_final, n_contrib)
+                            with a forward sweep instead of reading the saved one */
+    int32_t reserved[7];
+} lobe_config;
+
+/* Sizes implied by a batch under a config: out[0] = projected entries (sum over items of
+ * the set size), out[1] = tiles (sum over items of ceil(W/tw) ceil(H/th)), out[2] = pixels. */
+lobe_status lobe_batch_sizes(const lobe_config *cfg, const lobe_batch *batch, int64_t out[3]);
+
+/* Projected splats, one entry per (item, Gaussian): entry = item_entry_offset + g, where
+ * item_entry_offset is the sum of the set sizes of the preceding items.
+ *   splat[e][0..11] = u, v, conic_a, conic_b, conic_c, opacity, r, g, b, depth, 0, 0
+ *     (conic = inverse 2D covariance [[a,b],[b,c]]; depth = camera-space z rounded to fp32)
+ *   radius[e]        = ceil(3 sqrt(lambda_max)), 0 when culled (splat then undefined)
+ *   tiles_touched[e] = number of tiles in the splat's tile rectangle, 0 when culled
+ * splat must be 16-byte aligned. */
+typedef struct {
+    float *splat;           /* [entries][12] */
+    int32_t *radius;        /* [entries] */
+    int32_t *tiles_touched; /* [entries] */
+} lobe_projected;
+
+/* Tile bins. gauss_ids[k] is the entry id of the k-th (Gaussian, tile) pair in
+ * (global tile, fp32 depth bits, entry) order; tile_start[t] is the first pair of global
+ * tile t (tile_start[n_tiles] = number of pairs). Global tile t of item i is
+ * item_tile_offset(i) + ty * ceil(W/tw) + tx. n_isect receives the pair count. */
+typedef struct {
+    int32_t *gauss_ids;  /* [capacity] */
+    int32_t *tile_start; /* [n_tiles + 1] */
+    int64_t *n_isect;    /* [1] */
+    int64_t capacity;
+} lobe_bins;
+
+/* Rendered images. Item i occupies pixels [pix_off(i), pix_off(i) + W*H) with pix_off the
+ * prefix sum of W*H. rgb is planar per item: rgb[3*pix_off + c*W*H + y*W + x].
+ * n_contrib = 1 + position (within the tile list) of the last Gaussian that contributed. */
+typedef struct {
+    float *rgb;         /* [3 * pixels] */
+    float *T_final;     /* [pixels] */
+    int32_t *n_contrib; /* [pixels] */
+} lobe_image;
+
+/* Parameter gradients of one set (device, caller-owned, same shapes as lobe_gaussians).
+ * sd_acc/sd_cnt (nullable) receive the selective-densification statistic of Sec. 3.3:
+ * per view in which the Gaussian is visible and its mean lies in the item's block box,
+ * sd_acc += |(dL/du * W/2, dL/dv * H/2)| and sd_cnt += 1 (always accumulated). */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+    float *sd_acc;   /* [n] or NULL */
+    int32_t *sd_cnt; /* [n] or NULL */
+} lobe_grads;
+
+int32_t lobe_abi_version(void);
+
+/* Creates a context bound to `stream` (a cudaStream_t, NULL = legacy default stream) on the
+ * current device. Allocates only a small device status word. */
+lobe_status lobe_ctx_create(lobe_ctx **out, void *stream, const lobe_config *cfg);
+lobe_status lobe_ctx_destroy(lobe_ctx *ctx);
+lobe_status lobe_ctx_set_stream(lobe_ctx *ctx, void *stream);
+lobe_status lobe_ctx_set_config(lobe_ctx *ctx, const lobe_config *cfg);
+/* Message of the last error on this context (static storage owned by the context). */
+const char *lobe_last_error(const lobe_ctx *ctx);
+/* Sizes the context-owned sort scratch for up to max_entries projected entries and
+ * max_isect pairs (grows only; never called implicitly inside a captured region). */
+lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect);
+/* Synchronises the stream, returns and clears the latched device status. */
+lobe_status lobe_get_status(lobe_ctx *ctx);
+
+/* EWA projection + SH colour + culling (near/far, 1.3x fov guard, crop mask, empty
+ * rectangle) of every (item, Gaussian). Writes `out` for all entries. */
+lobe_status lobe_project(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *out);
+
+/* Key duplication and sort of all (Gaussian, tile) pairs of the batch, tile ranges.
+ * If n_isect_host is non-NULL the call synchronises, stores the pair count there and
+ * returns LOBE_ERR_CAPACITY without sorting when it exceeds bins->capacity (the caller can
+ * grow the bins and call again). Otherwise an overflow is latched on the device and the
+ * bins describe empty tiles. */
+lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                          const lobe_bins *bins, int64_t *n_isect_host);
+
+/* Front-to-back compositing of every tile of every item. */
+lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                            const lobe_bins *bins, const lobe_image *image);
+
+/* Adjoint of lobe_render_fwd. dL_drgb has the layout of image->rgb. Reads image->rgb,
+ * T_final and n_contrib unless the context has recompute_T set (then only dL_drgb).
+ * Overwrites grad2d[entries][12] = dL/d(u, v, conic_a, conic_b, conic_c, opacity, r, g, b)
+ * followed by three zeros. grad2d must be 16-byte aligned. */
+lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                            const lobe_bins *bins, const lobe_image *image, const float *dL_drgb,
+                            float *grad2d);
+
+/* Adjoint of lobe_project: chain rule from grad2d to the raw parameters of every set,
+ * summed over the set's items. grads[s] belongs to batch->sets[s]. accumulate = 0
+ * overwrites the parameter gradients, 1 adds to them; sd_acc/sd_cnt always accumulate. */
+lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                             const float *grad2d, const lobe_grads *grads, int32_t accumulate);
+
+/* Visibility cropping (Sec. 3.3): for every set, mask[s][g] |= 1 when Gaussian g is visible
+ * (passes the culling rules, crop mask ignored) from at least one item of that set.
+ * masks[s] are device pointers (uint8 [n]); they are OR-ed into, not cleared. */
+lobe_status lobe_visibility_crop(lobe_ctx *ctx, const lobe_batch *batch, uint8_t *const *masks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOBE_H */

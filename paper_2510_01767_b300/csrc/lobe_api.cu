@@ -1,0 +1,417 @@
+// lobe_api.cu -- the extern "C" entry points declared in include/lobe.h.
+//
+// The host side only validates arguments, packs the batch into one parameter block and
+// enqueues kernels on the context's stream; every step of the rasterizer runs on the GPU.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lobe_internal.cuh"
+
+
+using namespace lobe;
+
+struct lobe_ctx {
+    cudaStream_t stream = nullptr;
+    lobe_config cfg{};
+    int device = 0;
+    int *status = nullptr;
+    void *entry_mem = nullptr;
+    void *isect_mem = nullptr;
+    long long max_entries = 0, max_isect = 0;
+    BinScratch bins{};
+    char err[512] = {0};
+};
+
+static lobe_status fail(lobe_ctx *ctx, lobe_status code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+static lobe_status cuda_fail(lobe_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, LOBE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, where)                              \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+    } while (0)
+
+static bool valid_tile(int tw, int th)
+{
+    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 16);
+}
+
+static lobe_status check_config(lobe_ctx *ctx, const lobe_config *cfg)
+{
+    if (!cfg) return fail(ctx, LOBE_ERR_ARG, "config is NULL");
+    if (!valid_tile(cfg->tile_w, cfg->tile_h))
+        return fail(ctx, LOBE_ERR_ARG, "tile %dx%d not one of 8x8, 16x16, 32x16", cfg->tile_w, cfg->tile_h);
+    if (cfg->sh_degree < 0 || cfg->sh_degree > 3) return fail(ctx, LOBE_ERR_ARG, "sh_degree %d not in 0..3", cfg->sh_degree);
+    return LOBE_OK;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Packs a host batch description into the kernel parameter block.
+static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lobe_batch *b, BatchParams &P)
+{
+    if (!b) return fail(ctx, LOBE_ERR_ARG, "batch is NULL");
+    if (b->n_sets < 1 || b->n_sets > LOBE_MAX_SETS) return fail(ctx, LOBE_ERR_ARG, "n_sets %d not in 1..%d", b->n_sets, LOBE_MAX_SETS);
+    if (b->n_items < 1 || b->n_items > LOBE_MAX_ITEMS)
+        return fail(ctx, LOBE_ERR_ARG, "n_items %d not in 1..%d", b->n_items, LOBE_MAX_ITEMS);
+    if (!b->sets || !b->items || !b->cameras || b->n_cameras < 1) return fail(ctx, LOBE_ERR_ARG, "batch arrays missing");
+    if (b->n_blocks > 0 && !b->blocks) return fail(ctx, LOBE_ERR_ARG, "blocks is NULL with n_blocks > 0");
+    memset(&P, 0, sizeof P);
+    P.n_sets = b->n_sets;
+    P.n_items = b->n_items;
+    P.tw = cfg.tile_w;
+    P.th = cfg.tile_h;
+    P.sh_degree = cfg.sh_degree;
+    for (int c = 0; c < 3; ++c) P.bg[c] = cfg.bg[c];
+    long long goff = 0;
+    for (int s = 0; s < b->n_sets; ++s) {
+        const lobe_gaussians &G = b->sets[s];
+        if (G.n < 0) return fail(ctx, LOBE_ERR_ARG, "set %d: n < 0", s);
+        if (G.n > 0 && (!G.means || !G.log_scales || !G.quats || !G.opacity_logits || !G.sh))
+            return fail(ctx, LOBE_ERR_ARG, "set %d: parameter pointer is NULL", s);
+        if (!aligned16(G.quats) || !aligned16(G.sh)) return fail(ctx, LOBE_ERR_ARG, "set %d: quats/sh not 16-byte aligned", s);
+        SetParams &S = P.set[s];
+        S.means = G.means;
+        S.log_scales = G.log_scales;
+        S.quats = G.quats;
+        S.logits = G.opacity_logits;
+        S.sh = G.sh;
+        S.crop = G.crop_mask;
+        S.n = G.n;
+        S.gauss_off = goff;
+        goff += G.n;
+    }
+    P.n_gauss = goff;
+    // items grouped by set (stable), for the set-major projection kernels
+    int k = 0;
+    for (int s = 0; s < b->n_sets; ++s) {
+        P.set[s].item_begin = k;
+        for (int i = 0; i < b->n_items; ++i)
+            if (b->items[i].set == s) P.set_items[k++] = i;
+        P.set[s].item_count = k - P.set[s].item_begin;
+    }
+    long long eoff = 0, poff = 0, toff = 0;
+    for (int i = 0; i < b->n_items; ++i) {
+        const lobe_item &it = b->items[i];
+        if (it.set < 0 || it.set >= b->n_sets) return fail(ctx, LOBE_ERR_ARG, "item %d: set %d out of range", i, it.set);
+        if (it.camera < 0 || it.camera >= b->n_cameras)
+            return fail(ctx, LOBE_ERR_ARG, "item %d: camera %d out of range", i, it.camera);
+        if (it.block >= b->n_blocks || it.block < -1)
+            return fail(ctx, LOBE_ERR_ARG, "item %d: block %d out of range", i, it.block);
+        const lobe_camera &c = b->cameras[it.camera];
+        if (c.width <= 0 || c.height <= 0 || !(c.fx > 0.f) || !(c.fy > 0.f))
+            return fail(ctx, LOBE_ERR_ARG, "camera %d: bad intrinsics", it.camera);
+        ItemParams &I = P.item[i];
+        for (int r = 0; r < 12; ++r) I.V[r] = c.viewmat[r];
+        for (int r = 0; r < 4; ++r) I.Vz[r] = (double)c.viewmat[8 + r];
+        I.fx = c.fx; I.fy = c.fy; I.cx = c.cx; I.cy = c.cy;
+        I.near_plane = (double)c.near_plane;
+        I.far_plane = (double)c.far_plane;
+        // camera centre of the rigid transform [R|t]: -R^T t
+        for (int a = 0; a < 3; ++a) {
+            double v = 0.0;
+            for (int r = 0; r < 3; ++r) v -= (double)c.viewmat[4 * r + a] * (double)c.viewmat[4 * r + 3];
+            I.campos[a] = (float)v;
+        }
+        I.limx = (float)(1.3 * (0.5 * c.width) / (double)c.fx);
+        I.limy = (float)(1.3 * (0.5 * c.height) / (double)c.fy);
+        for (int a = 0; a < 3; ++a) {
+            I.lo[a] = it.block >= 0 ? b->blocks[it.block].lo[a] : -INFINITY;
+            I.hi[a] = it.block >= 0 ? b->blocks[it.block].hi[a] : INFINITY;
+        }
+        I.W = c.width;
+        I.H = c.height;
+        I.gx = (c.width + cfg.tile_w - 1) / cfg.tile_w;
+        I.gy = (c.height + cfg.tile_h - 1) / cfg.tile_h;
+        I.tile_off = (int)toff;
+        I.set = it.set;
+        I.entry_off = eoff;
+        I.pix_off = poff;
+        eoff += b->sets[it.set].n;
+        poff += (long long)c.width * c.height;
+        toff += (long long)I.gx * I.gy;
+    }
+    if (eoff >= (1LL << 31)) return fail(ctx, LOBE_ERR_ARG, "%lld projected entries exceed 2^31", eoff);
+    if (toff >= (1LL << 30)) return fail(ctx, LOBE_ERR_ARG, "%lld tiles exceed 2^30", toff);
+    P.n_entries = eoff;
+    P.n_pixels = poff;
+    P.n_tiles = (int)toff;
+    return LOBE_OK;
+}
+
+extern "C" {
+
+int32_t lobe_abi_version(void) { return LOBE_ABI_VERSION; }
+
+lobe_status lobe_batch_sizes(const lobe_config *cfg, const lobe_batch *batch, int64_t out[3])
+{
+    if (!out) return LOBE_ERR_ARG;
+    lobe_status s = check_config(nullptr, cfg);
+    if (s != LOBE_OK) return s;
+    BatchParams *P = new (std::nothrow) BatchParams;
+    if (!P) return LOBE_ERR_OOM;
+    s = build_params(nullptr, *cfg, batch, *P);
+    if (s == LOBE_OK) {
+        out[0] = P->n_entries;
+        out[1] = P->n_tiles;
+        out[2] = P->n_pixels;
+    }
+    delete P;
+    return s;
+}
+
+lobe_status lobe_ctx_create(lobe_ctx **out, void *stream, const lobe_config *cfg)
+{
+    if (!out) return LOBE_ERR_ARG;
+    *out = nullptr;
+    lobe_status s = check_config(nullptr, cfg);
+    if (s != LOBE_OK) return s;
+    lobe_ctx *ctx = new (std::nothrow) lobe_ctx;
+    if (!ctx) return LOBE_ERR_OOM;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, 64);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, 64);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LOBE_ERR_CUDA;
+    }
+    *out = ctx;
+    return LOBE_OK;
+}
+
+lobe_status lobe_ctx_destroy(lobe_ctx *ctx)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(ctx->entry_mem);
+    cudaFree(ctx->isect_mem);
+    cudaFree(ctx->status);
+    delete ctx;
+    return LOBE_OK;
+}
+
+lobe_status lobe_ctx_set_stream(lobe_ctx *ctx, void *stream)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return LOBE_OK;
+}
+
+lobe_status lobe_ctx_set_config(lobe_ctx *ctx, const lobe_config *cfg)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    lobe_status s = check_config(ctx, cfg);
+    if (s != LOBE_OK) return s;
+    ctx->cfg = *cfg;
+    return LOBE_OK;
+}
+
+const char *lobe_last_error(const lobe_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+static lobe_status grow_entries(lobe_ctx *ctx, long long need)
+{
+    if (need <= ctx->max_entries && ctx->entry_mem) return LOBE_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->entry_mem);
+    ctx->entry_mem = nullptr;
+    ctx->max_entries = 0;
+    long long n = need < 1024 ? 1024 : need;
+    cudaError_t e = cudaMalloc(&ctx->entry_mem, entry_scratch_bytes(n));
+    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "entry scratch (%lld entries): %s", n, cudaGetErrorString(e));
+    entry_scratch_carve(ctx->entry_mem, n, ctx->status, ctx->bins);
+    ctx->max_entries = n;
+    return LOBE_OK;
+}
+
+static lobe_status grow_isect(lobe_ctx *ctx, long long need)
+{
+    if (need <= ctx->max_isect && ctx->isect_mem) return LOBE_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->isect_mem);
+    ctx->isect_mem = nullptr;
+    ctx->max_isect = 0;
+    long long n = need < 4096 ? 4096 : need;
+    cudaError_t e = cudaMalloc(&ctx->isect_mem, isect_scratch_bytes(n));
+    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "pair scratch (%lld pairs): %s", n, cudaGetErrorString(e));
+    isect_scratch_carve(ctx->isect_mem, n, ctx->bins);
+    ctx->max_isect = n;
+    return LOBE_OK;
+}
+
+lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect)
+{
+    if (!ctx || max_entries < 0 || max_isect < 0) return fail(ctx, LOBE_ERR_ARG, "bad reserve arguments");
+    lobe_status s = grow_entries(ctx, max_entries);
+    if (s != LOBE_OK) return s;
+    return grow_isect(ctx, max_isect);
+}
+
+lobe_status lobe_get_status(lobe_ctx *ctx)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    int st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status read");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "status sync");
+    CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status clear");
+    if (st == STATUS_CAPACITY) return fail(ctx, LOBE_ERR_CAPACITY, "pair count exceeded the bins' capacity");
+    if (st == STATUS_TIMEOUT) return fail(ctx, LOBE_ERR_TIMEOUT, "device wait expired");
+    return LOBE_OK;
+}
+
+// Parameter blocks are ~13 KB: keep them off the host stack of the caller's thread.
+struct ParamHolder {
+    BatchParams *p;
+    ParamHolder() : p(new (std::nothrow) BatchParams) {}
+    ~ParamHolder() { delete p; }
+};
+
+#define BUILD_PARAMS(H)                                                       \
+    if (!ctx) return LOBE_ERR_ARG;                                            \
+    ParamHolder H;                                                            \
+    if (!H.p) return fail(ctx, LOBE_ERR_OOM, "host parameter block");         \
+    {                                                                         \
+        lobe_status _s = build_params(ctx, ctx->cfg, batch, *H.p);            \
+        if (_s != LOBE_OK) return _s;                                         \
+    }
+
+lobe_status lobe_project(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *out)
+{
+    BUILD_PARAMS(H);
+    if (!out || !out->splat || !out->radius || !out->tiles_touched) return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
+    if (!aligned16(out->splat)) return fail(ctx, LOBE_ERR_ARG, "splat not 16-byte aligned");
+    CUDA_TRY(launch_project_fwd(*H.p, out->splat, out->radius, out->tiles_touched, ctx->stream), "project");
+    return LOBE_OK;
+}
+
+lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj, const lobe_bins *bins,
+                          int64_t *n_isect_host)
+{
+    BUILD_PARAMS(H);
+    const BatchParams &P = *H.p;
+    if (!proj || !proj->splat || !proj->radius || !proj->tiles_touched) return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
+    if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0)
+        return fail(ctx, LOBE_ERR_ARG, "bins missing");
+    if (P.n_entries > ctx->max_entries || !ctx->entry_mem) {
+        if (!n_isect_host)
+            return fail(ctx, LOBE_ERR_STATE, "scratch holds %lld entries, batch needs %lld: call lobe_ctx_reserve",
+                        ctx->max_entries, P.n_entries);
+        lobe_status s = grow_entries(ctx, P.n_entries);
+        if (s != LOBE_OK) return s;
+    }
+    if (!ctx->isect_mem) {
+        if (!n_isect_host) return fail(ctx, LOBE_ERR_STATE, "pair scratch not reserved: call lobe_ctx_reserve");
+        lobe_status s = grow_isect(ctx, 4096);
+        if (s != LOBE_OK) return s;
+    }
+    long long cap = bins->capacity;
+    if (!n_isect_host && cap > ctx->max_isect) cap = ctx->max_isect;
+    CUDA_TRY(bin_sort_count(P, proj->splat, proj->tiles_touched, ctx->bins, reinterpret_cast<long long *>(bins->n_isect),
+                            cap, ctx->stream),
+             "bin count");
+    long long isect_max = cap;
+    if (n_isect_host) {
+        long long total = 0;
+        CUDA_TRY(cudaMemcpyAsync(&total, bins->n_isect, sizeof total, cudaMemcpyDeviceToHost, ctx->stream), "n_isect read");
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream), "n_isect sync");
+        *n_isect_host = total;
+        if (total > bins->capacity) {
+            // the device latched the overflow too; the caller is told synchronously instead
+            CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status clear");
+            return fail(ctx, LOBE_ERR_CAPACITY, "%lld pairs exceed capacity %lld", total, (long long)bins->capacity);
+        }
+        if (total > ctx->max_isect) {
+            lobe_status s = grow_isect(ctx, total + total / 4);
+            if (s != LOBE_OK) return s;
+        }
+        isect_max = total;
+    }
+    CUDA_TRY(bin_sort_emit(P, proj->splat, proj->radius, proj->tiles_touched, ctx->bins, isect_max, bins->gauss_ids,
+                           bins->tile_start, ctx->stream),
+             "bin emit");
+    return LOBE_OK;
+}
+
+lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj, const lobe_bins *bins,
+                            const lobe_image *image)
+{
+    BUILD_PARAMS(H);
+    if (!proj || !proj->splat || !bins || !bins->gauss_ids || !bins->tile_start) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    if (!image || !image->rgb || !image->T_final || !image->n_contrib) return fail(ctx, LOBE_ERR_ARG, "image buffers missing");
+    CUDA_TRY(launch_render_fwd(*H.p, proj->splat, bins->tile_start, bins->gauss_ids, image->rgb, image->T_final,
+                               image->n_contrib, ctx->stream),
+             "render fwd");
+    return LOBE_OK;
+}
+
+lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj, const lobe_bins *bins,
+                            const lobe_image *image, const float *dL_drgb, float *grad2d)
+{
+    BUILD_PARAMS(H);
+    const bool rec = ctx->cfg.recompute_T != 0;
+    if (!proj || !proj->splat || !bins || !bins->gauss_ids || !bins->tile_start) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    if (!dL_drgb || !grad2d || !aligned16(grad2d)) return fail(ctx, LOBE_ERR_ARG, "dL_drgb/grad2d missing or misaligned");
+    if (!rec && (!image || !image->rgb || !image->n_contrib))
+        return fail(ctx, LOBE_ERR_ARG, "saved forward state missing (recompute_T = 0)");
+    CUDA_TRY(launch_render_bwd(*H.p, rec, proj->splat, bins->tile_start, bins->gauss_ids, rec ? nullptr : image->rgb,
+                               rec ? nullptr : image->n_contrib, dL_drgb, grad2d, ctx->stream),
+             "render bwd");
+    return LOBE_OK;
+}
+
+lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj, const float *grad2d,
+                             const lobe_grads *grads, int32_t accumulate)
+{
+    BUILD_PARAMS(H);
+    BatchParams &P = *H.p;
+    if (!proj || !proj->splat || !proj->radius || !grad2d || !grads) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    for (int s = 0; s < P.n_sets; ++s) {
+        const lobe_grads &g = grads[s];
+        if (P.set[s].n > 0 && (!g.means || !g.log_scales || !g.quats || !g.opacity_logits || !g.sh))
+            return fail(ctx, LOBE_ERR_ARG, "set %d: gradient pointer is NULL", s);
+        if (!aligned16(g.quats) || !aligned16(g.sh)) return fail(ctx, LOBE_ERR_ARG, "set %d: quats/sh grads misaligned", s);
+        if ((g.sd_acc == nullptr) != (g.sd_cnt == nullptr)) return fail(ctx, LOBE_ERR_ARG, "set %d: sd_acc/sd_cnt mismatch", s);
+        P.set[s].g_means = g.means;
+        P.set[s].g_log_scales = g.log_scales;
+        P.set[s].g_quats = g.quats;
+        P.set[s].g_logits = g.opacity_logits;
+        P.set[s].g_sh = g.sh;
+        P.set[s].sd_acc = g.sd_acc;
+        P.set[s].sd_cnt = g.sd_cnt;
+    }
+    CUDA_TRY(launch_project_bwd(P, proj->splat, proj->radius, grad2d, accumulate ? 1 : 0, ctx->stream), "project bwd");
+    return LOBE_OK;
+}
+
+lobe_status lobe_visibility_crop(lobe_ctx *ctx, const lobe_batch *batch, uint8_t *const *masks)
+{
+    BUILD_PARAMS(H);
+    BatchParams &P = *H.p;
+    if (!masks) return fail(ctx, LOBE_ERR_ARG, "masks is NULL");
+    for (int s = 0; s < P.n_sets; ++s) {
+        if (P.set[s].n > 0 && !masks[s]) return fail(ctx, LOBE_ERR_ARG, "set %d: mask is NULL", s);
+        P.set[s].vis_mask = masks[s];
+    }
+    CUDA_TRY(launch_visibility(P, ctx->stream), "visibility crop");
+    return LOBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// lobe_internal.cuh -- device-side parameter blocks and helpers shared by the kernels.
+//
+// Every kernel receives the whole batch description by value (a __grid_constant__
+// parameter block of ~13 KB), so a launch carries no host->device copy and a captured
+// CUDA graph replays with the parameters baked in.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lobe.h"
+
+namespace lobe {
+
+// ------------------------------------------------------------------ parameter blocks
+
+struct SetParams {
+    const float *means, *log_scales, *quats, *logits, *sh;
+    const uint8_t *crop;
+    // projection backward outputs (only read by the backward kernel)
+    float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+    float *sd_acc;
+    int32_t *sd_cnt;
+    uint8_t *vis_mask;
+    long long n;
+    long long gauss_off;  // first thread index of this set in set-major kernels
+    int item_begin;       // into BatchParams::set_items
+    int item_count;
+};
+
+struct ItemParams {
+    float V[12];          // rows 0..2 of the row-major world->camera matrix
+    double Vz[4];         // row 2 widened to double (exact), for the depth key
+    float fx, fy, cx, cy;
+    double near_plane, far_plane;
+    float campos[3];
+    float limx, limy;     // 1.3 * tan(fov/2) per axis
+    float lo[3], hi[3];   // block box
+    int W, H;
+    int gx, gy;           // tiles per row / column
+    int tile_off;         // first global tile id
+    int set;
+    long long entry_off;  // first projected entry
+    long long pix_off;    // first pixel
+};
+
+struct BatchParams {
+    SetParams set[LOBE_MAX_SETS];
+    ItemParams item[LOBE_MAX_ITEMS];
+    int set_items[LOBE_MAX_ITEMS];  // item indices grouped by set
+    int n_sets, n_items;
+    long long n_gauss;    // sum of set sizes
+    long long n_entries;  // sum over items of the set size
+    int n_tiles;
+    long long n_pixels;
+    int tw, th;
+    int sh_degree;
+    float bg[3];
+};
+
+// ------------------------------------------------------------------ device status
+
+enum : int { STATUS_OK = 0, STATUS_CAPACITY = 1, STATUS_TIMEOUT = 2 };
+
+__device__ __forceinline__ void set_status(int *status, int code)
+{
+    atomicCAS(status, STATUS_OK, code);
+}
+
+// ------------------------------------------------------------------ lookups
+
+__device__ __forceinline__ int item_of_tile(const BatchParams &P, int t)
+{
+    int lo = 0, hi = P.n_items - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.item[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int item_of_entry(const BatchParams &P, long long e)
+{
+    int lo = 0, hi = P.n_items - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.item[mid].entry_off <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int set_of_gauss(const BatchParams &P, long long t)
+{
+    int s = 0;
+    while (s + 1 < P.n_sets && t >= P.set[s + 1].gauss_off) ++s;
+    return s;
+}
+
+// Tile rectangle of a splat: [floor((u-r)/tw), ceil((u+r)/tw)) x [floor((v-r)/th), ceil((v+r)/th))
+// clamped to the grid. Evaluated in double so the result is exact for float u,v and
+// integer r (tw, th are powers of two): every kernel that needs it gets the same answer.
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int tw, int th, int gx, int gy,
+                                          int &x0, int &y0, int &x1, int &y1)
+{
+    double du = (double)u, dv = (double)v, dr = (double)r;
+    x0 = (int)fmin(fmax(floor((du - dr) / tw), 0.0), (double)gx);
+    y0 = (int)fmin(fmax(floor((dv - dr) / th), 0.0), (double)gy);
+    x1 = (int)fmin(fmax(ceil((du + dr) / tw), 0.0), (double)gx);
+    y1 = (int)fmin(fmax(ceil((dv + dr) / th), 0.0), (double)gy);
+}
+
+// ------------------------------------------------------------------ PTX helpers
+
+// hardware base-2 exponential (PTX ex2.approx.ftz.f32)
+__device__ __forceinline__ float ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// vector reduction-add of four floats into global memory (sm_90+)
+__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add_f32(float *addr, float a)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------------ compositing step
+//
+// One (pixel, splat) evaluation, shared by the forward and both backward sweeps so that
+// the alpha-skip and early-stop decisions are bit-identical between them. Explicit
+// round-to-nearest intrinsics keep the compiler from contracting differently per kernel.
+// The staged splat holds the conic pre-scaled into the base-2 exponent domain:
+//   A = -0.5 a log2(e), B = -b log2(e), C = -0.5 c log2(e)  =>  G = exp(-sigma) = 2^(A dx^2 + B dx dy + C dy^2)
+
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LN2 = 0.6931471805599453f;
+constexpr float ALPHA_MIN = 1.0f / 255.0f;
+constexpr float ALPHA_MAX = 0.99f;
+constexpr float T_MIN = 1e-4f;
+
+struct Eval {
+    float dx, dy, G, alpha;
+    bool use;      // contributes (sigma >= 0 and alpha >= 1/255)
+    bool clamped;  // alpha hit the 0.99 clamp
+};
+
+__device__ __forceinline__ Eval eval_pair(float u, float v, float A, float B, float C, float o, float pxc,
+                                          float pyc)
+{
+    Eval r;
+    r.dx = __fsub_rn(u, pxc);
+    r.dy = __fsub_rn(v, pyc);
+    float t = __fmaf_rn(A, r.dx, __fmul_rn(B, r.dy));
+    float p2 = __fmaf_rn(r.dx, t, __fmul_rn(__fmul_rn(C, r.dy), r.dy));
+    r.G = ex2(p2);
+    float araw = __fmul_rn(o, r.G);
+    r.clamped = araw >= ALPHA_MAX;
+    r.alpha = fminf(ALPHA_MAX, araw);
+    r.use = (p2 <= 0.0f) && (r.alpha >= ALPHA_MIN);
+    return r;
+}
+
+// T after a contributor; the stop rule is `next_T(T, alpha) < T_MIN` (checked before adding)
+__device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
+
+// ------------------------------------------------------------------ scratch and launchers
+
+struct SortScratch {
+    uint32_t *counts;      // radix digit counts per warp segment
+    uint32_t *block_sums;  // scan block totals
+};
+
+// Context-owned scratch of the binning stage. The "entry" part scales with the projected
+// entries, the "isect" part with the (splat, tile) pairs; they grow independently.
+struct BinScratch {
+    uint32_t *vis_pos, *dkA, *dvA, *dkB, *dvB, *offs;  // [max_entries]
+    uint32_t *tkA, *tvA, *tkB, *tvB;                   // [max_isect]
+    uint32_t *scalars;                                 // [0] visible count, [1] usable pair count
+    SortScratch sort;
+    int *status;
+};
+
+cudaError_t launch_project_fwd(const BatchParams &, float *, int *, int *, cudaStream_t);
+cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
+cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, cudaStream_t);
+cudaError_t launch_render_fwd(const BatchParams &, const float *, const int *, const int *, float *, float *, int *,
+                              cudaStream_t);
+cudaError_t launch_render_bwd(const BatchParams &, bool, const float *, const int *, const int *, const float *,
+                              const int *, const float *, float *, cudaStream_t);
+cudaError_t bin_sort_count(const BatchParams &, const float *, const int *, BinScratch &, long long *, long long,
+                           cudaStream_t);
+cudaError_t bin_sort_emit(const BatchParams &, const float *, const int *, const int *, BinScratch &, long long, int *,
+                          int *, cudaStream_t);
+size_t entry_scratch_bytes(long long max_entries);
+size_t isect_scratch_bytes(long long max_isect);
+void entry_scratch_carve(void *mem, long long max_entries, int *status, BinScratch &b);
+void isect_scratch_carve(void *mem, long long max_isect, BinScratch &b);
+
+}  // namespace lobe

@@ -1,0 +1,478 @@
+// project.cu -- EWA projection of 3D Gaussians (forward and adjoint), SH colour, culling,
+// visibility cropping.
+//
+// One thread per (set, Gaussian); the thread loops over the items that render that set, so
+// the Gaussian's 236 bytes of parameters are read from HBM once per set rather than once per
+// view (the multi-view batches of a KD block share one Gaussian set), and the adjoint
+// accumulates its per-view gradients in registers and writes each parameter once.
+//
+// Mathematics (the 3DGS rasterizer the paper trains with; appendix "3DGS Training"):
+//   p_c = V mu + t; Sigma = R S S^T R^T (R from the normalised quaternion, S = diag(exp(log_s)))
+//   J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]];  cov2d = J W Sigma W^T J^T + 0.3 I
+//   conic = cov2d^-1; radius = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det))
+//   u = fx x/z + cx, v = fy y/z + cy; colour = max(0, SH(normalize(mu - campos)) + 0.5);
+//   opacity = sigmoid(logit). Culled (radius 0): z outside [near, far] (z in double, Sec. 3.3
+//   frustum culling), |x/z| or |y/z| beyond 1.3 tan(fov/2), det <= 0, empty tile rectangle,
+//   crop_mask == 0 (visibility cropping, Sec. 3.3).
+#include "lobe_internal.cuh"
+
+namespace lobe {
+
+// Real SH normalisation constants sqrt((2l+1)/(4pi) (l-|m|)!/(l+|m|)!) * (sqrt 2 for m != 0),
+// folded with the integer coefficients of the Cartesian polynomials (Condon-Shortley phase).
+__constant__ float kSH[16] = {
+    0.28209479177387814f,                                                  // l0: 1/(2 sqrt(pi))
+    -0.48860251190291992f, 0.48860251190291992f, -0.48860251190291992f,   // l1: sqrt(3/(4pi)) * (-y, z, -x)
+    1.0925484305920792f, -1.0925484305920792f, 0.31539156525252005f,      // l2: xy, yz, (2zz-xx-yy)
+    -1.0925484305920792f, 0.54627421529603959f,                           //     xz, (xx-yy)
+    -0.59004358992664352f, 2.8906114426405538f, -0.45704579946446572f,    // l3: y(3xx-yy), xyz, y(4zz-xx-yy)
+    0.37317633259011540f, -0.45704579946446572f, 1.4453057213202769f,     //     z(2zz-3xx-3yy), x(4zz-xx-yy), z(xx-yy)
+    -0.59004358992664352f};                                               //     x(xx-3yy)
+
+// Basis polynomials (without the constant) and their gradients w.r.t. (x, y, z).
+__device__ __forceinline__ void sh_poly(int deg, float x, float y, float z, float P[16])
+{
+    P[0] = 1.0f;
+    if (deg < 1) return;
+    P[1] = y; P[2] = z; P[3] = x;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    P[4] = x * y; P[5] = y * z; P[6] = 2.0f * zz - xx - yy; P[7] = x * z; P[8] = xx - yy;
+    if (deg < 3) return;
+    P[9] = y * (3.0f * xx - yy);
+    P[10] = x * y * z;
+    P[11] = y * (4.0f * zz - xx - yy);
+    P[12] = z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    P[13] = x * (4.0f * zz - xx - yy);
+    P[14] = z * (xx - yy);
+    P[15] = x * (xx - 3.0f * yy);
+}
+
+__device__ __forceinline__ void sh_poly_grad(int k, float x, float y, float z, float &gx, float &gy, float &gz)
+{
+    float xx = x * x, yy = y * y, zz = z * z;
+    switch (k) {
+    case 1: gx = 0; gy = 1; gz = 0; break;
+    case 2: gx = 0; gy = 0; gz = 1; break;
+    case 3: gx = 1; gy = 0; gz = 0; break;
+    case 4: gx = y; gy = x; gz = 0; break;
+    case 5: gx = 0; gy = z; gz = y; break;
+    case 6: gx = -2 * x; gy = -2 * y; gz = 4 * z; break;
+    case 7: gx = z; gy = 0; gz = x; break;
+    case 8: gx = 2 * x; gy = -2 * y; gz = 0; break;
+    case 9: gx = 6 * x * y; gy = 3 * xx - 3 * yy; gz = 0; break;
+    case 10: gx = y * z; gy = x * z; gz = x * y; break;
+    case 11: gx = -2 * x * y; gy = 4 * zz - xx - 3 * yy; gz = 8 * y * z; break;
+    case 12: gx = -6 * x * z; gy = -6 * y * z; gz = 6 * zz - 3 * xx - 3 * yy; break;
+    case 13: gx = 4 * zz - 3 * xx - yy; gy = -2 * x * y; gz = 8 * x * z; break;
+    case 14: gx = 2 * x * z; gy = -2 * y * z; gz = xx - yy; break;
+    case 15: gx = 3 * xx - 3 * yy; gy = -6 * x * y; gz = 0; break;
+    default: gx = gy = gz = 0; break;
+    }
+}
+
+struct World {
+    float mx, my, mz;
+    float qw, qx, qy, qz, qinv;  // normalised quaternion and 1/|q|
+    float s[3];
+    float R[9];
+    float Sig[6];  // 00 01 02 11 12 22
+};
+
+__device__ __forceinline__ void load_world(const SetParams &S, long long g, World &w)
+{
+    w.mx = S.means[3 * g + 0];
+    w.my = S.means[3 * g + 1];
+    w.mz = S.means[3 * g + 2];
+    float4 q = reinterpret_cast<const float4 *>(S.quats)[g];
+    float qn = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    w.qinv = rsqrtf(qn);
+    w.qw = q.x * w.qinv; w.qx = q.y * w.qinv; w.qy = q.z * w.qinv; w.qz = q.w * w.qinv;
+    for (int i = 0; i < 3; ++i) w.s[i] = __expf(S.log_scales[3 * g + i]);
+    float x = w.qx, y = w.qy, z = w.qz, r = w.qw;
+    w.R[0] = 1.f - 2.f * (y * y + z * z); w.R[1] = 2.f * (x * y - r * z);       w.R[2] = 2.f * (x * z + r * y);
+    w.R[3] = 2.f * (x * y + r * z);       w.R[4] = 1.f - 2.f * (x * x + z * z); w.R[5] = 2.f * (y * z - r * x);
+    w.R[6] = 2.f * (x * z - r * y);       w.R[7] = 2.f * (y * z + r * x);       w.R[8] = 1.f - 2.f * (x * x + y * y);
+    float M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = w.R[3 * i + j] * w.s[j];
+    w.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    w.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    w.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    w.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    w.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    w.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+// Camera-dependent part of the projection. Returns false when culled.
+struct Cam2D {
+    float x, y, z;      // camera-space mean (z rounded from the double evaluation)
+    double zd;
+    float T0[3], T1[3]; // rows of J W
+    float ST0[3], ST1[3];
+    float c00, c01, c11;
+    float ca, cb, cc;
+    float u, v;
+    int radius;
+    int x0, y0, x1, y1;
+};
+
+__device__ __forceinline__ double depth_of(const ItemParams &I, const World &w)
+{
+    // ((V20 x + V21 y) + V22 z) + V23, each operation rounded in double
+    double t = __dadd_rn(__dmul_rn(I.Vz[0], (double)w.mx), __dmul_rn(I.Vz[1], (double)w.my));
+    t = __dadd_rn(t, __dmul_rn(I.Vz[2], (double)w.mz));
+    return __dadd_rn(t, I.Vz[3]);
+}
+
+__device__ __forceinline__ bool project_cam(const BatchParams &P, const ItemParams &I, const World &w, Cam2D &c)
+{
+    c.zd = depth_of(I, w);
+    if (!(c.zd >= I.near_plane && c.zd <= I.far_plane)) return false;
+    const float *V = I.V;
+    c.x = V[0] * w.mx + V[1] * w.my + V[2] * w.mz + V[3];
+    c.y = V[4] * w.mx + V[5] * w.my + V[6] * w.mz + V[7];
+    c.z = (float)c.zd;
+    float iz = 1.0f / c.z;
+    float tx = c.x * iz, ty = c.y * iz;
+    if (fabsf(tx) > I.limx || fabsf(ty) > I.limy) return false;
+    float j00 = I.fx * iz, j02 = -I.fx * tx * iz, j11 = I.fy * iz, j12 = -I.fy * ty * iz;
+    for (int k = 0; k < 3; ++k) {
+        c.T0[k] = j00 * V[k] + j02 * V[8 + k];
+        c.T1[k] = j11 * V[4 + k] + j12 * V[8 + k];
+    }
+    const float *S = w.Sig;
+    c.ST0[0] = S[0] * c.T0[0] + S[1] * c.T0[1] + S[2] * c.T0[2];
+    c.ST0[1] = S[1] * c.T0[0] + S[3] * c.T0[1] + S[4] * c.T0[2];
+    c.ST0[2] = S[2] * c.T0[0] + S[4] * c.T0[1] + S[5] * c.T0[2];
+    c.ST1[0] = S[0] * c.T1[0] + S[1] * c.T1[1] + S[2] * c.T1[2];
+    c.ST1[1] = S[1] * c.T1[0] + S[3] * c.T1[1] + S[4] * c.T1[2];
+    c.ST1[2] = S[2] * c.T1[0] + S[4] * c.T1[1] + S[5] * c.T1[2];
+    c.c00 = c.T0[0] * c.ST0[0] + c.T0[1] * c.ST0[1] + c.T0[2] * c.ST0[2] + 0.3f;
+    c.c01 = c.T1[0] * c.ST0[0] + c.T1[1] * c.ST0[1] + c.T1[2] * c.ST0[2];
+    c.c11 = c.T1[0] * c.ST1[0] + c.T1[1] * c.ST1[1] + c.T1[2] * c.ST1[2] + 0.3f;
+    float det = c.c00 * c.c11 - c.c01 * c.c01;
+    if (!(det > 0.0f)) return false;
+    float idet = 1.0f / det;
+    c.ca = c.c11 * idet;
+    c.cb = -c.c01 * idet;
+    c.cc = c.c00 * idet;
+    float mid = 0.5f * (c.c00 + c.c11);
+    float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+    c.radius = (int)ceilf(3.0f * sqrtf(lam));
+    c.u = I.fx * tx + I.cx;
+    c.v = I.fy * ty + I.cy;
+    tile_rect(c.u, c.v, c.radius, P.tw, P.th, I.gx, I.gy, c.x0, c.y0, c.x1, c.y1);
+    return c.radius > 0 && c.x1 > c.x0 && c.y1 > c.y0;
+}
+
+// --------------------------------------------------------------------------- forward
+
+__global__ void __launch_bounds__(256) k_project_fwd(const __grid_constant__ BatchParams P, float4 *__restrict__ splat,
+                                                     int *__restrict__ radius, int *__restrict__ tiles)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.n_gauss) return;
+    const int s = set_of_gauss(P, t);
+    const SetParams &S = P.set[s];
+    const long long g = t - S.gauss_off;
+    const bool cropped = S.crop != nullptr && S.crop[g] == 0;
+    World w;
+    if (!cropped) load_world(S, g, w);
+    float sh[48];
+    bool sh_loaded = false;
+    float opacity = 0.0f;
+    for (int k = 0; k < S.item_count; ++k) {
+        const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
+        const long long e = I.entry_off + g;
+        Cam2D c;
+        if (cropped || !project_cam(P, I, w, c)) {
+            radius[e] = 0;
+            tiles[e] = 0;
+            continue;
+        }
+        if (!sh_loaded) {
+            const float4 *src = reinterpret_cast<const float4 *>(S.sh + 48 * g);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                float4 q = src[i];
+                sh[4 * i + 0] = q.x; sh[4 * i + 1] = q.y; sh[4 * i + 2] = q.z; sh[4 * i + 3] = q.w;
+            }
+            opacity = 1.0f / (1.0f + __expf(-S.logits[g]));
+            sh_loaded = true;
+        }
+        float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
+        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Pp[16];
+        sh_poly(P.sh_degree, dx * il, dy * il, dz * il, Pp);
+        const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
+        float col[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            if (b < nb) {
+                float y = kSH[b] * Pp[b];
+                col[0] += y * sh[3 * b + 0];
+                col[1] += y * sh[3 * b + 1];
+                col[2] += y * sh[3 * b + 2];
+            }
+        }
+        float4 *o = splat + 3 * e;
+        o[0] = make_float4(c.u, c.v, c.ca, c.cb);
+        o[1] = make_float4(c.cc, opacity, fmaxf(0.f, col[0] + 0.5f), fmaxf(0.f, col[1] + 0.5f));
+        o[2] = make_float4(fmaxf(0.f, col[2] + 0.5f), c.z, 0.f, 0.f);
+        radius[e] = c.radius;
+        tiles[e] = (c.x1 - c.x0) * (c.y1 - c.y0);
+    }
+}
+
+// --------------------------------------------------------------------------- visibility crop
+
+__global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ BatchParams P)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.n_gauss) return;
+    const int s = set_of_gauss(P, t);
+    const SetParams &S = P.set[s];
+    const long long g = t - S.gauss_off;
+    World w;
+    load_world(S, g, w);
+    bool vis = false;
+    for (int k = 0; k < S.item_count && !vis; ++k) {
+        Cam2D c;
+        vis = project_cam(P, P.item[P.set_items[S.item_begin + k]], w, c);
+    }
+    if (vis) S.vis_mask[g] = 1;
+}
+
+// --------------------------------------------------------------------------- backward
+//
+// Chain rule from dL/d(u, v, conic, colour, opacity) to (mu, log_s, q, logit, sh):
+//   conic = cov^-1:  dL/dcov = -C Gs C,  Gs = [[da, db/2], [db/2, dc]]
+//   cov = T Sigma T^T + 0.3 I, T = J W:  dL/dT = 2 H T Sigma,  dL/dSigma = T^T H T
+//   J(p_c), (u, v)(p_c) -> dL/dp_c -> dL/dmu = W^T dL/dp_c
+//   Sigma = M M^T, M = R diag(s): dL/dM = 2 dL/dSigma M; dL/ds_j = sum_i dM_ij R_ij; dL/dR = dM diag(s)
+//   q -> R (normalised quaternion), then through the normalisation
+//   colour = max(0, SH + 0.5): masked where the raw value is negative; the view direction
+//   mu - campos carries a gradient to mu through the normalisation.
+// Per-view contributions to dL/dSigma (6 values), dL/dmu, dL/dlogit and dL/dsh are summed in
+// registers over the set's items; the Sigma -> (s, q) step runs once per Gaussian.
+
+__global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                                                     const int *__restrict__ radius,
+                                                     const float4 *__restrict__ grad2d, int accumulate)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.n_gauss) return;
+    const int s = set_of_gauss(P, t);
+    const SetParams &S = P.set[s];
+    const long long g = t - S.gauss_off;
+    float gmu[3] = {0.f, 0.f, 0.f};
+    float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float glogit = 0.f;
+    float gsh[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) gsh[i] = 0.f;
+    float sd_acc = 0.f;
+    int sd_cnt = 0;
+    bool any = false;
+    World w;
+    float sh[48];
+    for (int k = 0; k < S.item_count; ++k) {
+        const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
+        const long long e = I.entry_off + g;
+        if (radius[e] <= 0) continue;
+        if (!any) {
+            load_world(S, g, w);
+            const float4 *src = reinterpret_cast<const float4 *>(S.sh + 48 * g);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                float4 q = src[i];
+                sh[4 * i + 0] = q.x; sh[4 * i + 1] = q.y; sh[4 * i + 2] = q.z; sh[4 * i + 3] = q.w;
+            }
+            any = true;
+        }
+        Cam2D c;
+        project_cam(P, I, w, c);  // recompute the forward intermediates (visible by radius > 0)
+        const float4 g0 = grad2d[3 * e + 0], g1 = grad2d[3 * e + 1], g2 = grad2d[3 * e + 2];
+        const float du = g0.x, dv = g0.y, da = g0.z, db = g0.w, dc = g1.x, dop = g1.y;
+        const float dcol[3] = {g1.z, g1.w, g2.x};
+        const float4 sp1 = splat[3 * e + 1];
+        const float o = sp1.y;
+        glogit += dop * o * (1.f - o);
+        // ---- colour / SH
+        float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
+        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float nx = dx * il, ny = dy * il, nz = dz * il;
+        float Pp[16];
+        sh_poly(P.sh_degree, nx, ny, nz, Pp);
+        const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
+        float raw[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+            if (b < nb)
+                for (int ch = 0; ch < 3; ++ch) raw[ch] += kSH[b] * Pp[b] * sh[3 * b + ch];
+        float dn[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (raw[ch] + 0.5f < 0.f) continue;
+            const float d = dcol[ch];
+#pragma unroll
+            for (int b = 0; b < 16; ++b) {
+                if (b < nb) {
+                    gsh[3 * b + ch] += kSH[b] * Pp[b] * d;
+                    if (b > 0) {
+                        float ax, ay, az;
+                        sh_poly_grad(b, nx, ny, nz, ax, ay, az);
+                        float f = kSH[b] * sh[3 * b + ch] * d;
+                        dn[0] += f * ax; dn[1] += f * ay; dn[2] += f * az;
+                    }
+                }
+            }
+        }
+        float ndn = nx * dn[0] + ny * dn[1] + nz * dn[2];
+        gmu[0] += (dn[0] - nx * ndn) * il;
+        gmu[1] += (dn[1] - ny * ndn) * il;
+        gmu[2] += (dn[2] - nz * ndn) * il;
+        // ---- conic -> cov2d
+        const float ca = c.ca, cb = c.cb, cc = c.cc;
+        const float hb = 0.5f * db;
+        const float CG00 = ca * da + cb * hb, CG01 = ca * hb + cb * dc;
+        const float CG10 = cb * da + cc * hb, CG11 = cb * hb + cc * dc;
+        const float H00 = -(CG00 * ca + CG01 * cb);
+        const float H01 = -(CG00 * cb + CG01 * cc);
+        const float H11 = -(CG10 * cb + CG11 * cc);
+        // ---- cov2d = T Sigma T^T
+        float dT0[3], dT1[3];
+        for (int i = 0; i < 3; ++i) {
+            dT0[i] = 2.f * (H00 * c.ST0[i] + H01 * c.ST1[i]);
+            dT1[i] = 2.f * (H01 * c.ST0[i] + H11 * c.ST1[i]);
+        }
+        // dSigma = H00 T0 T0^T + H01 (T0 T1^T + T1 T0^T) + H11 T1 T1^T
+        {
+            const float *a = c.T0, *b = c.T1;
+            gSig[0] += H00 * a[0] * a[0] + 2.f * H01 * a[0] * b[0] + H11 * b[0] * b[0];
+            gSig[1] += H00 * a[0] * a[1] + H01 * (a[0] * b[1] + b[0] * a[1]) + H11 * b[0] * b[1];
+            gSig[2] += H00 * a[0] * a[2] + H01 * (a[0] * b[2] + b[0] * a[2]) + H11 * b[0] * b[2];
+            gSig[3] += H00 * a[1] * a[1] + 2.f * H01 * a[1] * b[1] + H11 * b[1] * b[1];
+            gSig[4] += H00 * a[1] * a[2] + H01 * (a[1] * b[2] + b[1] * a[2]) + H11 * b[1] * b[2];
+            gSig[5] += H00 * a[2] * a[2] + 2.f * H01 * a[2] * b[2] + H11 * b[2] * b[2];
+        }
+        // ---- T = J W  ->  J entries
+        const float *V = I.V;
+        const float dJ00 = dT0[0] * V[0] + dT0[1] * V[1] + dT0[2] * V[2];
+        const float dJ02 = dT0[0] * V[8] + dT0[1] * V[9] + dT0[2] * V[10];
+        const float dJ11 = dT1[0] * V[4] + dT1[1] * V[5] + dT1[2] * V[6];
+        const float dJ12 = dT1[0] * V[8] + dT1[1] * V[9] + dT1[2] * V[10];
+        const float iz = 1.f / c.z, iz2 = iz * iz, iz3 = iz2 * iz;
+        const float fx = I.fx, fy = I.fy;
+        float dpx = du * fx * iz - dJ02 * fx * iz2;
+        float dpy = dv * fy * iz - dJ12 * fy * iz2;
+        float dpz = -du * fx * c.x * iz2 - dv * fy * c.y * iz2 - dJ00 * fx * iz2 + dJ02 * 2.f * fx * c.x * iz3 -
+                    dJ11 * fy * iz2 + dJ12 * 2.f * fy * c.y * iz3;
+        gmu[0] += V[0] * dpx + V[4] * dpy + V[8] * dpz;
+        gmu[1] += V[1] * dpx + V[5] * dpy + V[9] * dpz;
+        gmu[2] += V[2] * dpx + V[6] * dpy + V[10] * dpz;
+        // ---- selective densification statistic (Sec. 3.3)
+        if (w.mx >= I.lo[0] && w.mx < I.hi[0] && w.my >= I.lo[1] && w.my < I.hi[1] && w.mz >= I.lo[2] &&
+            w.mz < I.hi[2]) {
+            float a = du * 0.5f * (float)I.W, b = dv * 0.5f * (float)I.H;
+            sd_acc += sqrtf(a * a + b * b);
+            sd_cnt += 1;
+        }
+    }
+    // ---- Sigma -> (log_s, q) once per Gaussian
+    float gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+    if (any) {
+        // gSig holds the entries G_kl (k <= l) of the symmetric full-matrix gradient T^T H T
+        float D[9] = {gSig[0], gSig[1], gSig[2], gSig[1], gSig[3], gSig[4], gSig[2], gSig[4], gSig[5]};
+        float M[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[3 * i + j] = w.R[3 * i + j] * w.s[j];
+        float dM[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                dM[3 * i + j] = 2.f * (D[3 * i + 0] * M[0 + j] + D[3 * i + 1] * M[3 + j] + D[3 * i + 2] * M[6 + j]);
+        float dR[9];
+        for (int j = 0; j < 3; ++j) {
+            float ds = dM[j] * w.R[j] + dM[3 + j] * w.R[3 + j] + dM[6 + j] * w.R[6 + j];
+            gls[j] = ds * w.s[j];
+            dR[j] = dM[j] * w.s[j];
+            dR[3 + j] = dM[3 + j] * w.s[j];
+            dR[6 + j] = dM[6 + j] * w.s[j];
+        }
+        const float r = w.qw, x = w.qx, y = w.qy, z = w.qz;
+        float dqw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+        float dqx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - r * dR[5] + z * dR[6] + r * dR[7] -
+                           2.f * x * dR[8]);
+        float dqy = 2.f * (-2.f * y * dR[0] + x * dR[1] + r * dR[2] + x * dR[3] + z * dR[5] - r * dR[6] + z * dR[7] -
+                           2.f * y * dR[8]);
+        float dqz = 2.f * (-2.f * z * dR[0] - r * dR[1] + x * dR[2] + r * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] +
+                           y * dR[7]);
+        float qd = r * dqw + x * dqx + y * dqy + z * dqz;
+        gq[0] = (dqw - r * qd) * w.qinv;
+        gq[1] = (dqx - x * qd) * w.qinv;
+        gq[2] = (dqy - y * qd) * w.qinv;
+        gq[3] = (dqz - z * qd) * w.qinv;
+    }
+    // ---- write
+    if (accumulate) {
+        for (int i = 0; i < 3; ++i) {
+            S.g_means[3 * g + i] += gmu[i];
+            S.g_log_scales[3 * g + i] += gls[i];
+        }
+        float4 *gq4 = reinterpret_cast<float4 *>(S.g_quats) + g;
+        float4 q = *gq4;
+        *gq4 = make_float4(q.x + gq[0], q.y + gq[1], q.z + gq[2], q.w + gq[3]);
+        S.g_logits[g] += glogit;
+        float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            float4 a = d[i];
+            d[i] = make_float4(a.x + gsh[4 * i], a.y + gsh[4 * i + 1], a.z + gsh[4 * i + 2], a.w + gsh[4 * i + 3]);
+        }
+    } else {
+        for (int i = 0; i < 3; ++i) {
+            S.g_means[3 * g + i] = gmu[i];
+            S.g_log_scales[3 * g + i] = gls[i];
+        }
+        reinterpret_cast<float4 *>(S.g_quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        S.g_logits[g] = glogit;
+        float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) d[i] = make_float4(gsh[4 * i], gsh[4 * i + 1], gsh[4 * i + 2], gsh[4 * i + 3]);
+    }
+    if (S.sd_acc != nullptr && sd_cnt > 0) {
+        S.sd_acc[g] += sd_acc;
+        S.sd_cnt[g] += sd_cnt;
+    }
+}
+
+// --------------------------------------------------------------------------- launchers
+
+cudaError_t launch_project_fwd(const BatchParams &P, float *splat, int *radius, int *tiles, cudaStream_t st)
+{
+    if (P.n_gauss == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
+    k_project_fwd<<<blocks, 256, 0, st>>>(P, reinterpret_cast<float4 *>(splat), radius, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_visibility(const BatchParams &P, cudaStream_t st)
+{
+    if (P.n_gauss == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
+    k_visibility<<<blocks, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const int *radius, const float *grad2d,
+                               int accumulate, cudaStream_t st)
+{
+    if (P.n_gauss == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((P.n_gauss + 127) / 128);
+    k_project_bwd<<<blocks, 128, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
+                                          reinterpret_cast<const float4 *>(grad2d), accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace lobe

@@ -1,0 +1,359 @@
+"""Python binding of the C ABI: the same stages as include/lobe.h, on torch CUDA tensors.
+
+PyTorch supplies device memory and the stream; every stage runs in liblobe.so. The names
+mirror the C entry points: :func:`project`, :func:`bin_sort`, :func:`render_fwd`,
+:func:`render_bwd`, :func:`project_bwd`, :func:`visibility_crop`.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _abi as A
+
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+@dataclass
+class GaussianSet:
+    """Device parameters of one Gaussian set (float32, contiguous)."""
+    means: torch.Tensor           # [n,3]
+    log_scales: torch.Tensor      # [n,3]
+    quats: torch.Tensor           # [n,4] (w,x,y,z)
+    opacity_logits: torch.Tensor  # [n]
+    sh: torch.Tensor              # [n,16,3]
+    crop_mask: torch.Tensor | None = None  # [n] uint8
+
+    @property
+    def n(self):
+        return int(self.means.shape[0])
+
+    @classmethod
+    def from_numpy(cls, g, device="cuda"):
+        a = g.arrays() if hasattr(g, "arrays") else g
+        t = {k: torch.as_tensor(a[k], dtype=torch.float32).contiguous().to(device) for k in PARAM_KEYS}
+        crop = getattr(g, "crop_mask", None)
+        if crop is not None:
+            crop = torch.as_tensor(crop, dtype=torch.uint8).to(device)
+        return cls(**t, crop_mask=crop)
+
+    def params(self):
+        return [getattr(self, k) for k in PARAM_KEYS]
+
+
+def camera_struct(cam) -> A.Camera:
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    s = A.Camera()
+    vm = [float(x) for x in torch.as_tensor(c["viewmat"], dtype=torch.float32).reshape(16).tolist()]
+    s.viewmat[:] = vm
+    s.fx, s.fy, s.cx, s.cy = float(c["fx"]), float(c["fy"]), float(c["cx"]), float(c["cy"])
+    s.width, s.height = int(c["width"]), int(c["height"])
+    s.near_plane, s.far_plane = float(c.get("near", 0.01)), float(c.get("far", 1e10))
+    return s
+
+
+def aabb_struct(box) -> A.AABB:
+    s = A.AABB()
+    lo = getattr(box, "lo", None) if box is not None else None
+    hi = getattr(box, "hi", None) if box is not None else None
+    s.lo[:] = [float(x) for x in (lo if lo is not None else (-math.inf,) * 3)]
+    s.hi[:] = [float(x) for x in (hi if hi is not None else (math.inf,) * 3)]
+    return s
+
+
+class Batch:
+    """Host description of a batch of (set, camera, block) items (a lobe_batch)."""
+
+    def __init__(self, sets, cameras, items, blocks=()):
+        if len(sets) > A.MAX_SETS or len(items) > A.MAX_ITEMS:
+            raise ValueError("too many sets or items for one batch")
+        self.sets = list(sets)
+        self.cameras = [c if isinstance(c, dict) else c.as_dict() for c in cameras]
+        self.blocks = list(blocks)
+        self.items = [tuple(int(x) for x in it) for it in items]
+        for g in self.sets:
+            for k in PARAM_KEYS:
+                _require_cuda(getattr(g, k), k)
+            if g.crop_mask is not None:
+                _require_cuda(g.crop_mask, "crop_mask", torch.uint8)
+        self._c_sets = (A.Gaussians * len(self.sets))()
+        for i, g in enumerate(self.sets):
+            s = self._c_sets[i]
+            s.means, s.log_scales, s.quats = g.means.data_ptr(), g.log_scales.data_ptr(), g.quats.data_ptr()
+            s.opacity_logits, s.sh = g.opacity_logits.data_ptr(), g.sh.data_ptr()
+            s.crop_mask = g.crop_mask.data_ptr() if g.crop_mask is not None else None
+            s.n = g.n
+        self._c_cams = (A.Camera * len(self.cameras))(*[camera_struct(c) for c in self.cameras])
+        nb = max(1, len(self.blocks))
+        self._c_blocks = (A.AABB * nb)(*([aabb_struct(b) for b in self.blocks] or [aabb_struct(None)]))
+        self._c_items = (A.Item * len(self.items))(*[A.Item(s, c, b) for s, c, b in self.items])
+        self.c = A.Batch(self._c_sets, len(self.sets), self._c_cams, len(self.cameras), self._c_blocks,
+                         len(self.blocks), self._c_items, len(self.items))
+        # host-side layout (mirrors the library's offsets)
+        self.entry_off, self.pix_off = [], []
+        e = p = 0
+        for s, c, _ in self.items:
+            self.entry_off.append(e)
+            self.pix_off.append(p)
+            e += self.sets[s].n
+            p += self.cameras[c]["width"] * self.cameras[c]["height"]
+        self.n_entries, self.n_pixels = e, p
+
+    def tiles(self, tile):
+        t = 0
+        offs = []
+        for _, c, _ in self.items:
+            cam = self.cameras[c]
+            offs.append(t)
+            t += -(-cam["width"] // tile[0]) * -(-cam["height"] // tile[1])
+        return t, offs
+
+    def image_views(self, flat: torch.Tensor, channels=3):
+        """Split a flat planar image buffer into per-item [C,H,W] views."""
+        out = []
+        for (s, c, _), p in zip(self.items, self.pix_off):
+            cam = self.cameras[c]
+            W, H = cam["width"], cam["height"]
+            out.append(flat[channels * p: channels * (p + W * H)].view(channels, H, W) if channels > 1
+                       else flat[p: p + W * H].view(H, W))
+        return out
+
+
+class Context:
+    """A lobe_ctx bound to a CUDA stream (the current torch stream by default)."""
+
+    def __init__(self, tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0), recompute_T=False, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the lobe rasterizer needs a CUDA device (no CPU fallback)")
+        self.lib = A.lib()
+        self.tile = tuple(tile)
+        self.sh_degree = sh_degree
+        self.bg = tuple(float(b) for b in bg)
+        self.recompute_T = bool(recompute_T)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = ctypes.c_void_p()
+        A.check(self.lib.lobe_ctx_create(ctypes.byref(self.handle), ctypes.c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(self._config())))
+        self._bins = None
+
+    def _config(self) -> A.Config:
+        c = A.Config()
+        c.tile_w, c.tile_h = self.tile
+        c.sh_degree = self.sh_degree
+        c.bg[:] = list(self.bg)
+        c.recompute_T = int(self.recompute_T)
+        return c
+
+    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None):
+        if tile is not None:
+            self.tile = tuple(tile)
+        if recompute_T is not None:
+            self.recompute_T = bool(recompute_T)
+        if sh_degree is not None:
+            self.sh_degree = sh_degree
+        if bg is not None:
+            self.bg = tuple(float(b) for b in bg)
+        self._check(self.lib.lobe_ctx_set_config(self.handle, ctypes.byref(self._config())))
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.lib.lobe_ctx_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
+
+    def reserve(self, max_entries, max_isect):
+        self._check(self.lib.lobe_ctx_reserve(self.handle, int(max_entries), int(max_isect)))
+
+    def status(self):
+        self._check(self.lib.lobe_get_status(self.handle))
+
+    def _check(self, code):
+        A.check(code, self.handle)
+
+    def close(self):
+        if self.handle:
+            self.lib.lobe_ctx_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- stage outputs
+
+@dataclass
+class Projection:
+    splat: torch.Tensor   # [E,12] float32
+    radius: torch.Tensor  # [E] int32
+    tiles: torch.Tensor   # [E] int32
+
+    def c(self):
+        return A.Projected(self.splat.data_ptr(), self.radius.data_ptr(), self.tiles.data_ptr())
+
+
+@dataclass
+class Bins:
+    gauss_ids: torch.Tensor   # [capacity] int32
+    tile_start: torch.Tensor  # [n_tiles+1] int32
+    n_isect: torch.Tensor     # [1] int64
+    count: int | None = None  # host copy when known
+
+    @property
+    def capacity(self):
+        return int(self.gauss_ids.shape[0])
+
+    def c(self):
+        return A.Bins(self.gauss_ids.data_ptr(), self.tile_start.data_ptr(), self.n_isect.data_ptr(), self.capacity)
+
+    def ids(self):
+        n = self.count if self.count is not None else int(self.n_isect.item())
+        return self.gauss_ids[:n]
+
+
+@dataclass
+class Image:
+    rgb: torch.Tensor        # [3*pixels] float32 (planar per item)
+    T_final: torch.Tensor    # [pixels]
+    n_contrib: torch.Tensor  # [pixels] int32
+
+    def c(self):
+        return A.Image(self.rgb.data_ptr(), self.T_final.data_ptr(), self.n_contrib.data_ptr())
+
+
+def empty_projection(n_entries, device="cuda") -> Projection:
+    return Projection(torch.empty((n_entries, 12), dtype=torch.float32, device=device),
+                      torch.empty(n_entries, dtype=torch.int32, device=device),
+                      torch.empty(n_entries, dtype=torch.int32, device=device))
+
+
+def empty_bins(capacity, n_tiles, device="cuda") -> Bins:
+    return Bins(torch.empty(max(1, int(capacity)), dtype=torch.int32, device=device),
+                torch.empty(n_tiles + 1, dtype=torch.int32, device=device),
+                torch.zeros(1, dtype=torch.int64, device=device))
+
+
+def empty_image(n_pixels, device="cuda") -> Image:
+    return Image(torch.empty(3 * n_pixels, dtype=torch.float32, device=device),
+                 torch.empty(n_pixels, dtype=torch.float32, device=device),
+                 torch.empty(n_pixels, dtype=torch.int32, device=device))
+
+
+# --------------------------------------------------------------------------- stages
+
+def project(ctx: Context, batch: Batch, out: Projection | None = None) -> Projection:
+    out = out if out is not None else empty_projection(batch.n_entries)
+    ctx._check(ctx.lib.lobe_project(ctx.handle, ctypes.byref(batch.c), ctypes.byref(out.c())))
+    return out
+
+
+def bin_sort(ctx: Context, batch: Batch, proj: Projection, bins: Bins | None = None, sync: bool = True) -> Bins:
+    """Sorts all (splat, tile) pairs. With sync=True the pair count is read back and the bins
+    grow as needed (not graph-capturable); with sync=False the given bins must be large enough
+    (an overflow is latched on the device and read by Context.status())."""
+    n_tiles, _ = batch.tiles(ctx.tile)
+    if bins is None:
+        bins = ctx._bins
+        if bins is None or bins.tile_start.shape[0] != n_tiles + 1:
+            cap = bins.capacity if bins is not None else max(1 << 16, 8 * batch.n_entries)
+            bins = empty_bins(cap, n_tiles)
+    if not sync:
+        ctx._check(ctx.lib.lobe_bin_sort(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()),
+                                         ctypes.byref(bins.c()), None))
+        bins.count = None
+        return bins
+    n = ctypes.c_int64(0)
+    code = ctx.lib.lobe_bin_sort(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()), ctypes.byref(bins.c()),
+                                 ctypes.byref(n))
+    if code == A.ERR_CAPACITY:
+        bins = empty_bins(int(n.value * 1.25) + 1024, n_tiles)
+        code = ctx.lib.lobe_bin_sort(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()),
+                                     ctypes.byref(bins.c()), ctypes.byref(n))
+    ctx._check(code)
+    bins.count = int(n.value)
+    ctx._bins = bins
+    return bins
+
+
+def render_fwd(ctx: Context, batch: Batch, proj: Projection, bins: Bins, out: Image | None = None) -> Image:
+    out = out if out is not None else empty_image(batch.n_pixels)
+    ctx._check(ctx.lib.lobe_render_fwd(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()),
+                                       ctypes.byref(bins.c()), ctypes.byref(out.c())))
+    return out
+
+
+def render_bwd(ctx: Context, batch: Batch, proj: Projection, bins: Bins, image: Image | None,
+               dL_drgb: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    _require_cuda(dL_drgb, "dL_drgb")
+    out = out if out is not None else torch.empty((batch.n_entries, 12), dtype=torch.float32, device="cuda")
+    img = ctypes.byref(image.c()) if image is not None else None
+    ctx._check(ctx.lib.lobe_render_bwd(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()),
+                                       ctypes.byref(bins.c()), img, _ptr(dL_drgb), _ptr(out)))
+    return out
+
+
+def zero_grads(batch: Batch, sd=True):
+    out = []
+    for g in batch.sets:
+        d = {k: torch.zeros_like(getattr(g, k)) for k in PARAM_KEYS}
+        if sd:
+            d["sd_acc"] = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+            d["sd_cnt"] = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        out.append(d)
+    return out
+
+
+def project_bwd(ctx: Context, batch: Batch, proj: Projection, grad2d: torch.Tensor, grads=None,
+                accumulate: bool = False):
+    """Parameter gradients per set (list of dicts with the PARAM_KEYS, plus optional
+    sd_acc / sd_cnt which always accumulate)."""
+    if grads is None:
+        grads = []
+        for g in batch.sets:
+            d = {k: torch.empty_like(getattr(g, k)) for k in PARAM_KEYS}
+            grads.append(d)
+        accumulate = False
+    arr = (A.Grads * len(batch.sets))()
+    for i, d in enumerate(grads):
+        s = arr[i]
+        s.means, s.log_scales, s.quats = d["means"].data_ptr(), d["log_scales"].data_ptr(), d["quats"].data_ptr()
+        s.opacity_logits, s.sh = d["opacity_logits"].data_ptr(), d["sh"].data_ptr()
+        s.sd_acc = d["sd_acc"].data_ptr() if d.get("sd_acc") is not None else None
+        s.sd_cnt = d["sd_cnt"].data_ptr() if d.get("sd_cnt") is not None else None
+    ctx._check(ctx.lib.lobe_project_bwd(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()), _ptr(grad2d),
+                                        arr, int(bool(accumulate))))
+    return grads
+
+
+def visibility_crop(ctx: Context, batch: Batch, masks=None):
+    """Visibility cropping (Sec. 3.3): per set, uint8 mask of Gaussians visible from at
+    least one item of that set (OR-ed into ``masks`` when given)."""
+    if masks is None:
+        masks = [torch.zeros(g.n, dtype=torch.uint8, device="cuda") for g in batch.sets]
+    arr = (ctypes.c_void_p * len(masks))(*[m.data_ptr() for m in masks])
+    ctx._check(ctx.lib.lobe_visibility_crop(ctx.handle, ctypes.byref(batch.c), arr))
+    return masks
+
+
+def forward(ctx: Context, batch: Batch, sync=True):
+    """project -> bin_sort -> render_fwd. Returns (proj, bins, image)."""
+    proj = project(ctx, batch)
+    bins = bin_sort(ctx, batch, proj, sync=sync)
+    img = render_fwd(ctx, batch, proj, bins)
+    return proj, bins, img

@@ -1,0 +1,348 @@
+"""GPU path vs the FP64 oracle, stage by stage and end to end, through the C ABI.
+
+Stage tests feed every GPU stage the oracle's own upstream result rounded to float32, so
+the comparison isolates one kernel's arithmetic; end-to-end tests chain the GPU stages.
+Pixels (and, for gradients, their dL/dC) whose compositing decisions are marginal under
+float32 (alpha at 1/255, T at 1e-4, the 0.99 clamp, a radius or rectangle edge at a
+boundary) are excluded; their count is bounded in each test.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+from tests.helpers import (IMG_ATOL, assert_grad_close, oracle_grad2d_array, rect_tiles, splat_array)
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2510_01767_b300 as lobe
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def make_batch(wl, crop=None):
+    sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
+    if crop is not None:
+        sets[0].crop_mask = dev(crop, torch.uint8)
+    return lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
+
+
+def gpu_projection_from_oracle(p, cam, tile):
+    return lobe.Projection(dev(splat_array(p)), dev(p.radius, torch.int32),
+                           dev(rect_tiles(p.mean2d, p.radius, cam, tile), torch.int32))
+
+
+@pytest.fixture(scope="module")
+def small():
+    wl = scenes.small_scene()
+    g64 = oracle.set_dict(wl.sets[0])
+    return wl, g64
+
+
+def ctx_for(wl, **kw):
+    return lobe.Context(tile=wl.tile, **kw)
+
+
+# ----------------------------------------------------------------------------- project
+
+@pytest.mark.parametrize("posed", [False, True])
+def test_project_matches_oracle(small, posed):
+    wl, g = small
+    cam = wl.cameras[0].as_dict()
+    if posed:
+        cam = dict(cam, viewmat=scenes.look_at((0.8, -0.6, -0.5), (0.0, 0.0, 4.0), up=(0, -1, 0)))
+        wl = scenes.Workload(wl.name, wl.sets, [scenes.Camera(**{**cam})], wl.blocks, wl.items, wl.tile)
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    proj = lobe.project(ctx, batch)
+    torch.cuda.synchronize()
+    p = oracle.project(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
+    rad = proj.radius.cpu().numpy()
+    s = proj.splat.cpu().numpy().astype(np.float64)
+    marg = (p.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) != 0
+    ok = ~marg
+    np.testing.assert_array_equal(rad[ok], p.radius[ok])
+    vis = ok & (p.radius > 0)
+    assert vis.sum() > 500
+    np.testing.assert_allclose(s[vis, 0:2], p.mean2d[vis], rtol=1e-5, atol=2e-4)
+    np.testing.assert_allclose(s[vis, 2:5], p.conic[vis], rtol=2e-4, atol=1e-7)
+    np.testing.assert_allclose(s[vis, 5], p.opacity[vis], rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(s[vis, 6:9], p.color[vis], atol=2e-5)
+    # depth key: float32 rounding of the double-precision z, bit for bit
+    np.testing.assert_array_equal(s[vis, 9].astype(np.float32), p.depth[vis].astype(np.float32))
+    tiles = proj.tiles.cpu().numpy()
+    np.testing.assert_array_equal(tiles[ok], np.where(p.radius[ok] > 0, (p.rect[ok, 2] - p.rect[ok, 0]) *
+                                                      (p.rect[ok, 3] - p.rect[ok, 1]), 0))
+
+
+# ----------------------------------------------------------------------------- bin + sort
+
+def test_bin_sort_bit_exact_on_oracle_projection(small):
+    wl, g = small
+    cam = wl.cameras[0].as_dict()
+    p = oracle.project(g, cam, wl.tile).rounded()
+    ids, ts = oracle.bin_sort(p, cam, wl.tile)
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    gp = gpu_projection_from_oracle(p, cam, wl.tile)
+    bins = lobe.bin_sort(ctx, batch, gp)
+    assert bins.count == len(ids)
+    np.testing.assert_array_equal(bins.ids().cpu().numpy(), ids)
+    np.testing.assert_array_equal(bins.tile_start.cpu().numpy(), ts)
+
+
+def test_bin_sort_bit_exact_multi_item_large_tile_count():
+    """Several items (global tile ids across items), 8x8 tiles (>65536 tiles => 3 radix passes),
+    ragged image sizes; each item's pairs must equal the oracle's for that item."""
+    rng = np.random.default_rng(11)
+    g = scenes.uniform_gaussians(rng, 3000, 1.0, 2.0, 6.0)
+    cams = [scenes.pinhole(1920, 1080, 1500.0), scenes.pinhole(1000, 750, 800.0), scenes.pinhole(333, 201, 260.0),
+            scenes.pinhole(2048, 1536, 1600.0)]
+    tile = (8, 8)
+    wl = scenes.Workload("t", [g], cams, [scenes.AABB()], [(0, i, 0) for i in range(4)], tile)
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    gd = oracle.set_dict(g)
+    parts, want_ids, want_ts = [], [], []
+    n_tiles, toffs = batch.tiles(tile)
+    assert n_tiles > 65536
+    off_e = 0
+    total = 0
+    for i, cam in enumerate(cams):
+        p = oracle.project(gd, cam.as_dict(), tile).rounded()
+        ids, ts = oracle.bin_sort(p, cam.as_dict(), tile)
+        parts.append(p)
+        want_ids.append(ids + off_e)
+        want_ts.append(ts[:-1] + total)
+        off_e += g.n
+        total += len(ids)
+    want_ts.append(np.array([total]))
+    splat = np.concatenate([splat_array(p) for p in parts])
+    rad = np.concatenate([p.radius for p in parts])
+    tl = np.concatenate([rect_tiles(p.mean2d, p.radius, c, tile) for p, c in zip(parts, cams)])
+    gp = lobe.Projection(dev(splat), dev(rad, torch.int32), dev(tl, torch.int32))
+    bins = lobe.bin_sort(ctx, batch, gp)
+    assert bins.count == total
+    np.testing.assert_array_equal(bins.ids().cpu().numpy(), np.concatenate(want_ids))
+    np.testing.assert_array_equal(bins.tile_start.cpu().numpy(), np.concatenate(want_ts))
+
+
+# ----------------------------------------------------------------------------- render
+
+def stage_inputs(wl, g, cam):
+    p = oracle.project(g, cam, wl.tile).rounded()
+    ids, ts = oracle.bin_sort(p, cam, wl.tile)
+    return p, ids, ts
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+def test_render_fwd_matches_oracle(small, tile):
+    wl, g = small
+    wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
+    cam = wl.cameras[0].as_dict()
+    p, ids, ts = stage_inputs(wl, g, cam)
+    bg = (0.1, 0.2, 0.3)
+    img = oracle.render_fwd(p, ids, ts, cam, tile, bg, oracle.MARGINS_STAGE)
+    ctx = ctx_for(wl, bg=bg)
+    batch = make_batch(wl)
+    gp = gpu_projection_from_oracle(p, cam, tile)
+    bins = lobe.bin_sort(ctx, batch, gp)
+    out = lobe.render_fwd(ctx, batch, gp, bins)
+    rgb = out.rgb.view(3, 128, 128).cpu().numpy()
+    T = out.T_final.view(128, 128).cpu().numpy()
+    nc = out.n_contrib.view(128, 128).cpu().numpy()
+    ok = img.flags == 0
+    assert ok.mean() > 0.99
+    assert np.abs(rgb - img.rgb)[:, ok].max() <= IMG_ATOL
+    assert np.abs(T - img.T_final)[ok].max() <= IMG_ATOL
+    np.testing.assert_array_equal(nc[ok], img.n_contrib[ok])
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_render_bwd_matches_oracle(small, recompute):
+    wl, g = small
+    cam = wl.cameras[0].as_dict()
+    p, ids, ts = stage_inputs(wl, g, cam)
+    bg = (0.1, 0.2, 0.3)
+    img = oracle.render_fwd(p, ids, ts, cam, wl.tile, bg, oracle.MARGINS_STAGE)
+    dL = np.random.default_rng(3).standard_normal((3, 128, 128)) * (img.flags == 0)[None]
+    dL = dL.astype(np.float32).astype(np.float64)
+    want = oracle_grad2d_array(oracle.render_bwd(p, ids, ts, cam, dL, wl.tile, bg))
+    ctx = ctx_for(wl, bg=bg, recompute_T=recompute)
+    batch = make_batch(wl)
+    gp = gpu_projection_from_oracle(p, cam, wl.tile)
+    bins = lobe.bin_sort(ctx, batch, gp)
+    out = lobe.render_fwd(ctx, batch, gp, bins)
+    g2d = lobe.render_bwd(ctx, batch, gp, bins, out, dev(dL).reshape(-1)).cpu().numpy()
+    vis = p.radius > 0
+    for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                       ("color", slice(6, 9))]:
+        assert_grad_close(g2d[vis, cols], want[vis, cols], name)
+    assert np.all(g2d[:, 9:] == 0)
+
+
+def test_project_bwd_matches_oracle(small):
+    wl, g = small
+    cam = wl.cameras[0].as_dict()
+    f = oracle.forward(g, cam, wl.tile, margins=oracle.MARGINS_STAGE)
+    dL = np.random.default_rng(4).standard_normal((3, 128, 128)) * (f.pixel_flags == 0)[None]
+    box = scenes.AABB((-0.5, -0.5, -math.inf), (0.5, 0.5, math.inf))
+    g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
+    g2d_r = oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
+                            (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity)))
+    want = oracle.project_bwd(g, cam, g2d_r, wl.tile, aabb=box)
+    ctx = ctx_for(wl)
+    wl2 = scenes.Workload(wl.name, wl.sets, wl.cameras, [box], wl.items, wl.tile)
+    batch = make_batch(wl2)
+    proj = lobe.project(ctx, batch)
+    grads = lobe.zero_grads(batch)
+    lobe.project_bwd(ctx, batch, proj, dev(oracle_grad2d_array(g2d_r)), grads, accumulate=True)
+    gr = {k: v.cpu().numpy() for k, v in grads[0].items()}
+    ok = (f.proj.flags == 0) & (f.proj.radius > 0)
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        assert_grad_close(gr[k][ok], getattr(want, k)[ok], k)
+    assert_grad_close(gr["sh"][ok], want.sh[ok], "sh")
+    np.testing.assert_array_equal(gr["sd_cnt"][ok], want.sd_cnt[ok])
+    assert_grad_close(gr["sd_acc"][ok], want.sd_acc[ok], "sd_acc")
+
+
+# ----------------------------------------------------------------------------- end to end
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_end_to_end_small(small, recompute):
+    wl, g = small
+    cam = wl.cameras[0].as_dict()
+    f = oracle.forward(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
+    ok_px = f.pixel_flags == 0
+    assert ok_px.mean() > 0.97, ok_px.mean()
+    ctx = ctx_for(wl, recompute_T=recompute)
+    batch = make_batch(wl)
+    proj, bins, img = lobe.forward(ctx, batch)
+    rgb = img.rgb.view(3, 128, 128).cpu().numpy()
+    assert np.abs(rgb - f.image.rgb)[:, ok_px].max() <= IMG_ATOL
+    # sort order: per tile, identical lists once marginal Gaussians are removed
+    marg = (f.proj.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) != 0
+    gids = bins.ids().cpu().numpy()
+    gts = bins.tile_start.cpu().numpy()
+    for t in range(len(f.tile_start) - 1):
+        a = gids[gts[t]:gts[t + 1]]
+        b = f.ids[f.tile_start[t]:f.tile_start[t + 1]]
+        np.testing.assert_array_equal(a[~marg[a]], b[~marg[b]])
+    dL = (np.random.default_rng(5).standard_normal((3, 128, 128)) * ok_px[None]).astype(np.float32)
+    g2d_o, pg = oracle.backward(g, cam, f, dL.astype(np.float64), wl.tile)
+    g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dev(dL).reshape(-1))
+    grads = lobe.project_bwd(ctx, batch, proj, g2d)
+    gr = {k: v.cpu().numpy() for k, v in grads[0].items()}
+    okg = ~marg & ((f.proj.flags & oracle.F_COLOR) == 0) & (f.proj.radius > 0)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert_grad_close(gr[k][okg], getattr(pg, k)[okg], k)
+
+
+def test_batched_equals_plain():
+    rng = np.random.default_rng(21)
+    sets = [scenes.uniform_gaussians(rng, 800, 1.0, 2.0, 6.0), scenes.uniform_gaussians(rng, 500, 1.0, 2.0, 6.0)]
+    cams = [scenes.pinhole(160, 120, 140.0), scenes.pinhole(100, 75, 90.0),
+            scenes.pinhole(128, 128, 128.0, viewmat=scenes.look_at((0.3, 0.2, -0.2), (0, 0, 4.0), up=(0, -1, 0)))]
+    items = [(0, 0, -1), (1, 1, -1), (0, 2, -1), (1, 0, -1)]
+    wl = scenes.Workload("b", sets, cams, [], items, (16, 16))
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    proj, bins, img = lobe.forward(ctx, batch)
+    rgbs = batch.image_views(img.rgb)
+    for i, it in enumerate(items):
+        one = scenes.Workload("o", [sets[it[0]]], [cams[it[1]]], [], [(0, 0, -1)], (16, 16))
+        b1 = make_batch(one)
+        _, _, im1 = lobe.forward(ctx, b1)
+        torch.testing.assert_close(rgbs[i], b1.image_views(im1.rgb)[0], rtol=0, atol=0)
+
+
+def test_visibility_crop_matches_oracle():
+    wl = scenes.small_scene()
+    cams = [wl.cameras[0].as_dict(),
+            dict(wl.cameras[0].as_dict(), viewmat=scenes.look_at((3.0, 0.0, 4.0), (0.0, 0.0, 4.0), up=(0, -1, 0)))]
+    g = oracle.set_dict(wl.sets[0])
+    want = oracle.visibility_crop(g, cams, wl.tile)
+    w2 = scenes.Workload("v", wl.sets, [scenes.Camera(**c) for c in cams], [], [(0, 0, -1), (0, 1, -1)], wl.tile)
+    ctx = ctx_for(w2)
+    batch = make_batch(w2)
+    m = lobe.visibility_crop(ctx, batch)[0].cpu().numpy()
+    flags = np.zeros(g["means"].shape[0], np.int32)
+    for c in cams:
+        flags |= oracle.project(g, c, wl.tile, margins=oracle.MARGINS_E2E).flags
+    ok = (flags & (oracle.F_GUARD | oracle.F_RECT | oracle.F_RADIUS)) == 0
+    np.testing.assert_array_equal(m[ok], want[ok])
+    assert 0 < want.sum() < len(want)
+
+
+def test_crop_mask_culls():
+    wl = scenes.small_scene(n=300)
+    crop = (np.arange(300) % 3 != 0).astype(np.uint8)
+    ctx = ctx_for(wl)
+    batch = make_batch(wl, crop=crop)
+    proj = lobe.project(ctx, batch)
+    r = proj.radius.cpu().numpy()
+    assert np.all(r[crop == 0] == 0)
+    g = oracle.set_dict(wl.sets[0])
+    p = oracle.project(g, wl.cameras[0].as_dict(), wl.tile, crop=crop)
+    np.testing.assert_array_equal(r > 0, p.radius > 0)
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_empty_set_and_all_culled():
+    empty = scenes.uniform_gaussians(np.random.default_rng(0), 0, 1.0, 2.0, 6.0)
+    behind = scenes.uniform_gaussians(np.random.default_rng(1), 200, 1.0, -6.0, -2.0)
+    cam = scenes.pinhole(64, 48, 60.0)
+    for gs in (empty, behind):
+        wl = scenes.Workload("e", [gs], [cam], [], [(0, 0, -1)], (16, 16))
+        ctx = ctx_for(wl, bg=(0.25, 0.5, 0.75))
+        batch = make_batch(wl)
+        proj, bins, img = lobe.forward(ctx, batch)
+        assert bins.count == 0
+        rgb = img.rgb.view(3, 48, 64).cpu()
+        for c, v in enumerate((0.25, 0.5, 0.75)):
+            assert torch.all(rgb[c] == v)
+        assert torch.all(img.T_final == 1.0) and torch.all(img.n_contrib == 0)
+        dL = torch.ones(3 * 48 * 64, device="cuda")
+        g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
+        grads = lobe.project_bwd(ctx, batch, proj, g2d)
+        for v in grads[0].values():
+            assert torch.all(v == 0)
+
+
+def test_ragged_image_matches_oracle():
+    rng = np.random.default_rng(7)
+    g = scenes.uniform_gaussians(rng, 600, 1.0, 2.0, 6.0)
+    cam = scenes.pinhole(100, 75, 90.0, cx=50.0, cy=37.5)
+    wl = scenes.Workload("r", [g], [cam], [], [(0, 0, -1)], (16, 16))
+    gd = oracle.set_dict(g)
+    f = oracle.forward(gd, cam.as_dict(), wl.tile, margins=oracle.MARGINS_E2E)
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    _, _, img = lobe.forward(ctx, batch)
+    rgb = img.rgb.view(3, 75, 100).cpu().numpy()
+    ok = f.pixel_flags == 0
+    assert np.abs(rgb - f.image.rgb)[:, ok].max() <= IMG_ATOL
+
+
+def test_capacity_overflow_is_reported_without_sync():
+    wl = scenes.small_scene()
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    proj = lobe.project(ctx, batch)
+    ctx.reserve(batch.n_entries, 1 << 16)
+    n_tiles, _ = batch.tiles(wl.tile)
+    small_bins = lobe.raster.empty_bins(100, n_tiles)
+    lobe.bin_sort(ctx, batch, proj, small_bins, sync=False)
+    with pytest.raises(lobe._abi.LobeError) as e:
+        ctx.status()
+    assert e.value.code == lobe._abi.ERR_CAPACITY
+    # the bins then describe empty tiles, and the context stays usable
+    assert int(small_bins.tile_start.max().item()) == 0
+    ctx.status()
