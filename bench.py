@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Throughput of the differentiable tile rasterizer: one step = project -> bin/sort ->
+render fwd -> render bwd -> project bwd over one synthetic view (the per-block training
+step's rasterizer pass; the loss gradient dL/dC is computed once before timing).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lobe|reference] [--workload NAME]
+
+Default workload: 200k Gaussians in a 20 m box, one 1600x1066 pinhole view (fx=fy=1200),
+16x16 tiles, SH degree 3, dL/dC of L1 + 0.2 (1 - SSIM) against a render of a perturbed copy.
+Prints ONE JSON line (rank 0). Under torchrun every rank renders its own independent
+replica (a different seeded block): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "fwd+bwd rasterization Mpix/s"
+UNIT = "Mpix/s"
+L2_BYTES = 126 * 2 ** 20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Algorithmic work per unit, counted from the operations the method needs (not the SIMT
+# lanes a kernel happens to burn): see DESIGN.md, "Roofline per stage".
+FLOP_FWD_PAIR = 19    # per (pixel, splat) pair up to the last contributor, FMA = 2 FLOP
+FLOP_BWD_PAIR = 55
+PROJ_BYTES_VISIBLE = 236 + 56   # params in, splat record + radius + tile count out
+PROJ_BYTES_CULLED = 44 + 8      # mean/scale/quat/logit in, radius + count out
+PROJ_BWD_BYTES = 236 + 48 + 236 + 8  # params + 2D grads in, param grads + radius/opacity out
+SORT_BYTES_PAIR = 4 + 4 + 4     # pair written once (tile key), id read once, sorted id written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lobe", choices=["lobe", "reference"])
+    ap.add_argument("--workload", default="medium", choices=["medium", "small", "city", "multi"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--recompute", action="store_true")
+    return ap.parse_args()
+
+
+def build_workload(name, seed):
+    if name == "small":
+        return scenes.small_scene(seed=seed)
+    if name == "medium":
+        return scenes.medium_scene(seed=seed)
+    if name == "city":
+        return scenes.city_block_scene(seed=seed)
+    return scenes.multi_block_scene(seed=seed)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while running (the timed region)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+
+def oracle_sample(wl, win=128, seed=0):
+    """Runs the FP64 oracle's fwd+bwd on a win x win pixel window of the workload's first item
+    (every Gaussian projected, only the window's tiles binned and rendered). Returns
+    (seconds, pixels, gaussians)."""
+    import oracle
+    s, c, b = wl.items[0]
+    g = oracle.set_dict(wl.sets[s])
+    cam = wl.cameras[c].as_dict()
+    W, H = cam["width"], cam["height"]
+    w = min(win, W, H)
+    x0, y0 = (W - w) // 2, (H - w) // 2
+    dL = np.zeros((3, H, W))
+    dL[:, y0:y0 + w, x0:x0 + w] = np.random.default_rng(seed).standard_normal((3, w, w))
+    t0 = time.perf_counter()
+    with oracle.window(x0, y0, x0 + w, y0 + w):
+        f = oracle.forward(g, cam, wl.tile)
+        oracle.backward(g, cam, f, dL, wl.tile, aabb=wl.blocks[b] if b >= 0 and wl.blocks else None)
+    return time.perf_counter() - t0, w * w, g["means"].shape[0]
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    done, t, px, gs = 0, 0.0, 0, 0
+    while t < budget_s and done < 50:
+        dt, p, n = oracle_sample(wl, seed=done)
+        t += dt
+        px += p
+        gs += n
+        done += 1
+    return {"value": px / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} steps of the FP64 C oracle (single thread) on a 128x128 pixel window of the "
+                      f"workload's view: all {gs // done} Gaussians projected, the window's tiles binned, "
+                      f"composited and differentiated; {t:.1f} s total",
+            "gaussians_per_s": gs / t}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = build_workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_sample(wl)
+    times, px = [], 0
+    for k in range(args.steps):
+        dt, p, _ = oracle_sample(wl, seed=k)
+        times.append(dt)
+        px = p
+    tot = sum(times)
+    value = px * args.steps / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "sample": "128x128 pixel window per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "128x128 pixel window of the workload's view per step, FP64 C oracle, "
+                                       "single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2510_01767_b300 as lobe
+    from paper_2510_01767_b300 import _abi
+    from paper_2510_01767_b300.losses import loss_and_grad
+
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    wl = build_workload(args.workload, seed=rank)
+    wl.tile = tile
+    sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
+    batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
+    ctx = lobe.Context(tile=tile, recompute_T=args.recompute)
+
+    # one-time: bins sized from a first pass, dL/dC of the training loss against a target
+    proj, bins, img = lobe.forward(ctx, batch, sync=True)
+    n_isect = bins.count
+    n_tiles, _ = batch.tiles(tile)
+    ctx.reserve(batch.n_entries, int(n_isect * 1.25) + 4096)
+    bins = lobe.raster.empty_bins(int(n_isect * 1.25) + 4096, n_tiles)
+    tgt_sets = [lobe.GaussianSet.from_numpy(scenes.perturbed_copy(s, seed=2 + rank)) for s in wl.sets]
+    tbatch = lobe.Batch(tgt_sets, wl.cameras, wl.items, wl.blocks)
+    _, _, timg = lobe.forward(ctx, tbatch, sync=True)
+    dL = torch.empty_like(img.rgb)
+    for v, t, d in zip(batch.image_views(img.rgb), tbatch.image_views(timg.rgb), batch.image_views(dL)):
+        d.copy_(loss_and_grad(v, t)[1])
+    grad2d = torch.empty((batch.n_entries, 12), dtype=torch.float32, device="cuda")
+    grads = lobe.zero_grads(batch, sd=True)
+    image = lobe.raster.empty_image(batch.n_pixels)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        lobe.project(ctx, batch, proj)
+        if ev:
+            ev[1].record(stream)
+        lobe.bin_sort(ctx, batch, proj, bins, sync=False)
+        if ev:
+            ev[2].record(stream)
+        lobe.render_fwd(ctx, batch, proj, bins, image)
+        if ev:
+            ev[3].record(stream)
+        lobe.render_bwd(ctx, batch, proj, bins, image, dL, grad2d)
+        if ev:
+            ev[4].record(stream)
+        lobe.project_bwd(ctx, batch, proj, grad2d, grads, accumulate=True)
+        if ev:
+            ev[5].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ctx.status()
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    launches0 = _abi.lib().lobe_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(K):
+            flush.zero_()  # inputs of the next step start cold in L2
+            step(evs[k])
+        torch.cuda.synchronize()
+    launches = _abi.lib().lobe_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    ctx.status()
+    stage_ms = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(5)] for k in range(K)])
+    step_ms = stage_ms.sum(axis=1)
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    pixels = batch.n_pixels * K * world
+    gaussians = sum(s.n for s in sets) * K * world
+    value = pixels / total_s / 1e6
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    host_params = [{k: getattr(s, k).detach().cpu().pin_memory() for k in lobe.PARAM_KEYS} for s in sets]
+    host_dL = dL.cpu().pin_memory()
+    host_rgb = torch.empty_like(image.rgb, device="cpu").pin_memory()
+    host_grads = [{k: torch.empty_like(g[k], device="cpu").pin_memory() for k in lobe.PARAM_KEYS} for g in grads]
+    h2d = sum(t.numel() * t.element_size() for d in host_params for t in d.values()) + host_dL.numel() * 4
+    d2h = host_rgb.numel() * 4 + sum(t.numel() * t.element_size() for d in host_grads for t in d.values())
+
+    def e2e_step():
+        for s, hp in zip(sets, host_params):
+            for k in lobe.PARAM_KEYS:
+                getattr(s, k).copy_(hp[k], non_blocking=True)
+        dL.copy_(host_dL, non_blocking=True)
+        lobe.project(ctx, batch, proj)
+        lobe.bin_sort(ctx, batch, proj, bins, sync=False)
+        lobe.render_fwd(ctx, batch, proj, bins, image)
+        lobe.render_bwd(ctx, batch, proj, bins, image, dL, grad2d)
+        lobe.project_bwd(ctx, batch, proj, grad2d, grads, accumulate=False)
+        host_rgb.copy_(image.rgb, non_blocking=True)
+        for g, hg in zip(grads, host_grads):
+            for k in lobe.PARAM_KEYS:
+                hg[k].copy_(g[k], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(K):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = pixels / e2e_s / 1e6
+
+    # ---- roofline of the dominant stage
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    csum = clk.summary()
+    sm_mhz = csum["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    alu_peak_tflops = 2 * 128 * 148 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x SMs x clock, FMA = 2 FLOP
+    torch.cuda.synchronize()
+    nc = int(image.n_contrib.to(torch.int64).sum().item())
+    vis = int((proj.tiles > 0).sum().item())
+    n_entries = batch.n_entries
+    n_isect = int(bins.n_isect.item())
+    mean_ms = stage_ms.mean(axis=0)
+    names = ["project", "bin_sort", "render_fwd", "render_bwd", "project_bwd"]
+    units = {
+        "project": ("hbm", (vis * PROJ_BYTES_VISIBLE + (n_entries - vis) * PROJ_BYTES_CULLED) / 1e9, "GB/s", hbm_peak),
+        "bin_sort": ("hbm", n_isect * SORT_BYTES_PAIR / 1e9, "GB/s", hbm_peak),
+        "render_fwd": ("alu", nc * FLOP_FWD_PAIR / 1e12, "TFLOP/s", alu_peak_tflops),
+        "render_bwd": ("alu", nc * FLOP_BWD_PAIR / 1e12, "TFLOP/s", alu_peak_tflops),
+        "project_bwd": ("hbm", vis * PROJ_BWD_BYTES / 1e9, "GB/s", hbm_peak),
+    }
+    stages = {}
+    for i, n in enumerate(names):
+        bound, work, unit, peak = units[n]
+        ach = work / (mean_ms[i] / 1e3)
+        stages[n] = {"ms": round(float(mean_ms[i]), 4), "bound": bound, "achieved": round(ach, 3), "unit": unit,
+                     "peak": round(peak, 2), "frac": round(ach / peak, 4)}
+    dom = names[int(np.argmax(mean_ms))]
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", f"traffic_{dom}_{wl.name}.json")
+    if os.path.exists(tf):
+        traffic = json.load(open(tf)).get("bytes_per_launch")
+    roof = {"stage": dom, "bound": stages[dom]["bound"], "achieved": stages[dom]["achieved"],
+            "peak": stages[dom]["peak"], "unit": stages[dom]["unit"], "frac": stages[dom]["frac"],
+            "traffic": traffic,
+            "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if stages[dom]["bound"] == "hbm" else
+                            "derived: 2 x 128 FP32 lanes x 148 SMs x median SM clock sampled in the timed region")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(float(step_ms.mean()), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "gaussians": sum(s.n for s in sets), "pixels": batch.n_pixels,
+                       "tile": list(tile), "sh_degree": 3, "intersections": n_isect, "visible": vis,
+                       "bwd_mode": "recompute" if args.recompute else "store",
+                       "l2": "flushed between timed steps (2x126 MB write)",
+                       "dL_dC": "L1+0.2(1-SSIM) vs perturbed-copy render, computed once before timing",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "gaussians_per_s": round(gaussians / total_s, 1),
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": {k: csum[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "roofline": roof,
+            "stages": stages,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,10 @@ typedef struct {
 
 int32_t lobe_abi_version(void);
 
+/* Number of CUDA kernels this library has enqueued since it was loaded (all contexts,
+ * all threads). Kernels replayed from a captured CUDA graph are not counted again. */
+int64_t lobe_kernel_launches(void);
+
 /* Creates a context bound to `stream` (a cudaStream_t, NULL = legacy default stream) on the
  * current device. Allocates only a small device status word. */
 lobe_status lobe_ctx_create(lobe_ctx **out, void *stream, const lobe_config *cfg);

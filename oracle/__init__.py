@@ -330,6 +330,21 @@ def sh_basis(dirs, degree=3):
     return Y, dY
 
 
+class window:
+    """Context manager restricting bin/render/render_bwd to the pixel window [x0,x1) x [y0,y1)
+    (a bounded sample of a large image for timing; per-pixel work is unchanged)."""
+
+    def __init__(self, x0, y0, x1, y1):
+        self.w = (int(x0), int(y0), int(x1), int(y1))
+
+    def __enter__(self):
+        lib().orc_set_window(*self.w)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_window(0, 0, 1 << 30, 1 << 30)
+
+
 def depth_key(z: float) -> int:
     return int(lib().orc_depth_key(float(z)))
 

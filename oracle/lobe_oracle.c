@@ -409,6 +409,23 @@ int orc_project(int64_t n, const double *means, const double *log_scales, const 
     return 0;
 }
 
+/* ------------------------------------------------------------------ sampling window
+ * A pixel window [x0,x1) x [y0,y1) that bin/render/render_bwd restrict themselves to, so a
+ * timing run can process a bounded sample of a large image with unchanged per-pixel work
+ * (pairs of tiles outside the window are not emitted, pixels outside are not touched).
+ * Default: no restriction. It changes no arithmetic. */
+static int g_win[4] = {0, 0, 1 << 30, 1 << 30};
+
+void orc_set_window(int x0, int y0, int x1, int y1)
+{
+    g_win[0] = x0; g_win[1] = y0; g_win[2] = x1; g_win[3] = y1;
+}
+
+static int tile_in_window(int tx, int ty, int tw, int th)
+{
+    return (tx + 1) * tw > g_win[0] && tx * tw < g_win[2] && (ty + 1) * th > g_win[1] && ty * th < g_win[3];
+}
+
 /* ------------------------------------------------------------------ public: bin + sort */
 
 typedef struct {
@@ -437,7 +454,8 @@ int64_t orc_bin(int64_t n, const double *mean2d, const int32_t *radius, const do
         if (radius[g] <= 0) continue;
         int r[4];
         tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, r);
-        total += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
+        for (int ty = r[1]; ty < r[3]; ++ty)
+            for (int tx = r[0]; tx < r[2]; ++tx) total += tile_in_window(tx, ty, tw, th);
     }
     if (!ids) return total;
     pair_t *pairs = malloc(sizeof(pair_t) * (total ? total : 1));
@@ -448,6 +466,7 @@ int64_t orc_bin(int64_t n, const double *mean2d, const int32_t *radius, const do
         tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, r);
         for (int ty = r[1]; ty < r[3]; ++ty)
             for (int tx = r[0]; tx < r[2]; ++tx) {
+                if (!tile_in_window(tx, ty, tw, th)) continue;
                 pairs[k].tile = (uint32_t)(ty * gx + tx);
                 pairs[k].dbits = f32_bits(depth[g]);
                 pairs[k].g = (int32_t)g;
@@ -559,8 +578,8 @@ int orc_render_fwd(int W, int H, int tw, int th, const double *mean2d, const dou
 {
     int gx = (W + tw - 1) / tw;
     int64_t HW = (int64_t)W * H;
-    for (int py = 0; py < H; ++py)
-        for (int px = 0; px < W; ++px) {
+    for (int py = g_win[1]; py < H && py < g_win[3]; ++py)
+        for (int px = g_win[0]; px < W && px < g_win[2]; ++px) {
             int t = (py / th) * gx + px / tw;
             double C[3], T, ws;
             int32_t nc;
@@ -662,8 +681,8 @@ int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const dou
     for (int t = 0; t < gx * ((H + th - 1) / th); ++t)
         if (tile_start[t + 1] - tile_start[t] > maxlen) maxlen = tile_start[t + 1] - tile_start[t];
     contrib_t *rec = malloc(sizeof(contrib_t) * (maxlen ? maxlen : 1));
-    for (int py = 0; py < H; ++py)
-        for (int px = 0; px < W; ++px) {
+    for (int py = g_win[1]; py < H && py < g_win[3]; ++py)
+        for (int px = g_win[0]; px < W && px < g_win[2]; ++px) {
             int64_t p = (int64_t)py * W + px;
             double gC[3] = {dL_drgb[p], dL_drgb[HW + p], dL_drgb[2 * HW + p]};
             if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;

@@ -74,6 +74,7 @@ class Grads(ctypes.Structure):
 # name -> (restype, argtypes); the exported symbols of liblobe.so (checked by the tests)
 SIGNATURES = {
     "lobe_abi_version": (ctypes.c_int32, []),
+    "lobe_kernel_launches": (ctypes.c_int64, []),
     "lobe_batch_sizes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Batch), ctypes.POINTER(ctypes.c_int64)]),
     "lobe_ctx_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, ctypes.POINTER(Config)]),
     "lobe_ctx_destroy": (ctypes.c_int, [vp]),

@@ -11,6 +11,12 @@
 #include "lobe_internal.cuh"
 
 
+#include <atomic>
+
+static std::atomic<long long> g_launches{0};
+
+void lobe::count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 using namespace lobe;
 
 struct lobe_ctx {
@@ -159,6 +165,8 @@ extern "C" {
 
 int32_t lobe_abi_version(void) { return LOBE_ABI_VERSION; }
 
+int64_t lobe_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 lobe_status lobe_batch_sizes(const lobe_config *cfg, const lobe_batch *batch, int64_t out[3])
 {
     if (!out) return LOBE_ERR_ARG;
@@ -296,7 +304,8 @@ struct ParamHolder {
 lobe_status lobe_project(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *out)
 {
     BUILD_PARAMS(H);
-    if (!out || !out->splat || !out->radius || !out->tiles_touched) return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
+    if (!out || (H.p->n_entries > 0 && (!out->splat || !out->radius || !out->tiles_touched)))
+        return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
     if (!aligned16(out->splat)) return fail(ctx, LOBE_ERR_ARG, "splat not 16-byte aligned");
     CUDA_TRY(launch_project_fwd(*H.p, out->splat, out->radius, out->tiles_touched, ctx->stream), "project");
     return LOBE_OK;
@@ -307,7 +316,8 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
 {
     BUILD_PARAMS(H);
     const BatchParams &P = *H.p;
-    if (!proj || !proj->splat || !proj->radius || !proj->tiles_touched) return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
+    if (!proj || (P.n_entries > 0 && (!proj->splat || !proj->radius || !proj->tiles_touched)))
+        return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
     if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0)
         return fail(ctx, LOBE_ERR_ARG, "bins missing");
     if (P.n_entries > ctx->max_entries || !ctx->entry_mem) {
@@ -354,7 +364,8 @@ lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
                             const lobe_image *image)
 {
     BUILD_PARAMS(H);
-    if (!proj || !proj->splat || !bins || !bins->gauss_ids || !bins->tile_start) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    if (!proj || (H.p->n_entries > 0 && !proj->splat) || !bins || !bins->gauss_ids || !bins->tile_start)
+        return fail(ctx, LOBE_ERR_ARG, "inputs missing");
     if (!image || !image->rgb || !image->T_final || !image->n_contrib) return fail(ctx, LOBE_ERR_ARG, "image buffers missing");
     CUDA_TRY(launch_render_fwd(*H.p, proj->splat, bins->tile_start, bins->gauss_ids, image->rgb, image->T_final,
                                image->n_contrib, ctx->stream),
@@ -367,8 +378,11 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
 {
     BUILD_PARAMS(H);
     const bool rec = ctx->cfg.recompute_T != 0;
-    if (!proj || !proj->splat || !bins || !bins->gauss_ids || !bins->tile_start) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
-    if (!dL_drgb || !grad2d || !aligned16(grad2d)) return fail(ctx, LOBE_ERR_ARG, "dL_drgb/grad2d missing or misaligned");
+    const bool has_e = H.p->n_entries > 0;
+    if (!proj || (has_e && !proj->splat) || !bins || !bins->gauss_ids || !bins->tile_start)
+        return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    if (!dL_drgb || (has_e && (!grad2d || !aligned16(grad2d))))
+        return fail(ctx, LOBE_ERR_ARG, "dL_drgb/grad2d missing or misaligned");
     if (!rec && (!image || !image->rgb || !image->n_contrib))
         return fail(ctx, LOBE_ERR_ARG, "saved forward state missing (recompute_T = 0)");
     CUDA_TRY(launch_render_bwd(*H.p, rec, proj->splat, bins->tile_start, bins->gauss_ids, rec ? nullptr : image->rgb,
@@ -382,7 +396,8 @@ lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_
 {
     BUILD_PARAMS(H);
     BatchParams &P = *H.p;
-    if (!proj || !proj->splat || !proj->radius || !grad2d || !grads) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    if (!grads || (P.n_entries > 0 && (!proj || !proj->splat || !proj->radius || !grad2d)))
+        return fail(ctx, LOBE_ERR_ARG, "inputs missing");
     for (int s = 0; s < P.n_sets; ++s) {
         const lobe_grads &g = grads[s];
         if (P.set[s].n > 0 && (!g.means || !g.log_scales || !g.quats || !g.opacity_logits || !g.sh))

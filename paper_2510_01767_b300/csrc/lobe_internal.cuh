@@ -195,6 +195,9 @@ struct BinScratch {
     int *status;
 };
 
+// Counts kernel launches made by this library (process-wide, all contexts).
+void count_launch(int n = 1);
+
 cudaError_t launch_project_fwd(const BatchParams &, float *, int *, int *, cudaStream_t);
 cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
 cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, cudaStream_t);

@@ -453,6 +453,7 @@ cudaError_t launch_project_fwd(const BatchParams &P, float *splat, int *radius, 
 {
     if (P.n_gauss == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
+    count_launch();
     k_project_fwd<<<blocks, 256, 0, st>>>(P, reinterpret_cast<float4 *>(splat), radius, tiles);
     return cudaGetLastError();
 }
@@ -461,6 +462,7 @@ cudaError_t launch_visibility(const BatchParams &P, cudaStream_t st)
 {
     if (P.n_gauss == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
+    count_launch();
     k_visibility<<<blocks, 256, 0, st>>>(P);
     return cudaGetLastError();
 }
@@ -470,6 +472,7 @@ cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const i
 {
     if (P.n_gauss == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n_gauss + 127) / 128);
+    count_launch();
     k_project_bwd<<<blocks, 128, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
                                           reinterpret_cast<const float4 *>(grad2d), accumulate);
     return cudaGetLastError();

@@ -240,6 +240,7 @@ template <int TW, int TH>
 static cudaError_t fwd_t(const BatchParams &P, const float *splat, const int *ts, const int *ids, float *rgb, float *T,
                          int *nc, cudaStream_t st)
 {
+    count_launch();
     k_render_fwd<TW, TH><<<P.n_tiles, TW * TH, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts, ids, rgb, T, nc);
     return cudaGetLastError();
 }
@@ -248,6 +249,7 @@ template <int TW, int TH>
 static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *splat, const int *ts, const int *ids,
                          const float *rgb, const int *nc, const float *dL, float *g2d, cudaStream_t st)
 {
+    count_launch();
     if (recompute)
         k_render_bwd<TW, TH, true><<<P.n_tiles, TW * TH, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts, ids,
                                                                    rgb, nc, dL, g2d);
@@ -270,7 +272,8 @@ cudaError_t launch_render_fwd(const BatchParams &P, const float *splat, const in
 cudaError_t launch_render_bwd(const BatchParams &P, bool recompute, const float *splat, const int *ts, const int *ids,
                               const float *rgb, const int *nc, const float *dL, float *g2d, cudaStream_t st)
 {
-    cudaError_t err = cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)P.n_entries, st);
+    cudaError_t err = P.n_entries > 0 ? cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)P.n_entries, st)
+                                      : cudaSuccess;
     if (err != cudaSuccess || P.n_tiles == 0) return err;
     if (P.tw == 16 && P.th == 16) return bwd_t<16, 16>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
     if (P.tw == 8 && P.th == 8) return bwd_t<8, 8>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);

@@ -153,6 +153,7 @@ static void scan(L load, const uint32_t *n_dev, long long n_max, uint32_t *out, 
     int nb = (int)((n_max + 4 * SCAN_THREADS - 1) / (4 * SCAN_THREADS));
     nb = nb < 1 ? 1 : (nb > SCAN_MAX_BLOCKS ? SCAN_MAX_BLOCKS : nb);
     long long n_host = n_dev ? 0 : n_max;
+    count_launch(3);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, block_sums);
     k_scan_top<<<1, 1024, 0, st>>>(block_sums, nb, total32, total64, n_use, capacity, status);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, block_sums, out);
@@ -293,6 +294,7 @@ static void radix_sort(const uint32_t *n_dev, long long n_max, int nbits, uint32
             kd = kf;
             vd = vf;
         }
+        count_launch(2);
         k_radix_count<<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift, bits, s.counts);
         scan(LoadPlain{s.counts}, nullptr, ncounts, s.counts, s.block_sums, nullptr, nullptr, nullptr, -1, nullptr, st);
         k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift, bits, s.counts);
@@ -375,6 +377,7 @@ cudaError_t bin_sort_count(const BatchParams &P, const float *splat, const int *
     uint32_t *V = b.scalars, *n_use = b.scalars + 1;
     // 1. visible entries -> compact (depth key, entry)
     scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, b.sort.block_sums, V, nullptr, nullptr, -1, nullptr, st);
+    if (n > 0) count_launch();
     if (n > 0) k_compact<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tiles, splat, b.vis_pos, b.dkA, b.dvA);
     // 2. sort visible splats by depth (32 key bits); result (keys unused) ends in dvB
     radix_sort(V, n, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA /*final keys*/, b.vis_pos /*final order*/, b.sort, st);
@@ -389,6 +392,7 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
 {
     const long long n = P.n_entries;
     uint32_t *V = b.scalars, *n_use = b.scalars + 1;
+    if (n > 0) count_launch();
     if (n > 0)
         k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, b.offs, splat, radius, tiles, n_use,
                                                                  b.tkA, b.tvA);
@@ -400,6 +404,7 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
     radix_sort(n_use, isect_max, nbits, b.tkA, b.tvA, b.tkB, b.tvB, kfinal, reinterpret_cast<uint32_t *>(gauss_ids),
                b.sort, st);
     const long long nr = isect_max + 1;
+    count_launch();
     k_tile_ranges<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(kfinal, n_use, isect_max, P.n_tiles, tile_start);
     return cudaGetLastError();
 }

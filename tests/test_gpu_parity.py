@@ -264,8 +264,9 @@ def test_batched_equals_plain():
 
 def test_visibility_crop_matches_oracle():
     wl = scenes.small_scene()
-    cams = [wl.cameras[0].as_dict(),
-            dict(wl.cameras[0].as_dict(), viewmat=scenes.look_at((3.0, 0.0, 4.0), (0.0, 0.0, 4.0), up=(0, -1, 0)))]
+    # two oblique views that each see only part of the scene
+    cams = [dict(wl.cameras[0].as_dict(), viewmat=scenes.look_at((-0.5, 0.0, 4.0), (5.0, 0.0, 4.0))),
+            dict(wl.cameras[0].as_dict(), viewmat=scenes.look_at((0.0, -0.5, 4.0), (0.0, 5.0, 4.0)))]
     g = oracle.set_dict(wl.sets[0])
     want = oracle.visibility_crop(g, cams, wl.tile)
     w2 = scenes.Workload("v", wl.sets, [scenes.Camera(**c) for c in cams], [], [(0, 0, -1), (0, 1, -1)], wl.tile)
