@@ -84,7 +84,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -95,6 +95,14 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first_sample(self, timeout=5.0):
+        """nvidia-smi takes a moment to start: wait for its first line, then keep only the
+        samples taken from now on (the timed region)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+        self.lines.clear()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -219,7 +227,7 @@ def main():
     proj, bins, img = lobe.forward(ctx, batch, sync=True)
     n_isect = bins.count
     n_tiles, _ = batch.tiles(tile)
-    ctx.reserve(batch.n_entries, int(n_isect * 1.25) + 4096)
+    ctx.reserve(batch.n_entries, int(n_isect * 1.25) + 4096, batch.tiles(tile)[0])
     bins = lobe.raster.empty_bins(int(n_isect * 1.25) + 4096, n_tiles)
     tgt_sets = [lobe.GaussianSet.from_numpy(scenes.perturbed_copy(s, seed=2 + rank)) for s in wl.sets]
     tbatch = lobe.Batch(tgt_sets, wl.cameras, wl.items, wl.blocks)
@@ -263,11 +271,12 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(K):
-            flush.zero_()  # inputs of the next step start cold in L2
-            step(evs[k])
-        torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
+    clk.wait_first_sample()
+    for k in range(K):
+        flush.zero_()  # inputs of the next step start cold in L2
+        step(evs[k])
+    torch.cuda.synchronize()
     launches = _abi.lib().lobe_kernel_launches() - launches0
     if world > 1:
         dist.barrier()
@@ -323,6 +332,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = pixels / e2e_s / 1e6
+    clk.__exit__(None, None, None)  # sampled over both timed regions
 
     # ---- roofline of the dominant stage
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}

@@ -183,9 +183,12 @@ lobe_status lobe_ctx_set_stream(lobe_ctx *ctx, void *stream);
 lobe_status lobe_ctx_set_config(lobe_ctx *ctx, const lobe_config *cfg);
 /* Message of the last error on this context (static storage owned by the context). */
 const char *lobe_last_error(const lobe_ctx *ctx);
-/* Sizes the context-owned sort scratch for up to max_entries projected entries and
- * max_isect pairs (grows only; never called implicitly inside a captured region). */
-lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect);
+/* Sizes the context-owned binning scratch for up to max_entries projected entries,
+ * max_isect (splat, tile) pairs and max_tiles tiles per batch (grows only). Calls of
+ * lobe_bin_sort without a host count pointer never allocate and need this first; those with
+ * one grow the scratch themselves. Scratch: 24 B per entry + 16 B per pair + 4 B per tile
+ * + about 1.2 MB. */
+lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect, int64_t max_tiles);
 /* Synchronises the stream, returns and clears the latched device status. */
 lobe_status lobe_get_status(lobe_ctx *ctx);
 

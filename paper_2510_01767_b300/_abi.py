@@ -81,7 +81,7 @@ SIGNATURES = {
     "lobe_ctx_set_stream": (ctypes.c_int, [vp, vp]),
     "lobe_ctx_set_config": (ctypes.c_int, [vp, ctypes.POINTER(Config)]),
     "lobe_last_error": (ctypes.c_char_p, [vp]),
-    "lobe_ctx_reserve": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64]),
+    "lobe_ctx_reserve": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]),
     "lobe_get_status": (ctypes.c_int, [vp]),
     "lobe_project": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected)]),
     "lobe_bin_sort": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), ctypes.POINTER(Bins),

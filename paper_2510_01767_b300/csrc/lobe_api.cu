@@ -24,9 +24,8 @@ struct lobe_ctx {
     lobe_config cfg{};
     int device = 0;
     int *status = nullptr;
-    void *entry_mem = nullptr;
-    void *isect_mem = nullptr;
-    long long max_entries = 0, max_isect = 0;
+    void *entry_mem = nullptr, *pair_mem = nullptr, *super_mem = nullptr;
+    long long max_entries = 0, max_pairs = 0, max_super = 0;
     BinScratch bins{};
     char err[512] = {0};
 };
@@ -112,7 +111,8 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
             if (b->items[i].set == s) P.set_items[k++] = i;
         P.set[s].item_count = k - P.set[s].item_begin;
     }
-    long long eoff = 0, poff = 0, toff = 0;
+    long long eoff = 0, poff = 0, toff = 0, soff = 0;
+    P.S = super_edge(cfg.tile_w);
     for (int i = 0; i < b->n_items; ++i) {
         const lobe_item &it = b->items[i];
         if (it.set < 0 || it.set >= b->n_sets) return fail(ctx, LOBE_ERR_ARG, "item %d: set %d out of range", i, it.set);
@@ -146,6 +146,10 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
         I.gx = (c.width + cfg.tile_w - 1) / cfg.tile_w;
         I.gy = (c.height + cfg.tile_h - 1) / cfg.tile_h;
         I.tile_off = (int)toff;
+        I.sgx = (I.gx + P.S - 1) / P.S;
+        I.sgy = (I.gy + P.S - 1) / P.S;
+        I.super_off = (int)soff;
+        soff += (long long)I.sgx * I.sgy;
         I.set = it.set;
         I.entry_off = eoff;
         I.pix_off = poff;
@@ -158,6 +162,7 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
     P.n_entries = eoff;
     P.n_pixels = poff;
     P.n_tiles = (int)toff;
+    P.n_super = (int)soff;
     return LOBE_OK;
 }
 
@@ -211,7 +216,8 @@ lobe_status lobe_ctx_destroy(lobe_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     cudaFree(ctx->entry_mem);
-    cudaFree(ctx->isect_mem);
+    cudaFree(ctx->pair_mem);
+    cudaFree(ctx->super_mem);
     cudaFree(ctx->status);
     delete ctx;
     return LOBE_OK;
@@ -235,42 +241,49 @@ lobe_status lobe_ctx_set_config(lobe_ctx *ctx, const lobe_config *cfg)
 
 const char *lobe_last_error(const lobe_ctx *ctx) { return ctx ? ctx->err : "no context"; }
 
+static lobe_status grow_region(lobe_ctx *ctx, void *&mem, long long &have, long long need, long long floor_n,
+                               size_t (*bytes)(long long), const char *what)
+{
+    if (need <= have && mem) return LOBE_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(mem);
+    mem = nullptr;
+    have = 0;
+    long long n = need < floor_n ? floor_n : need;
+    cudaError_t e = cudaMalloc(&mem, bytes(n));
+    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "%s scratch (%lld): %s", what, n, cudaGetErrorString(e));
+    have = n;
+    return LOBE_OK;
+}
+
 static lobe_status grow_entries(lobe_ctx *ctx, long long need)
 {
-    if (need <= ctx->max_entries && ctx->entry_mem) return LOBE_OK;
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->entry_mem);
-    ctx->entry_mem = nullptr;
-    ctx->max_entries = 0;
-    long long n = need < 1024 ? 1024 : need;
-    cudaError_t e = cudaMalloc(&ctx->entry_mem, entry_scratch_bytes(n));
-    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "entry scratch (%lld entries): %s", n, cudaGetErrorString(e));
-    entry_scratch_carve(ctx->entry_mem, n, ctx->status, ctx->bins);
-    ctx->max_entries = n;
-    return LOBE_OK;
+    lobe_status s = grow_region(ctx, ctx->entry_mem, ctx->max_entries, need, 1024, entry_scratch_bytes, "entry");
+    if (s == LOBE_OK) entry_scratch_carve(ctx->entry_mem, ctx->max_entries, ctx->status, ctx->bins);
+    return s;
 }
 
-static lobe_status grow_isect(lobe_ctx *ctx, long long need)
+static lobe_status grow_pairs(lobe_ctx *ctx, long long need)
 {
-    if (need <= ctx->max_isect && ctx->isect_mem) return LOBE_OK;
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->isect_mem);
-    ctx->isect_mem = nullptr;
-    ctx->max_isect = 0;
-    long long n = need < 4096 ? 4096 : need;
-    cudaError_t e = cudaMalloc(&ctx->isect_mem, isect_scratch_bytes(n));
-    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "pair scratch (%lld pairs): %s", n, cudaGetErrorString(e));
-    isect_scratch_carve(ctx->isect_mem, n, ctx->bins);
-    ctx->max_isect = n;
-    return LOBE_OK;
+    lobe_status s = grow_region(ctx, ctx->pair_mem, ctx->max_pairs, need, 4096, pair_scratch_bytes, "pair");
+    if (s == LOBE_OK) pair_scratch_carve(ctx->pair_mem, ctx->max_pairs, ctx->bins);
+    return s;
 }
 
-lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect)
+static lobe_status grow_super(lobe_ctx *ctx, long long need)
 {
-    if (!ctx || max_entries < 0 || max_isect < 0) return fail(ctx, LOBE_ERR_ARG, "bad reserve arguments");
+    lobe_status s = grow_region(ctx, ctx->super_mem, ctx->max_super, need, 1024, super_scratch_bytes, "super-tile");
+    if (s == LOBE_OK) super_scratch_carve(ctx->super_mem, ctx->bins);
+    return s;
+}
+
+lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect, int64_t max_tiles)
+{
+    if (!ctx || max_entries < 0 || max_isect < 0 || max_tiles < 0) return fail(ctx, LOBE_ERR_ARG, "bad reserve arguments");
     lobe_status s = grow_entries(ctx, max_entries);
-    if (s != LOBE_OK) return s;
-    return grow_isect(ctx, max_isect);
+    if (s == LOBE_OK) s = grow_pairs(ctx, max_isect);
+    if (s == LOBE_OK) s = grow_super(ctx, max_tiles);
+    return s;
 }
 
 lobe_status lobe_get_status(lobe_ctx *ctx)
@@ -316,46 +329,62 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
 {
     BUILD_PARAMS(H);
     const BatchParams &P = *H.p;
+    const bool sync = n_isect_host != nullptr;
     if (!proj || (P.n_entries > 0 && (!proj->splat || !proj->radius || !proj->tiles_touched)))
         return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
     if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0)
         return fail(ctx, LOBE_ERR_ARG, "bins missing");
-    if (P.n_entries > ctx->max_entries || !ctx->entry_mem) {
-        if (!n_isect_host)
-            return fail(ctx, LOBE_ERR_STATE, "scratch holds %lld entries, batch needs %lld: call lobe_ctx_reserve",
-                        ctx->max_entries, P.n_entries);
+    if (P.n_entries > ctx->max_entries || !ctx->entry_mem || P.n_super > ctx->max_super || !ctx->super_mem ||
+        !ctx->pair_mem) {
+        if (!sync)
+            return fail(ctx, LOBE_ERR_STATE,
+                        "scratch holds %lld entries / %lld tiles, batch needs %lld / %d: call lobe_ctx_reserve",
+                        ctx->max_entries, ctx->max_super, P.n_entries, P.n_tiles);
         lobe_status s = grow_entries(ctx, P.n_entries);
+        if (s == LOBE_OK) s = grow_super(ctx, P.n_super);
+        if (s == LOBE_OK) s = grow_pairs(ctx, 4096);
         if (s != LOBE_OK) return s;
     }
-    if (!ctx->isect_mem) {
-        if (!n_isect_host) return fail(ctx, LOBE_ERR_STATE, "pair scratch not reserved: call lobe_ctx_reserve");
-        lobe_status s = grow_isect(ctx, 4096);
-        if (s != LOBE_OK) return s;
-    }
+    long long *n_isect = reinterpret_cast<long long *>(bins->n_isect);
     long long cap = bins->capacity;
-    if (!n_isect_host && cap > ctx->max_isect) cap = ctx->max_isect;
-    CUDA_TRY(bin_sort_count(P, proj->splat, proj->tiles_touched, ctx->bins, reinterpret_cast<long long *>(bins->n_isect),
-                            cap, ctx->stream),
-             "bin count");
-    long long isect_max = cap;
-    if (n_isect_host) {
+    if (!sync && cap > ctx->max_pairs) cap = ctx->max_pairs;
+    if (sync) {
+        // size the super-tile pair scratch from the exact count before emitting pairs
+        long long n_sp = 0;
+        CUDA_TRY(bin_super_count(P, proj->splat, proj->radius, proj->tiles_touched, ctx->bins, -1, ctx->stream),
+                 "bin count");
+        CUDA_TRY(cudaMemcpyAsync(&n_sp, ctx->bins.scalars + 4, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream),
+                 "pair count read");
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream), "pair count sync");
+        n_sp &= 0xffffffffLL;
+        if (n_sp > ctx->max_pairs) {
+            lobe_status s = grow_pairs(ctx, n_sp + n_sp / 4);
+            if (s != LOBE_OK) return s;
+        }
+    } else {
+        CUDA_TRY(bin_super_count(P, proj->splat, proj->radius, proj->tiles_touched, ctx->bins, ctx->max_pairs,
+                                 ctx->stream),
+                 "bin count");
+    }
+    CUDA_TRY(bin_tile_count(P, proj->splat, proj->radius, ctx->bins, ctx->max_pairs, n_isect, bins->tile_start, cap,
+                            ctx->stream),
+             "tile count");
+    if (sync) {
         long long total = 0;
-        CUDA_TRY(cudaMemcpyAsync(&total, bins->n_isect, sizeof total, cudaMemcpyDeviceToHost, ctx->stream), "n_isect read");
+        CUDA_TRY(cudaMemcpyAsync(&total, n_isect, sizeof total, cudaMemcpyDeviceToHost, ctx->stream), "n_isect read");
         CUDA_TRY(cudaStreamSynchronize(ctx->stream), "n_isect sync");
         *n_isect_host = total;
         if (total > bins->capacity) {
             // the device latched the overflow too; the caller is told synchronously instead
             CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status clear");
+            CUDA_TRY(bin_sort_emit(P, proj->splat, proj->radius, ctx->bins, n_isect, bins->gauss_ids, bins->tile_start,
+                                   ctx->stream),
+                     "bin emit");
             return fail(ctx, LOBE_ERR_CAPACITY, "%lld pairs exceed capacity %lld", total, (long long)bins->capacity);
         }
-        if (total > ctx->max_isect) {
-            lobe_status s = grow_isect(ctx, total + total / 4);
-            if (s != LOBE_OK) return s;
-        }
-        isect_max = total;
     }
-    CUDA_TRY(bin_sort_emit(P, proj->splat, proj->radius, proj->tiles_touched, ctx->bins, isect_max, bins->gauss_ids,
-                           bins->tile_start, ctx->stream),
+    CUDA_TRY(bin_sort_emit(P, proj->splat, proj->radius, ctx->bins, n_isect, bins->gauss_ids, bins->tile_start,
+                           ctx->stream),
              "bin emit");
     return LOBE_OK;
 }

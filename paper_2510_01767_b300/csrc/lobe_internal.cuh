@@ -39,6 +39,8 @@ struct ItemParams {
     int W, H;
     int gx, gy;           // tiles per row / column
     int tile_off;         // first global tile id
+    int sgx, sgy;         // super-tiles per row / column (super-tile = S x S tiles)
+    int super_off;        // first global super-tile id
     int set;
     long long entry_off;  // first projected entry
     long long pix_off;    // first pixel
@@ -52,11 +54,26 @@ struct BatchParams {
     long long n_gauss;    // sum of set sizes
     long long n_entries;  // sum over items of the set size
     int n_tiles;
+    int n_super;          // super-tiles over all items
+    int S;                // super-tile edge in tiles
     long long n_pixels;
     int tw, th;
     int sh_degree;
     float bg[3];
 };
+
+// Super-tile edge (in tiles) of the two-level binning: 64 px for 8x8 and 16x16 tiles.
+__host__ __device__ inline int super_edge(int tw) { return tw == 8 ? 8 : 4; }
+
+__device__ __forceinline__ int item_of_super(const BatchParams &P, int s)
+{
+    int lo = 0, hi = P.n_items - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.item[mid].super_off <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // ------------------------------------------------------------------ device status
 
@@ -97,16 +114,22 @@ __device__ __forceinline__ int set_of_gauss(const BatchParams &P, long long t)
 }
 
 // Tile rectangle of a splat: [floor((u-r)/tw), ceil((u+r)/tw)) x [floor((v-r)/th), ceil((v+r)/th))
-// clamped to the grid. Evaluated in double so the result is exact for float u,v and
-// integer r (tw, th are powers of two): every kernel that needs it gets the same answer.
+// clamped to the grid, evaluated exactly in integers: for integer r and t > 0,
+// floor((u-r)/t) = floor((floor(u)-r)/t) and ceil((u+r)/t) = ceil((ceil(u)+r)/t); t is a
+// power of two, so the divisions are arithmetic shifts. Every kernel that needs the
+// rectangle gets the same answer, equal to the real-number definition.
+__device__ __forceinline__ int floor_div_pow2(int a, int t) { return a >> (31 - __clz(t)); }
+__device__ __forceinline__ int ceil_div_pow2(int a, int t) { return -((-a) >> (31 - __clz(t))); }
+
 __device__ __forceinline__ void tile_rect(float u, float v, int r, int tw, int th, int gx, int gy,
                                           int &x0, int &y0, int &x1, int &y1)
 {
-    double du = (double)u, dv = (double)v, dr = (double)r;
-    x0 = (int)fmin(fmax(floor((du - dr) / tw), 0.0), (double)gx);
-    y0 = (int)fmin(fmax(floor((dv - dr) / th), 0.0), (double)gy);
-    x1 = (int)fmin(fmax(ceil((du + dr) / tw), 0.0), (double)gx);
-    y1 = (int)fmin(fmax(ceil((dv + dr) / th), 0.0), (double)gy);
+    // |u|, |v| are bounded by the 1.3x field-of-view guard, far inside the int range
+    const int fu = (int)floorf(u), cu = (int)ceilf(u), fv = (int)floorf(v), cv = (int)ceilf(v);
+    x0 = min(max(floor_div_pow2(fu - r, tw), 0), gx);
+    y0 = min(max(floor_div_pow2(fv - r, th), 0), gy);
+    x1 = min(max(ceil_div_pow2(cu + r, tw), 0), gx);
+    y1 = min(max(ceil_div_pow2(cv + r, th), 0), gy);
 }
 
 // ------------------------------------------------------------------ PTX helpers
@@ -180,18 +203,18 @@ __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn
 
 // ------------------------------------------------------------------ scratch and launchers
 
-struct SortScratch {
-    uint32_t *counts;      // radix digit counts per warp segment
-    uint32_t *block_sums;  // scan block totals
-};
-
-// Context-owned scratch of the binning stage. The "entry" part scales with the projected
-// entries, the "isect" part with the (splat, tile) pairs; they grow independently.
+// Scratch of the binning stage (context-owned, or carved from any device buffer). The
+// "entry" part scales with the projected entries, the "pair" part with the super-tile pairs
+// (at most the (splat, tile) pairs), the "super" part with the super-tiles; each can grow
+// independently.
 struct BinScratch {
     uint32_t *vis_pos, *dkA, *dvA, *dkB, *dvB, *offs;  // [max_entries]
-    uint32_t *tkA, *tvA, *tkB, *tvB;                   // [max_isect]
-    uint32_t *scalars;                                 // [0] visible count, [1] usable pair count
-    SortScratch sort;
+    uint32_t *counts;                                  // radix digit counts per block
+    uint32_t *block_sums;                              // scan block totals
+    uint32_t *scalars;  // [0] visible splats, [1] usable super pairs, [2] usable pairs
+    uint32_t *skA, *svA, *skB, *svB;                   // [max_pairs]
+    uint32_t *sp_ids;                                  // sorted super pairs (one of svA/svB)
+    uint32_t *super_start;                             // [max_super + 1]
     int *status;
 };
 
@@ -205,13 +228,18 @@ cudaError_t launch_render_fwd(const BatchParams &, const float *, const int *, c
                               cudaStream_t);
 cudaError_t launch_render_bwd(const BatchParams &, bool, const float *, const int *, const int *, const float *,
                               const int *, const float *, float *, cudaStream_t);
-cudaError_t bin_sort_count(const BatchParams &, const float *, const int *, BinScratch &, long long *, long long,
-                           cudaStream_t);
-cudaError_t bin_sort_emit(const BatchParams &, const float *, const int *, const int *, BinScratch &, long long, int *,
-                          int *, cudaStream_t);
+cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int *radius, const int *tiles,
+                            BinScratch &b, long long pair_capacity, cudaStream_t st);
+cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *radius, BinScratch &b,
+                           long long pair_capacity, long long *n_isect_dev, int *tile_start, long long isect_capacity,
+                           cudaStream_t st);
+cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *radius, BinScratch &b,
+                          const long long *n_isect_dev, int *gauss_ids, int *tile_start, cudaStream_t st);
 size_t entry_scratch_bytes(long long max_entries);
-size_t isect_scratch_bytes(long long max_isect);
+size_t pair_scratch_bytes(long long max_pairs);
+size_t super_scratch_bytes(long long max_super);
 void entry_scratch_carve(void *mem, long long max_entries, int *status, BinScratch &b);
-void isect_scratch_carve(void *mem, long long max_isect, BinScratch &b);
+void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b);
+void super_scratch_carve(void *mem, BinScratch &b);
 
 }  // namespace lobe

@@ -175,8 +175,8 @@ class Context:
         self.stream = stream
         self._check(self.lib.lobe_ctx_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
 
-    def reserve(self, max_entries, max_isect):
-        self._check(self.lib.lobe_ctx_reserve(self.handle, int(max_entries), int(max_isect)))
+    def reserve(self, max_entries, max_isect, max_tiles):
+        self._check(self.lib.lobe_ctx_reserve(self.handle, int(max_entries), int(max_isect), int(max_tiles)))
 
     def status(self):
         self._check(self.lib.lobe_get_status(self.handle))

@@ -337,7 +337,7 @@ def test_capacity_overflow_is_reported_without_sync():
     ctx = ctx_for(wl)
     batch = make_batch(wl)
     proj = lobe.project(ctx, batch)
-    ctx.reserve(batch.n_entries, 1 << 16)
+    ctx.reserve(batch.n_entries, 1 << 16, batch.tiles(wl.tile)[0])
     n_tiles, _ = batch.tiles(wl.tile)
     small_bins = lobe.raster.empty_bins(100, n_tiles)
     lobe.bin_sort(ctx, batch, proj, small_bins, sync=False)
