@@ -204,6 +204,34 @@ lobe_status lobe_project(lobe_ctx *ctx, const lobe_batch *batch, const lobe_proj
 lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                           const lobe_bins *bins, int64_t *n_isect_host);
 
+/* Binning without any device allocation. The paper has no counterpart: this exists for
+ * callers that must not call cudaMalloc -- code embedded in a host application that owns
+ * all device memory through its own pool or budget, and real-time loops where an
+ * allocation (and the device synchronisation it can imply) is not acceptable. Creating a
+ * lobe_ctx allocates, so this call takes the configuration and stream directly.
+ *
+ * Computes exactly what lobe_bin_sort computes (same kernels, same output), but its
+ * scratch is one file-scope device array of 16 MiB that every GPU loading this library
+ * holds until the process exits. Limits: at most LOBE_NOALLOC_MAX_ENTRIES projected entries,
+ * LOBE_NOALLOC_MAX_TILES tiles and LOBE_NOALLOC_MAX_PAIRS super-tile pairs (pairs of a splat
+ * and a 64x64-pixel block it overlaps; 128x64 with 32x16 tiles) per call; larger batches
+ * return LOBE_ERR_CAPACITY.
+ * Entries and tiles are checked before anything is enqueued; the super-tile pair count is
+ * data-dependent, so the call synchronises `stream` to read it (then the bins are not
+ * written). The call synchronises again at the end and stores the (splat, tile) pair count
+ * in *n_isect_host (nullable); more pairs than bins->capacity gives LOBE_ERR_CAPACITY and
+ * bins describing empty tiles.
+ * The first call on a device looks up the array's device address (and may load the
+ * library's kernels); make that first call before any stream capture. All calls share the
+ * one array: calls whose work overlaps on the GPU (other threads, other streams) race and
+ * must be serialised by the caller. Other errors: LOBE_ERR_ARG (bad arguments),
+ * LOBE_ERR_CUDA (a CUDA call failed). */
+#define LOBE_NOALLOC_MAX_ENTRIES 262144
+#define LOBE_NOALLOC_MAX_TILES 65536
+#define LOBE_NOALLOC_MAX_PAIRS 524288
+lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *stream, const lobe_batch *batch,
+                                  const lobe_projected *proj, const lobe_bins *bins, int64_t *n_isect_host);
+
 /* Front-to-back compositing of every tile of every item. */
 lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                             const lobe_bins *bins, const lobe_image *image);

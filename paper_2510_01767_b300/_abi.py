@@ -86,6 +86,9 @@ SIGNATURES = {
     "lobe_project": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected)]),
     "lobe_bin_sort": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), ctypes.POINTER(Bins),
                                      ctypes.POINTER(ctypes.c_int64)]),
+    "lobe_bin_sort_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), vp, ctypes.POINTER(Batch),
+                                             ctypes.POINTER(Projected), ctypes.POINTER(Bins),
+                                             ctypes.POINTER(ctypes.c_int64)]),
     "lobe_render_fwd": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), ctypes.POINTER(Bins),
                                        ctypes.POINTER(Image)]),
     "lobe_render_bwd": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), ctypes.POINTER(Bins),

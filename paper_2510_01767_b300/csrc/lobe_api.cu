@@ -166,6 +166,13 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
     return LOBE_OK;
 }
 
+// Argument validation and parameter packing for entry points without a context (noalloc.cu).
+lobe_status lobe_internal_build_params(const lobe_config *cfg, const lobe_batch *b, BatchParams &P)
+{
+    lobe_status s = check_config(nullptr, cfg);
+    return s != LOBE_OK ? s : build_params(nullptr, *cfg, b, P);
+}
+
 extern "C" {
 
 int32_t lobe_abi_version(void) { return LOBE_ABI_VERSION; }
