@@ -9,5 +9,7 @@ paper_2510_01767_b300.build``) and a CUDA device.
 from .raster import (Batch, Bins, Context, GaussianSet, Image, Projection, PARAM_KEYS, bin_sort, forward,
                      project, project_bwd, render_bwd, render_fwd, visibility_crop, zero_grads)
 
-__all__ = ["Batch", "Bins", "Context", "GaussianSet", "Image", "Projection", "PARAM_KEYS", "bin_sort", "forward",
+from .autograd import LobeRasterize, Rasterizer, crop_compact, rasterize
+
+__all__ = ["LobeRasterize", "Rasterizer", "crop_compact", "rasterize","Batch", "Bins", "Context", "GaussianSet", "Image", "Projection", "PARAM_KEYS", "bin_sort", "forward",
            "project", "project_bwd", "render_bwd", "render_fwd", "visibility_crop", "zero_grads"]
