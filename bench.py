@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", default="medium", choices=["medium", "small", "city", "multi"])
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multi-block measurement")
     ap.add_argument("--recompute", action="store_true")
     return ap.parse_args()
 
@@ -192,6 +193,42 @@ def run_reference(args, rank, world):
                                        "single thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- batched vs plain
+
+def batched_vs_plain(reps=5):
+    """Multi-block workload (4 KD blocks of 0.5/1/2/3 M Gaussians, 16 views of uneven
+    resolution, 4 per block): one autotuned CUDA-graph step over all views vs the plain path
+    (one view per call sequence, eager, same tile shape). Returns a dict for the JSON line."""
+    import torch
+    import paper_2510_01767_b300 as lobe
+    from paper_2510_01767_b300.batched import PlainSteps, _time, autotune
+
+    wl = scenes.multi_block_scene(seed=0)
+    sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
+    cams = [c.as_dict() for c in wl.cameras]
+    gen = torch.Generator(device="cuda").manual_seed(7)
+
+    def fill(st):
+        st.dL.copy_(torch.randn(st.dL.shape, generator=gen, device="cuda"))
+
+    best, times = autotune(sets, cams, wl.items, wl.blocks, reps=reps, use_cache=False, dL_init=fill)
+    batched_ms = _time(best.replay, reps, best.stream)
+    pixels = best.batch.n_pixels
+    tile = best.tile
+    n_isect = best.n_isect
+    del best
+    torch.cuda.empty_cache()
+    plain = PlainSteps(sets, cams, wl.items, wl.blocks, tile=tile)
+    for st in plain.steps:
+        fill(st)
+    plain_ms = _time(plain.run, reps, torch.cuda.current_stream())
+    return {"workload": wl.name, "gaussians": sum(s.n for s in sets), "views": len(cams), "pixels": pixels,
+            "intersections": n_isect, "tile": list(tile), "autotune_ms": {k: round(v, 3) for k, v in times.items()},
+            "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
+            "batched_mpix_s": round(pixels / batched_ms / 1e3, 1), "plain_mpix_s": round(pixels / plain_ms / 1e3, 1),
+            "ratio": round(plain_ms / batched_ms, 3)}
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -374,6 +411,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    bvp = None
+    if world == 1 and not args.no_batched:
+        del proj, bins, image, grad2d, grads, flush
+        torch.cuda.empty_cache()
+        bvp = batched_vs_plain()
 
     if rank == 0:
         line = {
@@ -394,6 +436,7 @@ def main():
             "roofline": roof,
             "stages": stages,
             "cpu_baseline": cpu,
+            "batched_vs_plain": bvp,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

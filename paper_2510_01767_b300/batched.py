@@ -1,0 +1,156 @@
+"""Batched multi-view, multi-block forward + backward in one CUDA graph, and its autotuner.
+
+A ``BatchedStep`` owns every buffer of one training step over a batch of items (many views
+of uneven resolution across several KD-tree blocks of uneven Gaussian counts): projection
+(one thread per Gaussian of a set, looping over that set's views), binning of all items'
+tiles in one global tile space, compositing of all tiles of all items in one launch,
+the adjoint, and the per-set parameter gradients summed over views in registers. Because
+the binning scratch is reserved up front and no stage synchronises with the host, the whole
+step is captured once in a CUDA graph and replayed as a single launch.
+
+``autotune`` picks the tile shape (8x8, 16x16, 32x16) by timing graph replays on the actual
+batch; results are cached per (GPU, batch signature) in ``~/.cache/lobe/autotune.json``.
+``PlainSteps`` is the reference it is compared with: one view per call sequence, eager,
+each view projecting its block's Gaussians itself.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import torch
+
+from . import raster as R
+
+TILES = ((8, 8), (16, 16), (32, 16))
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lobe", "autotune.json")
+
+
+class BatchedStep:
+    def __init__(self, sets, cameras, items, blocks=(), tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0),
+                 recompute_T=False, slack=1.25, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.ctx = R.Context(tile=tile, sh_degree=sh_degree, bg=bg, recompute_T=recompute_T, stream=self.stream)
+        self.batch = R.Batch(sets, cameras, items, blocks)
+        self.tile = tuple(tile)
+        with torch.cuda.stream(self.stream):
+            proj, bins, _ = R.forward(self.ctx, self.batch, sync=True)
+            self.n_isect = bins.count
+            n_tiles, _ = self.batch.tiles(self.tile)
+            cap = int(self.n_isect * slack) + 4096
+            self.ctx.reserve(self.batch.n_entries, cap, n_tiles)
+            self.proj = proj
+            self.bins = R.empty_bins(cap, n_tiles)
+            self.image = R.empty_image(self.batch.n_pixels)
+            self.grad2d = torch.empty((self.batch.n_entries, 12), dtype=torch.float32, device="cuda")
+            self.grads = R.zero_grads(self.batch, sd=True)
+            self.dL = torch.zeros(3 * self.batch.n_pixels, dtype=torch.float32, device="cuda")
+        self.stream.synchronize()
+        self.graph = None
+
+    # one step, every stage enqueued on self.stream, no host synchronisation
+    def run(self):
+        c, b = self.ctx, self.batch
+        R.project(c, b, self.proj)
+        R.bin_sort(c, b, self.proj, self.bins, sync=False)
+        R.render_fwd(c, b, self.proj, self.bins, self.image)
+        R.render_bwd(c, b, self.proj, self.bins, self.image, self.dL, self.grad2d)
+        R.project_bwd(c, b, self.proj, self.grad2d, self.grads, accumulate=False)
+
+    def capture(self, warmup=2):
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                self.run()
+        self.stream.synchronize()
+        self.ctx.status()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self.run()
+        self.graph = g
+        return self
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("call capture() first")
+        self.graph.replay()
+
+    def images(self):
+        return self.batch.image_views(self.image.rgb)
+
+    def dL_views(self):
+        return self.batch.image_views(self.dL)
+
+
+class PlainSteps:
+    """The one-view-per-call reference: each item is its own batch, run eagerly in turn."""
+
+    def __init__(self, sets, cameras, items, blocks=(), tile=(16, 16), **kw):
+        self.steps = []
+        for s, c, b in items:
+            bl = [blocks[b]] if b >= 0 and blocks else []
+            self.steps.append(BatchedStep([sets[s]], [cameras[c]], [(0, 0, 0 if bl else -1)], bl, tile=tile,
+                                          stream=torch.cuda.current_stream(), **kw))
+
+    def run(self):
+        for st in self.steps:
+            st.run()
+
+
+def _time(fn, reps, stream):
+    fn()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def signature(sets, cameras, items):
+    h = hashlib.sha1()
+    h.update(repr([s.n for s in sets]).encode())
+    h.update(repr([(c["width"], c["height"]) if isinstance(c, dict) else (c.width, c.height) for c in cameras]).encode())
+    h.update(repr(items).encode())
+    return h.hexdigest()[:16]
+
+
+def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=True, dL_init=None, **kw):
+    """Returns (best BatchedStep captured in a graph, {tile: ms per step})."""
+    key = f"{torch.cuda.get_device_name()}|{signature(sets, cameras, items)}"
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            cache = json.load(open(CACHE))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        tile = tuple(cache[key]["tile"])
+        st = BatchedStep(sets, cameras, items, blocks, tile=tile, **kw)
+        if dL_init is not None:
+            dL_init(st)
+        return st.capture(), cache[key]["times"]
+    times, best, best_ms = {}, None, float("inf")
+    for tile in tiles:
+        st = BatchedStep(sets, cameras, items, blocks, tile=tile, **kw)
+        if dL_init is not None:
+            dL_init(st)
+        st.capture()
+        ms = _time(st.replay, reps, st.stream)
+        times[f"{tile[0]}x{tile[1]}"] = ms
+        if ms < best_ms:
+            if best is not None:
+                del best
+            best, best_ms = st, ms
+        else:
+            del st
+        torch.cuda.empty_cache()
+    if use_cache:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        cache[key] = {"tile": list(best.tile), "times": times, "when": time.time()}
+        with open(CACHE, "w") as f:
+            json.dump(cache, f)
+    return best, times

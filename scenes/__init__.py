@@ -332,7 +332,8 @@ def multi_block_scene(seed=0, block_sizes=(500_000, 1_000_000, 2_000_000, 3_000_
     oblique poses at 120-180 m altitude looking at the block."""
     rng = np.random.default_rng(seed + 1)
     total = sum(block_sizes)
-    city = city_layout(seed, city_n if city_n is not None else int(total * 1.25))
+    # median KD leaves hold ~1/4 of the city each: the largest block needs 4x its size
+    city = city_layout(seed, city_n if city_n is not None else int(max(block_sizes) * 4 * 1.05))
     leaves = kd_median_leaves(city.means, 2)
     order = np.argsort([len(ix) for ix, _ in leaves])
     sets, blocks, cams, items = [], [], [], []
