@@ -74,7 +74,8 @@ class BatchedStep:
     def replay(self):
         if self.graph is None:
             raise RuntimeError("call capture() first")
-        self.graph.replay()
+        with torch.cuda.stream(self.stream):  # replay is enqueued on the current stream
+            self.graph.replay()
 
     def images(self):
         return self.batch.image_views(self.image.rgb)
