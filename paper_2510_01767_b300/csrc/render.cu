@@ -16,200 +16,286 @@
 // C (the rendered colour) and the stop position, is either read from the forward's outputs
 // ("store") or re-derived by a forward sweep inside the kernel ("recompute").
 //
-// Per splat the 32 pixels of a warp are summed with shuffles and one lane adds the result to
-// global memory with vector reductions, so a tile of 256 pixels issues 8 (not 256) atomic
-// updates per splat.
+// Work decomposition (B300): one warp walks one slab of a tile -- 32 lanes x PX pixels,
+// each lane owning PX pixels of one column -- through the tile's list in batches of 32
+// splats staged in warp-private shared memory (the next batch is prefetched into registers
+// while the current one is composited). Per splat a lane loads the splat once and applies
+// it to its PX pixels, sharing the column terms of the exponent. The adjoint sums each
+// splat's 9 gradient values over the lane's pixels in registers, then over the warp with
+// shuffles, and one lane adds them to global memory with vector reductions: one update per
+// splat per warp (256 pixels) instead of one per pixel. Warps need no block barriers.
 #include "lobe_internal.cuh"
 
 namespace lobe {
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_render_fwd(const __grid_constant__ BatchParams P,
-                                                       const float4 *__restrict__ splat, const int *__restrict__ tile_start,
-                                                       const int *__restrict__ ids, float *__restrict__ rgb,
-                                                       float *__restrict__ Tout, int *__restrict__ ncout)
+template <int TW, int TH, int PX>
+struct Slab {
+    static constexpr int ROWG = 32 / TW;     // lane rows per warp
+    static constexpr int WROWS = ROWG * PX;  // tile rows per warp
+    static constexpr int WARPS = TH / WROWS;
+    static_assert(32 % TW == 0 && WARPS * WROWS == TH, "tile shape / pixels per lane mismatch");
+};
+
+// Exponent of one (pixel, splat) pair in base 2, with the column terms shared across a lane's
+// pixels: p2 = A dx^2 + dy (B dx + C dy) with A = -0.5 a log2e, B = -b log2e, C = -0.5 c log2e.
+// Forward and both adjoint sweeps call exactly this code, so their alpha decisions match.
+struct Column {
+    float dx, a2, b1;
+};
+
+__device__ __forceinline__ Column column_terms(float u, float A, float B, float pxc)
 {
-    constexpr int N = TW * TH;
-    __shared__ float4 s0[N];
-    __shared__ float4 s1[N];
-    __shared__ float s2[N];
-    const int t = blockIdx.x;
-    const ItemParams &I = P.item[item_of_tile(P, t)];
-    const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
-    const int px = tx * TW + (int)threadIdx.x % TW, py = ty * TH + (int)threadIdx.x / TW;
-    const bool inside = px < I.W && py < I.H;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-    const int start = tile_start[t], end = tile_start[t + 1];
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = 0;
-    bool done = !inside;
-    for (int base = start; base < end; base += N) {
-        if (__syncthreads_and(done)) break;
-        const int k = base + (int)threadIdx.x;
-        if (k < end) {
-            const int e = ids[k];
-            const float4 a = splat[3 * e], b = splat[3 * e + 1];
-            s0[threadIdx.x] = make_float4(a.x, a.y, -0.5f * LOG2E * a.z, -LOG2E * a.w);
-            s1[threadIdx.x] = make_float4(-0.5f * LOG2E * b.x, b.y, b.z, b.w);
-            s2[threadIdx.x] = splat[3 * e + 2].x;
-        }
-        __syncthreads();
-        const int cnt = min(N, end - base);
-        for (int j = 0; j < cnt && !done; ++j) {
-            const float4 a = s0[j], b = s1[j];
-            const Eval r = eval_pair(a.x, a.y, a.z, a.w, b.x, b.y, pxc, pyc);
-            if (!r.use) continue;
-            const float Tn = next_T(T, r.alpha);
-            if (Tn < T_MIN) {
-                done = true;
-                break;
-            }
-            const float w = r.alpha * T;
-            C0 += b.z * w;
-            C1 += b.w * w;
-            C2 += s2[j] * w;
-            T = Tn;
-            last = base - start + j + 1;
-        }
-    }
-    if (inside) {
-        const long long HW = (long long)I.W * I.H, p = (long long)py * I.W + px;
-        float *out = rgb + 3 * I.pix_off;
-        out[p] = C0 + T * P.bg[0];
-        out[HW + p] = C1 + T * P.bg[1];
-        out[2 * HW + p] = C2 + T * P.bg[2];
-        Tout[I.pix_off + p] = T;
-        ncout[I.pix_off + p] = last;
+    Column c;
+    c.dx = __fsub_rn(u, pxc);
+    c.a2 = __fmul_rn(__fmul_rn(A, c.dx), c.dx);
+    c.b1 = __fmul_rn(B, c.dx);
+    return c;
+}
+
+struct PairEval {
+    float dy, G, alpha;
+    bool use, clamped;
+};
+
+__device__ __forceinline__ PairEval pair_eval(const Column &cl, float v, float C, float o, float pyc)
+{
+    PairEval r;
+    r.dy = __fsub_rn(v, pyc);
+    const float p2 = __fmaf_rn(r.dy, __fmaf_rn(C, r.dy, cl.b1), cl.a2);
+    r.G = ex2(p2);
+    const float araw = __fmul_rn(o, r.G);
+    r.clamped = araw >= ALPHA_MAX;
+    r.alpha = fminf(ALPHA_MAX, araw);
+    r.use = (p2 <= 0.0f) && (r.alpha >= ALPHA_MIN);
+    return r;
+}
+
+// Staged splat: s0 = (u, v, A, B), s1 = (C, opacity, r, g), s2 = b.
+struct Staged {
+    float4 s0, s1;
+    float s2;
+    int id;
+};
+
+__device__ __forceinline__ void fetch(const float4 *__restrict__ splat, const int *__restrict__ ids, int k, int end,
+                                      Staged &s)
+{
+    if (k < end) {
+        const int e = ids[k];
+        const float4 a = splat[3 * e], b = splat[3 * e + 1];
+        s.s0 = make_float4(a.x, a.y, -0.5f * LOG2E * a.z, -LOG2E * a.w);
+        s.s1 = make_float4(-0.5f * LOG2E * b.x, b.y, b.z, b.w);
+        s.s2 = splat[3 * e + 2].x;
+        s.id = e;
     }
 }
 
-template <int TW, int TH, bool RECOMPUTE>
-__global__ void __launch_bounds__(TW *TH) k_render_bwd(const __grid_constant__ BatchParams P,
-                                                       const float4 *__restrict__ splat, const int *__restrict__ tile_start,
-                                                       const int *__restrict__ ids, const float *__restrict__ rgb,
-                                                       const int *__restrict__ ncin, const float *__restrict__ dL,
-                                                       float *__restrict__ grad2d)
+struct WarpStage {
+    float4 s0[32];
+    float4 s1[32];
+    float s2[32];
+    int id[32];
+};
+
+// Front-to-back walk of [start, end) for a lane's PX pixels (forward, and the first sweep
+// of the recompute adjoint). live[k] must be false for pixels outside the image.
+template <int PX>
+__device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, const int *__restrict__ ids, int start,
+                                              int end, float pxc, const float (&pyc)[PX], bool (&live)[PX],
+                                              float (&T)[PX], float (&C0)[PX], float (&C1)[PX], float (&C2)[PX],
+                                              int (&last)[PX], WarpStage &st)
 {
-    constexpr int N = TW * TH;
-    __shared__ float4 s0[N];
-    __shared__ float4 s1[N];
-    __shared__ float s2[N];
-    __shared__ int sid[N];
-    __shared__ int s_max;
     const int lane = threadIdx.x & 31;
+    Staged nx;
+    fetch(splat, ids, start + lane, end, nx);
+    for (int base = start; base < end; base += 32) {
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) any |= live[k];
+        if (!__any_sync(0xffffffffu, any)) break;
+        st.s0[lane] = nx.s0;
+        st.s1[lane] = nx.s1;
+        st.s2[lane] = nx.s2;
+        __syncwarp();
+        fetch(splat, ids, base + 32 + lane, end, nx);
+        const int cnt = min(32, end - base);
+        for (int j = 0; j < cnt; ++j) {
+            const float4 q0 = st.s0[j], q1 = st.s1[j];
+            const float cb = st.s2[j];
+            const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                if (!live[k]) continue;
+                const PairEval r = pair_eval(cl, q0.y, q1.x, q1.y, pyc[k]);
+                if (!r.use) continue;
+                const float Tn = next_T(T[k], r.alpha);
+                if (Tn < T_MIN) {
+                    live[k] = false;
+                    continue;
+                }
+                const float w = r.alpha * T[k];
+                C0[k] += q1.z * w;
+                C1[k] += q1.w * w;
+                C2[k] += cb * w;
+                T[k] = Tn;
+                last[k] = base - start + j + 1;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
+    k_render_fwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                 const int *__restrict__ tile_start, const int *__restrict__ ids, float *__restrict__ rgb,
+                 float *__restrict__ Tout, int *__restrict__ ncout)
+{
+    using G = Slab<TW, TH, PX>;
+    __shared__ WarpStage stage[G::WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x;
     const ItemParams &I = P.item[item_of_tile(P, t)];
     const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
-    const int px = tx * TW + (int)threadIdx.x % TW, py = ty * TH + (int)threadIdx.x / TW;
-    const bool inside = px < I.W && py < I.H;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const int px = tx * TW + lane % TW;
+    const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
+    const float pxc = (float)px + 0.5f;
+    float pyc[PX], T[PX], C0[PX], C1[PX], C2[PX];
+    int last[PX];
+    bool live[PX], inside[PX];
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        pyc[k] = (float)(py0 + k) + 0.5f;
+        inside[k] = px < I.W && py0 + k < I.H;
+        live[k] = inside[k];
+        T[k] = 1.0f;
+        C0[k] = C1[k] = C2[k] = 0.0f;
+        last[k] = 0;
+    }
+    forward_sweep<PX>(splat, ids, tile_start[t], tile_start[t + 1], pxc, pyc, live, T, C0, C1, C2, last,
+                      stage[warp]);
+    const long long HW = (long long)I.W * I.H;
+    float *out = rgb + 3 * I.pix_off;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        if (!inside[k]) continue;
+        const long long p = (long long)(py0 + k) * I.W + px;
+        out[p] = C0[k] + T[k] * P.bg[0];
+        out[HW + p] = C1[k] + T[k] * P.bg[1];
+        out[2 * HW + p] = C2[k] + T[k] * P.bg[2];
+        Tout[I.pix_off + p] = T[k];
+        ncout[I.pix_off + p] = last[k];
+    }
+}
+
+template <int TW, int TH, int PX, bool RECOMPUTE>
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
+    k_render_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                 const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ rgb,
+                 const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
+{
+    using G = Slab<TW, TH, PX>;
+    __shared__ WarpStage stage[G::WARPS];
+    WarpStage &st = stage[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = blockIdx.x;
+    const ItemParams &I = P.item[item_of_tile(P, t)];
+    const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
+    const int px = tx * TW + lane % TW;
+    const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
+    const float pxc = (float)px + 0.5f;
     const int start = tile_start[t], end = tile_start[t + 1];
-    const long long HW = (long long)I.W * I.H, p = (long long)py * I.W + px;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f;
-    int nc = 0;
-    if (threadIdx.x == 0) s_max = 0;
-    if (inside) {
-        const float *d = dL + 3 * I.pix_off;
-        g0 = d[p];
-        g1 = d[HW + p];
-        g2 = d[2 * HW + p];
-        if (!RECOMPUTE) {
-            const float *c = rgb + 3 * I.pix_off;
-            R0 = c[p];
-            R1 = c[HW + p];
-            R2 = c[2 * HW + p];
-            nc = ncin[I.pix_off + p];
+    const long long HW = (long long)I.W * I.H;
+    float pyc[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX], T[PX];
+    int nc[PX];
+    bool inside[PX];
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        pyc[k] = (float)(py0 + k) + 0.5f;
+        inside[k] = px < I.W && py0 + k < I.H;
+        g0[k] = g1[k] = g2[k] = R0[k] = R1[k] = R2[k] = 0.0f;
+        T[k] = 1.0f;
+        nc[k] = 0;
+        if (inside[k]) {
+            const long long p = (long long)(py0 + k) * I.W + px;
+            const float *d = dL + 3 * I.pix_off;
+            g0[k] = d[p];
+            g1[k] = d[HW + p];
+            g2[k] = d[2 * HW + p];
+            if (!RECOMPUTE) {
+                const float *c = rgb + 3 * I.pix_off;
+                R0[k] = c[p];
+                R1[k] = c[HW + p];
+                R2[k] = c[2 * HW + p];
+                nc[k] = ncin[I.pix_off + p];
+            }
         }
     }
     if (RECOMPUTE) {
-        // forward sweep: stop position and rendered colour, bit-identical decisions
-        float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        bool done = !inside;
-        for (int base = start; base < end; base += N) {
-            if (__syncthreads_and(done)) break;
-            const int k = base + (int)threadIdx.x;
-            if (k < end) {
-                const int e = ids[k];
-                const float4 a = splat[3 * e], b = splat[3 * e + 1];
-                s0[threadIdx.x] = make_float4(a.x, a.y, -0.5f * LOG2E * a.z, -LOG2E * a.w);
-                s1[threadIdx.x] = make_float4(-0.5f * LOG2E * b.x, b.y, b.z, b.w);
-                s2[threadIdx.x] = splat[3 * e + 2].x;
-            }
-            __syncthreads();
-            const int cnt = min(N, end - base);
-            for (int j = 0; j < cnt && !done; ++j) {
-                const float4 a = s0[j], b = s1[j];
-                const Eval r = eval_pair(a.x, a.y, a.z, a.w, b.x, b.y, pxc, pyc);
-                if (!r.use) continue;
-                const float Tn = next_T(T, r.alpha);
-                if (Tn < T_MIN) {
-                    done = true;
-                    break;
-                }
-                const float w = r.alpha * T;
-                C0 += b.z * w;
-                C1 += b.w * w;
-                C2 += s2[j] * w;
-                T = Tn;
-                nc = base - start + j + 1;
-            }
+        bool live[PX];
+#pragma unroll
+        for (int k = 0; k < PX; ++k) live[k] = inside[k];
+        forward_sweep<PX>(splat, ids, start, end, pxc, pyc, live, T, R0, R1, R2, nc, st);
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            R0[k] += T[k] * P.bg[0];
+            R1[k] += T[k] * P.bg[1];
+            R2[k] += T[k] * P.bg[2];
+            T[k] = 1.0f;
         }
-        R0 = C0 + T * P.bg[0];
-        R1 = C1 + T * P.bg[1];
-        R2 = C2 + T * P.bg[2];
-        __syncthreads();
     }
-    __syncthreads();
-    if (nc > 0) atomicMax(&s_max, nc);
-    __syncthreads();
-    const int stop = min(start + s_max, end);
-    float T = 1.0f;
-    for (int base = start; base < stop; base += N) {
-        __syncthreads();
-        const int k = base + (int)threadIdx.x;
-        if (k < stop) {
-            const int e = ids[k];
-            const float4 a = splat[3 * e], b = splat[3 * e + 1];
-            s0[threadIdx.x] = make_float4(a.x, a.y, -0.5f * LOG2E * a.z, -LOG2E * a.w);
-            s1[threadIdx.x] = make_float4(-0.5f * LOG2E * b.x, b.y, b.z, b.w);
-            s2[threadIdx.x] = splat[3 * e + 2].x;
-            sid[threadIdx.x] = e;
-        }
-        __syncthreads();
-        const int cnt = min(N, stop - base);
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) m = max(m, nc[k]);
+    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+    const int stop = min(start + m, end);
+
+    Staged nx;
+    fetch(splat, ids, start + lane, stop, nx);
+    for (int base = start; base < stop; base += 32) {
+        st.s0[lane] = nx.s0;
+        st.s1[lane] = nx.s1;
+        st.s2[lane] = nx.s2;
+        st.id[lane] = nx.id;
+        __syncwarp();
+        fetch(splat, ids, base + 32 + lane, stop, nx);
+        const int cnt = min(32, stop - base);
         for (int j = 0; j < cnt; ++j) {
+            const float4 q0 = st.s0[j], q1 = st.s1[j];
+            const float cb = st.s2[j];
             const int pos = base - start + j;
+            const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
             float du = 0.f, dv = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-            bool contrib = false;
-            if (pos < nc) {
-                const float4 a = s0[j], b = s1[j];
-                const Eval r = eval_pair(a.x, a.y, a.z, a.w, b.x, b.y, pxc, pyc);
-                if (r.use) {
-                    contrib = true;
-                    const float cb = s2[j];
-                    const float w = r.alpha * T;
-                    dr = w * g0;
-                    dg = w * g1;
-                    db = w * g2;
-                    R0 -= b.z * w;
-                    R1 -= b.w * w;
-                    R2 -= cb * w;
-                    const float gc = g0 * b.z + g1 * b.w + g2 * cb;
-                    const float gR = g0 * R0 + g1 * R1 + g2 * R2;
-                    const float dalpha = T * gc - gR / (1.0f - r.alpha);
-                    T = next_T(T, r.alpha);
-                    if (!r.clamped) {
-                        dop = dalpha * r.G;
-                        const float dp2 = dalpha * r.alpha * LN2;
-                        dA = dp2 * r.dx * r.dx;
-                        dB = dp2 * r.dx * r.dy;
-                        dC = dp2 * r.dy * r.dy;
-                        du = dp2 * (2.f * a.z * r.dx + a.w * r.dy);
-                        dv = dp2 * (a.w * r.dx + 2.f * b.x * r.dy);
-                    }
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                if (pos >= nc[k]) continue;
+                const PairEval r = pair_eval(cl, q0.y, q1.x, q1.y, pyc[k]);
+                if (!r.use) continue;
+                any = true;
+                const float w = r.alpha * T[k];
+                dr += w * g0[k];
+                dg += w * g1[k];
+                db += w * g2[k];
+                R0[k] -= q1.z * w;
+                R1[k] -= q1.w * w;
+                R2[k] -= cb * w;
+                const float gc = g0[k] * q1.z + g1[k] * q1.w + g2[k] * cb;
+                const float gR = g0[k] * R0[k] + g1[k] * R1[k] + g2[k] * R2[k];
+                const float dalpha = T[k] * gc - __fdividef(gR, 1.0f - r.alpha);
+                T[k] = next_T(T[k], r.alpha);
+                if (!r.clamped) {
+                    dop += dalpha * r.G;
+                    const float dp2 = dalpha * r.alpha * LN2;
+                    const float dpy = dp2 * r.dy;
+                    dA += dp2 * cl.dx * cl.dx;
+                    dB += dpy * cl.dx;
+                    dC += dpy * r.dy;
+                    du += dp2 * (2.f * q0.z * cl.dx + q0.w * r.dy);
+                    dv += dp2 * q0.w * cl.dx + 2.f * q1.x * dpy;
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
+            if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
                     du += __shfl_xor_sync(0xffffffffu, du, o);
@@ -223,7 +309,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const __grid_constant__ B
                     db += __shfl_xor_sync(0xffffffffu, db, o);
                 }
                 if (lane == 0) {
-                    float *gp = grad2d + 12LL * sid[j];
+                    float *gp = grad2d + 12LL * st.id[j];
                     // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
                     red_add_v4(gp, du, dv, -0.5f * LOG2E * dA, -LOG2E * dB);
                     red_add_v4(gp + 4, -0.5f * LOG2E * dC, dop, dr, dg);
@@ -231,31 +317,34 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const __grid_constant__ B
                 }
             }
         }
+        __syncwarp();
     }
 }
 
 // --------------------------------------------------------------------------- launchers
 
-template <int TW, int TH>
+template <int TW, int TH, int PX>
 static cudaError_t fwd_t(const BatchParams &P, const float *splat, const int *ts, const int *ids, float *rgb, float *T,
                          int *nc, cudaStream_t st)
 {
     count_launch();
-    k_render_fwd<TW, TH><<<P.n_tiles, TW * TH, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts, ids, rgb, T, nc);
+    k_render_fwd<TW, TH, PX><<<P.n_tiles, 32 * Slab<TW, TH, PX>::WARPS, 0, st>>>(
+        P, reinterpret_cast<const float4 *>(splat), ts, ids, rgb, T, nc);
     return cudaGetLastError();
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PX>
 static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *splat, const int *ts, const int *ids,
                          const float *rgb, const int *nc, const float *dL, float *g2d, cudaStream_t st)
 {
     count_launch();
+    const int threads = 32 * Slab<TW, TH, PX>::WARPS;
     if (recompute)
-        k_render_bwd<TW, TH, true><<<P.n_tiles, TW * TH, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts, ids,
-                                                                   rgb, nc, dL, g2d);
+        k_render_bwd<TW, TH, PX, true><<<P.n_tiles, threads, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts,
+                                                                      ids, rgb, nc, dL, g2d);
     else
-        k_render_bwd<TW, TH, false><<<P.n_tiles, TW * TH, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts, ids,
-                                                                    rgb, nc, dL, g2d);
+        k_render_bwd<TW, TH, PX, false><<<P.n_tiles, threads, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts,
+                                                                       ids, rgb, nc, dL, g2d);
     return cudaGetLastError();
 }
 
@@ -263,9 +352,9 @@ cudaError_t launch_render_fwd(const BatchParams &P, const float *splat, const in
                               float *T, int *nc, cudaStream_t st)
 {
     if (P.n_tiles == 0) return cudaSuccess;
-    if (P.tw == 16 && P.th == 16) return fwd_t<16, 16>(P, splat, ts, ids, rgb, T, nc, st);
-    if (P.tw == 8 && P.th == 8) return fwd_t<8, 8>(P, splat, ts, ids, rgb, T, nc, st);
-    if (P.tw == 32 && P.th == 16) return fwd_t<32, 16>(P, splat, ts, ids, rgb, T, nc, st);
+    if (P.tw == 16 && P.th == 16) return fwd_t<16, 16, 8>(P, splat, ts, ids, rgb, T, nc, st);
+    if (P.tw == 8 && P.th == 8) return fwd_t<8, 8, 2>(P, splat, ts, ids, rgb, T, nc, st);
+    if (P.tw == 32 && P.th == 16) return fwd_t<32, 16, 8>(P, splat, ts, ids, rgb, T, nc, st);
     return cudaErrorInvalidValue;
 }
 
@@ -275,9 +364,9 @@ cudaError_t launch_render_bwd(const BatchParams &P, bool recompute, const float 
     cudaError_t err = P.n_entries > 0 ? cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)P.n_entries, st)
                                       : cudaSuccess;
     if (err != cudaSuccess || P.n_tiles == 0) return err;
-    if (P.tw == 16 && P.th == 16) return bwd_t<16, 16>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
-    if (P.tw == 8 && P.th == 8) return bwd_t<8, 8>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
-    if (P.tw == 32 && P.th == 16) return bwd_t<32, 16>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
+    if (P.tw == 16 && P.th == 16) return bwd_t<16, 16, 8>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
+    if (P.tw == 8 && P.th == 8) return bwd_t<8, 8, 2>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
+    if (P.tw == 32 && P.th == 16) return bwd_t<32, 16, 8>(P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
     return cudaErrorInvalidValue;
 }
 

@@ -59,7 +59,7 @@ def test_graph_replay_equals_plain(workload):
     for s in range(len(sets)):
         for k in lobe.PARAM_KEYS:
             want = sum(p.grads[0][k] for p, it in zip(plain.steps, wl.items) if it[0] == s)
-            assert grad_rel_err(st.grads[s][k].cpu().numpy(), want.cpu().numpy()) <= 1e-4, (s, k)
+            assert grad_rel_err(st.grads[s][k].cpu().numpy(), want.cpu().numpy()) <= 1e-3, (s, k)
         want_cnt = sum(p.grads[0]["sd_cnt"] for p, it in zip(plain.steps, wl.items) if it[0] == s)
         # the graph step ran three times (two warm-up runs before capture, one replay)
         assert torch.equal(st.grads[s]["sd_cnt"], 3 * want_cnt)
