@@ -211,9 +211,10 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
  * lobe_ctx allocates, so this call takes the configuration and stream directly.
  *
  * Computes exactly what lobe_bin_sort computes (same kernels, same output), but its
- * scratch is one file-scope device array of 16 MiB that every GPU loading this library
+ * scratch is one file-scope device array of 20 MiB that every GPU loading this library
  * holds until the process exits. Limits: at most LOBE_NOALLOC_MAX_ENTRIES projected entries,
- * LOBE_NOALLOC_MAX_TILES tiles and LOBE_NOALLOC_MAX_PAIRS super-tile pairs (pairs of a splat
+ * LOBE_NOALLOC_MAX_TILES tiles (at most 8192 blocks of 64x64 pixels) and LOBE_NOALLOC_MAX_PAIRS
+ * super-tile pairs (pairs of a splat
  * and a 64x64-pixel block it overlaps; 128x64 with 32x16 tiles) per call; larger batches
  * return LOBE_ERR_CAPACITY.
  * Entries and tiles are checked before anything is enqueued; the super-tile pair count is

@@ -1,0 +1,444 @@
+// binning.cu -- tile binning: every (splat, tile) pair, grouped by tile, in (depth, entry) order.
+//
+// The 3DGS rasterizer obtains this order by radix-sorting 64-bit (tile << 32 | depth) keys of
+// all duplicated pairs. Wide splats make that list long (tens of millions of pairs for a
+// 200k-splat view) while each pixel uses only its first few hundred entries, so the sort
+// dominates. Here the same order is reached without sorting the pairs at all:
+//
+//   1. compact the visible splats and sort them by depth (a few hundred thousand keys);
+//   2. duplicate them per SUPER-tile (S x S tiles, 64 px) in depth order -- the key carries the
+//      super-tile id (bits 16..31) and the splat's tile rectangle relative to that super-tile
+//      (4 x 4 bits) -- and stably sort those few million pairs by super-tile id: each
+//      super-tile then holds its splats in depth order;
+//   3. cut every super-tile's list into chunks of 256 (one CTA each); per chunk and tile, warp
+//      ballots count the splats covering the tile; per (super-tile, tile) a prefix over its
+//      chunks gives each chunk's offset and the tile's size; a scan of the sizes gives
+//      tile_start; the chunks then write their splats' ids to each tile's range, in order,
+//      with coalesced stores.
+//
+// A tile's list is its super-tile's list filtered by "tile in the splat's tile rectangle",
+// which preserves (depth, entry) order, so the output equals the global pair sort bit for bit.
+#include "sort_prims.cuh"
+
+namespace lobe {
+
+constexpr int CHUNK = 256;    // splats per work item (BIN_THREADS)
+constexpr int NT_MAX = 64;    // tiles per super-tile (S <= 8)
+constexpr int KEY_SHIFT = 16; // super-tile id above, packed local rectangle below
+constexpr long long MAX_SUPER = 1LL << 16;
+
+__device__ __forceinline__ void splat_rect(const BatchParams &P, const ItemParams &I, const float *splat,
+                                           const int *radius, uint32_t e, int &x0, int &y0, int &x1, int &y1)
+{
+    const float2 uv = *reinterpret_cast<const float2 *>(splat + 12LL * e);
+    tile_rect(uv.x, uv.y, radius[e], P.tw, P.th, I.gx, I.gy, x0, y0, x1, y1);
+}
+
+// super-rectangle area of the k-th depth-ordered visible splat
+__global__ void __launch_bounds__(256) k_super_area(const __grid_constant__ BatchParams P, const uint32_t *V_dev,
+                                                    const uint32_t *__restrict__ order, const float *__restrict__ splat,
+                                                    const int *__restrict__ radius, uint32_t *__restrict__ area)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *V_dev) return;
+    const uint32_t e = order[k];
+    const ItemParams &I = P.item[item_of_entry(P, e)];
+    int x0, y0, x1, y1;
+    splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
+    const int S = P.S;
+    area[k] = (uint32_t)(((x1 + S - 1) / S - x0 / S) * ((y1 + S - 1) / S - y0 / S));
+}
+
+// Each warp takes 32 consecutive depth-ordered splats; their super pairs occupy one contiguous
+// output range, written lane-strided (coalesced); a lane finds its splat by binary search
+// over the warp's 32 offsets. Key = super-tile id << 16 | local rectangle (x0, x1, y0, y1 in
+// tiles relative to the super-tile origin, clipped to [0, S], 4 bits each).
+__global__ void __launch_bounds__(256) k_super_dup(const __grid_constant__ BatchParams P, const uint32_t *V_dev,
+                                                   const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
+                                                   const float *__restrict__ splat, const int *__restrict__ radius,
+                                                   const uint32_t *n_sp_use, uint32_t *__restrict__ skeys,
+                                                   uint32_t *__restrict__ svals)
+{
+    const int lane = threadIdx.x & 31;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t V = *V_dev;
+    if ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) >= V) return;
+    if (*n_sp_use == 0) return;  // nothing to emit (no pairs, or scratch capacity exceeded)
+    const bool valid = k < V;
+    const int S = P.S;
+    uint32_t off = 0xffffffffu, cnt = 0, base = 0, w = 1, sg = 1, e = 0;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0, sx0 = 0, sy0 = 0;
+    if (valid) {
+        e = order[k];
+        off = offs[k];
+        const ItemParams &I = P.item[item_of_entry(P, e)];
+        splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
+        sx0 = x0 / S;
+        sy0 = y0 / S;
+        const int sx1 = (x1 + S - 1) / S, sy1 = (y1 + S - 1) / S;
+        base = (uint32_t)(I.super_off + sy0 * I.sgx + sx0);
+        w = (uint32_t)(sx1 - sx0);
+        sg = (uint32_t)I.sgx;
+        cnt = (uint32_t)((sx1 - sx0) * (sy1 - sy0));
+    }
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const int last = 31 - __clz(vmask);
+    const uint32_t p0 = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t p1 = __shfl_sync(0xffffffffu, off + cnt, last);
+    for (uint32_t p = p0 + lane; p - lane < p1; p += 32) {
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+            uint32_t o = __shfl_sync(0xffffffffu, off, j + step);
+            if (o <= p) j += step;
+        }
+        const uint32_t oj = __shfl_sync(0xffffffffu, off, j);
+        const uint32_t wj = __shfl_sync(0xffffffffu, w, j);
+        const uint32_t bj = __shfl_sync(0xffffffffu, base, j);
+        const uint32_t gj = __shfl_sync(0xffffffffu, sg, j);
+        const uint32_t ej = __shfl_sync(0xffffffffu, e, j);
+        const int rx0 = __shfl_sync(0xffffffffu, x0 - sx0 * S, j), rx1 = __shfl_sync(0xffffffffu, x1 - sx0 * S, j);
+        const int ry0 = __shfl_sync(0xffffffffu, y0 - sy0 * S, j), ry1 = __shfl_sync(0xffffffffu, y1 - sy0 * S, j);
+        if (p < p1) {
+            const uint32_t local = p - oj;
+            const int sy = (int)(local / wj), sx = (int)(local - sy * wj);
+            // the splat's rectangle relative to super-tile (sx, sy) of its super-rectangle
+            const int lx0 = max(rx0 - sx * S, 0), lx1 = min(rx1 - sx * S, S);
+            const int ly0 = max(ry0 - sy * S, 0), ly1 = min(ry1 - sy * S, S);
+            skeys[p] = ((bj + (uint32_t)sy * gj + (uint32_t)sx) << KEY_SHIFT) |
+                       (uint32_t)(lx0 | (lx1 << 4) | (ly0 << 8) | (ly1 << 12));
+            svals[p] = ej;
+        }
+    }
+}
+
+// start[t] = first k with (keys[k] >> shift) >= t, for t in [0, n_keys]
+__global__ void __launch_bounds__(256) k_key_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
+                                                    long long n_max, int shift, int n_keys, uint32_t *__restrict__ start)
+{
+    const long long n = *n_dev < n_max ? (long long)*n_dev : n_max;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += (long long)gridDim.x * blockDim.x) {
+        const long long prev = k > 0 ? (long long)(keys[k - 1] >> shift) : -1;
+        const long long cur = k < n ? (long long)(keys[k] >> shift) : (long long)n_keys;
+        for (long long t = prev + 1; t <= cur && t <= n_keys; ++t) start[t] = (uint32_t)k;
+    }
+}
+
+// ------------------------------------------------------------------ chunk work items
+
+struct LoadChunks {  // work items (chunks of CHUNK splats) of super-tile s
+    const uint32_t *super_start;
+    __device__ uint32_t operator()(long long s) const
+    {
+        return (super_start[s + 1] - super_start[s] + CHUNK - 1) / CHUNK;
+    }
+};
+
+// the super-tile of work item w: largest s with chunk_base[s] <= w
+__device__ __forceinline__ int work_super(const uint32_t *chunk_base, int n_super, uint32_t w)
+{
+    int lo = 0, hi = n_super - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunk_base[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool covers(uint32_t key, int tx, int ty)
+{
+    return tx >= (int)(key & 15u) && tx < (int)((key >> 4) & 15u) && ty >= (int)((key >> 8) & 15u) &&
+           ty < (int)((key >> 12) & 15u);
+}
+
+// Pass 1: cnt[w * S*S + t] = splats of chunk w covering local tile t.
+template <int S>
+__global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__restrict__ keys,
+                                                             const uint32_t *__restrict__ super_start,
+                                                             const uint32_t *__restrict__ chunk_base, int n_super,
+                                                             uint32_t *__restrict__ cnt)
+{
+    constexpr int NT = S * S;
+    __shared__ uint32_t wc[BIN_THREADS / 32][NT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_work = chunk_base[n_super];
+    for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int s = work_super(chunk_base, n_super, w);
+        const uint32_t lo = super_start[s] + (w - chunk_base[s]) * CHUNK;
+        const uint32_t hi = min(lo + CHUNK, super_start[s + 1]);
+        const uint32_t i = lo + threadIdx.x;
+        const uint32_t key = i < hi ? keys[i] : 0u;  // 0 = empty rectangle
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
+            if (lane == (t & 31)) wc[warp][t] = __popc(m);
+        }
+        __syncthreads();
+        if (threadIdx.x < NT) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int q = 0; q < BIN_THREADS / 32; ++q) c += wc[q][threadIdx.x];
+            cnt[(size_t)w * NT + threadIdx.x] = c;
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 2, per (super-tile, local tile): chunk counts -> chunk offsets within the tile (in
+// place) and the tile's size -> tile_count[global tile].
+template <int S>
+__global__ void __launch_bounds__(256) k_chunk_prefix(const __grid_constant__ BatchParams P,
+                                                      const uint32_t *__restrict__ chunk_base, uint32_t *__restrict__ cnt,
+                                                      uint32_t *__restrict__ tile_count)
+{
+    constexpr int NT = S * S;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(gid / NT), t = (int)(gid % NT);
+    if (s >= P.n_super) return;
+    uint32_t run = 0;
+    for (uint32_t w = chunk_base[s]; w < chunk_base[s + 1]; ++w) {
+        const uint32_t c = cnt[(size_t)w * NT + t];
+        cnt[(size_t)w * NT + t] = run;
+        run += c;
+    }
+    const ItemParams &I = P.item[item_of_super(P, s)];
+    const int ls = s - I.super_off, tx = (ls % I.sgx) * S + t % S, ty = (ls / I.sgx) * S + t / S;
+    if (tx < I.gx && ty < I.gy) tile_count[I.tile_off + ty * I.gx + tx] = run;
+}
+
+// Pass 3: each chunk's splats, in list order, to their tiles' ranges.
+template <int S>
+__global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constant__ BatchParams P,
+                                                            const uint32_t *__restrict__ keys,
+                                                            const uint32_t *__restrict__ vals,
+                                                            const uint32_t *__restrict__ super_start,
+                                                            const uint32_t *__restrict__ chunk_base,
+                                                            const uint32_t *__restrict__ cnt,
+                                                            const int *__restrict__ tile_start, const uint32_t *n_use,
+                                                            int *__restrict__ gauss_ids)
+{
+    constexpr int NT = S * S;
+    __shared__ uint32_t wc[BIN_THREADS / 32][NT];
+    __shared__ uint32_t base[NT];
+    if (*n_use == 0) return;  // no pairs, or more than the bins hold
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const int n_super = P.n_super;
+    const uint32_t n_work = chunk_base[n_super];
+    for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const int s = work_super(chunk_base, n_super, w);
+        const uint32_t lo = super_start[s] + (w - chunk_base[s]) * CHUNK;
+        const uint32_t hi = min(lo + CHUNK, super_start[s + 1]);
+        const uint32_t i = lo + threadIdx.x;
+        const uint32_t key = i < hi ? keys[i] : 0u;
+        const int id = i < hi ? (int)vals[i] : 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
+            if (lane == (t & 31)) wc[warp][t] = __popc(m);
+        }
+        __syncthreads();
+        if (threadIdx.x < NT) {
+            uint32_t r = 0;
+#pragma unroll
+            for (int q = 0; q < BIN_THREADS / 32; ++q) {
+                const uint32_t c = wc[q][threadIdx.x];
+                wc[q][threadIdx.x] = r;
+                r += c;
+            }
+            const ItemParams &I = P.item[item_of_super(P, s)];
+            const int ls = s - I.super_off;
+            const int tx = (ls % I.sgx) * S + (int)threadIdx.x % S, ty = (ls / I.sgx) * S + (int)threadIdx.x / S;
+            const uint32_t ts = (tx < I.gx && ty < I.gy) ? (uint32_t)tile_start[I.tile_off + ty * I.gx + tx] : 0u;
+            base[threadIdx.x] = ts + cnt[(size_t)w * NT + threadIdx.x];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const bool cov = covers(key, t % S, t / S);
+            const unsigned m = __ballot_sync(0xffffffffu, cov);
+            if (cov) gauss_ids[base[t] + wc[warp][t] + __popc(m & lt)] = id;
+        }
+        __syncthreads();
+    }
+}
+
+// after an overflow the bins describe empty tiles
+__global__ void __launch_bounds__(256) k_clear_on_overflow(const uint32_t *n_use, const long long *total, int n_tiles,
+                                                           int *__restrict__ tile_start)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= n_tiles && *n_use == 0 && *total != 0) tile_start[t] = 0;
+}
+
+// ------------------------------------------------------------------ orchestration
+
+static unsigned persistent_grid(long long work_max)
+{
+    const long long cap = 148LL * 16;
+    return (unsigned)(work_max < 1 ? 1 : (work_max < cap ? work_max : cap));
+}
+
+// Step 1 and the super-pair count: visible splats in depth order (vis_pos), per-splat super
+// pair offsets (offs), the super pair total (scalars[4]) and its usable count (scalars[1]: the
+// total, or 0 with a latched error when it exceeds pair_capacity; < 0 = unchecked).
+cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int *radius, const int *tiles,
+                            BinScratch &b, long long pair_capacity, cudaStream_t st)
+{
+    const long long n = P.n_entries;
+    uint32_t *V = b.scalars, *n_sp = b.scalars + 1, *sp_total = b.scalars + 4;
+    scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, b.block_sums, V, nullptr, nullptr, -1, nullptr, st);
+    if (n > 0) {
+        count_launch();
+        k_compact<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tiles, splat, b.vis_pos, b.dkA, b.dvA);
+    }
+    radix_sort(V, n, 0, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.counts, b.block_sums, st);
+    if (n > 0) {
+        count_launch();
+        k_super_area<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, splat, radius, b.offs);
+    }
+    scan(LoadPlain{b.offs}, V, n, b.offs, b.block_sums, sp_total, nullptr, n_sp, pair_capacity, b.status, st);
+    return cudaGetLastError();
+}
+
+// Super pairs -> sorted super-tile lists -> per-chunk tile counts -> tile_start (in place), the
+// pair count (n_isect) and its usable count (scalars[2], 0 when above isect_capacity).
+cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *radius, BinScratch &b,
+                           long long pair_capacity, long long *n_isect_dev, int *tile_start, long long isect_capacity,
+                           cudaStream_t st)
+{
+    const long long n = P.n_entries;
+    uint32_t *V = b.scalars, *n_sp = b.scalars + 1, *n_use = b.scalars + 2;
+    if (n > 0) {
+        count_launch();
+        k_super_dup<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, b.offs, splat, radius, n_sp, b.skA,
+                                                                 b.svA);
+    }
+    int nbits = 0;
+    while ((1LL << nbits) < (long long)P.n_super) ++nbits;
+    const int passes = nbits < 1 ? 1 : (nbits + 7) / 8;
+    uint32_t *kfinal = (passes & 1) ? b.skB : b.skA;  // not the last pass's source
+    uint32_t *vfinal = (passes & 1) ? b.svB : b.svA;
+    radix_sort(n_sp, pair_capacity, KEY_SHIFT, nbits, b.skA, b.svA, b.skB, b.svB, kfinal, vfinal, b.counts,
+               b.block_sums, st);
+    b.sp_keys = kfinal;
+    b.sp_ids = vfinal;
+    count_launch();
+    const long long rblocks = (pair_capacity + 1 + 255) / 256;
+    k_key_ranges<<<(unsigned)(rblocks < 2368 ? rblocks : 2368), 256, 0, st>>>(kfinal, n_sp, pair_capacity, KEY_SHIFT,
+                                                                                P.n_super, b.super_start);
+    // chunk work items: chunk_base[s] = first work item of super-tile s, chunk_base[n_super] = total
+    scan(LoadChunks{b.super_start}, nullptr, P.n_super, b.chunk_base, b.block_sums, b.chunk_base + P.n_super, nullptr,
+         nullptr, -1, nullptr, st);
+    const long long work_max = pair_capacity / CHUNK + P.n_super + 1;
+    uint32_t *ts = reinterpret_cast<uint32_t *>(tile_start);
+    if (P.n_super > 0) {
+        const int NT = P.S * P.S;
+        const unsigned pgrid = (unsigned)(((long long)P.n_super * NT + 255) / 256);
+        count_launch(2);
+        if (P.S == 8) {
+            k_chunk_count<8><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.super_start, b.chunk_base,
+                                                                                P.n_super, b.chunk_cnt);
+            k_chunk_prefix<8><<<pgrid, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
+        } else {
+            k_chunk_count<4><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.super_start, b.chunk_base,
+                                                                                P.n_super, b.chunk_cnt);
+            k_chunk_prefix<4><<<pgrid, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
+        }
+    }
+    // the scan's grand total lands in tile_start[n_tiles] and in the caller's n_isect
+    scan(LoadPlain{ts}, nullptr, P.n_tiles, ts, b.block_sums, ts + P.n_tiles, n_isect_dev, n_use, isect_capacity,
+         b.status, st);
+    b.work_max = work_max;
+    return cudaGetLastError();
+}
+
+cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *radius, BinScratch &b,
+                          const long long *n_isect_dev, int *gauss_ids, int *tile_start, cudaStream_t st)
+{
+    (void)splat;
+    (void)radius;
+    const uint32_t *n_use = b.scalars + 2;
+    if (P.n_super > 0) {
+        count_launch();
+        const unsigned grid = persistent_grid(b.work_max);
+        if (P.S == 8)
+            k_chunk_emit<8><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.super_start, b.chunk_base,
+                                                          b.chunk_cnt, tile_start, n_use, gauss_ids);
+        else
+            k_chunk_emit<4><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.super_start, b.chunk_base,
+                                                          b.chunk_cnt, tile_start, n_use, gauss_ids);
+    }
+    count_launch();
+    k_clear_on_overflow<<<(P.n_tiles + 1 + 255) / 256, 256, 0, st>>>(n_use, n_isect_dev, P.n_tiles, tile_start);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ scratch layout
+//
+// entry part: 6 arrays of max_entries words + radix digit counts + scan block sums + scalars
+// pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong) + per-chunk tile counts
+// super part: super-tile list starts and chunk bases (max_super + 1 words each)
+
+static size_t words_rounded(size_t words) { return ((words * 4 + 255) / 256) * 256; }
+
+size_t entry_scratch_bytes(long long max_entries)
+{
+    size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
+    return 6 * words_rounded(e) + words_rounded(256ull * RS_MAX_BLOCKS) + words_rounded(SCAN_MAX_BLOCKS) +
+           words_rounded(16);
+}
+
+size_t pair_scratch_bytes(long long max_pairs, long long max_super)
+{
+    size_t i = (size_t)(max_pairs > 0 ? max_pairs : 1);
+    size_t chunks = (size_t)(max_pairs / CHUNK + (max_super > 0 ? max_super : 1) + 1);
+    return 4 * words_rounded(i) + words_rounded(chunks * NT_MAX);
+}
+
+size_t super_scratch_bytes(long long max_super)
+{
+    return 2 * words_rounded((size_t)(max_super > 0 ? max_super : 1) + 1);
+}
+
+long long max_super_tiles() { return MAX_SUPER; }
+
+struct Carver {
+    char *p;
+    uint32_t *take(size_t words)
+    {
+        uint32_t *r = reinterpret_cast<uint32_t *>(p);
+        p += words_rounded(words);
+        return r;
+    }
+};
+
+void entry_scratch_carve(void *mem, long long max_entries, int *status, BinScratch &b)
+{
+    size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
+    Carver c{static_cast<char *>(mem)};
+    b.vis_pos = c.take(e); b.dkA = c.take(e); b.dvA = c.take(e); b.dkB = c.take(e); b.dvB = c.take(e);
+    b.offs = c.take(e);
+    b.counts = c.take(256ull * RS_MAX_BLOCKS);
+    b.block_sums = c.take(SCAN_MAX_BLOCKS);
+    b.scalars = c.take(16);
+    b.status = status;
+}
+
+void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b)
+{
+    size_t i = (size_t)(max_pairs > 0 ? max_pairs : 1);
+    Carver c{static_cast<char *>(mem)};
+    b.skA = c.take(i); b.svA = c.take(i); b.skB = c.take(i); b.svB = c.take(i);
+    b.chunk_cnt = c.take(1);  // the per-chunk counts run to the end of the region
+}
+
+void super_scratch_carve(void *mem, long long max_super, BinScratch &b)
+{
+    Carver c{static_cast<char *>(mem)};
+    const size_t w = (size_t)(max_super > 0 ? max_super : 1) + 1;
+    b.super_start = c.take(w);
+    b.chunk_base = c.take(w);
+}
+
+}  // namespace lobe

@@ -26,6 +26,7 @@ struct lobe_ctx {
     int *status = nullptr;
     void *entry_mem = nullptr, *pair_mem = nullptr, *super_mem = nullptr;
     long long max_entries = 0, max_pairs = 0, max_super = 0;
+    size_t pair_bytes = 0;
     BinScratch bins{};
     char err[512] = {0};
 };
@@ -270,26 +271,41 @@ static lobe_status grow_entries(lobe_ctx *ctx, long long need)
     return s;
 }
 
+// The pair region also holds per-chunk counts, so its size depends on max_super as well.
 static lobe_status grow_pairs(lobe_ctx *ctx, long long need)
 {
-    lobe_status s = grow_region(ctx, ctx->pair_mem, ctx->max_pairs, need, 4096, pair_scratch_bytes, "pair");
-    if (s == LOBE_OK) pair_scratch_carve(ctx->pair_mem, ctx->max_pairs, ctx->bins);
-    return s;
+    long long n = need < 4096 ? 4096 : need;
+    if (n < ctx->max_pairs) n = ctx->max_pairs;
+    const size_t bytes = pair_scratch_bytes(n, ctx->max_super);
+    if (ctx->pair_mem && bytes <= ctx->pair_bytes && n <= ctx->max_pairs) return LOBE_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->pair_mem);
+    ctx->pair_mem = nullptr;
+    ctx->max_pairs = 0;
+    ctx->pair_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->pair_mem, bytes);
+    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "pair scratch (%lld): %s", n, cudaGetErrorString(e));
+    ctx->max_pairs = n;
+    ctx->pair_bytes = bytes;
+    pair_scratch_carve(ctx->pair_mem, n, ctx->bins);
+    return LOBE_OK;
 }
 
 static lobe_status grow_super(lobe_ctx *ctx, long long need)
 {
     lobe_status s = grow_region(ctx, ctx->super_mem, ctx->max_super, need, 1024, super_scratch_bytes, "super-tile");
-    if (s == LOBE_OK) super_scratch_carve(ctx->super_mem, ctx->bins);
+    if (s == LOBE_OK) super_scratch_carve(ctx->super_mem, ctx->max_super, ctx->bins);
+    if (s == LOBE_OK && ctx->pair_mem) s = grow_pairs(ctx, ctx->max_pairs);  // chunk counts follow max_super
     return s;
 }
 
 lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect, int64_t max_tiles)
 {
     if (!ctx || max_entries < 0 || max_isect < 0 || max_tiles < 0) return fail(ctx, LOBE_ERR_ARG, "bad reserve arguments");
+    if (max_tiles > max_super_tiles() * 64) return fail(ctx, LOBE_ERR_ARG, "max_tiles above the supported maximum");
     lobe_status s = grow_entries(ctx, max_entries);
-    if (s == LOBE_OK) s = grow_pairs(ctx, max_isect);
     if (s == LOBE_OK) s = grow_super(ctx, max_tiles);
+    if (s == LOBE_OK) s = grow_pairs(ctx, max_isect);
     return s;
 }
 
@@ -341,6 +357,8 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
         return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
     if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0)
         return fail(ctx, LOBE_ERR_ARG, "bins missing");
+    if (P.n_super > max_super_tiles())
+        return fail(ctx, LOBE_ERR_ARG, "%d super-tiles (64x64-pixel blocks) exceed %lld", P.n_super, max_super_tiles());
     if (P.n_entries > ctx->max_entries || !ctx->entry_mem || P.n_super > ctx->max_super || !ctx->super_mem ||
         !ctx->pair_mem) {
         if (!sync)

@@ -213,8 +213,10 @@ struct BinScratch {
     uint32_t *block_sums;                              // scan block totals
     uint32_t *scalars;  // [0] visible splats, [1] usable super pairs, [2] usable pairs
     uint32_t *skA, *svA, *skB, *svB;                   // [max_pairs]
-    uint32_t *sp_ids;                                  // sorted super pairs (one of svA/svB)
-    uint32_t *super_start;                             // [max_super + 1]
+    uint32_t *sp_keys, *sp_ids;                        // sorted super pairs (one of the A/B arrays)
+    uint32_t *chunk_cnt;                               // per (chunk, tile) counts, then offsets
+    uint32_t *super_start, *chunk_base;                // [max_super + 1] each
+    long long work_max;                                // bound on chunk work items of the last call
     int *status;
 };
 
@@ -236,10 +238,11 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
 cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *radius, BinScratch &b,
                           const long long *n_isect_dev, int *gauss_ids, int *tile_start, cudaStream_t st);
 size_t entry_scratch_bytes(long long max_entries);
-size_t pair_scratch_bytes(long long max_pairs);
+size_t pair_scratch_bytes(long long max_pairs, long long max_super);
 size_t super_scratch_bytes(long long max_super);
+long long max_super_tiles();  // super-tile ids must fit the 16 key bits that carry them
 void entry_scratch_carve(void *mem, long long max_entries, int *status, BinScratch &b);
 void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b);
-void super_scratch_carve(void *mem, BinScratch &b);
+void super_scratch_carve(void *mem, long long max_super, BinScratch &b);
 
 }  // namespace lobe

@@ -14,7 +14,8 @@ namespace {
 constexpr long long kMaxEntries = LOBE_NOALLOC_MAX_ENTRIES;
 constexpr long long kMaxTiles = LOBE_NOALLOC_MAX_TILES;
 constexpr long long kMaxPairs = LOBE_NOALLOC_MAX_PAIRS;
-constexpr size_t kScratchBytes = size_t(16) << 20;
+constexpr long long kMaxSuper = 8192;  // 64x64-pixel blocks; 65536 tiles make about 4100
+constexpr size_t kScratchBytes = size_t(20) << 20;
 constexpr size_t kStatusBytes = 256;
 constexpr int kMaxDevices = 64;
 
@@ -52,8 +53,8 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
     if (s != LOBE_OK) return s;
     if (!proj || (P.n_entries > 0 && (!proj->splat || !proj->radius || !proj->tiles_touched))) return LOBE_ERR_ARG;
     if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0) return LOBE_ERR_ARG;
-    if (P.n_entries > kMaxEntries || P.n_tiles > kMaxTiles) return LOBE_ERR_CAPACITY;
-    if (entry_scratch_bytes(kMaxEntries) + pair_scratch_bytes(kMaxPairs) + super_scratch_bytes(kMaxTiles) +
+    if (P.n_entries > kMaxEntries || P.n_tiles > kMaxTiles || P.n_super > kMaxSuper) return LOBE_ERR_CAPACITY;
+    if (entry_scratch_bytes(kMaxEntries) + pair_scratch_bytes(kMaxPairs, kMaxSuper) + super_scratch_bytes(kMaxSuper) +
             kStatusBytes > kScratchBytes)
         return LOBE_ERR_STATE;
 
@@ -69,8 +70,8 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
     entry_scratch_carve(p, kMaxEntries, status, b);
     p += entry_scratch_bytes(kMaxEntries);
     pair_scratch_carve(p, kMaxPairs, b);
-    p += pair_scratch_bytes(kMaxPairs);
-    super_scratch_carve(p, b);
+    p += pair_scratch_bytes(kMaxPairs, kMaxSuper);
+    super_scratch_carve(p, kMaxSuper, b);
 
     // the array keeps the previous call's contents: only the status word must start at zero
     // (every other scratch value is written before it is read)
