@@ -115,7 +115,9 @@ typedef struct {
     float bg[3];        /* background colour */
     int32_t recompute_T; /* 1: render_bwd re-derives the per-pixel state (T_final, n_contrib)
                             with a forward sweep instead of reading the saved one */
-    int32_t reserved[7];
+    int32_t px_fwd;      /* pixels per lane in render_fwd: 0 = default; 2, 4, 8 (8x8 tiles: 1, 2) */
+    int32_t px_bwd;      /* pixels per lane in render_bwd: same choices */
+    int32_t reserved[5];
 } lobe_config;
 
 /* Sizes implied by a batch under a config: out[0] = projected entries (sum over items of

@@ -64,6 +64,9 @@ static lobe_status check_config(lobe_ctx *ctx, const lobe_config *cfg)
     if (!valid_tile(cfg->tile_w, cfg->tile_h))
         return fail(ctx, LOBE_ERR_ARG, "tile %dx%d not one of 8x8, 16x16, 32x16", cfg->tile_w, cfg->tile_h);
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3) return fail(ctx, LOBE_ERR_ARG, "sh_degree %d not in 0..3", cfg->sh_degree);
+    if (!valid_px(cfg->tile_w, cfg->px_fwd) || !valid_px(cfg->tile_w, cfg->px_bwd))
+        return fail(ctx, LOBE_ERR_ARG, "pixels per lane %d/%d not supported with %dx%d tiles", cfg->px_fwd, cfg->px_bwd,
+                    cfg->tile_w, cfg->tile_h);
     return LOBE_OK;
 }
 
@@ -83,6 +86,8 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
     P.n_items = b->n_items;
     P.tw = cfg.tile_w;
     P.th = cfg.tile_h;
+    P.px_fwd = cfg.px_fwd;
+    P.px_bwd = cfg.px_bwd;
     P.sh_degree = cfg.sh_degree;
     for (int c = 0; c < 3; ++c) P.bg[c] = cfg.bg[c];
     long long goff = 0;

@@ -58,9 +58,13 @@ struct BatchParams {
     int S;                // super-tile edge in tiles
     long long n_pixels;
     int tw, th;
+    int px_fwd, px_bwd;   // pixels per lane of the render kernels (0 = default)
     int sh_degree;
     float bg[3];
 };
+
+int default_px(int tw, bool backward);
+bool valid_px(int tw, int px);
 
 // Super-tile edge (in tiles) of the two-level binning: 64 px for 8x8 and 16x16 tiles.
 __host__ __device__ inline int super_edge(int tw) { return tw == 8 ? 8 : 4; }

@@ -138,7 +138,8 @@ class Batch:
 class Context:
     """A lobe_ctx bound to a CUDA stream (the current torch stream by default)."""
 
-    def __init__(self, tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0), recompute_T=False, stream=None):
+    def __init__(self, tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0), recompute_T=False, stream=None, px_fwd=0,
+                 px_bwd=0):
         if not torch.cuda.is_available():
             raise RuntimeError("the lobe rasterizer needs a CUDA device (no CPU fallback)")
         self.lib = A.lib()
@@ -146,6 +147,7 @@ class Context:
         self.sh_degree = sh_degree
         self.bg = tuple(float(b) for b in bg)
         self.recompute_T = bool(recompute_T)
+        self.px = (int(px_fwd), int(px_bwd))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = ctypes.c_void_p()
         A.check(self.lib.lobe_ctx_create(ctypes.byref(self.handle), ctypes.c_void_p(self.stream.cuda_stream),
@@ -158,9 +160,13 @@ class Context:
         c.sh_degree = self.sh_degree
         c.bg[:] = list(self.bg)
         c.recompute_T = int(self.recompute_T)
+        c.px_fwd, c.px_bwd = self.px
         return c
 
-    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None):
+    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None, px=None):
+        """Change the configuration (tile changes need new bins; px = (fwd, bwd) pixels per lane)."""
+        if px is not None:
+            self.px = (int(px[0]), int(px[1]))
         if tile is not None:
             self.tile = tuple(tile)
         if recompute_T is not None:
