@@ -239,8 +239,8 @@ lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *stream, const lo
 lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                             const lobe_bins *bins, const lobe_image *image);
 
-/* Adjoint of lobe_render_fwd. dL_drgb has the layout of image->rgb. Reads image->rgb,
- * T_final and n_contrib unless the context has recompute_T set (then only dL_drgb).
+/* Adjoint of lobe_render_fwd. dL_drgb has the layout of image->rgb. Reads image->T_final
+ * and image->n_contrib unless the context has recompute_T set (then only dL_drgb).
  * Overwrites grad2d[entries][12] = dL/d(u, v, conic_a, conic_b, conic_c, opacity, r, g, b)
  * followed by three zeros. grad2d must be 16-byte aligned. */
 lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,

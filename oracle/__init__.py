@@ -330,6 +330,22 @@ def sh_basis(dirs, degree=3):
     return Y, dY
 
 
+class abs_sums:
+    """Context manager: while active, render_bwd also accumulates, per Gaussian, the sum of
+    the absolute values of the per-pixel terms of each 2D gradient into ``self.a``
+    ([n,12], grad2d layout: u, v, conic a, b, c, opacity, r, g, b)."""
+
+    def __init__(self, n):
+        self.a = np.zeros((n, 12))
+
+    def __enter__(self):
+        lib().orc_set_abs_out(self.a.ctypes.data_as(ctypes.c_void_p))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_abs_out(None)
+
+
 class window:
     """Context manager restricting bin/render/render_bwd to the pixel window [x0,x1) x [y0,y1)
     (a bounded sample of a large image for timing; per-pixel work is unchanged)."""

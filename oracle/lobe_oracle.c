@@ -421,6 +421,13 @@ void orc_set_window(int x0, int y0, int x1, int y1)
     g_win[0] = x0; g_win[1] = y0; g_win[2] = x1; g_win[3] = y1;
 }
 
+/* Optional per-Gaussian sums of the absolute values of the per-pixel terms that
+ * orc_render_bwd adds up ([n][12], the grad2d layout): the scale against which a float32
+ * sum of those terms can be resolved. NULL = not collected. Changes no arithmetic. */
+static double *g_abs = NULL;
+
+void orc_set_abs_out(double *a12) { g_abs = a12; }
+
 static int tile_in_window(int tx, int ty, int tw, int th)
 {
     return (tx + 1) * tw > g_win[0] && tx * tw < g_win[2] && (ty + 1) * th > g_win[1] && ty * th < g_win[3];
@@ -701,6 +708,7 @@ int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const dou
                 double dalpha = 0.0;
                 for (int ch = 0; ch < 3; ++ch) {
                     d_color[3 * g + ch] += r->alpha * r->T * gC[ch];
+                    if (g_abs) g_abs[12 * g + 6 + ch] += fabs(r->alpha * r->T * gC[ch]);
                     dalpha += r->T * (c[ch] - B[ch]) * gC[ch];
                     B[ch] = r->alpha * c[ch] + (1.0 - r->alpha) * B[ch];
                 }
@@ -713,6 +721,15 @@ int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const dou
                 d_conic[3 * g + 2] += dsig * 0.5 * r->dy * r->dy;
                 d_mean2d[2 * g + 0] += dsig * (cn[0] * r->dx + cn[1] * r->dy);
                 d_mean2d[2 * g + 1] += dsig * (cn[1] * r->dx + cn[2] * r->dy);
+                if (g_abs) {
+                    double *a = g_abs + 12 * g;
+                    a[0] += fabs(dsig * (cn[0] * r->dx + cn[1] * r->dy));
+                    a[1] += fabs(dsig * (cn[1] * r->dx + cn[2] * r->dy));
+                    a[2] += fabs(dsig * 0.5 * r->dx * r->dx);
+                    a[3] += fabs(dsig * r->dx * r->dy);
+                    a[4] += fabs(dsig * 0.5 * r->dy * r->dy);
+                    a[5] += fabs(dalpha * r->G);
+                }
             }
         }
     free(rec);

@@ -442,9 +442,9 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
         return fail(ctx, LOBE_ERR_ARG, "inputs missing");
     if (!dL_drgb || (has_e && (!grad2d || !aligned16(grad2d))))
         return fail(ctx, LOBE_ERR_ARG, "dL_drgb/grad2d missing or misaligned");
-    if (!rec && (!image || !image->rgb || !image->n_contrib))
+    if (!rec && (!image || !image->T_final || !image->n_contrib))
         return fail(ctx, LOBE_ERR_ARG, "saved forward state missing (recompute_T = 0)");
-    CUDA_TRY(launch_render_bwd(*H.p, rec, proj->splat, bins->tile_start, bins->gauss_ids, rec ? nullptr : image->rgb,
+    CUDA_TRY(launch_render_bwd(*H.p, rec, proj->splat, bins->tile_start, bins->gauss_ids, rec ? nullptr : image->T_final,
                                rec ? nullptr : image->n_contrib, dL_drgb, grad2d, ctx->stream),
              "render bwd");
     return LOBE_OK;

@@ -6,15 +6,16 @@
 //   a splat is skipped when sigma < 0 or alpha < 1/255; the walk stops, before adding, at the
 //   first splat with T (1 - alpha) < 1e-4.
 //
-// Adjoint, walked front to back (the same order and the same alpha decisions as the
-// forward, so no per-pixel list has to be reversed): with R_i = C - sum_{j<=i} c_j alpha_j T_j
-// the colour still to come after splat i (background included),
+// Adjoint, walked back to front from each pixel's last contributor with the same alpha
+// decisions as the forward: with B_i the colour seen behind splat i (B starts as the
+// background) and T_i the transmittance in front of it (recovered as T_{i+1} / (1 - alpha_i)
+// from T_final),
 //   dL/dc_i     = alpha_i T_i dL/dC
-//   dL/dalpha_i = T_i (c_i . dL/dC) - (R_i . dL/dC) / (1 - alpha_i)
-// which equals the textbook reverse-order form T_i (c_i - B_i) . dL/dC with B_i the colour
-// seen behind splat i, because T_i B_i = R_i / (1 - alpha_i). The per-pixel state it needs,
-// C (the rendered colour) and the stop position, is either read from the forward's outputs
-// ("store") or re-derived by a forward sweep inside the kernel ("recompute").
+//   dL/dalpha_i = T_i (c_i - B_i) . dL/dC,      B_{i-1} = alpha_i c_i + (1 - alpha_i) B_i.
+// B is accumulated from the back, so it keeps relative precision even deep in a long list
+// (a front-to-back form C - sum c_j w_j loses it to cancellation). The per-pixel state it
+// needs, T_final and the stop position, is either read from the forward's outputs ("store")
+// or re-derived by a forward sweep inside the kernel ("recompute").
 //
 // Work decomposition (B300): one warp walks one slab of a tile -- 32 lanes x PX pixels,
 // each lane owning PX pixels of one column -- through the tile's list in batches of 32
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 template <int TW, int TH, int PX, bool RECOMPUTE>
 __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     k_render_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
-                 const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ rgb,
+                 const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
                  const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
 {
     using G = Slab<TW, TH, PX>;
@@ -214,14 +215,16 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     const float pxc = (float)px + 0.5f;
     const int start = tile_start[t], end = tile_start[t + 1];
     const long long HW = (long long)I.W * I.H;
-    float pyc[PX], g0[PX], g1[PX], g2[PX], R0[PX], R1[PX], R2[PX], T[PX];
+    // per pixel: dL/dC, the colour seen behind the current splat (B, background included),
+    // the transmittance after it (T, starting from T_final) and the stop position
+    float pyc[PX], g0[PX], g1[PX], g2[PX], B0[PX], B1[PX], B2[PX], T[PX];
     int nc[PX];
     bool inside[PX];
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
         pyc[k] = (float)(py0 + k) + 0.5f;
         inside[k] = px < I.W && py0 + k < I.H;
-        g0[k] = g1[k] = g2[k] = R0[k] = R1[k] = R2[k] = 0.0f;
+        g0[k] = g1[k] = g2[k] = 0.0f;
         T[k] = 1.0f;
         nc[k] = 0;
         if (inside[k]) {
@@ -231,10 +234,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
             g1[k] = d[HW + p];
             g2[k] = d[2 * HW + p];
             if (!RECOMPUTE) {
-                const float *c = rgb + 3 * I.pix_off;
-                R0[k] = c[p];
-                R1[k] = c[HW + p];
-                R2[k] = c[2 * HW + p];
+                T[k] = Tfin[I.pix_off + p];
                 nc[k] = ncin[I.pix_off + p];
             }
         }
@@ -242,15 +242,17 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     if (RECOMPUTE) {
         bool live[PX];
 #pragma unroll
-        for (int k = 0; k < PX; ++k) live[k] = inside[k];
-        forward_sweep<PX>(splat, ids, start, end, pxc, pyc, live, T, R0, R1, R2, nc, st);
-#pragma unroll
         for (int k = 0; k < PX; ++k) {
-            R0[k] += T[k] * P.bg[0];
-            R1[k] += T[k] * P.bg[1];
-            R2[k] += T[k] * P.bg[2];
-            T[k] = 1.0f;
+            live[k] = inside[k];
+            B0[k] = B1[k] = B2[k] = 0.0f;  // colour accumulators of the sweep (unused after it)
         }
+        forward_sweep<PX>(splat, ids, start, end, pxc, pyc, live, T, B0, B1, B2, nc, st);
+    }
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        B0[k] = P.bg[0];
+        B1[k] = P.bg[1];
+        B2[k] = P.bg[2];
     }
     int m = 0;
 #pragma unroll
@@ -258,17 +260,19 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
     const int stop = min(start + m, end);
 
+    // walk the list back to front in batches of 32, prefetching the batch below
+    int top = stop, base = max(start, stop - 32);
     Staged nx;
-    fetch(splat, ids, start + lane, stop, nx);
-    for (int base = start; base < stop; base += 32) {
+    fetch(splat, ids, base + lane, top, nx);
+    while (top > start) {
         st.s0[lane] = nx.s0;
         st.s1[lane] = nx.s1;
         st.s2[lane] = nx.s2;
         st.id[lane] = nx.id;
         __syncwarp();
-        fetch(splat, ids, base + 32 + lane, stop, nx);
-        const int cnt = min(32, stop - base);
-        for (int j = 0; j < cnt; ++j) {
+        const int nbase = max(start, base - 32);
+        fetch(splat, ids, nbase + lane, base, nx);
+        for (int j = top - base - 1; j >= 0; --j) {
             const float4 q0 = st.s0[j], q1 = st.s1[j];
             const float cb = st.s2[j].x, pmin = st.s2[j].y;
             const int pos = base - start + j;
@@ -281,17 +285,16 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
                 const PairEval r = pair_eval(cl, q0.y, q1.x, q1.y, pmin, pyc[k]);
                 if (!r.use) continue;
                 any = true;
-                const float w = r.alpha * T[k];
+                const float Ti = __fdividef(T[k], 1.0f - r.alpha);  // transmittance in front of it
+                const float w = r.alpha * Ti;
                 dr += w * g0[k];
                 dg += w * g1[k];
                 db += w * g2[k];
-                R0[k] -= q1.z * w;
-                R1[k] -= q1.w * w;
-                R2[k] -= cb * w;
-                const float gc = g0[k] * q1.z + g1[k] * q1.w + g2[k] * cb;
-                const float gR = g0[k] * R0[k] + g1[k] * R1[k] + g2[k] * R2[k];
-                const float dalpha = T[k] * gc - __fdividef(gR, 1.0f - r.alpha);
-                T[k] = next_T(T[k], r.alpha);
+                const float dalpha = Ti * (g0[k] * (q1.z - B0[k]) + g1[k] * (q1.w - B1[k]) + g2[k] * (cb - B2[k]));
+                B0[k] = fmaf(r.alpha, q1.z - B0[k], B0[k]);
+                B1[k] = fmaf(r.alpha, q1.w - B1[k], B1[k]);
+                B2[k] = fmaf(r.alpha, cb - B2[k], B2[k]);
+                T[k] = Ti;
                 if (!r.clamped) {
                     dop += dalpha * r.G;
                     const float dp2 = dalpha * r.alpha * LN2;
@@ -326,6 +329,8 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
             }
         }
         __syncwarp();
+        top = base;
+        base = nbase;
     }
 }
 

@@ -33,6 +33,28 @@ def rect_tiles(mean2d, radius, cam, tile):
     return t
 
 
+def rect_of(mean2d, radius, cam, tile):
+    """[n,4] tile rectangles (x0, y0, x1, y1) from float32 u, v and integer r (exact)."""
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    gx = -(-c["width"] // tile[0])
+    gy = -(-c["height"] // tile[1])
+    u = mean2d[:, 0].astype(np.float32).astype(np.float64)
+    v = mean2d[:, 1].astype(np.float32).astype(np.float64)
+    r = radius.astype(np.float64)
+    out = np.stack([np.clip(np.floor((u - r) / tile[0]), 0, gx), np.clip(np.floor((v - r) / tile[1]), 0, gy),
+                    np.clip(np.ceil((u + r) / tile[0]), 0, gx), np.clip(np.ceil((v + r) / tile[1]), 0, gy)], 1)
+    out[radius <= 0] = 0
+    return out.astype(np.int32)
+
+
+def differing_rects(p: oracle.Projection, gpu_mean2d, gpu_radius, cam, tile) -> np.ndarray:
+    """Gaussians whose tile rectangle differs between the GPU projection and the oracle's
+    (float32 took a marginal radius / rectangle / culling decision the other way)."""
+    a = rect_of(gpu_mean2d, gpu_radius, cam, tile)
+    b = np.where((p.radius > 0)[:, None], p.rect, 0)
+    return np.any(a != b, axis=1)
+
+
 def splat_array(p: oracle.Projection) -> np.ndarray:
     s = np.zeros((p.n, 12), np.float32)
     s[:, 0:2] = p.mean2d
@@ -50,6 +72,21 @@ def grad_rel_err(gpu, orc):
         return 0.0
     floor = GRAD_FLOOR * max(np.abs(orc).max(), 1e-30)
     return float((np.abs(gpu - orc) / np.maximum(np.abs(orc), floor)).max())
+
+
+SUM_FLOOR = 3e-3
+
+
+def sum_rel_err(gpu, orc, abs_sum):
+    """Relative error of a float32 sum: |gpu - oracle| / max(|oracle|, 3e-3 * sum|terms|).
+    Where the terms cancel (|oracle| much smaller than sum|terms|) float32 arithmetic can only
+    resolve the result to some ulps of sum|terms|; the floor grants 3e-6 of it (about 25 ulps)
+    at the 1e-3 tolerance, and nothing more."""
+    gpu = np.asarray(gpu, np.float64)
+    orc = np.asarray(orc, np.float64)
+    den = np.maximum(np.abs(orc), SUM_FLOOR * np.asarray(abs_sum, np.float64))
+    den = np.maximum(den, 1e-30)
+    return float((np.abs(gpu - orc) / den).max()) if orc.size else 0.0
 
 
 def assert_grad_close(gpu, orc, name, rtol=GRAD_RTOL):

@@ -2,10 +2,14 @@
 
 The oracle cannot composite whole 1600x1066 / 1920x1080 views in seconds, so it renders
 sampled windows of pixels (every Gaussian projected, only the windows' tiles binned and
-composited) and the comparison runs on those: per-tile lists of the windows' tiles
-(bit-exact once marginal Gaussians are removed), pixel values (max-abs 1e-4), and -- with
-dL/dC nonzero only inside the windows -- every parameter gradient (relative 1e-3), since the
-adjoint of a sparse dL/dC is exactly the oracle's windowed backward.
+composited) and the comparison runs on those:
+- end to end (GPU projection -> GPU bins -> GPU image vs the FP64 oracle): per-tile lists of
+  the windows' tiles, bit-exact once the few Gaussians whose tile rectangles came out
+  differently in float32 are removed, and pixel values, max-abs 1e-4;
+- the composite adjoint, with dL/dC nonzero only inside the windows (its adjoint is exactly
+  the oracle's windowed backward), on the GPU's own float32 splats: per-splat 2D gradients,
+  relative 1e-3 of each float32 sum, floored at 1e-3 of the sum of its terms' magnitudes;
+- the projection adjoint fed the oracle's 2D gradients: every parameter gradient, relative 1e-3.
 """
 import numpy as np
 import pytest
@@ -13,7 +17,7 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import IMG_ATOL, grad_rel_err
+from tests.helpers import IMG_ATOL, differing_rects, grad_rel_err, oracle_grad2d_array, rect_of, sum_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -32,19 +36,30 @@ def windows_of(cam, n=3, size=32, seed=0):
     return out
 
 
-def check_item(g64, cam, tile, gpu_rgb, gpu_ids, gpu_ts, tile_off, entry_off, wins, grads_gpu=None, crop=None,
-               aabb=None, dL_full=None):
-    """Compare one item's windows against the oracle. Returns pixels compared."""
+def only_differing(p, diff):
+    """The projection with the rectangle flag kept only on Gaussians whose rectangles differ."""
+    q = oracle.Projection(p.mean2d, p.conic, p.color, p.opacity, p.depth, p.radius, p.rect,
+                          np.where(diff, oracle.F_RECT, 0).astype(np.int32), p.radius_all)
+    return q
+
+
+def check_item(g64, cam, tile, gpu_rgb, gpu_ids, gpu_ts, tile_off, entry_off, wins, gpu_splat, gpu_radius, crop=None):
+    """Compare one item's windows against the oracle. Returns (oracle projection, pixel
+    flags of the windows, pixels compared)."""
     W, H = cam["width"], cam["height"]
     p = oracle.project(g64, cam, tile, crop=crop, margins=oracle.MARGINS_E2E)
-    marg = (p.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) != 0
+    marg = differing_rects(p, gpu_splat[:, 0:2], gpu_radius, cam, tile)
+    assert marg.mean() < 1e-3
+    pm = only_differing(p, marg)
     gx = (W + tile[0] - 1) // tile[0]
     compared = 0
+    pxf_all = np.zeros((H, W), np.int32)
     for (x0, y0, x1, y1) in wins:
         with oracle.window(x0, y0, x1, y1):
             ids, ts = oracle.bin_sort(p, cam, tile)
-            pxf = oracle.flag_pixels(p, cam, tile)
+            pxf = oracle.flag_pixels(pm, cam, tile)
             img = oracle.render_fwd(p, ids, ts, cam, tile, (0, 0, 0), oracle.MARGINS_E2E, pxf)
+        pxf_all |= img.flags
         for ty in range(y0 // tile[1], (y1 + tile[1] - 1) // tile[1]):
             for tx in range(x0 // tile[0], (x1 + tile[0] - 1) // tile[0]):
                 t = ty * gx + tx
@@ -56,7 +71,7 @@ def check_item(g64, cam, tile, gpu_rgb, gpu_ids, gpu_ts, tile_off, entry_off, wi
         d = np.abs(gpu_rgb[:, y0:y1, x0:x1] - img.rgb[:, y0:y1, x0:x1])[:, ok]
         assert d.max() <= IMG_ATOL, d.max()
         compared += int(ok.sum())
-    return p, compared
+    return p, marg, pxf_all, compared
 
 
 def windowed_backward(g64, cam, tile, p, dL, wins, crop=None, aabb=None):
@@ -95,22 +110,45 @@ def run_single(wl, crop=None, n_win=3):
     rgb = img.rgb.view(3, cam["height"], cam["width"]).cpu().numpy()
     g64 = oracle.set_dict(g)
     wins = windows_of(cam, n_win)
-    p, n = check_item(g64, cam, tile, rgb, bins.ids().cpu().numpy(), bins.tile_start.cpu().numpy(), 0, 0, wins,
-                      crop=crop)
+    p, marg, pxf, n = check_item(g64, cam, tile, rgb, bins.ids().cpu().numpy(), bins.tile_start.cpu().numpy(), 0, 0,
+                                 wins, proj.splat.cpu().numpy(), proj.radius.cpu().numpy(), crop=crop)
     assert n > 0.9 * n_win * 32 * 32
     # gradients from a dL/dC that is nonzero only on the windows' unflagged pixels
-    pxf = np.zeros((cam["height"], cam["width"]), np.int32)
+    aabb = wl.blocks[0] if wl.blocks else None
+    # composite adjoint at full size, on the GPU's own float32 splats (the oracle composites and
+    # differentiates the same splats in FP64): per-splat 2D gradients, each a float32 sum over
+    # up to thousands of pixels
+    sp = proj.splat.cpu().numpy().astype(np.float64)
+    rad = proj.radius.cpu().numpy()
+    pg = oracle.Projection(sp[:, 0:2].copy(), sp[:, 2:5].copy(), sp[:, 6:9].copy(), sp[:, 5].copy(),
+                           sp[:, 9].copy(), rad.copy(), rect_of(sp[:, 0:2], rad, cam, tile), np.zeros_like(rad),
+                           rad.copy())
+    pxf_s = np.zeros_like(pxf)
     for (x0, y0, x1, y1) in wins:
         with oracle.window(x0, y0, x1, y1):
-            ids, ts = oracle.bin_sort(p, cam, tile)
-            pxf |= oracle.render_fwd(p, ids, ts, cam, tile, (0, 0, 0), oracle.MARGINS_E2E,
-                                     oracle.flag_pixels(p, cam, tile)).flags
-    dL = sparse_dL(cam, wins, pxf == 0)
-    aabb = wl.blocks[0] if wl.blocks else None
-    want = windowed_backward(g64, cam, tile, p, dL.astype(np.float64), wins, crop=crop, aabb=aabb)
+            ids, ts = oracle.bin_sort(pg, cam, tile)
+            pxf_s |= oracle.render_fwd(pg, ids, ts, cam, tile, (0, 0, 0), oracle.MARGINS_STAGE).flags
+    dL = sparse_dL(cam, wins, (pxf == 0) & (pxf_s == 0))
+    with oracle.abs_sums(g.n) as A:
+        tot = None
+        for (x0, y0, x1, y1) in wins:
+            with oracle.window(x0, y0, x1, y1):
+                ids, ts = oracle.bin_sort(pg, cam, tile)
+                g2 = oracle.render_bwd(pg, ids, ts, cam, dL.astype(np.float64), tile)
+            tot = g2 if tot is None else oracle.Grad2D(tot.mean2d + g2.mean2d, tot.conic + g2.conic,
+                                                       tot.color + g2.color, tot.opacity + g2.opacity)
+    want2 = oracle_grad2d_array(tot)
     g2d = lobe.render_bwd(ctx, batch, proj, bins, img, torch.as_tensor(dL).cuda().reshape(-1))
-    grads = lobe.project_bwd(ctx, batch, proj, g2d)
-    ok = (p.flags == 0) & (p.radius > 0)
+    ok = ~marg & ((p.flags & oracle.F_COLOR) == 0) & (p.radius > 0)
+    got2 = g2d.cpu().numpy()
+    assert (np.abs(want2[ok, :9]).sum(1) > 0).sum() > 50
+    for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                       ("color", slice(6, 9))]:
+        err = sum_rel_err(got2[ok, cols], want2[ok, cols], A.a[ok, cols])
+        assert err <= 1e-3, (name, err)
+    # projection adjoint at full size, fed the oracle's 2D gradients
+    want = oracle.project_bwd(g64, cam, tot, tile, crop=crop, aabb=aabb)
+    grads = lobe.project_bwd(ctx, batch, proj, torch.as_tensor(want2, dtype=torch.float32).cuda())
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
         err = grad_rel_err(grads[0][k].cpu().numpy()[ok], getattr(want, k)[ok])
         assert err <= 1e-3, (k, err)
@@ -151,9 +189,13 @@ def test_fullsize_multi_block_batched_graph_items():
     ts = st.bins.tile_start.cpu().numpy()
     _, toffs = st.batch.tiles(tile)
     views = st.images()
+    splat = st.proj.splat.cpu().numpy()
+    radius = st.proj.radius.cpu().numpy()
     for i in (0, len(wl.items) - 1):
         s, c, b = wl.items[i]
         cam = cams[c]
         g64 = oracle.set_dict(wl.sets[s])
         wins = windows_of(cam, 2, seed=i)
-        check_item(g64, cam, tile, views[i].cpu().numpy(), ids, ts, toffs[i], st.batch.entry_off[i], wins)
+        e0, n = st.batch.entry_off[i], wl.sets[s].n
+        check_item(g64, cam, tile, views[i].cpu().numpy(), ids, ts, toffs[i], e0, wins, splat[e0:e0 + n],
+                   radius[e0:e0 + n])
