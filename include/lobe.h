@@ -127,7 +127,9 @@ lobe_status lobe_batch_sizes(const lobe_config *cfg, const lobe_batch *batch, in
 /* Projected splats, one entry per (item, Gaussian): entry = item_entry_offset + g, where
  * item_entry_offset is the sum of the set sizes of the preceding items.
  *   splat[e][0..11] = u, v, conic_a, conic_b, conic_c, opacity, r, g, b, depth, 0, 0
- *     (conic = inverse 2D covariance [[a,b],[b,c]]; depth = camera-space z rounded to fp32)
+ *     (conic = inverse 2D covariance [[a,b],[b,c]]; depth = camera-space z rounded to fp32;
+ *     r, g, b = max(0, SH + 0.5), a clamped channel stored as -0.0 so that lobe_project_bwd
+ *     can mask its gradient by the forward's own decision)
  *   radius[e]        = ceil(3 sqrt(lambda_max)), 0 when culled (splat then undefined)
  *   tiles_touched[e] = number of tiles in the splat's tile rectangle, 0 when culled
  * splat must be 16-byte aligned. */
@@ -248,7 +250,8 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
                             float *grad2d);
 
 /* Adjoint of lobe_project: chain rule from grad2d to the raw parameters of every set,
- * summed over the set's items. grads[s] belongs to batch->sets[s]. accumulate = 0
+ * summed over the set's items. proj must be the output of lobe_project for this batch (the
+ * colour clamp is read from the sign of the stored colour). grads[s] belongs to batch->sets[s]. accumulate = 0
  * overwrites the parameter gradients, 1 adds to them; sd_acc/sd_cnt always accumulate. */
 lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                              const float *grad2d, const lobe_grads *grads, int32_t accumulate);

@@ -75,9 +75,16 @@ struct World {
     float mx, my, mz;
     float qw, qx, qy, qz, qinv;  // normalised quaternion and 1/|q|
     float s[3];
-    float R[9];
     float Sig[6];  // 00 01 02 11 12 22
 };
+
+// Rotation matrix (row-major) of the unit quaternion (r, x, y, z).
+__device__ __forceinline__ void rotation(float r, float x, float y, float z, float R[9])
+{
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - r * z);       R[2] = 2.f * (x * z + r * y);
+    R[3] = 2.f * (x * y + r * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - r * x);
+    R[6] = 2.f * (x * z - r * y);       R[7] = 2.f * (y * z + r * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
 
 __device__ __forceinline__ void load_world(const SetParams &S, long long g, World &w)
 {
@@ -89,13 +96,11 @@ __device__ __forceinline__ void load_world(const SetParams &S, long long g, Worl
     w.qinv = rsqrtf(qn);
     w.qw = q.x * w.qinv; w.qx = q.y * w.qinv; w.qy = q.z * w.qinv; w.qz = q.w * w.qinv;
     for (int i = 0; i < 3; ++i) w.s[i] = __expf(S.log_scales[3 * g + i]);
-    float x = w.qx, y = w.qy, z = w.qz, r = w.qw;
-    w.R[0] = 1.f - 2.f * (y * y + z * z); w.R[1] = 2.f * (x * y - r * z);       w.R[2] = 2.f * (x * z + r * y);
-    w.R[3] = 2.f * (x * y + r * z);       w.R[4] = 1.f - 2.f * (x * x + z * z); w.R[5] = 2.f * (y * z - r * x);
-    w.R[6] = 2.f * (x * z - r * y);       w.R[7] = 2.f * (y * z + r * x);       w.R[8] = 1.f - 2.f * (x * x + y * y);
+    float R[9];
+    rotation(w.qw, w.qx, w.qy, w.qz, R);
     float M[9];
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) M[3 * i + j] = w.R[3 * i + j] * w.s[j];
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * w.s[j];
     w.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
     w.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
     w.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
@@ -103,6 +108,11 @@ __device__ __forceinline__ void load_world(const SetParams &S, long long g, Worl
     w.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     w.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
 }
+
+// colour = max(0, raw). A clamped channel is stored as -0.0: it composites exactly like +0.0,
+// and its sign bit carries the clamp decision to the adjoint (gradient passes iff raw >= 0).
+__device__ __forceinline__ float clamp_color(float raw) { return raw < 0.f ? -0.0f : raw; }
+__device__ __forceinline__ bool color_clamped(float stored) { return (__float_as_uint(stored) >> 31) != 0; }
 
 // Camera-dependent part of the projection. Returns false when culled.
 struct Cam2D {
@@ -168,7 +178,7 @@ __device__ __forceinline__ bool project_cam(const BatchParams &P, const ItemPara
 
 // --------------------------------------------------------------------------- forward
 
-__global__ void __launch_bounds__(256) k_project_fwd(const __grid_constant__ BatchParams P, float4 *__restrict__ splat,
+__global__ void __launch_bounds__(256, 4) k_project_fwd(const __grid_constant__ BatchParams P, float4 *__restrict__ splat,
                                                      int *__restrict__ radius, int *__restrict__ tiles)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,9 +189,10 @@ __global__ void __launch_bounds__(256) k_project_fwd(const __grid_constant__ Bat
     const bool cropped = S.crop != nullptr && S.crop[g] == 0;
     World w;
     if (!cropped) load_world(S, g, w);
-    float sh[48];
-    bool sh_loaded = false;
+    const float4 *shg = reinterpret_cast<const float4 *>(S.sh + 48 * g);
+    const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
     float opacity = 0.0f;
+    bool first = true;
     for (int k = 0; k < S.item_count; ++k) {
         const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
         const long long e = I.entry_off + g;
@@ -191,35 +202,31 @@ __global__ void __launch_bounds__(256) k_project_fwd(const __grid_constant__ Bat
             tiles[e] = 0;
             continue;
         }
-        if (!sh_loaded) {
-            const float4 *src = reinterpret_cast<const float4 *>(S.sh + 48 * g);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                float4 q = src[i];
-                sh[4 * i + 0] = q.x; sh[4 * i + 1] = q.y; sh[4 * i + 2] = q.z; sh[4 * i + 3] = q.w;
-            }
+        if (first) {
             opacity = 1.0f / (1.0f + __expf(-S.logits[g]));
-            sh_loaded = true;
+            first = false;
         }
         float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
         float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Pp[16];
         sh_poly(P.sh_degree, dx * il, dy * il, dz * il, Pp);
-        const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
+        // colour: the coefficients stream from memory per view (cache hits after the first view)
         float col[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            if (b < nb) {
-                float y = kSH[b] * Pp[b];
-                col[0] += y * sh[3 * b + 0];
-                col[1] += y * sh[3 * b + 1];
-                col[2] += y * sh[3 * b + 2];
+        for (int i = 0; i < 12; ++i) {
+            if (4 * i >= 3 * nb) break;
+            const float4 q = shg[i];
+            const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int idx = 4 * i + m, b = idx / 3;
+                if (b < nb) col[idx % 3] += kSH[b] * Pp[b] * qv[m];
             }
         }
         float4 *o = splat + 3 * e;
         o[0] = make_float4(c.u, c.v, c.ca, c.cb);
-        o[1] = make_float4(c.cc, opacity, fmaxf(0.f, col[0] + 0.5f), fmaxf(0.f, col[1] + 0.5f));
-        o[2] = make_float4(fmaxf(0.f, col[2] + 0.5f), c.z, 0.f, 0.f);
+        o[1] = make_float4(c.cc, opacity, clamp_color(col[0] + 0.5f), clamp_color(col[1] + 0.5f));
+        o[2] = make_float4(clamp_color(col[2] + 0.5f), c.z, 0.f, 0.f);
         radius[e] = c.radius;
         tiles[e] = (c.x1 - c.x0) * (c.y1 - c.y0);
     }
@@ -254,196 +261,263 @@ __global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ Batc
 //   q -> R (normalised quaternion), then through the normalisation
 //   colour = max(0, SH + 0.5): masked where the raw value is negative; the view direction
 //   mu - campos carries a gradient to mu through the normalisation.
-// Per-view contributions to dL/dSigma (6 values), dL/dmu, dL/dlogit and dL/dsh are summed in
-// registers over the set's items; the Sigma -> (s, q) step runs once per Gaussian.
+// Per-view contributions to dL/dSigma (6 values), dL/dmu and dL/dlogit are summed in registers
+// over the set's items, the 48 SH gradients in a padded shared-memory row per thread; the
+// Sigma -> (s, q) step runs once per Gaussian. A block takes 64 consecutive Gaussians (one
+// contiguous 12 KB range of SH coefficients and of SH gradients per set): it first finds which
+// of them some item sees, stages their SH coefficients into shared memory with coalesced loads,
+// runs the per-Gaussian chain rule, then writes the SH gradients back with coalesced stores. In
+// accumulate mode a Gaussian no item sees is left untouched.
 
-__global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
-                                                     const int *__restrict__ radius,
-                                                     const float4 *__restrict__ grad2d, int accumulate)
+constexpr int PB_THREADS = 64;
+constexpr int PB_ROW = 49;  // odd row stride: the per-thread rows fall in distinct banks
+
+// Walks the sets in step with an increasing Gaussian index (blocks may straddle set boundaries).
+struct SetCursor {
+    int s;
+    long long end;
+    __device__ SetCursor(const BatchParams &P, long long t0) : s(set_of_gauss(P, t0)) { end = end_of(P); }
+    __device__ long long end_of(const BatchParams &P) const { return s + 1 < P.n_sets ? P.set[s + 1].gauss_off : P.n_gauss; }
+    __device__ void seek(const BatchParams &P, long long t)
+    {
+        while (t >= end) {
+            ++s;
+            end = end_of(P);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(PB_THREADS, 8)
+    k_project_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                  const int *__restrict__ radius, const float4 *__restrict__ grad2d, int accumulate)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P.n_gauss) return;
-    const int s = set_of_gauss(P, t);
+    __shared__ float s_sh[PB_THREADS * PB_ROW];
+    __shared__ float s_gsh[PB_THREADS * PB_ROW];
+    __shared__ unsigned char s_any[PB_THREADS];
+    const long long t0 = (long long)blockIdx.x * PB_THREADS;
+    const long long t = t0 + threadIdx.x;
+    const int nblk = (int)(P.n_gauss - t0 < PB_THREADS ? P.n_gauss - t0 : PB_THREADS);
+    const bool valid = threadIdx.x < nblk;
+    const int s = valid ? set_of_gauss(P, t) : 0;
     const SetParams &S = P.set[s];
     const long long g = t - S.gauss_off;
-    float gmu[3] = {0.f, 0.f, 0.f};
-    float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float glogit = 0.f;
-    float gsh[48];
+    bool any = false;
+    if (valid)
+        for (int k = 0; k < S.item_count && !any; ++k)
+            any = radius[P.item[P.set_items[S.item_begin + k]].entry_off + g] > 0;
+    s_any[threadIdx.x] = any ? 1 : 0;
+    World w;
+    if (any) load_world(S, g, w);  // in flight while the block stages its SH coefficients
+    float *gsh = s_gsh + threadIdx.x * PB_ROW;
+    const float *shr = s_sh + threadIdx.x * PB_ROW;
 #pragma unroll
     for (int i = 0; i < 48; ++i) gsh[i] = 0.f;
-    float sd_acc = 0.f;
-    int sd_cnt = 0;
-    bool any = false;
-    World w;
-    float sh[48];
-    for (int k = 0; k < S.item_count; ++k) {
-        const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
-        const long long e = I.entry_off + g;
-        if (radius[e] <= 0) continue;
-        if (!any) {
-            load_world(S, g, w);
-            const float4 *src = reinterpret_cast<const float4 *>(S.sh + 48 * g);
+    __syncthreads();
+    const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
+    {
+        // all loads first (no load waits on another), then the shared-memory stores
+        SetCursor cur(P, t0);
+        const int per = (3 * nb + 3) / 4;  // float4 chunks holding the used coefficients
+        const int total = nblk * per;       // <= 12 * PB_THREADS
+        float4 q[12];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                float4 q = src[i];
-                sh[4 * i + 0] = q.x; sh[4 * i + 1] = q.y; sh[4 * i + 2] = q.z; sh[4 * i + 3] = q.w;
-            }
-            any = true;
-        }
-        Cam2D c;
-        project_cam(P, I, w, c);  // recompute the forward intermediates (visible by radius > 0)
-        const float4 g0 = grad2d[3 * e + 0], g1 = grad2d[3 * e + 1], g2 = grad2d[3 * e + 2];
-        const float du = g0.x, dv = g0.y, da = g0.z, db = g0.w, dc = g1.x, dop = g1.y;
-        const float dcol[3] = {g1.z, g1.w, g2.x};
-        const float4 sp1 = splat[3 * e + 1];
-        const float o = sp1.y;
-        glogit += dop * o * (1.f - o);
-        // ---- colour / SH
-        float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
-        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-        float nx = dx * il, ny = dy * il, nz = dz * il;
-        float Pp[16];
-        sh_poly(P.sh_degree, nx, ny, nz, Pp);
-        const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
-        float raw[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int b = 0; b < 16; ++b)
-            if (b < nb)
-                for (int ch = 0; ch < 3; ++ch) raw[ch] += kSH[b] * Pp[b] * sh[3 * b + ch];
-        float dn[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            if (raw[ch] + 0.5f < 0.f) continue;
-            const float d = dcol[ch];
-#pragma unroll
-            for (int b = 0; b < 16; ++b) {
-                if (b < nb) {
-                    gsh[3 * b + ch] += kSH[b] * Pp[b] * d;
-                    if (b > 0) {
-                        float ax, ay, az;
-                        sh_poly_grad(b, nx, ny, nz, ax, ay, az);
-                        float f = kSH[b] * sh[3 * b + ch] * d;
-                        dn[0] += f * ax; dn[1] += f * ay; dn[2] += f * az;
-                    }
+        for (int r = 0; r < 12; ++r) {
+            const int j = threadIdx.x + r * PB_THREADS;
+            q[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < total) {
+                const int gi = j / per, c = j - gi * per;
+                if (s_any[gi]) {
+                    cur.seek(P, t0 + gi);
+                    const SetParams &Sg = P.set[cur.s];
+                    q[r] = reinterpret_cast<const float4 *>(Sg.sh + 48 * (t0 + gi - Sg.gauss_off))[c];
                 }
             }
         }
-        float ndn = nx * dn[0] + ny * dn[1] + nz * dn[2];
-        gmu[0] += (dn[0] - nx * ndn) * il;
-        gmu[1] += (dn[1] - ny * ndn) * il;
-        gmu[2] += (dn[2] - nz * ndn) * il;
-        // ---- conic -> cov2d
-        const float ca = c.ca, cb = c.cb, cc = c.cc;
-        const float hb = 0.5f * db;
-        const float CG00 = ca * da + cb * hb, CG01 = ca * hb + cb * dc;
-        const float CG10 = cb * da + cc * hb, CG11 = cb * hb + cc * dc;
-        const float H00 = -(CG00 * ca + CG01 * cb);
-        const float H01 = -(CG00 * cb + CG01 * cc);
-        const float H11 = -(CG10 * cb + CG11 * cc);
-        // ---- cov2d = T Sigma T^T
-        float dT0[3], dT1[3];
-        for (int i = 0; i < 3; ++i) {
-            dT0[i] = 2.f * (H00 * c.ST0[i] + H01 * c.ST1[i]);
-            dT1[i] = 2.f * (H01 * c.ST0[i] + H11 * c.ST1[i]);
-        }
-        // dSigma = H00 T0 T0^T + H01 (T0 T1^T + T1 T0^T) + H11 T1 T1^T
-        {
-            const float *a = c.T0, *b = c.T1;
-            gSig[0] += H00 * a[0] * a[0] + 2.f * H01 * a[0] * b[0] + H11 * b[0] * b[0];
-            gSig[1] += H00 * a[0] * a[1] + H01 * (a[0] * b[1] + b[0] * a[1]) + H11 * b[0] * b[1];
-            gSig[2] += H00 * a[0] * a[2] + H01 * (a[0] * b[2] + b[0] * a[2]) + H11 * b[0] * b[2];
-            gSig[3] += H00 * a[1] * a[1] + 2.f * H01 * a[1] * b[1] + H11 * b[1] * b[1];
-            gSig[4] += H00 * a[1] * a[2] + H01 * (a[1] * b[2] + b[1] * a[2]) + H11 * b[1] * b[2];
-            gSig[5] += H00 * a[2] * a[2] + 2.f * H01 * a[2] * b[2] + H11 * b[2] * b[2];
-        }
-        // ---- T = J W  ->  J entries
-        const float *V = I.V;
-        const float dJ00 = dT0[0] * V[0] + dT0[1] * V[1] + dT0[2] * V[2];
-        const float dJ02 = dT0[0] * V[8] + dT0[1] * V[9] + dT0[2] * V[10];
-        const float dJ11 = dT1[0] * V[4] + dT1[1] * V[5] + dT1[2] * V[6];
-        const float dJ12 = dT1[0] * V[8] + dT1[1] * V[9] + dT1[2] * V[10];
-        const float iz = 1.f / c.z, iz2 = iz * iz, iz3 = iz2 * iz;
-        const float fx = I.fx, fy = I.fy;
-        float dpx = du * fx * iz - dJ02 * fx * iz2;
-        float dpy = dv * fy * iz - dJ12 * fy * iz2;
-        float dpz = -du * fx * c.x * iz2 - dv * fy * c.y * iz2 - dJ00 * fx * iz2 + dJ02 * 2.f * fx * c.x * iz3 -
-                    dJ11 * fy * iz2 + dJ12 * 2.f * fy * c.y * iz3;
-        gmu[0] += V[0] * dpx + V[4] * dpy + V[8] * dpz;
-        gmu[1] += V[1] * dpx + V[5] * dpy + V[9] * dpz;
-        gmu[2] += V[2] * dpx + V[6] * dpy + V[10] * dpz;
-        // ---- selective densification statistic (Sec. 3.3)
-        if (w.mx >= I.lo[0] && w.mx < I.hi[0] && w.my >= I.lo[1] && w.my < I.hi[1] && w.mz >= I.lo[2] &&
-            w.mz < I.hi[2]) {
-            float a = du * 0.5f * (float)I.W, b = dv * 0.5f * (float)I.H;
-            sd_acc += sqrtf(a * a + b * b);
-            sd_cnt += 1;
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int j = threadIdx.x + r * PB_THREADS;
+            if (j < total) {
+                const int gi = j / per, c = j - gi * per;
+                float *d = s_sh + gi * PB_ROW + 4 * c;
+                d[0] = q[r].x; d[1] = q[r].y; d[2] = q[r].z; d[3] = q[r].w;
+            }
         }
     }
-    // ---- Sigma -> (log_s, q) once per Gaussian
+    __syncthreads();
+    float gmu[3] = {0.f, 0.f, 0.f};
     float gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+    float glogit = 0.f;
+    float sd_acc = 0.f;
+    int sd_cnt = 0;
     if (any) {
-        // gSig holds the entries G_kl (k <= l) of the symmetric full-matrix gradient T^T H T
-        float D[9] = {gSig[0], gSig[1], gSig[2], gSig[1], gSig[3], gSig[4], gSig[2], gSig[4], gSig[5]};
-        float M[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) M[3 * i + j] = w.R[3 * i + j] * w.s[j];
-        float dM[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                dM[3 * i + j] = 2.f * (D[3 * i + 0] * M[0 + j] + D[3 * i + 1] * M[3 + j] + D[3 * i + 2] * M[6 + j]);
-        float dR[9];
-        for (int j = 0; j < 3; ++j) {
-            float ds = dM[j] * w.R[j] + dM[3 + j] * w.R[3 + j] + dM[6 + j] * w.R[6 + j];
-            gls[j] = ds * w.s[j];
-            dR[j] = dM[j] * w.s[j];
-            dR[3 + j] = dM[3 + j] * w.s[j];
-            dR[6 + j] = dM[6 + j] * w.s[j];
-        }
-        const float r = w.qw, x = w.qx, y = w.qy, z = w.qz;
-        float dqw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-        float dqx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - r * dR[5] + z * dR[6] + r * dR[7] -
-                           2.f * x * dR[8]);
-        float dqy = 2.f * (-2.f * y * dR[0] + x * dR[1] + r * dR[2] + x * dR[3] + z * dR[5] - r * dR[6] + z * dR[7] -
-                           2.f * y * dR[8]);
-        float dqz = 2.f * (-2.f * z * dR[0] - r * dR[1] + x * dR[2] + r * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] +
-                           y * dR[7]);
-        float qd = r * dqw + x * dqx + y * dqy + z * dqz;
-        gq[0] = (dqw - r * qd) * w.qinv;
-        gq[1] = (dqx - x * qd) * w.qinv;
-        gq[2] = (dqy - y * qd) * w.qinv;
-        gq[3] = (dqz - z * qd) * w.qinv;
-    }
-    // ---- write
-    if (accumulate) {
-        for (int i = 0; i < 3; ++i) {
-            S.g_means[3 * g + i] += gmu[i];
-            S.g_log_scales[3 * g + i] += gls[i];
-        }
-        float4 *gq4 = reinterpret_cast<float4 *>(S.g_quats) + g;
-        float4 q = *gq4;
-        *gq4 = make_float4(q.x + gq[0], q.y + gq[1], q.z + gq[2], q.w + gq[3]);
-        S.g_logits[g] += glogit;
-        float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+        float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < S.item_count; ++k) {
+            const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
+            const long long e = I.entry_off + g;
+            if (radius[e] <= 0) continue;
+            Cam2D c;
+            project_cam(P, I, w, c);  // recompute the forward intermediates (visible by radius > 0)
+            const float4 g0 = grad2d[3 * e + 0], g1 = grad2d[3 * e + 1], g2 = grad2d[3 * e + 2];
+            const float du = g0.x, dv = g0.y, da = g0.z, db = g0.w, dc = g1.x, dop = g1.y;
+            const float4 sp1 = splat[3 * e + 1];
+            const float o = sp1.y;
+            glogit += dop * o * (1.f - o);
+            // ---- colour / SH. The forward's clamp decisions (sign bits of the stored colour)
+            // mask the colour gradient: md_ch = dL/dcolour_ch where the channel was not clamped.
+            const float md[3] = {color_clamped(sp1.z) ? 0.f : g1.z, color_clamped(sp1.w) ? 0.f : g1.w,
+                                 color_clamped(splat[3 * e + 2].x) ? 0.f : g2.x};
+            // dL/dsh_b,ch = k_b P_b md_ch; the view direction n gets sum_b k_b grad P_b (sum_ch md_ch sh_b,ch)
+            float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
+            float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+            float nx = dx * il, ny = dy * il, nz = dz * il;
+            float Pp[16];
+            sh_poly(P.sh_degree, nx, ny, nz, Pp);
+            float dn[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            float4 a = d[i];
-            d[i] = make_float4(a.x + gsh[4 * i], a.y + gsh[4 * i + 1], a.z + gsh[4 * i + 2], a.w + gsh[4 * i + 3]);
-        }
-    } else {
-        for (int i = 0; i < 3; ++i) {
-            S.g_means[3 * g + i] = gmu[i];
-            S.g_log_scales[3 * g + i] = gls[i];
-        }
-        reinterpret_cast<float4 *>(S.g_quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-        S.g_logits[g] = glogit;
-        float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+            for (int b = 0; b < 16; ++b) {
+                if (b >= nb) break;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) d[i] = make_float4(gsh[4 * i], gsh[4 * i + 1], gsh[4 * i + 2], gsh[4 * i + 3]);
+                for (int ch = 0; ch < 3; ++ch) gsh[3 * b + ch] += kSH[b] * Pp[b] * md[ch];
+                if (b > 0) {
+                    float ax, ay, az;
+                    sh_poly_grad(b, nx, ny, nz, ax, ay, az);
+                    const float f = kSH[b] * (md[0] * shr[3 * b] + md[1] * shr[3 * b + 1] + md[2] * shr[3 * b + 2]);
+                    dn[0] += f * ax; dn[1] += f * ay; dn[2] += f * az;
+                }
+            }
+            float ndn = nx * dn[0] + ny * dn[1] + nz * dn[2];
+            gmu[0] += (dn[0] - nx * ndn) * il;
+            gmu[1] += (dn[1] - ny * ndn) * il;
+            gmu[2] += (dn[2] - nz * ndn) * il;
+            // ---- conic -> cov2d
+            const float ca = c.ca, cb = c.cb, cc = c.cc;
+            const float hb = 0.5f * db;
+            const float CG00 = ca * da + cb * hb, CG01 = ca * hb + cb * dc;
+            const float CG10 = cb * da + cc * hb, CG11 = cb * hb + cc * dc;
+            const float H00 = -(CG00 * ca + CG01 * cb);
+            const float H01 = -(CG00 * cb + CG01 * cc);
+            const float H11 = -(CG10 * cb + CG11 * cc);
+            // ---- cov2d = T Sigma T^T
+            float dT0[3], dT1[3];
+            for (int i = 0; i < 3; ++i) {
+                dT0[i] = 2.f * (H00 * c.ST0[i] + H01 * c.ST1[i]);
+                dT1[i] = 2.f * (H01 * c.ST0[i] + H11 * c.ST1[i]);
+            }
+            // dSigma = H00 T0 T0^T + H01 (T0 T1^T + T1 T0^T) + H11 T1 T1^T
+            {
+                const float *a = c.T0, *b = c.T1;
+                gSig[0] += H00 * a[0] * a[0] + 2.f * H01 * a[0] * b[0] + H11 * b[0] * b[0];
+                gSig[1] += H00 * a[0] * a[1] + H01 * (a[0] * b[1] + b[0] * a[1]) + H11 * b[0] * b[1];
+                gSig[2] += H00 * a[0] * a[2] + H01 * (a[0] * b[2] + b[0] * a[2]) + H11 * b[0] * b[2];
+                gSig[3] += H00 * a[1] * a[1] + 2.f * H01 * a[1] * b[1] + H11 * b[1] * b[1];
+                gSig[4] += H00 * a[1] * a[2] + H01 * (a[1] * b[2] + b[1] * a[2]) + H11 * b[1] * b[2];
+                gSig[5] += H00 * a[2] * a[2] + 2.f * H01 * a[2] * b[2] + H11 * b[2] * b[2];
+            }
+            // ---- T = J W  ->  J entries
+            const float *V = I.V;
+            const float dJ00 = dT0[0] * V[0] + dT0[1] * V[1] + dT0[2] * V[2];
+            const float dJ02 = dT0[0] * V[8] + dT0[1] * V[9] + dT0[2] * V[10];
+            const float dJ11 = dT1[0] * V[4] + dT1[1] * V[5] + dT1[2] * V[6];
+            const float dJ12 = dT1[0] * V[8] + dT1[1] * V[9] + dT1[2] * V[10];
+            const float iz = 1.f / c.z, iz2 = iz * iz, iz3 = iz2 * iz;
+            const float fx = I.fx, fy = I.fy;
+            float dpx = du * fx * iz - dJ02 * fx * iz2;
+            float dpy = dv * fy * iz - dJ12 * fy * iz2;
+            float dpz = -du * fx * c.x * iz2 - dv * fy * c.y * iz2 - dJ00 * fx * iz2 + dJ02 * 2.f * fx * c.x * iz3 -
+                        dJ11 * fy * iz2 + dJ12 * 2.f * fy * c.y * iz3;
+            gmu[0] += V[0] * dpx + V[4] * dpy + V[8] * dpz;
+            gmu[1] += V[1] * dpx + V[5] * dpy + V[9] * dpz;
+            gmu[2] += V[2] * dpx + V[6] * dpy + V[10] * dpz;
+            // ---- selective densification statistic (Sec. 3.3)
+            if (w.mx >= I.lo[0] && w.mx < I.hi[0] && w.my >= I.lo[1] && w.my < I.hi[1] && w.mz >= I.lo[2] &&
+                w.mz < I.hi[2]) {
+                float a = du * 0.5f * (float)I.W, b = dv * 0.5f * (float)I.H;
+                sd_acc += sqrtf(a * a + b * b);
+                sd_cnt += 1;
+            }
+        }
+        // ---- Sigma -> (log_s, q) once per Gaussian
+        {
+            // gSig holds the entries G_kl (k <= l) of the symmetric full-matrix gradient T^T H T
+            float D[9] = {gSig[0], gSig[1], gSig[2], gSig[1], gSig[3], gSig[4], gSig[2], gSig[4], gSig[5]};
+            float R[9];
+            rotation(w.qw, w.qx, w.qy, w.qz, R);  // recomputed here rather than kept live over the views
+            float M[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * w.s[j];
+            float dM[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    dM[3 * i + j] = 2.f * (D[3 * i + 0] * M[0 + j] + D[3 * i + 1] * M[3 + j] + D[3 * i + 2] * M[6 + j]);
+            float dR[9];
+            for (int j = 0; j < 3; ++j) {
+                float ds = dM[j] * R[j] + dM[3 + j] * R[3 + j] + dM[6 + j] * R[6 + j];
+                gls[j] = ds * w.s[j];
+                dR[j] = dM[j] * w.s[j];
+                dR[3 + j] = dM[3 + j] * w.s[j];
+                dR[6 + j] = dM[6 + j] * w.s[j];
+            }
+            const float r = w.qw, x = w.qx, y = w.qy, z = w.qz;
+            float dqw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+            float dqx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - r * dR[5] + z * dR[6] + r * dR[7] -
+                               2.f * x * dR[8]);
+            float dqy = 2.f * (-2.f * y * dR[0] + x * dR[1] + r * dR[2] + x * dR[3] + z * dR[5] - r * dR[6] + z * dR[7] -
+                               2.f * y * dR[8]);
+            float dqz = 2.f * (-2.f * z * dR[0] - r * dR[1] + x * dR[2] + r * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                               x * dR[6] + y * dR[7]);
+            float qd = r * dqw + x * dqx + y * dqy + z * dqz;
+            gq[0] = (dqw - r * qd) * w.qinv;
+            gq[1] = (dqx - x * qd) * w.qinv;
+            gq[2] = (dqy - y * qd) * w.qinv;
+            gq[3] = (dqz - z * qd) * w.qinv;
+        }
     }
-    if (S.sd_acc != nullptr && sd_cnt > 0) {
-        S.sd_acc[g] += sd_acc;
-        S.sd_cnt[g] += sd_cnt;
+    // ---- write the per-Gaussian parameters
+    if (valid) {
+        if (accumulate) {
+            if (any) {
+                for (int i = 0; i < 3; ++i) {
+                    S.g_means[3 * g + i] += gmu[i];
+                    S.g_log_scales[3 * g + i] += gls[i];
+                }
+                float4 *gq4 = reinterpret_cast<float4 *>(S.g_quats) + g;
+                float4 q = *gq4;
+                *gq4 = make_float4(q.x + gq[0], q.y + gq[1], q.z + gq[2], q.w + gq[3]);
+                S.g_logits[g] += glogit;
+            }
+        } else {
+            for (int i = 0; i < 3; ++i) {
+                S.g_means[3 * g + i] = gmu[i];
+                S.g_log_scales[3 * g + i] = gls[i];
+            }
+            reinterpret_cast<float4 *>(S.g_quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+            S.g_logits[g] = glogit;
+        }
+        if (S.sd_acc != nullptr && sd_cnt > 0) {
+            S.sd_acc[g] += sd_acc;
+            S.sd_cnt[g] += sd_cnt;
+        }
+    }
+    __syncthreads();
+    // ---- SH gradients of the block's Gaussians, coalesced: consecutive threads take
+    // consecutive floats of the block's (set-contiguous) gradient range
+    SetCursor cur(P, t0);
+#pragma unroll
+    for (int r = 0; r < 12; ++r) {
+        const int j = threadIdx.x + r * PB_THREADS;  // float4 slot: Gaussian j / 12, chunk j % 12
+        if (j >= nblk * 12) break;
+        const int gi = j / 12, c = j - gi * 12;
+        if (accumulate && !s_any[gi]) continue;
+        cur.seek(P, t0 + gi);
+        const SetParams &Sg = P.set[cur.s];
+        float4 *dst = reinterpret_cast<float4 *>(Sg.g_sh + 48 * (t0 + gi - Sg.gauss_off)) + c;
+        const float *v = s_gsh + gi * PB_ROW + 4 * c;
+        float4 a = make_float4(v[0], v[1], v[2], v[3]);
+        if (accumulate) {
+            const float4 b = *dst;
+            a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+        }
+        *dst = a;
     }
 }
 
@@ -471,9 +545,9 @@ cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const i
                                int accumulate, cudaStream_t st)
 {
     if (P.n_gauss == 0) return cudaSuccess;
-    unsigned blocks = (unsigned)((P.n_gauss + 127) / 128);
+    unsigned blocks = (unsigned)((P.n_gauss + PB_THREADS - 1) / PB_THREADS);
     count_launch();
-    k_project_bwd<<<blocks, 128, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
+    k_project_bwd<<<blocks, PB_THREADS, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
                                           reinterpret_cast<const float4 *>(grad2d), accumulate);
     return cudaGetLastError();
 }
