@@ -86,9 +86,46 @@ struct Staged {
     int id;
 };
 
-__device__ __forceinline__ void fetch(const float4 *__restrict__ splat, const int *__restrict__ ids, int k, int end,
-                                      Staged &s)
+// Pixel-centre extent of the slab a warp composites.
+struct SlabBox {
+    float xa, xb, ya, yb;
+};
+
+// Conservative reachability of the alpha >= 1/255 test from the slab: false only when every
+// pixel centre of the slab fails it, so a splat for which this is false changes nothing there
+// and the warp skips it as a whole. The largest base-2 exponent p2 = A dx^2 + B dx dy + C dy^2
+// (a concave quadratic, A, C < 0) over the box is 0 when the mean is inside it, else it is
+// attained on the edge(s) facing the mean, each a 1D concave maximum clamped to the edge. The
+// margin covers float32 rounding of p2 at any pixel of the box (a few ulps of the largest
+// term sum S there); the clamp at 0.99 sits above 1/255 and does not enter.
+__device__ __forceinline__ bool slab_reachable(const SlabBox &bx, float u, float v, float A, float B, float C,
+                                               float pmin)
 {
+    if (!(pmin <= 0.0f)) return false;  // opacity below 1/255: no pixel passes
+    const float dxa = bx.xa - u, dxb = bx.xb - u, dya = bx.ya - v, dyb = bx.yb - v;
+    const bool in_x = dxa <= 0.0f && dxb >= 0.0f, in_y = dya <= 0.0f && dyb >= 0.0f;
+    if (in_x && in_y) return true;
+    float best = -INFINITY;
+    if (!in_x) {  // vertical edge facing the mean
+        const float dx = dxa > 0.0f ? dxa : dxb;
+        const float dy = fminf(fmaxf(__fdividef(-B * dx, 2.0f * C), dya), dyb);
+        best = fmaxf(best, A * dx * dx + B * dx * dy + C * dy * dy);
+    }
+    if (!in_y) {  // horizontal edge facing the mean
+        const float dy = dya > 0.0f ? dya : dyb;
+        const float dx = fminf(fmaxf(__fdividef(-B * dy, 2.0f * A), dxa), dxb);
+        best = fmaxf(best, A * dx * dx + B * dx * dy + C * dy * dy);
+    }
+    const float DX = fmaxf(fabsf(dxa), fabsf(dxb)), DY = fmaxf(fabsf(dya), fabsf(dyb));
+    const float S = fabsf(A) * DX * DX + fabsf(B) * DX * DY + fabsf(C) * DY * DY;
+    return best + (2e-6f * S + 1e-6f) >= pmin;
+}
+
+// Loads list position k (if k < end) into s and tests it against the warp's slab.
+__device__ __forceinline__ void fetch(const float4 *__restrict__ splat, const int *__restrict__ ids, int k, int end,
+                                      const SlabBox &bx, Staged &s, bool &hit)
+{
+    hit = false;
     if (k < end) {
         const int e = ids[k];
         const float4 a = splat[3 * e], b = splat[3 * e + 1];
@@ -96,6 +133,7 @@ __device__ __forceinline__ void fetch(const float4 *__restrict__ splat, const in
         s.s1 = make_float4(-0.5f * LOG2E * b.x, b.y, b.z, b.w);
         s.s2 = make_float2(splat[3 * e + 2].x, -log2f(255.0f * b.y));
         s.id = e;
+        hit = slab_reachable(bx, s.s0.x, s.s0.y, s.s0.z, s.s0.w, s.s1.x, s.s2.y);
     }
 }
 
@@ -110,13 +148,14 @@ struct WarpStage {
 // of the recompute adjoint). live[k] must be false for pixels outside the image.
 template <int PX>
 __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, const int *__restrict__ ids, int start,
-                                              int end, float pxc, const float (&pyc)[PX], bool (&live)[PX],
-                                              float (&T)[PX], float (&C0)[PX], float (&C1)[PX], float (&C2)[PX],
-                                              int (&last)[PX], WarpStage &st)
+                                              int end, const SlabBox &bx, float pxc, const float (&pyc)[PX],
+                                              bool (&live)[PX], float (&T)[PX], float (&C0)[PX], float (&C1)[PX],
+                                              float (&C2)[PX], int (&last)[PX], WarpStage &st)
 {
     const int lane = threadIdx.x & 31;
     Staged nx;
-    fetch(splat, ids, start + lane, end, nx);
+    bool nh;
+    fetch(splat, ids, start + lane, end, bx, nx, nh);
     for (int base = start; base < end; base += 32) {
         bool any = false;
 #pragma unroll
@@ -125,10 +164,12 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
         st.s0[lane] = nx.s0;
         st.s1[lane] = nx.s1;
         st.s2[lane] = nx.s2;
+        unsigned hits = __ballot_sync(0xffffffffu, nh);  // splats of the batch that can reach the slab
         __syncwarp();
-        fetch(splat, ids, base + 32 + lane, end, nx);
-        const int cnt = min(32, end - base);
-        for (int j = 0; j < cnt; ++j) {
+        fetch(splat, ids, base + 32 + lane, end, bx, nx, nh);
+        while (hits) {
+            const int j = __ffs(hits) - 1;
+            hits &= hits - 1;
             const float4 q0 = st.s0[j], q1 = st.s1[j];
             const float cb = st.s2[j].x, pmin = st.s2[j].y;
             const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
@@ -152,6 +193,19 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
         }
         __syncwarp();
     }
+}
+
+// Pixel-centre box of the slab of warp `warp` in tile (tx, ty).
+template <int TW, int TH, int PX>
+__device__ __forceinline__ SlabBox slab_box(int tx, int ty, int warp)
+{
+    using G = Slab<TW, TH, PX>;
+    SlabBox b;
+    b.xa = (float)(tx * TW) + 0.5f;
+    b.xb = b.xa + (float)(TW - 1);
+    b.ya = (float)(ty * TH + warp * G::WROWS) + 0.5f;
+    b.yb = b.ya + (float)(G::WROWS - 1);
+    return b;
 }
 
 template <int TW, int TH, int PX>
@@ -181,8 +235,8 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
         C0[k] = C1[k] = C2[k] = 0.0f;
         last[k] = 0;
     }
-    forward_sweep<PX>(splat, ids, tile_start[t], tile_start[t + 1], pxc, pyc, live, T, C0, C1, C2, last,
-                      stage[warp]);
+    forward_sweep<PX>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc, live,
+                      T, C0, C1, C2, last, stage[warp]);
     const long long HW = (long long)I.W * I.H;
     float *out = rgb + 3 * I.pix_off;
 #pragma unroll
@@ -214,6 +268,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
     const float pxc = (float)px + 0.5f;
     const int start = tile_start[t], end = tile_start[t + 1];
+    const SlabBox bx = slab_box<TW, TH, PX>(tx, ty, warp);
     const long long HW = (long long)I.W * I.H;
     // per pixel: dL/dC, the colour seen behind the current splat (B, background included),
     // the transmittance after it (T, starting from T_final) and the stop position
@@ -246,7 +301,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
             live[k] = inside[k];
             B0[k] = B1[k] = B2[k] = 0.0f;  // colour accumulators of the sweep (unused after it)
         }
-        forward_sweep<PX>(splat, ids, start, end, pxc, pyc, live, T, B0, B1, B2, nc, st);
+        forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, B0, B1, B2, nc, st);
     }
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
@@ -263,16 +318,20 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     // walk the list back to front in batches of 32, prefetching the batch below
     int top = stop, base = max(start, stop - 32);
     Staged nx;
-    fetch(splat, ids, base + lane, top, nx);
+    bool nh;
+    fetch(splat, ids, base + lane, top, bx, nx, nh);
     while (top > start) {
         st.s0[lane] = nx.s0;
         st.s1[lane] = nx.s1;
         st.s2[lane] = nx.s2;
         st.id[lane] = nx.id;
+        unsigned hits = __ballot_sync(0xffffffffu, nh);
         __syncwarp();
         const int nbase = max(start, base - 32);
-        fetch(splat, ids, nbase + lane, base, nx);
-        for (int j = top - base - 1; j >= 0; --j) {
+        fetch(splat, ids, nbase + lane, base, bx, nx, nh);
+        while (hits) {  // back to front: highest position first
+            const int j = 31 - __clz(hits);
+            hits &= ~(1u << j);
             const float4 q0 = st.s0[j], q1 = st.s1[j];
             const float cb = st.s2[j].x, pmin = st.s2[j].y;
             const int pos = base - start + j;
