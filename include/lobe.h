@@ -190,8 +190,8 @@ const char *lobe_last_error(const lobe_ctx *ctx);
 /* Sizes the context-owned binning scratch for up to max_entries projected entries,
  * max_isect (splat, tile) pairs and max_tiles tiles per batch (grows only). Calls of
  * lobe_bin_sort without a host count pointer never allocate and need this first; those with
- * one grow the scratch themselves. Scratch: 24 B per entry + 16 B per pair + 4 B per tile
- * + about 1.2 MB. */
+ * one grow the scratch themselves. Scratch: 25 B per entry + 18 B per pair + 8 B per
+ * 64x64-pixel block + about 20 KB. */
 lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect, int64_t max_tiles);
 /* Synchronises the stream, returns and clears the latched device status. */
 lobe_status lobe_get_status(lobe_ctx *ctx);

@@ -26,6 +26,7 @@ constexpr int CHUNK = 256;    // splats per work item (BIN_THREADS)
 constexpr int NT_MAX = 64;    // tiles per super-tile (S <= 8)
 constexpr int KEY_SHIFT = 16; // super-tile id above, packed local rectangle below
 constexpr long long MAX_SUPER = 1LL << 16;
+constexpr long long MAX_SCAN_TILES = 1LL << 22;  // tiles per call (the tile scan's length)
 
 __device__ __forceinline__ void splat_rect(const BatchParams &P, const ItemParams &I, const float *splat,
                                            const int *radius, uint32_t e, int &x0, int &y0, int &x1, int &y1)
@@ -62,52 +63,54 @@ __global__ void __launch_bounds__(256) k_super_dup(const __grid_constant__ Batch
     const int lane = threadIdx.x & 31;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t V = *V_dev;
-    if ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) >= V) return;
-    if (*n_sp_use == 0) return;  // nothing to emit (no pairs, or scratch capacity exceeded)
-    const bool valid = k < V;
-    const int S = P.S;
-    uint32_t off = 0xffffffffu, cnt = 0, base = 0, w = 1, sg = 1, e = 0;
-    int x0 = 0, y0 = 0, x1 = 0, y1 = 0, sx0 = 0, sy0 = 0;
-    if (valid) {
-        e = order[k];
-        off = offs[k];
-        const ItemParams &I = P.item[item_of_entry(P, e)];
-        splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
-        sx0 = x0 / S;
-        sy0 = y0 / S;
-        const int sx1 = (x1 + S - 1) / S, sy1 = (y1 + S - 1) / S;
-        base = (uint32_t)(I.super_off + sy0 * I.sgx + sx0);
-        w = (uint32_t)(sx1 - sx0);
-        sg = (uint32_t)I.sgx;
-        cnt = (uint32_t)((sx1 - sx0) * (sy1 - sy0));
-    }
-    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-    const int last = 31 - __clz(vmask);
-    const uint32_t p0 = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t p1 = __shfl_sync(0xffffffffu, off + cnt, last);
-    for (uint32_t p = p0 + lane; p - lane < p1; p += 32) {
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step; step >>= 1) {
-            uint32_t o = __shfl_sync(0xffffffffu, off, j + step);
-            if (o <= p) j += step;
+    const bool warp_live = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) < V && *n_sp_use != 0;
+    if (warp_live) {  // (no pairs to emit when the scratch capacity was exceeded)
+        const bool valid = k < V;
+        const int S = P.S;
+        uint32_t off = 0xffffffffu, cnt = 0, base = 0, w = 1, sg = 1, e = 0;
+        int x0 = 0, y0 = 0, x1 = 0, y1 = 0, sx0 = 0, sy0 = 0;
+        if (valid) {
+            e = order[k];
+            off = offs[k];
+            const ItemParams &I = P.item[item_of_entry(P, e)];
+            splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
+            sx0 = x0 / S;
+            sy0 = y0 / S;
+            const int sx1 = (x1 + S - 1) / S, sy1 = (y1 + S - 1) / S;
+            base = (uint32_t)(I.super_off + sy0 * I.sgx + sx0);
+            w = (uint32_t)(sx1 - sx0);
+            sg = (uint32_t)I.sgx;
+            cnt = (uint32_t)((sx1 - sx0) * (sy1 - sy0));
         }
-        const uint32_t oj = __shfl_sync(0xffffffffu, off, j);
-        const uint32_t wj = __shfl_sync(0xffffffffu, w, j);
-        const uint32_t bj = __shfl_sync(0xffffffffu, base, j);
-        const uint32_t gj = __shfl_sync(0xffffffffu, sg, j);
-        const uint32_t ej = __shfl_sync(0xffffffffu, e, j);
-        const int rx0 = __shfl_sync(0xffffffffu, x0 - sx0 * S, j), rx1 = __shfl_sync(0xffffffffu, x1 - sx0 * S, j);
-        const int ry0 = __shfl_sync(0xffffffffu, y0 - sy0 * S, j), ry1 = __shfl_sync(0xffffffffu, y1 - sy0 * S, j);
-        if (p < p1) {
-            const uint32_t local = p - oj;
-            const int sy = (int)(local / wj), sx = (int)(local - sy * wj);
-            // the splat's rectangle relative to super-tile (sx, sy) of its super-rectangle
-            const int lx0 = max(rx0 - sx * S, 0), lx1 = min(rx1 - sx * S, S);
-            const int ly0 = max(ry0 - sy * S, 0), ly1 = min(ry1 - sy * S, S);
-            skeys[p] = ((bj + (uint32_t)sy * gj + (uint32_t)sx) << KEY_SHIFT) |
-                       (uint32_t)(lx0 | (lx1 << 4) | (ly0 << 8) | (ly1 << 12));
-            svals[p] = ej;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const int last = 31 - __clz(vmask);
+        const uint32_t p0 = __shfl_sync(0xffffffffu, off, 0);
+        const uint32_t p1 = __shfl_sync(0xffffffffu, off + cnt, last);
+        for (uint32_t p = p0 + lane; p - lane < p1; p += 32) {
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                uint32_t o = __shfl_sync(0xffffffffu, off, j + step);
+                if (o <= p) j += step;
+            }
+            const uint32_t oj = __shfl_sync(0xffffffffu, off, j);
+            const uint32_t wj = __shfl_sync(0xffffffffu, w, j);
+            const uint32_t bj = __shfl_sync(0xffffffffu, base, j);
+            const uint32_t gj = __shfl_sync(0xffffffffu, sg, j);
+            const uint32_t ej = __shfl_sync(0xffffffffu, e, j);
+            const int rx0 = __shfl_sync(0xffffffffu, x0 - sx0 * S, j), rx1 = __shfl_sync(0xffffffffu, x1 - sx0 * S, j);
+            const int ry0 = __shfl_sync(0xffffffffu, y0 - sy0 * S, j), ry1 = __shfl_sync(0xffffffffu, y1 - sy0 * S, j);
+            if (p < p1) {
+                const uint32_t local = p - oj;
+                const int sy = (int)(local / wj), sx = (int)(local - sy * wj);
+                // the splat's rectangle relative to super-tile (sx, sy) of its super-rectangle
+                const int lx0 = max(rx0 - sx * S, 0), lx1 = min(rx1 - sx * S, S);
+                const int ly0 = max(ry0 - sy * S, 0), ly1 = min(ry1 - sy * S, S);
+                const uint32_t key = ((bj + (uint32_t)sy * gj + (uint32_t)sx) << KEY_SHIFT) |
+                                     (uint32_t)(lx0 | (lx1 << 4) | (ly0 << 8) | (ly1 << 12));
+                skeys[p] = key;
+                svals[p] = ej;
+            }
         }
     }
 }
@@ -279,25 +282,28 @@ static unsigned persistent_grid(long long work_max)
     return (unsigned)(work_max < 1 ? 1 : (work_max < cap ? work_max : cap));
 }
 
+static LB lb_of(const BinScratch &b, int stage) { return LB{b.scan_slots, b.ctl, stage}; }
+
 // Step 1 and the super-pair count: visible splats in depth order (vis_pos), per-splat super
 // pair offsets (offs), the super pair total (scalars[4]) and its usable count (scalars[1]: the
-// total, or 0 with a latched error when it exceeds pair_capacity; < 0 = unchecked).
+// total, or 0 with a latched error when it exceeds pair_capacity; < 0 = unchecked). The first
+// kernel opens the call's look-back generation.
 cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int *radius, const int *tiles,
                             BinScratch &b, long long pair_capacity, cudaStream_t st)
 {
     const long long n = P.n_entries;
     uint32_t *V = b.scalars, *n_sp = b.scalars + 1, *sp_total = b.scalars + 4;
-    scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, b.block_sums, V, nullptr, nullptr, -1, nullptr, st);
+    scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, V, nullptr, nullptr, -1, lb_of(b, ST_SCAN_VISIBLE), st, true);
     if (n > 0) {
         count_launch();
         k_compact<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tiles, splat, b.vis_pos, b.dkA, b.dvA);
     }
-    radix_sort(V, n, 0, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.counts, b.block_sums, st);
+    radix_sort(V, n, 0, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.counts, lb_of(b, ST_DEPTH_PASS), st);
     if (n > 0) {
         count_launch();
         k_super_area<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, splat, radius, b.offs);
     }
-    scan(LoadPlain{b.offs}, V, n, b.offs, b.block_sums, sp_total, nullptr, n_sp, pair_capacity, b.status, st);
+    scan(LoadPlain{b.offs}, V, n, b.offs, sp_total, nullptr, n_sp, pair_capacity, lb_of(b, ST_SCAN_OFFS), st);
     return cudaGetLastError();
 }
 
@@ -320,7 +326,7 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
     uint32_t *kfinal = (passes & 1) ? b.skB : b.skA;  // not the last pass's source
     uint32_t *vfinal = (passes & 1) ? b.svB : b.svA;
     radix_sort(n_sp, pair_capacity, KEY_SHIFT, nbits, b.skA, b.svA, b.skB, b.svB, kfinal, vfinal, b.counts,
-               b.block_sums, st);
+               lb_of(b, ST_SUPER_PASS), st);
     b.sp_keys = kfinal;
     b.sp_ids = vfinal;
     count_launch();
@@ -328,8 +334,8 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
     k_key_ranges<<<(unsigned)(rblocks < 2368 ? rblocks : 2368), 256, 0, st>>>(kfinal, n_sp, pair_capacity, KEY_SHIFT,
                                                                                 P.n_super, b.super_start);
     // chunk work items: chunk_base[s] = first work item of super-tile s, chunk_base[n_super] = total
-    scan(LoadChunks{b.super_start}, nullptr, P.n_super, b.chunk_base, b.block_sums, b.chunk_base + P.n_super, nullptr,
-         nullptr, -1, nullptr, st);
+    scan(LoadChunks{b.super_start}, nullptr, P.n_super, b.chunk_base, b.chunk_base + P.n_super, nullptr, nullptr, -1,
+         lb_of(b, ST_SCAN_CHUNKS), st);
     const long long work_max = pair_capacity / CHUNK + P.n_super + 1;
     uint32_t *ts = reinterpret_cast<uint32_t *>(tile_start);
     if (P.n_super > 0) {
@@ -347,8 +353,8 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
         }
     }
     // the scan's grand total lands in tile_start[n_tiles] and in the caller's n_isect
-    scan(LoadPlain{ts}, nullptr, P.n_tiles, ts, b.block_sums, ts + P.n_tiles, n_isect_dev, n_use, isect_capacity,
-         b.status, st);
+    scan(LoadPlain{ts}, nullptr, P.n_tiles, ts, ts + P.n_tiles, n_isect_dev, n_use, isect_capacity,
+         lb_of(b, ST_SCAN_TILES), st);
     b.work_max = work_max;
     return cudaGetLastError();
 }
@@ -376,17 +382,20 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
 
 // ------------------------------------------------------------------ scratch layout
 //
-// entry part: 6 arrays of max_entries words + radix digit counts + scan block sums + scalars
-// pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong) + per-chunk tile counts
+// entry part: 6 arrays of max_entries words, radix digit counts, scalars, the scans' look-back
+//             words (one per 4096 elements of the longest scan)
+// pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong), per-chunk tile counts
 // super part: super-tile list starts and chunk bases (max_super + 1 words each)
+// Look-back slots must be zero (or hold words of earlier calls) before first use.
 
 static size_t words_rounded(size_t words) { return ((words * 4 + 255) / 256) * 256; }
+static size_t slots_rounded(long long slots) { return (((size_t)slots * 8 + 255) / 256) * 256; }
 
 size_t entry_scratch_bytes(long long max_entries)
 {
     size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
-    return 6 * words_rounded(e) + words_rounded(256ull * RS_MAX_BLOCKS) + words_rounded(SCAN_MAX_BLOCKS) +
-           words_rounded(16);
+    return 6 * words_rounded(e) + words_rounded(256ull * RS_MAX_BLOCKS) + words_rounded(16) +
+           slots_rounded(scan_slots(max_scan_length(max_entries)));
 }
 
 size_t pair_scratch_bytes(long long max_pairs, long long max_super)
@@ -402,6 +411,10 @@ size_t super_scratch_bytes(long long max_super)
 }
 
 long long max_super_tiles() { return MAX_SUPER; }
+long long max_scan_length(long long max_entries)
+{
+    return max_entries > MAX_SCAN_TILES ? max_entries : MAX_SCAN_TILES;
+}
 
 struct Carver {
     char *p;
@@ -411,18 +424,25 @@ struct Carver {
         p += words_rounded(words);
         return r;
     }
+    unsigned long long *take_slots(long long slots)
+    {
+        unsigned long long *r = reinterpret_cast<unsigned long long *>(p);
+        p += slots_rounded(slots);
+        return r;
+    }
 };
 
-void entry_scratch_carve(void *mem, long long max_entries, int *status, BinScratch &b)
+void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch &b)
 {
     size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
     Carver c{static_cast<char *>(mem)};
     b.vis_pos = c.take(e); b.dkA = c.take(e); b.dvA = c.take(e); b.dkB = c.take(e); b.dvB = c.take(e);
     b.offs = c.take(e);
     b.counts = c.take(256ull * RS_MAX_BLOCKS);
-    b.block_sums = c.take(SCAN_MAX_BLOCKS);
     b.scalars = c.take(16);
-    b.status = status;
+    b.scan_slots = c.take_slots(scan_slots(max_scan_length(max_entries)));
+    b.ctl = ctl;
+    b.status = ctl;
 }
 
 void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b)

@@ -213,8 +213,10 @@ lobe_status lobe_ctx_create(lobe_ctx **out, void *stream, const lobe_config *cfg
     ctx->stream = static_cast<cudaStream_t>(stream);
     ctx->cfg = *cfg;
     cudaError_t e = cudaGetDevice(&ctx->device);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, 64);
-    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, 64);
+    // status word + look-back control block of the binning scratch, zeroed once
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, CTL_BYTES);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, CTL_BYTES, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         delete ctx;
         return LOBE_ERR_CUDA;
@@ -265,6 +267,9 @@ static lobe_status grow_region(lobe_ctx *ctx, void *&mem, long long &have, long 
     long long n = need < floor_n ? floor_n : need;
     cudaError_t e = cudaMalloc(&mem, bytes(n));
     if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "%s scratch (%lld): %s", what, n, cudaGetErrorString(e));
+    e = cudaMemsetAsync(mem, 0, bytes(n), ctx->stream);  // look-back words start out matching no call
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_CUDA, "%s scratch clear: %s", what, cudaGetErrorString(e));
     have = n;
     return LOBE_OK;
 }
@@ -290,6 +295,9 @@ static lobe_status grow_pairs(lobe_ctx *ctx, long long need)
     ctx->pair_bytes = 0;
     cudaError_t e = cudaMalloc(&ctx->pair_mem, bytes);
     if (e != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "pair scratch (%lld): %s", n, cudaGetErrorString(e));
+    e = cudaMemsetAsync(ctx->pair_mem, 0, bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, LOBE_ERR_CUDA, "pair scratch clear: %s", cudaGetErrorString(e));
     ctx->max_pairs = n;
     ctx->pair_bytes = bytes;
     pair_scratch_carve(ctx->pair_mem, n, ctx->bins);
@@ -364,6 +372,8 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
         return fail(ctx, LOBE_ERR_ARG, "bins missing");
     if (P.n_super > max_super_tiles())
         return fail(ctx, LOBE_ERR_ARG, "%d super-tiles (64x64-pixel blocks) exceed %lld", P.n_super, max_super_tiles());
+    if (P.n_tiles > max_scan_length(0))
+        return fail(ctx, LOBE_ERR_ARG, "%d tiles exceed %lld", P.n_tiles, max_scan_length(0));
     if (P.n_entries > ctx->max_entries || !ctx->entry_mem || P.n_super > ctx->max_super || !ctx->super_mem ||
         !ctx->pair_mem) {
         if (!sync)

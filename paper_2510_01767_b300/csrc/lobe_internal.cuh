@@ -213,15 +213,16 @@ __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn
 // independently.
 struct BinScratch {
     uint32_t *vis_pos, *dkA, *dvA, *dkB, *dvB, *offs;  // [max_entries]
-    uint32_t *counts;                                  // radix digit counts per block
-    uint32_t *block_sums;                              // scan block totals
-    uint32_t *scalars;  // [0] visible splats, [1] usable super pairs, [2] usable pairs
+    uint32_t *counts;   // radix digit counts per block [256][blocks], scanned in place
+    uint32_t *scalars;  // [0] visible splats, [1] usable super pairs, [2] usable pairs, [4] super pairs
+    unsigned long long *scan_slots;                    // decoupled look-back words of the scans
     uint32_t *skA, *svA, *skB, *svB;                   // [max_pairs]
     uint32_t *sp_keys, *sp_ids;                        // sorted super pairs (one of the A/B arrays)
     uint32_t *chunk_cnt;                               // per (chunk, tile) counts, then offsets
     uint32_t *super_start, *chunk_base;                // [max_super + 1] each
     long long work_max;                                // bound on chunk work items of the last call
-    int *status;
+    int *ctl;     // control block: [0] status, [1] look-back generation, [2..17] ticket counters
+    int *status;  // == ctl
 };
 
 // Counts kernel launches made by this library (process-wide, all contexts).
@@ -245,7 +246,9 @@ size_t entry_scratch_bytes(long long max_entries);
 size_t pair_scratch_bytes(long long max_pairs, long long max_super);
 size_t super_scratch_bytes(long long max_super);
 long long max_super_tiles();  // super-tile ids must fit the 16 key bits that carry them
-void entry_scratch_carve(void *mem, long long max_entries, int *status, BinScratch &b);
+long long max_scan_length(long long max_entries);  // longest scan the entry scratch serves (>= 2^22 tiles)
+constexpr size_t CTL_BYTES = 256;                  // control block of a binning scratch (zeroed once)
+void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch &b);
 void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b);
 void super_scratch_carve(void *mem, long long max_super, BinScratch &b);
 

@@ -16,7 +16,7 @@ constexpr long long kMaxTiles = LOBE_NOALLOC_MAX_TILES;
 constexpr long long kMaxPairs = LOBE_NOALLOC_MAX_PAIRS;
 constexpr long long kMaxSuper = 8192;  // 64x64-pixel blocks; 65536 tiles make about 4100
 constexpr size_t kScratchBytes = size_t(20) << 20;
-constexpr size_t kStatusBytes = 256;
+constexpr size_t kStatusBytes = CTL_BYTES;  // status word + look-back control block
 constexpr int kMaxDevices = 64;
 
 std::mutex g_mu;
@@ -54,6 +54,7 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
     if (!proj || (P.n_entries > 0 && (!proj->splat || !proj->radius || !proj->tiles_touched))) return LOBE_ERR_ARG;
     if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0) return LOBE_ERR_ARG;
     if (P.n_entries > kMaxEntries || P.n_tiles > kMaxTiles || P.n_super > kMaxSuper) return LOBE_ERR_CAPACITY;
+    static_assert(kMaxTiles <= (1LL << 22), "the tile scan serves at most 2^22 tiles");
     if (entry_scratch_bytes(kMaxEntries) + pair_scratch_bytes(kMaxPairs, kMaxSuper) + super_scratch_bytes(kMaxSuper) +
             kStatusBytes > kScratchBytes)
         return LOBE_ERR_STATE;
@@ -74,7 +75,9 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
     super_scratch_carve(p, kMaxSuper, b);
 
     // the array keeps the previous call's contents: only the status word must start at zero
-    // (every other scratch value is written before it is read)
+    // (the look-back generation and ticket counters after it carry over between calls; every
+    // other scratch value is written before it is read, or is a look-back word of an earlier
+    // call, which matches no later one)
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return LOBE_ERR_CUDA;
     if (bin_super_count(P, proj->splat, proj->radius, proj->tiles_touched, b, kMaxPairs, st) != cudaSuccess)
         return LOBE_ERR_CUDA;

@@ -1,22 +1,135 @@
 // sort_prims.cuh -- device primitives of the binning stage (included by binning.cu only):
-// an exclusive scan with a device-side length, compaction of visible splats, and a stable
-// LSD radix sort of (key, value) pairs.
+// a single-pass exclusive scan with a device-side length, compaction of visible splats, and a
+// stable LSD radix sort of (key, value) pairs (per pass: digit counts per block, their scan,
+// a block-chunked scatter).
 //
-// Radix passes are block-chunked: each block owns a contiguous chunk, ranks 2048-element tiles
-// of it with warp ballots, reorders each tile by digit in shared memory, and writes runs of
-// equal digits with coalesced stores. No spin-waits anywhere; every result is deterministic.
+// The scan uses decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan with
+// Decoupled Look-back", 2016): a block takes a tile in ticket order, publishes the tile's
+// aggregate, then one warp reads the words of the 32 tiles before it at a time and adds their
+// values back to the nearest tile that already carries its inclusive prefix; the block then
+// publishes its own inclusive prefix. A tile only waits on tiles with smaller tickets, held by
+// blocks that are already running, so every wait ends; each wait is also bounded
+// (LB_SPIN_LIMIT polls, then STATUS_TIMEOUT is latched and the block carries on).
+//
+// A published word is (tag << 34 | flag << 32 | value). The tag combines a generation number,
+// advanced once per binning call by its first kernel, with the stage (which scan), so words
+// left by earlier launches never match and nothing has to be cleared between calls. The
+// generation, the per-stage ticket counters and the status word live in one small control
+// block that is zeroed once when it is allocated. Radix passes are block-chunked: each block
+// owns a contiguous chunk, ranks 2048-element tiles of it with warp ballots, reorders each
+// tile by digit in shared memory, and writes runs of equal digits with coalesced stores.
+// Every result is deterministic.
 #include "lobe_internal.cuh"
 
 namespace lobe {
 
-constexpr int SCAN_THREADS = 512;
-constexpr int SCAN_MAX_BLOCKS = 1024;
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;                       // per lane, warp-striped
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 4096 elements per tile
 constexpr int RS_WARPS = 8;
 constexpr int RS_THREADS = RS_WARPS * 32;
 constexpr int RS_ITEMS = 8;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // elements ranked and staged per step
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // elements ranked and staged per tile
 constexpr int RS_MAX_BLOCKS = 1184;             // 8 per SM on 148 SMs
 constexpr int BIN_THREADS = 256;
+
+// ------------------------------------------------------------------ look-back control
+
+constexpr int LB_STAGES = 16;
+constexpr int LB_SPIN_LIMIT = 1 << 22;
+enum : uint32_t { LB_AGG = 1u, LB_INC = 2u };
+// control block (int words): [0] status, [1] generation, [2 + stage] ticket counter
+constexpr int CTL_WORDS = 2 + LB_STAGES;
+
+enum : int {  // stages of one binning call (each scan has its own)
+    ST_SCAN_VISIBLE = 0,
+    ST_DEPTH_PASS = 1,  // .. 4: digit-count scans of the depth sort
+    ST_SCAN_OFFS = 5,
+    ST_SUPER_PASS = 6,  // .. 7: digit-count scans of the super-tile sort
+    ST_SCAN_CHUNKS = 8,
+    ST_SCAN_TILES = 9,
+};
+
+struct LB {
+    unsigned long long *slots;
+    int *ctl;
+    int stage;
+};
+
+__device__ __forceinline__ uint32_t lb_tag(uint32_t gen, int stage)
+{
+    return (((gen % ((1u << 26) - 1u)) + 1u) << 4) | (uint32_t)stage;  // never 0, 30 bits
+}
+
+__device__ __forceinline__ void lb_publish(unsigned long long *slot, uint32_t tag, uint32_t flag, uint32_t v)
+{
+    const unsigned long long w = ((unsigned long long)tag << 34) | ((unsigned long long)flag << 32) | v;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *slot)
+{
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(slot) : "memory");
+    return w;
+}
+
+// Called by one full warp: the sum of the values of tiles [0, tile) (the tile's exclusive
+// prefix), in every lane. Lane l reads tile j - l of the current window of 32; the window's
+// values up to the nearest inclusive word are summed; without one the window moves down 32.
+__device__ __forceinline__ uint32_t lb_exclusive_warp(const unsigned long long *slots, int tile, uint32_t tag,
+                                                      int *status)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t sum = 0;
+    int j = tile - 1, spins = 0;
+    while (j >= 0) {
+        const int k = j - lane;
+        bool ready = true, inc = false;
+        uint32_t v = 0;
+        if (k >= 0) {
+            const unsigned long long w = lb_load(slots + k);
+            ready = (uint32_t)(w >> 34) == tag;
+            inc = ready && (((uint32_t)(w >> 32) & 3u) == LB_INC);
+            v = ready ? (uint32_t)w : 0u;
+        }
+        const unsigned incm = __ballot_sync(0xffffffffu, inc);
+        const unsigned waitm = __ballot_sync(0xffffffffu, !ready);
+        const int first = incm ? __ffs(incm) - 1 : 31;  // nearest inclusive word (or the whole window)
+        const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+        if (waitm & need) {
+            if (++spins > LB_SPIN_LIMIT) {
+                if (lane == 0) set_status(status, STATUS_TIMEOUT);
+                break;
+            }
+            __nanosleep(40);
+            continue;
+        }
+        uint32_t part = lane <= first ? v : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        sum += part;
+        if (incm) break;
+        j -= 32;
+    }
+    return sum;
+}
+
+// Thread 0: the block's ticket and the generation of this call. With bump, this launch opens
+// the call: it uses generation + 1 and its last ticket holder stores it (every block read the
+// old value before taking its ticket). The last ticket holder also re-arms the counter.
+__device__ __forceinline__ void lb_take(int *ctl, int stage, bool bump, int &ticket, uint32_t &gen)
+{
+    volatile int *vctl = ctl;
+    const uint32_t g = (uint32_t)vctl[1];
+    __threadfence();
+    ticket = atomicAdd(ctl + 2 + stage, 1);
+    gen = bump ? g + 1u : g;
+    if (ticket == (int)gridDim.x - 1) {
+        atomicExch(ctl + 2 + stage, 0);
+        if (bump) atomicExch(ctl + 1, (int)(g + 1u));
+    }
+}
 
 // ------------------------------------------------------------------ block scan helper
 
@@ -51,13 +164,16 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t &e
     return total;
 }
 
-// ------------------------------------------------------------------ generic exclusive scan
+// ------------------------------------------------------------------ single-pass exclusive scan
 //
-// out[i] = sum_{j<i} in(j) for i < n, with n read from device memory when n_dev is given (the
-// launch shape then depends only on an upper bound, so the call is graph-capturable). Three
-// kernels: per-block totals, scan of the totals (one block), per-block scan with its offset.
-// In-place use (out == the loaded array) is safe: each element is read and then written by
-// the same thread.
+// out[i] = sum_{j<i} in(j) for i < n, n read from device memory when n_dev is given (the launch
+// shape then depends only on an upper bound, so the call is graph-capturable). Each block scans
+// one 4096-element tile (warp-striped, coalesced) and gets the tile's offset by look-back. The
+// block of the last tile writes the grand total to total32/total64 (nullable) and the count the
+// next stage may use to n_use: the total, or 0 with a latched capacity error when it exceeds
+// `capacity` (< 0: unlimited). In-place use (out == the loaded array) is safe: each element is
+// read and later written by the same thread. The block with ticket 0 zeroes zero_words words at
+// zero_buf (accumulators of later kernels).
 
 struct LoadVisible {  // 1 where a projected entry touches at least one tile
     const int *tiles;
@@ -68,86 +184,97 @@ struct LoadPlain {
     __device__ uint32_t operator()(long long i) const { return src[i]; }
 };
 
-__device__ __forceinline__ void chunk_of(long long n, int b, int nb, long long &lo, long long &hi)
-{
-    long long chunk = (n + nb - 1) / nb;
-    lo = (long long)b * chunk;
-    hi = lo + chunk < n ? lo + chunk : n;
-    if (lo > n) lo = n;
-}
-
 template <class L>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(L load, const uint32_t *n_dev, long long n_host,
-                                                              uint32_t *block_sums)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(L load, const uint32_t *n_dev, long long n_host, uint32_t *out,
+                                                       uint32_t *total32, long long *total64, uint32_t *n_use,
+                                                       long long capacity, LB lb, int bump, uint32_t *zero_buf,
+                                                       int zero_words)
 {
-    __shared__ uint32_t red[SCAN_THREADS / 32];
-    const long long n = n_dev ? (long long)*n_dev : n_host;
-    long long lo, hi;
-    chunk_of(n, blockIdx.x, gridDim.x, lo, hi);
-    uint32_t s = 0;
-    for (long long i = lo + threadIdx.x; i < hi; i += SCAN_THREADS) s += load(i);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __shared__ int s_tile;
+    __shared__ uint32_t s_gen, s_prefix;
+    __shared__ uint32_t s_warp[SCAN_THREADS / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        int t;
+        uint32_t g;
+        lb_take(lb.ctl, lb.stage, bump != 0, t, g);
+        s_tile = t;
+        s_gen = g;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += red[w];
-        block_sums[blockIdx.x] = t;
-    }
-}
-
-// Scans block_sums[0..nb) in place (exclusive), writes the grand total to total32/total64
-// (nullable), and the count the next stage may use: the total, or 0 with a latched
-// capacity error when it exceeds `capacity` (capacity < 0: unlimited).
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *block_sums, int nb, uint32_t *total32, long long *total64,
-                                                   uint32_t *n_use, long long capacity, int *status)
-{
-    __shared__ uint32_t sm[33];
-    uint32_t x = threadIdx.x < nb ? block_sums[threadIdx.x] : 0u, ex;
-    uint32_t total = block_exclusive_scan<1024>(x, ex, sm);
-    if (threadIdx.x < nb) block_sums[threadIdx.x] = ex;
-    if (threadIdx.x == 0) {
-        if (total32) *total32 = total;
-        if (total64) *total64 = (long long)total;
-        if (n_use) {
-            bool over = capacity >= 0 && (long long)total > capacity;
-            *n_use = over ? 0u : total;
-            if (over) set_status(status, STATUS_CAPACITY);
-        }
-    }
-}
-
-template <class L>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(L load, const uint32_t *n_dev, long long n_host,
-                                                            const uint32_t *block_sums, uint32_t *out)
-{
-    __shared__ uint32_t sm[SCAN_THREADS / 32 + 1];
+    const int tile = s_tile;
+    if (tile == 0)
+        for (int i = threadIdx.x; i < zero_words; i += SCAN_THREADS) zero_buf[i] = 0u;
     const long long n = n_dev ? (long long)*n_dev : n_host;
-    long long lo, hi;
-    chunk_of(n, blockIdx.x, gridDim.x, lo, hi);
-    uint32_t carry = block_sums[blockIdx.x];
-    for (long long base = lo; base < hi; base += SCAN_THREADS) {
-        long long i = base + threadIdx.x;
-        uint32_t x = i < hi ? load(i) : 0u, ex;
-        uint32_t tot = block_exclusive_scan<SCAN_THREADS>(x, ex, sm);
-        if (i < hi) out[i] = carry + ex;
+    const long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tile >= (ntiles > 0 ? ntiles : 1)) return;
+    const uint32_t tag = lb_tag(s_gen, lb.stage);
+    // warp w owns elements [t0 + w * 512, t0 + (w + 1) * 512), lane-striped per round
+    const long long w0 = (long long)tile * SCAN_TILE + (long long)warp * (32 * SCAN_ITEMS);
+    uint32_t x[SCAN_ITEMS];
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+        const long long i = w0 + r * 32 + lane;
+        x[r] = i < n ? load(i) : 0u;
+    }
+    uint32_t carry = 0;  // warp-exclusive running sum
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+        uint32_t inc = x[r];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+        x[r] = carry + inc - x[r];
         carry += tot;
     }
+    uint32_t wex;
+    const uint32_t agg = block_exclusive_scan<SCAN_THREADS>(lane == 0 ? carry : 0u, wex, s_warp);
+    wex = __shfl_sync(0xffffffffu, wex, 0);
+    if (warp == 0) {
+        unsigned long long *slot = lb.slots + tile;
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) lb_publish(slot, tag, LB_INC, agg);
+        } else {
+            if (lane == 0) lb_publish(slot, tag, LB_AGG, agg);
+            prefix = lb_exclusive_warp(lb.slots, tile, tag, lb.ctl);
+            if (lane == 0) lb_publish(slot, tag, LB_INC, prefix + agg);
+        }
+        if (lane == 0) s_prefix = prefix;
+        if (lane == 0 && tile == (ntiles > 0 ? ntiles - 1 : 0)) {
+            const uint32_t total = prefix + agg;
+            if (total32) *total32 = total;
+            if (total64) *total64 = (long long)total;
+            if (n_use) {
+                const bool over = capacity >= 0 && (long long)total > capacity;
+                *n_use = over ? 0u : total;
+                if (over) set_status(lb.ctl, STATUS_CAPACITY);
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t base = s_prefix + wex;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+        const long long i = w0 + r * 32 + lane;
+        if (i < n) out[i] = base + x[r];
+    }
 }
 
 template <class L>
-static void scan(L load, const uint32_t *n_dev, long long n_max, uint32_t *out, uint32_t *block_sums,
-                 uint32_t *total32, long long *total64, uint32_t *n_use, long long capacity, int *status,
-                 cudaStream_t st)
+static void scan(L load, const uint32_t *n_dev, long long n_max, uint32_t *out, uint32_t *total32, long long *total64,
+                 uint32_t *n_use, long long capacity, LB lb, cudaStream_t st, bool bump = false,
+                 uint32_t *zero_buf = nullptr, int zero_words = 0)
 {
-    int nb = (int)((n_max + 4 * SCAN_THREADS - 1) / (4 * SCAN_THREADS));
-    nb = nb < 1 ? 1 : (nb > SCAN_MAX_BLOCKS ? SCAN_MAX_BLOCKS : nb);
-    long long n_host = n_dev ? 0 : n_max;
-    count_launch(3);
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, block_sums);
-    k_scan_top<<<1, 1024, 0, st>>>(block_sums, nb, total32, total64, n_use, capacity, status);
-    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, block_sums, out);
+    long long nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb < 1) nb = 1;
+    const long long n_host = n_dev ? 0 : n_max;
+    count_launch();
+    k_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, out, total32, total64, n_use, capacity, lb,
+                                                  bump ? 1 : 0, zero_buf, zero_words);
 }
 
 // ------------------------------------------------------------------ compaction of visible splats
@@ -166,6 +293,14 @@ __global__ void __launch_bounds__(256) k_compact(long long n_entries, const int 
 
 // ------------------------------------------------------------------ radix sort (LSD, <= 8 bits/pass)
 
+__device__ __forceinline__ void chunk_of(long long n, int b, int nb, long long &lo, long long &hi)
+{
+    long long chunk = (n + nb - 1) / nb;
+    lo = (long long)b * chunk;
+    hi = lo + chunk < n ? lo + chunk : n;
+    if (lo > n) lo = n;
+}
+
 // Lanes of the warp holding the same digit as this lane (restricted to `valid`).
 __device__ __forceinline__ unsigned warp_peers(uint32_t d, int nbits, unsigned valid)
 {
@@ -177,6 +312,7 @@ __device__ __forceinline__ unsigned warp_peers(uint32_t d, int nbits, unsigned v
     return peers;
 }
 
+// counts[d * nb + b] = keys of block b's chunk with digit d
 __global__ void __launch_bounds__(RS_THREADS) k_radix_count(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
                                                             int shift, int nbits, uint32_t *__restrict__ counts)
 {
@@ -304,16 +440,17 @@ static int radix_blocks(long long n_max)
 // Stable LSD sort of (k0, v0) by key bits [shift0, shift0 + nbits); ping-pongs through
 // (k1, v1); the final pass writes to (kf, vf), which must not alias the last pass's source.
 // Digits of a pass are ceil(nbits / passes) wide. Keys move with their values, so bits
-// outside the sorted range travel along untouched.
+// outside the sorted range travel along untouched. Pass p's count scan is stage lb.stage + p.
 static void radix_sort(const uint32_t *n_dev, long long n_max, int shift0, int nbits, uint32_t *k0, uint32_t *v0,
-                       uint32_t *k1, uint32_t *v1, uint32_t *kf, uint32_t *vf, uint32_t *counts,
-                       uint32_t *block_sums, cudaStream_t st)
+                       uint32_t *k1, uint32_t *v1, uint32_t *kf, uint32_t *vf, uint32_t *counts, LB lb,
+                       cudaStream_t st)
 {
     if (nbits < 1) nbits = 1;
     const int passes = (nbits + 7) / 8;
     const int width = (nbits + passes - 1) / passes;
     const int nb = radix_blocks(n_max);
     const long long ncounts = 256LL * nb;
+    const int stage0 = lb.stage;
     for (int p = 0; p < passes; ++p) {
         const int lo = width * p, bits = nbits - lo < width ? nbits - lo : width;
         uint32_t *ks = (p & 1) ? k1 : k0, *vs = (p & 1) ? v1 : v0;
@@ -322,11 +459,15 @@ static void radix_sort(const uint32_t *n_dev, long long n_max, int shift0, int n
             kd = kf;
             vd = vf;
         }
+        lb.stage = stage0 + p;
         count_launch(2);
         k_radix_count<<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift0 + lo, bits, counts);
-        scan(LoadPlain{counts}, nullptr, ncounts, counts, block_sums, nullptr, nullptr, nullptr, -1, nullptr, st);
+        scan(LoadPlain{counts}, nullptr, ncounts, counts, nullptr, nullptr, nullptr, -1, lb, st);
         k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
     }
 }
+
+// Look-back words a scan of up to n elements needs (one per tile).
+static inline long long scan_slots(long long n) { return ((n > 0 ? n : 1) + SCAN_TILE - 1) / SCAN_TILE; }
 
 }  // namespace lobe
