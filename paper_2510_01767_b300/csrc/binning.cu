@@ -137,15 +137,19 @@ struct LoadChunks {  // work items (chunks of CHUNK splats) of super-tile s
     }
 };
 
-// the super-tile of work item w: largest s with chunk_base[s] <= w
-__device__ __forceinline__ int work_super(const uint32_t *chunk_base, int n_super, uint32_t w)
+// Work item table: work[w] = (super-tile, first pair, end pair) of chunk w, so that the chunk
+// kernels find their range with one load. One thread per super-tile writes its chunks.
+__global__ void __launch_bounds__(256) k_chunk_map(const uint32_t *__restrict__ super_start,
+                                                   const uint32_t *__restrict__ chunk_base, int n_super,
+                                                   uint4 *__restrict__ work)
 {
-    int lo = 0, hi = n_super - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (chunk_base[mid] <= w) lo = mid; else hi = mid - 1;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_super) return;
+    const uint32_t b0 = chunk_base[s], b1 = chunk_base[s + 1], p0 = super_start[s], p1 = super_start[s + 1];
+    for (uint32_t w = b0; w < b1; ++w) {
+        const uint32_t lo = p0 + (w - b0) * CHUNK;
+        work[w] = make_uint4((uint32_t)s, lo, min(lo + CHUNK, p1), 0u);
     }
-    return lo;
 }
 
 __device__ __forceinline__ bool covers(uint32_t key, int tx, int ty)
@@ -157,7 +161,7 @@ __device__ __forceinline__ bool covers(uint32_t key, int tx, int ty)
 // Pass 1: cnt[w * S*S + t] = splats of chunk w covering local tile t.
 template <int S>
 __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__restrict__ keys,
-                                                             const uint32_t *__restrict__ super_start,
+                                                             const uint4 *__restrict__ work,
                                                              const uint32_t *__restrict__ chunk_base, int n_super,
                                                              uint32_t *__restrict__ cnt)
 {
@@ -166,11 +170,9 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n_work = chunk_base[n_super];
     for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const int s = work_super(chunk_base, n_super, w);
-        const uint32_t lo = super_start[s] + (w - chunk_base[s]) * CHUNK;
-        const uint32_t hi = min(lo + CHUNK, super_start[s + 1]);
-        const uint32_t i = lo + threadIdx.x;
-        const uint32_t key = i < hi ? keys[i] : 0u;  // 0 = empty rectangle
+        const uint4 wk = work[w];
+        const uint32_t i = wk.y + threadIdx.x;
+        const uint32_t key = i < wk.z ? keys[i] : 0u;  // 0 = empty rectangle
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
@@ -187,26 +189,41 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__r
     }
 }
 
-// Pass 2, per (super-tile, local tile): chunk counts -> chunk offsets within the tile (in
-// place) and the tile's size -> tile_count[global tile].
+// Pass 2, one block per super-tile: per local tile, the chunk counts become each chunk's offset
+// within the tile (in place) and their sum the tile's size -> tile_count[global tile]. The
+// block's 256 threads are NT tiles x G groups; group g scans a contiguous run of the chunks.
 template <int S>
 __global__ void __launch_bounds__(256) k_chunk_prefix(const __grid_constant__ BatchParams P,
                                                       const uint32_t *__restrict__ chunk_base, uint32_t *__restrict__ cnt,
                                                       uint32_t *__restrict__ tile_count)
 {
-    constexpr int NT = S * S;
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(gid / NT), t = (int)(gid % NT);
-    if (s >= P.n_super) return;
-    uint32_t run = 0;
-    for (uint32_t w = chunk_base[s]; w < chunk_base[s + 1]; ++w) {
+    constexpr int NT = S * S, G = 256 / NT;
+    __shared__ uint32_t part[G][NT];
+    const int s = blockIdx.x, t = threadIdx.x % NT, g = threadIdx.x / NT;
+    const uint32_t c0 = chunk_base[s], c1 = chunk_base[s + 1];
+    const uint32_t per = (c1 - c0 + G - 1) / G;
+    const uint32_t w0 = min(c0 + g * per, c1), w1 = min(w0 + per, c1);
+    uint32_t sum = 0;
+    for (uint32_t w = w0; w < w1; ++w) sum += cnt[(size_t)w * NT + t];
+    part[g][t] = sum;
+    __syncthreads();
+    uint32_t run = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        const uint32_t v = part[q][t];
+        run += q < g ? v : 0u;
+        total += v;
+    }
+    for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t c = cnt[(size_t)w * NT + t];
         cnt[(size_t)w * NT + t] = run;
         run += c;
     }
-    const ItemParams &I = P.item[item_of_super(P, s)];
-    const int ls = s - I.super_off, tx = (ls % I.sgx) * S + t % S, ty = (ls / I.sgx) * S + t / S;
-    if (tx < I.gx && ty < I.gy) tile_count[I.tile_off + ty * I.gx + tx] = run;
+    if (g == 0) {
+        const ItemParams &I = P.item[item_of_super(P, s)];
+        const int ls = s - I.super_off, tx = (ls % I.sgx) * S + t % S, ty = (ls / I.sgx) * S + t / S;
+        if (tx < I.gx && ty < I.gy) tile_count[I.tile_off + ty * I.gx + tx] = total;
+    }
 }
 
 // Pass 3: each chunk's splats, in list order, to their tiles' ranges.
@@ -214,7 +231,7 @@ template <int S>
 __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constant__ BatchParams P,
                                                             const uint32_t *__restrict__ keys,
                                                             const uint32_t *__restrict__ vals,
-                                                            const uint32_t *__restrict__ super_start,
+                                                            const uint4 *__restrict__ work,
                                                             const uint32_t *__restrict__ chunk_base,
                                                             const uint32_t *__restrict__ cnt,
                                                             const int *__restrict__ tile_start, const uint32_t *n_use,
@@ -229,12 +246,11 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
     const int n_super = P.n_super;
     const uint32_t n_work = chunk_base[n_super];
     for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const int s = work_super(chunk_base, n_super, w);
-        const uint32_t lo = super_start[s] + (w - chunk_base[s]) * CHUNK;
-        const uint32_t hi = min(lo + CHUNK, super_start[s + 1]);
-        const uint32_t i = lo + threadIdx.x;
-        const uint32_t key = i < hi ? keys[i] : 0u;
-        const int id = i < hi ? (int)vals[i] : 0;
+        const uint4 wk = work[w];
+        const int s = (int)wk.x;
+        const uint32_t i = wk.y + threadIdx.x;
+        const uint32_t key = i < wk.z ? keys[i] : 0u;
+        const int id = i < wk.z ? (int)vals[i] : 0;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
@@ -339,17 +355,16 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
     const long long work_max = pair_capacity / CHUNK + P.n_super + 1;
     uint32_t *ts = reinterpret_cast<uint32_t *>(tile_start);
     if (P.n_super > 0) {
-        const int NT = P.S * P.S;
-        const unsigned pgrid = (unsigned)(((long long)P.n_super * NT + 255) / 256);
-        count_launch(2);
+        count_launch(3);
+        k_chunk_map<<<(P.n_super + 255) / 256, 256, 0, st>>>(b.super_start, b.chunk_base, P.n_super, b.work);
         if (P.S == 8) {
-            k_chunk_count<8><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.super_start, b.chunk_base,
+            k_chunk_count<8><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.work, b.chunk_base,
                                                                                 P.n_super, b.chunk_cnt);
-            k_chunk_prefix<8><<<pgrid, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
+            k_chunk_prefix<8><<<P.n_super, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
         } else {
-            k_chunk_count<4><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.super_start, b.chunk_base,
+            k_chunk_count<4><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.work, b.chunk_base,
                                                                                 P.n_super, b.chunk_cnt);
-            k_chunk_prefix<4><<<pgrid, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
+            k_chunk_prefix<4><<<P.n_super, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
         }
     }
     // the scan's grand total lands in tile_start[n_tiles] and in the caller's n_isect
@@ -369,10 +384,10 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
         count_launch();
         const unsigned grid = persistent_grid(b.work_max);
         if (P.S == 8)
-            k_chunk_emit<8><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.super_start, b.chunk_base,
+            k_chunk_emit<8><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.work, b.chunk_base,
                                                           b.chunk_cnt, tile_start, n_use, gauss_ids);
         else
-            k_chunk_emit<4><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.super_start, b.chunk_base,
+            k_chunk_emit<4><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.work, b.chunk_base,
                                                           b.chunk_cnt, tile_start, n_use, gauss_ids);
     }
     count_launch();
@@ -384,7 +399,8 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
 //
 // entry part: 6 arrays of max_entries words, radix digit counts, scalars, the scans' look-back
 //             words (one per 4096 elements of the longest scan)
-// pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong), per-chunk tile counts
+// pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong), the chunk work table
+//             (16 B per chunk), per-chunk tile counts
 // super part: super-tile list starts and chunk bases (max_super + 1 words each)
 // Look-back slots must be zero (or hold words of earlier calls) before first use.
 
@@ -402,7 +418,7 @@ size_t pair_scratch_bytes(long long max_pairs, long long max_super)
 {
     size_t i = (size_t)(max_pairs > 0 ? max_pairs : 1);
     size_t chunks = (size_t)(max_pairs / CHUNK + (max_super > 0 ? max_super : 1) + 1);
-    return 4 * words_rounded(i) + words_rounded(chunks * NT_MAX);
+    return 4 * words_rounded(i) + words_rounded(chunks * 4) + words_rounded(chunks * NT_MAX);
 }
 
 size_t super_scratch_bytes(long long max_super)
@@ -445,11 +461,13 @@ void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch 
     b.status = ctl;
 }
 
-void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b)
+void pair_scratch_carve(void *mem, long long max_pairs, long long max_super, BinScratch &b)
 {
     size_t i = (size_t)(max_pairs > 0 ? max_pairs : 1);
     Carver c{static_cast<char *>(mem)};
     b.skA = c.take(i); b.svA = c.take(i); b.skB = c.take(i); b.svB = c.take(i);
+    const size_t chunks = (size_t)(max_pairs / CHUNK) + (size_t)(max_super > 0 ? max_super : 1) + 1;
+    b.work = reinterpret_cast<uint4 *>(c.take(chunks * 4));
     b.chunk_cnt = c.take(1);  // the per-chunk counts run to the end of the region
 }
 

@@ -300,7 +300,7 @@ static lobe_status grow_pairs(lobe_ctx *ctx, long long need)
     if (e != cudaSuccess) return fail(ctx, LOBE_ERR_CUDA, "pair scratch clear: %s", cudaGetErrorString(e));
     ctx->max_pairs = n;
     ctx->pair_bytes = bytes;
-    pair_scratch_carve(ctx->pair_mem, n, ctx->bins);
+    pair_scratch_carve(ctx->pair_mem, n, ctx->max_super, ctx->bins);
     return LOBE_OK;
 }
 

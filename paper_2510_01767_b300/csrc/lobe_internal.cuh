@@ -218,6 +218,7 @@ struct BinScratch {
     unsigned long long *scan_slots;                    // decoupled look-back words of the scans
     uint32_t *skA, *svA, *skB, *svB;                   // [max_pairs]
     uint32_t *sp_keys, *sp_ids;                        // sorted super pairs (one of the A/B arrays)
+    uint4 *work;                                       // per chunk: (super-tile, first pair, end pair)
     uint32_t *chunk_cnt;                               // per (chunk, tile) counts, then offsets
     uint32_t *super_start, *chunk_base;                // [max_super + 1] each
     long long work_max;                                // bound on chunk work items of the last call
@@ -249,7 +250,7 @@ long long max_super_tiles();  // super-tile ids must fit the 16 key bits that ca
 long long max_scan_length(long long max_entries);  // longest scan the entry scratch serves (>= 2^22 tiles)
 constexpr size_t CTL_BYTES = 256;                  // control block of a binning scratch (zeroed once)
 void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch &b);
-void pair_scratch_carve(void *mem, long long max_pairs, BinScratch &b);
+void pair_scratch_carve(void *mem, long long max_pairs, long long max_super, BinScratch &b);
 void super_scratch_carve(void *mem, long long max_super, BinScratch &b);
 
 }  // namespace lobe

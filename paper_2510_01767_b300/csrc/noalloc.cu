@@ -70,7 +70,7 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
     BinScratch b{};
     entry_scratch_carve(p, kMaxEntries, status, b);
     p += entry_scratch_bytes(kMaxEntries);
-    pair_scratch_carve(p, kMaxPairs, b);
+    pair_scratch_carve(p, kMaxPairs, kMaxSuper, b);
     p += pair_scratch_bytes(kMaxPairs, kMaxSuper);
     super_scratch_carve(p, kMaxSuper, b);
 
