@@ -35,10 +35,15 @@ __device__ __forceinline__ void splat_rect(const BatchParams &P, const ItemParam
     tile_rect(uv.x, uv.y, radius[e], P.tw, P.th, I.gx, I.gy, x0, y0, x1, y1);
 }
 
-// super-rectangle area of the k-th depth-ordered visible splat
+// Per depth-ordered visible splat k: its super-rectangle area (area[k]) and what the pair
+// expansion needs, in three words: info0 = super-tile id of the rectangle's origin | super
+// grid width << 16, info1 = (x0, x1) and info2 = (y0, y1) of its tile rectangle relative to
+// that origin (16 bits each).
 __global__ void __launch_bounds__(256) k_super_area(const __grid_constant__ BatchParams P, const uint32_t *V_dev,
                                                     const uint32_t *__restrict__ order, const float *__restrict__ splat,
-                                                    const int *__restrict__ radius, uint32_t *__restrict__ area)
+                                                    const int *__restrict__ radius, uint32_t *__restrict__ area,
+                                                    uint32_t *__restrict__ info0, uint32_t *__restrict__ info1,
+                                                    uint32_t *__restrict__ info2)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= *V_dev) return;
@@ -47,71 +52,106 @@ __global__ void __launch_bounds__(256) k_super_area(const __grid_constant__ Batc
     int x0, y0, x1, y1;
     splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
     const int S = P.S;
-    area[k] = (uint32_t)(((x1 + S - 1) / S - x0 / S) * ((y1 + S - 1) / S - y0 / S));
+    const int sx0 = x0 / S, sy0 = y0 / S;
+    area[k] = (uint32_t)(((x1 + S - 1) / S - sx0) * ((y1 + S - 1) / S - sy0));
+    info0[k] = (uint32_t)(I.super_off + sy0 * I.sgx + sx0) | ((uint32_t)I.sgx << 16);
+    info1[k] = (uint32_t)(x0 - sx0 * S) | ((uint32_t)(x1 - sx0 * S) << 16);
+    info2[k] = (uint32_t)(y0 - sy0 * S) | ((uint32_t)(y1 - sy0 * S) << 16);
 }
 
-// Each warp takes 32 consecutive depth-ordered splats; their super pairs occupy one contiguous
-// output range, written lane-strided (coalesced); a lane finds its splat by binary search
-// over the warp's 32 offsets. Key = super-tile id << 16 | local rectangle (x0, x1, y0, y1 in
-// tiles relative to the super-tile origin, clipped to [0, S], 4 bits each).
-__global__ void __launch_bounds__(256) k_super_dup(const __grid_constant__ BatchParams P, const uint32_t *V_dev,
-                                                   const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
-                                                   const float *__restrict__ splat, const int *__restrict__ radius,
-                                                   const uint32_t *n_sp_use, uint32_t *__restrict__ skeys,
-                                                   uint32_t *__restrict__ svals)
+// Largest k in [0, n) with a[k] <= x, for non-decreasing a with a[0] <= x; called by a full
+// warp (32-way search: about log32(n) rounds of one load per lane).
+__device__ __forceinline__ uint32_t warp_upper_index(const uint32_t *a, uint32_t n, uint32_t x)
 {
     const int lane = threadIdx.x & 31;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + (uint32_t)lane * step;
+        const bool ok = idx < hi && a[idx] <= x;
+        const int c = __popc(__ballot_sync(0xffffffffu, ok));  // lanes 0..c-1 (a is sorted)
+        lo += (uint32_t)(c - 1) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// Expands the depth-ordered splats into super pairs, DUP_PAIRS output pairs per block (the
+// work is even whatever the splat sizes): the block finds the splats overlapping its output
+// range, marks each one's first pair, and a max-scan gives every pair its splat. Output p of
+// splat k (local index l = p - offs[k] over its super-rectangle, row-major) gets key
+// super-tile id << 16 | the splat's tile rectangle relative to that super-tile (x0, x1, y0, y1,
+// clipped to [0, S], 4 bits each), value = entry id.
+constexpr int DUP_PAIRS = 4096;
+constexpr int DUP_PER = DUP_PAIRS / 256;  // scan positions per thread
+
+__global__ void __launch_bounds__(256) k_super_dup(int S, const uint32_t *V_dev, const uint32_t *__restrict__ order,
+                                                   const uint32_t *__restrict__ offs,
+                                                   const uint32_t *__restrict__ info0,
+                                                   const uint32_t *__restrict__ info1,
+                                                   const uint32_t *__restrict__ info2, const uint32_t *n_sp_use,
+                                                   uint32_t *__restrict__ skeys, uint32_t *__restrict__ svals)
+{
+    __shared__ int s_idx[DUP_PAIRS + DUP_PAIRS / 32];  // padded: position j lives at j + j / 32
+    __shared__ uint32_t s_k[2];
+    __shared__ int s_wmax[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n = *n_sp_use;  // 0: no pairs, or more than the scratch holds
+    const uint32_t P0 = blockIdx.x * DUP_PAIRS;
+    if (P0 >= n) return;
+    const uint32_t P1 = min(P0 + DUP_PAIRS, n);
     const uint32_t V = *V_dev;
-    const bool warp_live = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) < V && *n_sp_use != 0;
-    if (warp_live) {  // (no pairs to emit when the scratch capacity was exceeded)
-        const bool valid = k < V;
-        const int S = P.S;
-        uint32_t off = 0xffffffffu, cnt = 0, base = 0, w = 1, sg = 1, e = 0;
-        int x0 = 0, y0 = 0, x1 = 0, y1 = 0, sx0 = 0, sy0 = 0;
-        if (valid) {
-            e = order[k];
-            off = offs[k];
-            const ItemParams &I = P.item[item_of_entry(P, e)];
-            splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
-            sx0 = x0 / S;
-            sy0 = y0 / S;
-            const int sx1 = (x1 + S - 1) / S, sy1 = (y1 + S - 1) / S;
-            base = (uint32_t)(I.super_off + sy0 * I.sgx + sx0);
-            w = (uint32_t)(sx1 - sx0);
-            sg = (uint32_t)I.sgx;
-            cnt = (uint32_t)((sx1 - sx0) * (sy1 - sy0));
-        }
-        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        const int last = 31 - __clz(vmask);
-        const uint32_t p0 = __shfl_sync(0xffffffffu, off, 0);
-        const uint32_t p1 = __shfl_sync(0xffffffffu, off + cnt, last);
-        for (uint32_t p = p0 + lane; p - lane < p1; p += 32) {
-            int j = 0;
+    if (warp < 2) {
+        const uint32_t k = warp_upper_index(offs, V, warp == 0 ? P0 : P1 - 1);
+        if (lane == 0) s_k[warp] = k;
+    }
+    for (int j = threadIdx.x; j < DUP_PAIRS + DUP_PAIRS / 32; j += 256) s_idx[j] = -1;
+    __syncthreads();
+    const uint32_t k0 = s_k[0], m = s_k[1] - k0 + 1;  // m <= DUP_PAIRS (every splat has a pair)
+    for (uint32_t i = threadIdx.x; i < m; i += 256) {
+        const uint32_t o = offs[k0 + i];
+        const uint32_t j = o > P0 ? o - P0 : 0u;
+        s_idx[j + j / 32] = (int)i;
+    }
+    __syncthreads();
+    // inclusive max-scan of s_idx: each thread owns DUP_PER consecutive positions
+    int v[DUP_PER], run = -1;
 #pragma unroll
-            for (int step = 16; step; step >>= 1) {
-                uint32_t o = __shfl_sync(0xffffffffu, off, j + step);
-                if (o <= p) j += step;
-            }
-            const uint32_t oj = __shfl_sync(0xffffffffu, off, j);
-            const uint32_t wj = __shfl_sync(0xffffffffu, w, j);
-            const uint32_t bj = __shfl_sync(0xffffffffu, base, j);
-            const uint32_t gj = __shfl_sync(0xffffffffu, sg, j);
-            const uint32_t ej = __shfl_sync(0xffffffffu, e, j);
-            const int rx0 = __shfl_sync(0xffffffffu, x0 - sx0 * S, j), rx1 = __shfl_sync(0xffffffffu, x1 - sx0 * S, j);
-            const int ry0 = __shfl_sync(0xffffffffu, y0 - sy0 * S, j), ry1 = __shfl_sync(0xffffffffu, y1 - sy0 * S, j);
-            if (p < p1) {
-                const uint32_t local = p - oj;
-                const int sy = (int)(local / wj), sx = (int)(local - sy * wj);
-                // the splat's rectangle relative to super-tile (sx, sy) of its super-rectangle
-                const int lx0 = max(rx0 - sx * S, 0), lx1 = min(rx1 - sx * S, S);
-                const int ly0 = max(ry0 - sy * S, 0), ly1 = min(ry1 - sy * S, S);
-                const uint32_t key = ((bj + (uint32_t)sy * gj + (uint32_t)sx) << KEY_SHIFT) |
-                                     (uint32_t)(lx0 | (lx1 << 4) | (ly0 << 8) | (ly1 << 12));
-                skeys[p] = key;
-                svals[p] = ej;
-            }
-        }
+    for (int r = 0; r < DUP_PER; ++r) {
+        const int j = DUP_PER * threadIdx.x + r;
+        run = max(run, s_idx[j + j / 32]);
+        v[r] = run;
+    }
+    int inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = max(inc, y);
+    }
+    if (lane == 31) s_wmax[warp] = inc;
+    __syncthreads();
+    int before = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) before = -1;
+    for (int w = 0; w < warp; ++w) before = max(before, s_wmax[w]);
+#pragma unroll
+    for (int r = 0; r < DUP_PER; ++r) {
+        const int j = DUP_PER * threadIdx.x + r;
+        s_idx[j + j / 32] = max(before, v[r]);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < (int)(P1 - P0); j += 256) {
+        const uint32_t k = k0 + (uint32_t)s_idx[j + j / 32];
+        const uint32_t p = P0 + (uint32_t)j;
+        const uint32_t i0 = info0[k], i1 = info1[k], i2 = info2[k];
+        const int rx0 = (int)(i1 & 0xffffu), rx1 = (int)(i1 >> 16), ry0 = (int)(i2 & 0xffffu), ry1 = (int)(i2 >> 16);
+        const uint32_t w = (uint32_t)((rx1 + S - 1) / S);
+        const uint32_t local = p - offs[k];
+        const int sy = (int)(local / w), sx = (int)(local - (uint32_t)sy * w);
+        const int lx0 = max(rx0 - sx * S, 0), lx1 = min(rx1 - sx * S, S);
+        const int ly0 = max(ry0 - sy * S, 0), ly1 = min(ry1 - sy * S, S);
+        skeys[p] = (((i0 & 0xffffu) + (uint32_t)sy * (i0 >> 16) + (uint32_t)sx) << KEY_SHIFT) |
+                   (uint32_t)(lx0 | (lx1 << 4) | (ly0 << 8) | (ly1 << 12));
+        svals[p] = order[k];
     }
 }
 
@@ -169,10 +209,13 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__r
     __shared__ uint32_t wc[BIN_THREADS / 32][NT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n_work = chunk_base[n_super];
-    for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const uint4 wk = work[w];
+    uint32_t w = blockIdx.x;
+    uint4 wk = w < n_work ? work[w] : make_uint4(0u, 0u, 0u, 0u);
+    while (w < n_work) {
         const uint32_t i = wk.y + threadIdx.x;
         const uint32_t key = i < wk.z ? keys[i] : 0u;  // 0 = empty rectangle
+        const uint32_t wn = w + gridDim.x;
+        const uint4 wkn = wn < n_work ? work[wn] : make_uint4(0u, 0u, 0u, 0u);  // next item, in flight
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
@@ -186,6 +229,8 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__r
             cnt[(size_t)w * NT + threadIdx.x] = c;
         }
         __syncthreads();
+        w = wn;
+        wk = wkn;
     }
 }
 
@@ -245,12 +290,24 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
     const unsigned lt = lanemask_lt();
     const int n_super = P.n_super;
     const uint32_t n_work = chunk_base[n_super];
-    for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const uint4 wk = work[w];
+    uint32_t w = blockIdx.x;
+    uint4 wk = w < n_work ? work[w] : make_uint4(0u, 0u, 0u, 0u);
+    while (w < n_work) {
+        // this chunk's splats, its tiles' bases and the next work item, loaded together
         const int s = (int)wk.x;
         const uint32_t i = wk.y + threadIdx.x;
         const uint32_t key = i < wk.z ? keys[i] : 0u;
         const int id = i < wk.z ? (int)vals[i] : 0;
+        uint32_t tbase = 0;
+        if (threadIdx.x < NT) {
+            const ItemParams &I = P.item[item_of_super(P, s)];
+            const int ls = s - I.super_off;
+            const int tx = (ls % I.sgx) * S + (int)threadIdx.x % S, ty = (ls / I.sgx) * S + (int)threadIdx.x / S;
+            const uint32_t ts = (tx < I.gx && ty < I.gy) ? (uint32_t)tile_start[I.tile_off + ty * I.gx + tx] : 0u;
+            tbase = ts + cnt[(size_t)w * NT + threadIdx.x];
+        }
+        const uint32_t wn = w + gridDim.x;
+        const uint4 wkn = wn < n_work ? work[wn] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
@@ -265,11 +322,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
                 wc[q][threadIdx.x] = r;
                 r += c;
             }
-            const ItemParams &I = P.item[item_of_super(P, s)];
-            const int ls = s - I.super_off;
-            const int tx = (ls % I.sgx) * S + (int)threadIdx.x % S, ty = (ls / I.sgx) * S + (int)threadIdx.x / S;
-            const uint32_t ts = (tx < I.gx && ty < I.gy) ? (uint32_t)tile_start[I.tile_off + ty * I.gx + tx] : 0u;
-            base[threadIdx.x] = ts + cnt[(size_t)w * NT + threadIdx.x];
+            base[threadIdx.x] = tbase;
         }
         __syncthreads();
 #pragma unroll
@@ -279,6 +332,8 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
             if (cov) gauss_ids[base[t] + wc[warp][t] + __popc(m & lt)] = id;
         }
         __syncthreads();
+        w = wn;
+        wk = wkn;
     }
 }
 
@@ -317,7 +372,8 @@ cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int 
     radix_sort(V, n, 0, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.counts, lb_of(b, ST_DEPTH_PASS), st);
     if (n > 0) {
         count_launch();
-        k_super_area<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, splat, radius, b.offs);
+        k_super_area<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, splat, radius, b.offs, b.dkA,
+                                                                  b.dvA, b.dkB);  // free after the depth sort
     }
     scan(LoadPlain{b.offs}, V, n, b.offs, sp_total, nullptr, n_sp, pair_capacity, lb_of(b, ST_SCAN_OFFS), st);
     return cudaGetLastError();
@@ -331,14 +387,15 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
 {
     const long long n = P.n_entries;
     uint32_t *V = b.scalars, *n_sp = b.scalars + 1, *n_use = b.scalars + 2;
-    if (n > 0) {
+    {
         count_launch();
-        k_super_dup<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, b.offs, splat, radius, n_sp, b.skA,
-                                                                 b.svA);
+        const long long nb = (pair_capacity + DUP_PAIRS - 1) / DUP_PAIRS;
+        k_super_dup<<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>(P.S, V, b.vis_pos, b.offs, b.dkA, b.dvA, b.dkB, n_sp,
+                                                                 b.skA, b.svA);
     }
     int nbits = 0;
     while ((1LL << nbits) < (long long)P.n_super) ++nbits;
-    const int passes = nbits < 1 ? 1 : (nbits + 7) / 8;
+    const int passes = nbits < 1 ? 1 : (nbits + 8) / 9;  // as radix_sort
     uint32_t *kfinal = (passes & 1) ? b.skB : b.skA;  // not the last pass's source
     uint32_t *vfinal = (passes & 1) ? b.svB : b.svA;
     radix_sort(n_sp, pair_capacity, KEY_SHIFT, nbits, b.skA, b.svA, b.skB, b.svB, kfinal, vfinal, b.counts,
@@ -410,7 +467,7 @@ static size_t slots_rounded(long long slots) { return (((size_t)slots * 8 + 255)
 size_t entry_scratch_bytes(long long max_entries)
 {
     size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
-    return 6 * words_rounded(e) + words_rounded(256ull * RS_MAX_BLOCKS) + words_rounded(16) +
+    return 6 * words_rounded(e) + words_rounded((size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS) + words_rounded(16) +
            slots_rounded(scan_slots(max_scan_length(max_entries)));
 }
 
@@ -454,7 +511,7 @@ void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch 
     Carver c{static_cast<char *>(mem)};
     b.vis_pos = c.take(e); b.dkA = c.take(e); b.dvA = c.take(e); b.dkB = c.take(e); b.dvB = c.take(e);
     b.offs = c.take(e);
-    b.counts = c.take(256ull * RS_MAX_BLOCKS);
+    b.counts = c.take((size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS);
     b.scalars = c.take(16);
     b.scan_slots = c.take_slots(scan_slots(max_scan_length(max_entries)));
     b.ctl = ctl;

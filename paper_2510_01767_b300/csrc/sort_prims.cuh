@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) k_compact(long long n_entries, const int 
     dvals[p] = (uint32_t)e;
 }
 
-// ------------------------------------------------------------------ radix sort (LSD, <= 8 bits/pass)
+// ------------------------------------------------------------------ radix sort (LSD, <= 9 bits/pass)
 
 __device__ __forceinline__ void chunk_of(long long n, int b, int nb, long long &lo, long long &hi)
 {
@@ -312,13 +312,17 @@ __device__ __forceinline__ unsigned warp_peers(uint32_t d, int nbits, unsigned v
     return peers;
 }
 
+// Radix passes take digits of up to 9 bits: DIG = 256 or 512 digit slots per pass.
+constexpr int RS_MAX_DIGITS = 512;
+
 // counts[d * nb + b] = keys of block b's chunk with digit d
+template <int DIG>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_count(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
                                                             int shift, int nbits, uint32_t *__restrict__ counts)
 {
-    __shared__ uint32_t h[RS_WARPS][256];
+    __shared__ uint32_t h[RS_WARPS][DIG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = lane; d < 256; d += 32) h[warp][d] = 0;
+    for (int d = lane; d < DIG; d += 32) h[warp][d] = 0;
     __syncwarp();
     long long lo, hi;
     chunk_of(*n_dev, blockIdx.x, gridDim.x, lo, hi);
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_count(const uint32_t *__re
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    for (int d = threadIdx.x; d < DIG; d += RS_THREADS) {
         uint32_t s = 0;
         for (int w = 0; w < RS_WARPS; ++w) s += h[w][d];
         counts[(long long)d * gridDim.x + blockIdx.x] = s;
@@ -349,25 +353,32 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_count(const uint32_t *__re
 }
 
 // One pass: block b scatters its chunk [lo, hi) to offsets[d * nb + b] + (running count).
+// Thread t handles digits t * DPT .. t * DPT + DPT - 1 (DPT = DIG / 256) in the per-digit steps.
+template <int DIG>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t *__restrict__ kin,
                                                               const uint32_t *__restrict__ vin,
                                                               uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                               const uint32_t *n_dev, int shift, int nbits,
                                                               const uint32_t *__restrict__ offsets)
 {
+    constexpr int DPT = DIG / RS_THREADS;
     __shared__ uint32_t s_k[RS_TILE];
     __shared__ uint32_t s_v[RS_TILE];
-    __shared__ uint32_t wcnt[RS_WARPS][256];
-    __shared__ uint32_t local_off[256], tile_cnt[256], grun[256];
+    __shared__ uint32_t wcnt[RS_WARPS][DIG];
+    __shared__ uint32_t local_off[DIG], tile_cnt[DIG], grun[DIG];
     __shared__ uint32_t scan_sm[RS_THREADS / 32 + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
     const unsigned lt = lanemask_lt();
     const uint32_t mask = (1u << nbits) - 1u;
     long long lo, hi;
     chunk_of(*n_dev, blockIdx.x, gridDim.x, lo, hi);
-    grun[tid] = offsets[(long long)tid * gridDim.x + blockIdx.x];  // RS_THREADS == 256 digits
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        grun[d] = offsets[(long long)d * gridDim.x + blockIdx.x];
+    }
     for (long long tb = lo; tb < hi; tb += RS_TILE) {
-        for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
+        for (int d = lane; d < DIG; d += 32) wcnt[warp][d] = 0;
         __syncwarp();
         uint32_t k[RS_ITEMS], v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
         bool ok[RS_ITEMS];
@@ -394,17 +405,28 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t *__
         }
         __syncthreads();
         {  // per digit: exclusive prefix over warps and the tile's digit totals
-            uint32_t run = 0;
+            uint32_t run[DPT], sum = 0;
 #pragma unroll
-            for (int w = 0; w < RS_WARPS; ++w) {
-                uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += c;
+            for (int q = 0; q < DPT; ++q) {
+                const int d = tid * DPT + q;
+                uint32_t r = 0;
+#pragma unroll
+                for (int w = 0; w < RS_WARPS; ++w) {
+                    uint32_t c = wcnt[w][d];
+                    wcnt[w][d] = r;
+                    r += c;
+                }
+                tile_cnt[d] = r;
+                run[q] = r;
+                sum += r;
             }
-            tile_cnt[tid] = run;
             uint32_t ex;
-            block_exclusive_scan<RS_THREADS>(run, ex, scan_sm);
-            local_off[tid] = ex;
+            block_exclusive_scan<RS_THREADS>(sum, ex, scan_sm);
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) {
+                local_off[tid * DPT + q] = ex;
+                ex += run[q];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -425,7 +447,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t *__
             vout[g] = s_v[i];
         }
         __syncthreads();
-        grun[tid] += tile_cnt[tid];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) grun[tid * DPT + q] += tile_cnt[tid * DPT + q];
         __syncthreads();
     }
 }
@@ -439,17 +462,17 @@ static int radix_blocks(long long n_max)
 
 // Stable LSD sort of (k0, v0) by key bits [shift0, shift0 + nbits); ping-pongs through
 // (k1, v1); the final pass writes to (kf, vf), which must not alias the last pass's source.
-// Digits of a pass are ceil(nbits / passes) wide. Keys move with their values, so bits
-// outside the sorted range travel along untouched. Pass p's count scan is stage lb.stage + p.
+// Passes = ceil(nbits / 9) with digits ceil(nbits / passes) wide. Keys move with their values,
+// so bits outside the sorted range travel along untouched. Pass p's count scan is stage
+// lb.stage + p.
 static void radix_sort(const uint32_t *n_dev, long long n_max, int shift0, int nbits, uint32_t *k0, uint32_t *v0,
                        uint32_t *k1, uint32_t *v1, uint32_t *kf, uint32_t *vf, uint32_t *counts, LB lb,
                        cudaStream_t st)
 {
     if (nbits < 1) nbits = 1;
-    const int passes = (nbits + 7) / 8;
+    const int passes = (nbits + 8) / 9;
     const int width = (nbits + passes - 1) / passes;
     const int nb = radix_blocks(n_max);
-    const long long ncounts = 256LL * nb;
     const int stage0 = lb.stage;
     for (int p = 0; p < passes; ++p) {
         const int lo = width * p, bits = nbits - lo < width ? nbits - lo : width;
@@ -461,9 +484,15 @@ static void radix_sort(const uint32_t *n_dev, long long n_max, int shift0, int n
         }
         lb.stage = stage0 + p;
         count_launch(2);
-        k_radix_count<<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift0 + lo, bits, counts);
-        scan(LoadPlain{counts}, nullptr, ncounts, counts, nullptr, nullptr, nullptr, -1, lb, st);
-        k_radix_scatter<<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
+        if (bits <= 8) {
+            k_radix_count<256><<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift0 + lo, bits, counts);
+            scan(LoadPlain{counts}, nullptr, 256LL * nb, counts, nullptr, nullptr, nullptr, -1, lb, st);
+            k_radix_scatter<256><<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
+        } else {
+            k_radix_count<512><<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift0 + lo, bits, counts);
+            scan(LoadPlain{counts}, nullptr, 512LL * nb, counts, nullptr, nullptr, nullptr, -1, lb, st);
+            k_radix_scatter<512><<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
+        }
     }
 }
 
