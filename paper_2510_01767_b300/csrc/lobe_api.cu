@@ -481,7 +481,15 @@ lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_
         P.set[s].sd_acc = g.sd_acc;
         P.set[s].sd_cnt = g.sd_cnt;
     }
-    CUDA_TRY(launch_project_bwd(P, proj->splat, proj->radius, grad2d, accumulate ? 1 : 0, ctx->stream), "project bwd");
+    // the list of Gaussians some item sees goes to the binning scratch (free once bin_sort has
+    // returned), its length to scalars[8]; at most n_entries Gaussians can be seen
+    if (!ctx->entry_mem || ctx->max_entries < P.n_entries) {
+        lobe_status s = grow_entries(ctx, P.n_entries);
+        if (s != LOBE_OK) return s;
+    }
+    CUDA_TRY(launch_project_bwd(P, proj->splat, proj->radius, grad2d, accumulate ? 1 : 0, ctx->bins.dkB,
+                                ctx->bins.scalars + 8, ctx->stream),
+             "project bwd");
     return LOBE_OK;
 }
 

@@ -261,53 +261,81 @@ __global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ Batc
 //   q -> R (normalised quaternion), then through the normalisation
 //   colour = max(0, SH + 0.5): masked where the raw value is negative; the view direction
 //   mu - campos carries a gradient to mu through the normalisation.
-// Per-view contributions to dL/dSigma (6 values), dL/dmu and dL/dlogit are summed in registers
-// over the set's items, the 48 SH gradients in a padded shared-memory row per thread; the
-// Sigma -> (s, q) step runs once per Gaussian. A block takes 64 consecutive Gaussians (one
-// contiguous 12 KB range of SH coefficients and of SH gradients per set): it first finds which
-// of them some item sees, stages their SH coefficients into shared memory with coalesced loads,
-// runs the per-Gaussian chain rule, then writes the SH gradients back with coalesced stores. In
-// accumulate mode a Gaussian no item sees is left untouched.
+// The adjoint runs in two kernels. The first visits every Gaussian once: it appends each one
+// that some item sees to a list (one atomic per warp; the list's order does not matter, every
+// Gaussian's result is computed on its own) and, unless accumulating, zeroes the gradients of
+// the others. The second walks the list, so every lane of every warp does the chain rule
+// (culled Gaussians, often most of a large set, cost no issue slots there). Per-view
+// contributions to dL/dSigma (6 values), dL/dmu and dL/dlogit are summed in registers over the
+// set's items, the 48 SH gradients in a padded shared-memory row per thread; the Sigma -> (s, q)
+// step runs once per Gaussian. A block of the second kernel takes 64 listed Gaussians, stages
+// their SH coefficients into shared memory (192 contiguous bytes per Gaussian) and writes their
+// SH gradients back the same way.
 
 constexpr int PB_THREADS = 64;
 constexpr int PB_ROW = 49;  // odd row stride: the per-thread rows fall in distinct banks
 
-// Walks the sets in step with an increasing Gaussian index (blocks may straddle set boundaries).
-struct SetCursor {
-    int s;
-    long long end;
-    __device__ SetCursor(const BatchParams &P, long long t0) : s(set_of_gauss(P, t0)) { end = end_of(P); }
-    __device__ long long end_of(const BatchParams &P) const { return s + 1 < P.n_sets ? P.set[s + 1].gauss_off : P.n_gauss; }
-    __device__ void seek(const BatchParams &P, long long t)
-    {
-        while (t >= end) {
-            ++s;
-            end = end_of(P);
-        }
+__global__ void __launch_bounds__(256) k_project_bwd_list(const __grid_constant__ BatchParams P,
+                                                          const int *__restrict__ radius, int accumulate,
+                                                          uint32_t *__restrict__ list, uint32_t *__restrict__ count)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    int s = 0;
+    long long g = 0;
+    if (t < P.n_gauss) {
+        s = set_of_gauss(P, t);
+        const SetParams &S = P.set[s];
+        g = t - S.gauss_off;
+        for (int k = 0; k < S.item_count && !any; ++k)
+            any = radius[P.item[P.set_items[S.item_begin + k]].entry_off + g] > 0;
     }
-};
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    if (m) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (any) list[base + __popc(m & lanemask_lt())] = (uint32_t)t;
+    }
+    if (t < P.n_gauss && !any && !accumulate) {
+        const SetParams &S = P.set[s];
+        for (int i = 0; i < 3; ++i) {
+            S.g_means[3 * g + i] = 0.f;
+            S.g_log_scales[3 * g + i] = 0.f;
+        }
+        reinterpret_cast<float4 *>(S.g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.g_logits[g] = 0.f;
+        float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
 
 __global__ void __launch_bounds__(PB_THREADS, 8)
     k_project_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
-                  const int *__restrict__ radius, const float4 *__restrict__ grad2d, int accumulate)
+                  const int *__restrict__ radius, const float4 *__restrict__ grad2d, int accumulate,
+                  const uint32_t *__restrict__ list, const uint32_t *__restrict__ count)
 {
     __shared__ float s_sh[PB_THREADS * PB_ROW];
     __shared__ float s_gsh[PB_THREADS * PB_ROW];
-    __shared__ unsigned char s_any[PB_THREADS];
-    const long long t0 = (long long)blockIdx.x * PB_THREADS;
-    const long long t = t0 + threadIdx.x;
-    const int nblk = (int)(P.n_gauss - t0 < PB_THREADS ? P.n_gauss - t0 : PB_THREADS);
-    const bool valid = threadIdx.x < nblk;
-    const int s = valid ? set_of_gauss(P, t) : 0;
+    __shared__ const float *s_src[PB_THREADS];  // the Gaussian's SH coefficients
+    __shared__ float *s_dst[PB_THREADS];        // and its SH gradients
+    const uint32_t nv = *count;
+    const long long b0 = (long long)blockIdx.x * PB_THREADS;
+    if (b0 >= (long long)nv) return;
+    const int nblk = (int)((long long)nv - b0 < PB_THREADS ? (long long)nv - b0 : PB_THREADS);
+    const bool any = threadIdx.x < nblk;  // every listed Gaussian is seen by some item
+    const long long t = any ? (long long)list[b0 + threadIdx.x] : 0;
+    const int s = any ? set_of_gauss(P, t) : 0;
     const SetParams &S = P.set[s];
     const long long g = t - S.gauss_off;
-    bool any = false;
-    if (valid)
-        for (int k = 0; k < S.item_count && !any; ++k)
-            any = radius[P.item[P.set_items[S.item_begin + k]].entry_off + g] > 0;
-    s_any[threadIdx.x] = any ? 1 : 0;
     World w;
-    if (any) load_world(S, g, w);  // in flight while the block stages its SH coefficients
+    if (any) {
+        load_world(S, g, w);  // in flight while the block stages its SH coefficients
+        s_src[threadIdx.x] = S.sh + 48 * g;
+        s_dst[threadIdx.x] = S.g_sh + 48 * g;
+    }
     float *gsh = s_gsh + threadIdx.x * PB_ROW;
     const float *shr = s_sh + threadIdx.x * PB_ROW;
 #pragma unroll
@@ -316,7 +344,6 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
     const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
     {
         // all loads first (no load waits on another), then the shared-memory stores
-        SetCursor cur(P, t0);
         const int per = (3 * nb + 3) / 4;  // float4 chunks holding the used coefficients
         const int total = nblk * per;       // <= 12 * PB_THREADS
         float4 q[12];
@@ -326,11 +353,7 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
             q[r] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (j < total) {
                 const int gi = j / per, c = j - gi * per;
-                if (s_any[gi]) {
-                    cur.seek(P, t0 + gi);
-                    const SetParams &Sg = P.set[cur.s];
-                    q[r] = reinterpret_cast<const float4 *>(Sg.sh + 48 * (t0 + gi - Sg.gauss_off))[c];
-                }
+                q[r] = reinterpret_cast<const float4 *>(s_src[gi])[c];
             }
         }
 #pragma unroll
@@ -473,18 +496,16 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
         }
     }
     // ---- write the per-Gaussian parameters
-    if (valid) {
+    if (any) {
         if (accumulate) {
-            if (any) {
-                for (int i = 0; i < 3; ++i) {
-                    S.g_means[3 * g + i] += gmu[i];
-                    S.g_log_scales[3 * g + i] += gls[i];
-                }
-                float4 *gq4 = reinterpret_cast<float4 *>(S.g_quats) + g;
-                float4 q = *gq4;
-                *gq4 = make_float4(q.x + gq[0], q.y + gq[1], q.z + gq[2], q.w + gq[3]);
-                S.g_logits[g] += glogit;
+            for (int i = 0; i < 3; ++i) {
+                S.g_means[3 * g + i] += gmu[i];
+                S.g_log_scales[3 * g + i] += gls[i];
             }
+            float4 *gq4 = reinterpret_cast<float4 *>(S.g_quats) + g;
+            float4 q = *gq4;
+            *gq4 = make_float4(q.x + gq[0], q.y + gq[1], q.z + gq[2], q.w + gq[3]);
+            S.g_logits[g] += glogit;
         } else {
             for (int i = 0; i < 3; ++i) {
                 S.g_means[3 * g + i] = gmu[i];
@@ -499,18 +520,14 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
         }
     }
     __syncthreads();
-    // ---- SH gradients of the block's Gaussians, coalesced: consecutive threads take
-    // consecutive floats of the block's (set-contiguous) gradient range
-    SetCursor cur(P, t0);
+    // ---- SH gradients of the block's Gaussians: 12 float4 per Gaussian, consecutive threads
+    // take consecutive chunks of one Gaussian's 192 bytes
 #pragma unroll
     for (int r = 0; r < 12; ++r) {
         const int j = threadIdx.x + r * PB_THREADS;  // float4 slot: Gaussian j / 12, chunk j % 12
         if (j >= nblk * 12) break;
         const int gi = j / 12, c = j - gi * 12;
-        if (accumulate && !s_any[gi]) continue;
-        cur.seek(P, t0 + gi);
-        const SetParams &Sg = P.set[cur.s];
-        float4 *dst = reinterpret_cast<float4 *>(Sg.g_sh + 48 * (t0 + gi - Sg.gauss_off)) + c;
+        float4 *dst = reinterpret_cast<float4 *>(s_dst[gi]) + c;
         const float *v = s_gsh + gi * PB_ROW + 4 * c;
         float4 a = make_float4(v[0], v[1], v[2], v[3]);
         if (accumulate) {
@@ -542,13 +559,16 @@ cudaError_t launch_visibility(const BatchParams &P, cudaStream_t st)
 }
 
 cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const int *radius, const float *grad2d,
-                               int accumulate, cudaStream_t st)
+                               int accumulate, uint32_t *list, uint32_t *count, cudaStream_t st)
 {
     if (P.n_gauss == 0) return cudaSuccess;
-    unsigned blocks = (unsigned)((P.n_gauss + PB_THREADS - 1) / PB_THREADS);
-    count_launch();
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    count_launch(2);
+    k_project_bwd_list<<<(unsigned)((P.n_gauss + 255) / 256), 256, 0, st>>>(P, radius, accumulate, list, count);
+    const unsigned blocks = (unsigned)((P.n_gauss + PB_THREADS - 1) / PB_THREADS);
     k_project_bwd<<<blocks, PB_THREADS, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
-                                          reinterpret_cast<const float4 *>(grad2d), accumulate);
+                                                 reinterpret_cast<const float4 *>(grad2d), accumulate, list, count);
     return cudaGetLastError();
 }
 
