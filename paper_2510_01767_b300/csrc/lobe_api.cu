@@ -483,12 +483,13 @@ lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_
     }
     // the list of Gaussians some item sees goes to the binning scratch (free once bin_sort has
     // returned), its length to scalars[8]; at most n_entries Gaussians can be seen
-    if (!ctx->entry_mem || ctx->max_entries < P.n_entries) {
-        lobe_status s = grow_entries(ctx, P.n_entries);
+    // (the compaction's look-back words, one per 4096 Gaussians, come from the same scratch)
+    if (!ctx->entry_mem || ctx->max_entries < P.n_entries || max_scan_length(ctx->max_entries) < P.n_gauss) {
+        lobe_status s = grow_entries(ctx, P.n_entries > P.n_gauss ? P.n_entries : P.n_gauss);
         if (s != LOBE_OK) return s;
     }
     CUDA_TRY(launch_project_bwd(P, proj->splat, proj->radius, grad2d, accumulate ? 1 : 0, ctx->bins.dkB,
-                                ctx->bins.scalars + 8, ctx->stream),
+                                ctx->bins.scalars + 8, ctx->bins.scan_slots, ctx->bins.ctl, ctx->stream),
              "project bwd");
     return LOBE_OK;
 }

@@ -232,7 +232,7 @@ void count_launch(int n = 1);
 cudaError_t launch_project_fwd(const BatchParams &, float *, int *, int *, cudaStream_t);
 cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
 cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, uint32_t *list,
-                               uint32_t *count, cudaStream_t);
+                               uint32_t *count, unsigned long long *lb_slots, int *ctl, cudaStream_t);
 cudaError_t launch_render_fwd(const BatchParams &, const float *, const int *, const int *, float *, float *, int *,
                               cudaStream_t);
 cudaError_t launch_render_bwd(const BatchParams &, bool, const float *, const int *, const int *, const float *,

@@ -14,7 +14,7 @@
 //   opacity = sigmoid(logit). Culled (radius 0): z outside [near, far] (z in double, Sec. 3.3
 //   frustum culling), |x/z| or |y/z| beyond 1.3 tan(fov/2), det <= 0, empty tile rectangle,
 //   crop_mask == 0 (visibility cropping, Sec. 3.3).
-#include "lobe_internal.cuh"
+#include "lookback.cuh"
 
 namespace lobe {
 
@@ -275,41 +275,86 @@ __global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ Batc
 constexpr int PB_THREADS = 64;
 constexpr int PB_ROW = 49;  // odd row stride: the per-thread rows fall in distinct banks
 
-__global__ void __launch_bounds__(256) k_project_bwd_list(const __grid_constant__ BatchParams P,
-                                                          const int *__restrict__ radius, int accumulate,
-                                                          uint32_t *__restrict__ list, uint32_t *__restrict__ count)
+constexpr int PL_THREADS = 256, PL_ITEMS = 16, PL_TILE = PL_THREADS * PL_ITEMS;  // 4096 Gaussians per tile
+
+// List (ascending, so neighbours in the list share cache sectors) of the Gaussians some item
+// sees, by a single-pass compaction with decoupled look-back; the last tile writes the count.
+// Unless accumulating, the gradients of the other Gaussians are zeroed here.
+__global__ void __launch_bounds__(PL_THREADS) k_project_bwd_list(const __grid_constant__ BatchParams P,
+                                                                 const int *__restrict__ radius, int accumulate,
+                                                                 uint32_t *__restrict__ list, uint32_t *__restrict__ count,
+                                                                 LB lb)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool any = false;
-    int s = 0;
-    long long g = 0;
-    if (t < P.n_gauss) {
-        s = set_of_gauss(P, t);
-        const SetParams &S = P.set[s];
-        g = t - S.gauss_off;
-        for (int k = 0; k < S.item_count && !any; ++k)
-            any = radius[P.item[P.set_items[S.item_begin + k]].entry_off + g] > 0;
+    __shared__ int s_tile;
+    __shared__ uint32_t s_gen, s_prefix;
+    __shared__ uint32_t s_warp[PL_THREADS / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        int tk;
+        uint32_t gen;
+        lb_take(lb.ctl, lb.stage, true, tk, gen);  // opens this call's look-back generation
+        s_tile = tk;
+        s_gen = gen;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, any);
-    if (m) {
-        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (any) list[base + __popc(m & lanemask_lt())] = (uint32_t)t;
-    }
-    if (t < P.n_gauss && !any && !accumulate) {
-        const SetParams &S = P.set[s];
-        for (int i = 0; i < 3; ++i) {
-            S.g_means[3 * g + i] = 0.f;
-            S.g_log_scales[3 * g + i] = 0.f;
-        }
-        reinterpret_cast<float4 *>(S.g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        S.g_logits[g] = 0.f;
-        float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+    __syncthreads();
+    const int tile = s_tile;
+    const long long n = P.n_gauss;
+    const long long ntiles = (n + PL_TILE - 1) / PL_TILE;
+    if (tile >= (ntiles > 0 ? ntiles : 1)) return;
+    const uint32_t tag = lb_tag(s_gen, lb.stage);
+    const long long w0 = (long long)tile * PL_TILE + (long long)warp * (32 * PL_ITEMS);
+    const unsigned lt = lanemask_lt();
+    bool vis[PL_ITEMS];
+    uint32_t rank[PL_ITEMS], carry = 0;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < PL_ITEMS; ++r) {
+        const long long t = w0 + r * 32 + lane;
+        vis[r] = false;
+        if (t < n) {
+            const int s = set_of_gauss(P, t);
+            const SetParams &S = P.set[s];
+            const long long g = t - S.gauss_off;
+            for (int k = 0; k < S.item_count && !vis[r]; ++k)
+                vis[r] = radius[P.item[P.set_items[S.item_begin + k]].entry_off + g] > 0;
+            if (!vis[r] && !accumulate) {
+                for (int i = 0; i < 3; ++i) {
+                    S.g_means[3 * g + i] = 0.f;
+                    S.g_log_scales[3 * g + i] = 0.f;
+                }
+                reinterpret_cast<float4 *>(S.g_quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                S.g_logits[g] = 0.f;
+                float4 *d = reinterpret_cast<float4 *>(S.g_sh + 48 * g);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, vis[r]);
+        rank[r] = carry + __popc(m & lt);
+        carry += __popc(m);
     }
+    uint32_t wex;
+    const uint32_t agg = block_exclusive_scan<PL_THREADS>(lane == 0 ? carry : 0u, wex, s_warp);
+    wex = __shfl_sync(0xffffffffu, wex, 0);
+    if (warp == 0) {
+        unsigned long long *slot = lb.slots + tile;
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) lb_publish(slot, tag, LB_INC, agg);
+        } else {
+            if (lane == 0) lb_publish(slot, tag, LB_AGG, agg);
+            prefix = lb_exclusive_warp(lb.slots, tile, tag, lb.ctl);
+            if (lane == 0) lb_publish(slot, tag, LB_INC, prefix + agg);
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (tile == (ntiles > 0 ? ntiles - 1 : 0)) *count = prefix + agg;
+        }
+    }
+    __syncthreads();
+    const uint32_t base = s_prefix + wex;
+#pragma unroll
+    for (int r = 0; r < PL_ITEMS; ++r)
+        if (vis[r]) list[base + rank[r]] = (uint32_t)(w0 + r * 32 + lane);
 }
 
 __global__ void __launch_bounds__(PB_THREADS, 8)
@@ -335,6 +380,12 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
         load_world(S, g, w);  // in flight while the block stages its SH coefficients
         s_src[threadIdx.x] = S.sh + 48 * g;
         s_dst[threadIdx.x] = S.g_sh + 48 * g;
+        // the first item's per-entry inputs, toward L2 meanwhile
+        const long long e0 = P.item[P.set_items[S.item_begin]].entry_off + g;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e0));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e0 + 2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(splat + 3 * e0 + 1));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(radius + e0));
     }
     float *gsh = s_gsh + threadIdx.x * PB_ROW;
     const float *shr = s_sh + threadIdx.x * PB_ROW;
@@ -559,13 +610,14 @@ cudaError_t launch_visibility(const BatchParams &P, cudaStream_t st)
 }
 
 cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const int *radius, const float *grad2d,
-                               int accumulate, uint32_t *list, uint32_t *count, cudaStream_t st)
+                               int accumulate, uint32_t *list, uint32_t *count, unsigned long long *lb_slots, int *ctl,
+                               cudaStream_t st)
 {
     if (P.n_gauss == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
     count_launch(2);
-    k_project_bwd_list<<<(unsigned)((P.n_gauss + 255) / 256), 256, 0, st>>>(P, radius, accumulate, list, count);
+    const unsigned lblocks = (unsigned)((P.n_gauss + PL_TILE - 1) / PL_TILE);
+    k_project_bwd_list<<<lblocks, PL_THREADS, 0, st>>>(P, radius, accumulate, list, count,
+                                                       LB{lb_slots, ctl, ST_PBWD_LIST});
     const unsigned blocks = (unsigned)((P.n_gauss + PB_THREADS - 1) / PB_THREADS);
     k_project_bwd<<<blocks, PB_THREADS, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
                                                  reinterpret_cast<const float4 *>(grad2d), accumulate, list, count);
