@@ -22,9 +22,10 @@
 // splats staged in warp-private shared memory (the next batch is prefetched into registers
 // while the current one is composited). Per splat a lane loads the splat once and applies
 // it to its PX pixels, sharing the column terms of the exponent. The adjoint sums each
-// splat's 9 gradient values over the lane's pixels in registers, then over the warp with
-// shuffles, and one lane adds them to global memory with vector reductions: one update per
-// splat per warp (256 pixels) instead of one per pixel. Warps need no block barriers.
+// splat's 9 gradient values over the lane's pixels in registers, then over the warp with a
+// reduce-scatter butterfly that leaves each total in its own lane, and nine lanes add them to
+// global memory in one instruction: one update per splat per warp (128 pixels) instead of one
+// per pixel. Warps need no block barriers.
 #include "lobe_internal.cuh"
 
 namespace lobe {
@@ -251,6 +252,41 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     }
 }
 
+// Sum over the warp of nine per-lane values, reduce-scattered (a butterfly that halves the set
+// of values each lane carries at every step: 5 + 3 + 2 + 1 + 1 shuffles instead of 9 x 5).
+// Returns the total of value `idx` in 18 lanes (idx in [0, 9), one writer per index: lanes with
+// bit 0 set get idx = -1) and idx = -1 elsewhere. Lane bits 4, 3, 2, 1 pick, in turn, which
+// half of the remaining values a lane keeps.
+__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int &idx)
+{
+    const int lane = threadIdx.x & 31;
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2;
+    float w[5];  // values {0..4} (bit 4 clear) or {5..8} (bit 4 set)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float lo = v[i], hi = i < 4 ? v[5 + i] : 0.0f;
+        w[i] = (b16 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b16 ? lo : hi, 16);
+    }
+    float x[3];  // w{0,1,2} or w{3,4}
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float a = w[i], b = i < 2 ? w[3 + i] : 0.0f;
+        x[i] = (b8 ? b : a) + __shfl_xor_sync(0xffffffffu, b8 ? a : b, 8);
+    }
+    float y[2];  // x{0,1} or x{2}
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float a = x[i], b = i < 1 ? x[2] : 0.0f;
+        y[i] = (b4 ? b : a) + __shfl_xor_sync(0xffffffffu, b4 ? a : b, 4);
+    }
+    float z = (b2 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, b2 ? y[0] : y[1], 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    const int q = b4 ? (b2 ? -1 : 2) : (b2 ? 1 : 0);   // position in x
+    const int p = q < 0 ? -1 : (b8 ? (q <= 1 ? 3 + q : -1) : q);  // position in w
+    idx = (p < 0 || (lane & 1)) ? -1 : (b16 ? (p <= 3 ? 5 + p : -1) : p);
+    return z;
+}
+
 template <int TW, int TH, int PX, bool RECOMPUTE>
 __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     k_render_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
@@ -366,24 +402,13 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
                 }
             }
             if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    du += __shfl_xor_sync(0xffffffffu, du, o);
-                    dv += __shfl_xor_sync(0xffffffffu, dv, o);
-                    dA += __shfl_xor_sync(0xffffffffu, dA, o);
-                    dB += __shfl_xor_sync(0xffffffffu, dB, o);
-                    dC += __shfl_xor_sync(0xffffffffu, dC, o);
-                    dop += __shfl_xor_sync(0xffffffffu, dop, o);
-                    dr += __shfl_xor_sync(0xffffffffu, dr, o);
-                    dg += __shfl_xor_sync(0xffffffffu, dg, o);
-                    db += __shfl_xor_sync(0xffffffffu, db, o);
-                }
-                if (lane == 0) {
-                    float *gp = grad2d + 12LL * st.id[j];
+                const float vals[9] = {du, dv, dA, dB, dC, dop, dr, dg, db};
+                int idx;
+                const float tot = warp_reduce9(vals, idx);
+                if (idx >= 0) {
                     // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
-                    red_add_v4(gp, du, dv, -0.5f * LOG2E * dA, -LOG2E * dB);
-                    red_add_v4(gp + 4, -0.5f * LOG2E * dC, dop, dr, dg);
-                    red_add_f32(gp + 8, db);
+                    const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
+                    red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
                 }
             }
         }
