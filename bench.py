@@ -329,39 +329,71 @@ def main():
     gaussians = sum(s.n for s in sets) * K * world
     value = pixels / total_s / 1e6
 
-    # ---- end to end through host buffers (pinned), copies inside the timed region
+    # ---- end to end through host buffers (pinned), copies inside the timed region. Every step
+    # uploads its inputs (parameters, dL/dC) and downloads its results (image, parameter
+    # gradients); device buffers are doubled so that step i+1's uploads and step i-1's downloads
+    # run on their own streams (copy engines) while step i's kernels run.
     host_params = [{k: getattr(s, k).detach().cpu().pin_memory() for k in lobe.PARAM_KEYS} for s in sets]
+    host_crop = [s.crop_mask.cpu().pin_memory() if s.crop_mask is not None else None for s in sets]
     host_dL = dL.cpu().pin_memory()
-    host_rgb = torch.empty_like(image.rgb, device="cpu").pin_memory()
-    host_grads = [{k: torch.empty_like(g[k], device="cpu").pin_memory() for k in lobe.PARAM_KEYS} for g in grads]
+    host_rgb = [torch.empty_like(image.rgb, device="cpu").pin_memory() for _ in range(2)]
+    host_grads = [[{k: torch.empty_like(g[k], device="cpu").pin_memory() for k in lobe.PARAM_KEYS} for g in grads]
+                  for _ in range(2)]
     h2d = sum(t.numel() * t.element_size() for d in host_params for t in d.values()) + host_dL.numel() * 4
-    d2h = host_rgb.numel() * 4 + sum(t.numel() * t.element_size() for d in host_grads for t in d.values())
+    h2d += sum(c.numel() for c in host_crop if c is not None)
+    d2h = host_rgb[0].numel() * 4 + sum(t.numel() * t.element_size() for d in host_grads[0] for t in d.values())
+    bsets = [[lobe.GaussianSet(**{k: torch.empty_like(getattr(s, k)) for k in lobe.PARAM_KEYS},
+                               crop_mask=torch.empty_like(s.crop_mask) if s.crop_mask is not None else None)
+              for s in sets] for _ in range(2)]
+    bbatch = [lobe.Batch(bs, wl.cameras, wl.items, wl.blocks) for bs in bsets]
+    bdL = [torch.empty_like(dL) for _ in range(2)]
+    bimage = [lobe.raster.empty_image(batch.n_pixels) for _ in range(2)]
+    bgrads = [lobe.zero_grads(batch, sd=False) for _ in range(2)]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]    # inputs of buffer b uploaded
+    ev_used = [torch.cuda.Event() for _ in range(2)]  # kernels done with buffer b
+    ev_out = [torch.cuda.Event() for _ in range(2)]   # results of buffer b downloaded
 
-    def e2e_step():
-        for s, hp in zip(sets, host_params):
-            for k in lobe.PARAM_KEYS:
-                getattr(s, k).copy_(hp[k], non_blocking=True)
-        dL.copy_(host_dL, non_blocking=True)
-        lobe.project(ctx, batch, proj)
-        lobe.bin_sort(ctx, batch, proj, bins, sync=False)
-        lobe.render_fwd(ctx, batch, proj, bins, image)
-        lobe.render_bwd(ctx, batch, proj, bins, image, dL, grad2d)
-        lobe.project_bwd(ctx, batch, proj, grad2d, grads, accumulate=False)
-        host_rgb.copy_(image.rgb, non_blocking=True)
-        for g, hg in zip(grads, host_grads):
-            for k in lobe.PARAM_KEYS:
-                hg[k].copy_(g[k], non_blocking=True)
+    def e2e_step(i):
+        b = i & 1
+        with torch.cuda.stream(up):
+            up.wait_event(ev_used[b])  # step i-2 finished reading these inputs
+            for s, hp, hc in zip(bsets[b], host_params, host_crop):
+                for k in lobe.PARAM_KEYS:
+                    getattr(s, k).copy_(hp[k], non_blocking=True)
+                if hc is not None:
+                    s.crop_mask.copy_(hc, non_blocking=True)
+            bdL[b].copy_(host_dL, non_blocking=True)
+            ev_in[b].record(up)
+        stream.wait_event(ev_in[b])
+        stream.wait_event(ev_out[b])  # step i-2's results have left these buffers
+        lobe.project(ctx, bbatch[b], proj)
+        lobe.bin_sort(ctx, bbatch[b], proj, bins, sync=False)
+        lobe.render_fwd(ctx, bbatch[b], proj, bins, bimage[b])
+        lobe.render_bwd(ctx, bbatch[b], proj, bins, bimage[b], bdL[b], grad2d)
+        lobe.project_bwd(ctx, bbatch[b], proj, grad2d, bgrads[b], accumulate=False)
+        ev_used[b].record(stream)
+        with torch.cuda.stream(down):
+            down.wait_event(ev_used[b])
+            host_rgb[b].copy_(bimage[b].rgb, non_blocking=True)
+            for g, hg in zip(bgrads[b], host_grads[b]):
+                for k in lobe.PARAM_KEYS:
+                    hg[k].copy_(g[k], non_blocking=True)
+            ev_out[b].record(down)
 
-    for _ in range(2):
-        e2e_step()
+    for i in range(2):
+        e2e_step(i)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
-    e0.record(stream)
-    for _ in range(K):
-        e2e_step()
-    e1.record(stream)
+    torch.cuda.synchronize()
+    e0.record(up)  # before the first upload
+    for i in range(K):
+        e2e_step(i)
+    for ev in ev_out:
+        stream.wait_event(ev)
+    e1.record(stream)  # after the last download
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
     if world > 1:
