@@ -35,13 +35,14 @@ L2_BYTES = 126 * 2 ** 20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 # Algorithmic work per unit, counted from the operations the method needs (not the SIMT
-# lanes a kernel happens to burn): see DESIGN.md, "Roofline per stage".
+# lanes a kernel happens to burn).
 FLOP_FWD_PAIR = 19    # per (pixel, splat) pair up to the last contributor, FMA = 2 FLOP
 FLOP_BWD_PAIR = 55
 PROJ_BYTES_VISIBLE = 236 + 56   # params in, splat record + radius + tile count out
 PROJ_BYTES_CULLED = 44 + 8      # mean/scale/quat/logit in, radius + count out
 PROJ_BWD_BYTES = 236 + 48 + 236 + 8  # params + 2D grads in, param grads + radius/opacity out
-SORT_BYTES_PAIR = 4 + 4 + 4     # pair written once (tile key), id read once, sorted id written
+SORT_BYTES_PAIR = 12 + 12 + 12 + 8  # per intersection for duplication + pair sort + ranges (key/value written,
+#                                     read, sorted and written, range read); this binning moves fewer (see traffic)
 
 
 def parse():

@@ -22,7 +22,7 @@
  * Every floating-point quantity is double. Inputs that the GPU sees as float32 are
  * passed in already widened, so both sides start from the same values.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - camera space is OpenCV (x right, y down, +z forward); pixel (i,j) has centre
  *     (i+0.5, j+0.5); u = fx*x/z + cx, v = fy*y/z + cy.
  *   - cull when z < near or z > far, when |x/z| > 1.3*W/(2fx) or |y/z| > 1.3*H/(2fy),
