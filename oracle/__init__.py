@@ -39,9 +39,13 @@ F_GUARD, F_RADIUS, F_RECT, F_COLOR = 1, 2, 4, 8
 def build(force: bool = False) -> str:
     """Compile lobe_oracle.c into liblobe_oracle.so (gcc, -O2, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        # compile to a private file and rename it into place, so that processes building at
+        # the same time (spawned test ranks) never load a half-written library
+        tmp = f"{_LIB}.{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", _LIB, _SRC, "-lm"]
+               "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
     return _LIB
 
 

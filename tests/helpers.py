@@ -15,6 +15,22 @@ IMG_ATOL = 1e-4
 GRAD_RTOL = 1e-3
 GRAD_FLOOR = 1e-3
 
+# largest error seen per named check in this session (printed at the end of the run)
+REPORT: dict = {}
+
+
+def record(name, value):
+    REPORT[name] = max(REPORT.get(name, 0.0), float(value))
+    return value
+
+
+def assert_img_close(gpu, orc, name):
+    """Max-abs image error (spec bar 1e-4), recorded under `name`."""
+    d = float(np.abs(np.asarray(gpu, np.float64) - np.asarray(orc, np.float64)).max()) if np.size(orc) else 0.0
+    record(name, d)
+    assert d <= IMG_ATOL, f"{name}: max-abs error {d:.3e} > {IMG_ATOL}"
+    return d
+
 
 def rect_tiles(mean2d, radius, cam, tile):
     """Tile rectangle area of each splat, computed exactly from float32 u, v and integer r."""
@@ -91,6 +107,7 @@ def sum_rel_err(gpu, orc, abs_sum):
 
 def assert_grad_close(gpu, orc, name, rtol=GRAD_RTOL):
     err = grad_rel_err(gpu, orc)
+    record("grad rel " + name, err)
     assert err <= rtol, f"{name}: relative error {err:.3e} > {rtol}"
     return err
 

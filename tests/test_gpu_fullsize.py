@@ -17,7 +17,7 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import IMG_ATOL, differing_rects, grad_rel_err, oracle_grad2d_array, rect_of, sum_rel_err
+from tests.helpers import IMG_ATOL, differing_rects, grad_rel_err, oracle_grad2d_array, rect_of, record, sum_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +69,7 @@ def check_item(g64, cam, tile, gpu_rgb, gpu_ids, gpu_ts, tile_off, entry_off, wi
         ok = img.flags[y0:y1, x0:x1] == 0
         assert ok.mean() > 0.9
         d = np.abs(gpu_rgb[:, y0:y1, x0:x1] - img.rgb[:, y0:y1, x0:x1])[:, ok]
+        record(f"image full size {cam['width']}x{cam['height']}", d.max())
         assert d.max() <= IMG_ATOL, d.max()
         compared += int(ok.sum())
     return p, marg, pxf_all, compared
@@ -145,12 +146,14 @@ def run_single(wl, crop=None, n_win=3):
     for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
                        ("color", slice(6, 9))]:
         err = sum_rel_err(got2[ok, cols], want2[ok, cols], A.a[ok, cols])
+        record(f"grad2d sum rel {name} full size {cam['width']}x{cam['height']}", err)
         assert err <= 1e-3, (name, err)
     # projection adjoint at full size, fed the oracle's 2D gradients
     want = oracle.project_bwd(g64, cam, tot, tile, crop=crop, aabb=aabb)
     grads = lobe.project_bwd(ctx, batch, proj, torch.as_tensor(want2, dtype=torch.float32).cuda())
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
         err = grad_rel_err(grads[0][k].cpu().numpy()[ok], getattr(want, k)[ok])
+        record(f"grad rel {k} full size {cam['width']}x{cam['height']}", err)
         assert err <= 1e-3, (k, err)
 
 

@@ -14,7 +14,8 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import (IMG_ATOL, assert_grad_close, oracle_grad2d_array, rect_tiles, splat_array)
+from tests.helpers import (IMG_ATOL, assert_grad_close, assert_img_close, oracle_grad2d_array, rect_tiles,
+                           splat_array)
 
 pytestmark = pytest.mark.gpu
 
@@ -159,8 +160,8 @@ def test_render_fwd_matches_oracle(small, tile):
     nc = out.n_contrib.view(128, 128).cpu().numpy()
     ok = img.flags == 0
     assert ok.mean() > 0.99
-    assert np.abs(rgb - img.rgb)[:, ok].max() <= IMG_ATOL
-    assert np.abs(T - img.T_final)[ok].max() <= IMG_ATOL
+    assert_img_close(rgb[:, ok], img.rgb[:, ok], "image small (stage)")
+    assert_img_close(T[ok], img.T_final[ok], "T_final small (stage)")
     np.testing.assert_array_equal(nc[ok], img.n_contrib[ok])
 
 
@@ -225,7 +226,7 @@ def test_end_to_end_small(small, recompute):
     batch = make_batch(wl)
     proj, bins, img = lobe.forward(ctx, batch)
     rgb = img.rgb.view(3, 128, 128).cpu().numpy()
-    assert np.abs(rgb - f.image.rgb)[:, ok_px].max() <= IMG_ATOL
+    assert_img_close(rgb[:, ok_px], f.image.rgb[:, ok_px], "image small (end to end)")
     # sort order: per tile, identical lists once marginal Gaussians are removed
     marg = (f.proj.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) != 0
     gids = bins.ids().cpu().numpy()
@@ -329,7 +330,7 @@ def test_ragged_image_matches_oracle():
     _, _, img = lobe.forward(ctx, batch)
     rgb = img.rgb.view(3, 75, 100).cpu().numpy()
     ok = f.pixel_flags == 0
-    assert np.abs(rgb - f.image.rgb)[:, ok].max() <= IMG_ATOL
+    assert_img_close(rgb[:, ok], f.image.rgb[:, ok], "image ragged (end to end)")
 
 
 def test_capacity_overflow_is_reported_without_sync():

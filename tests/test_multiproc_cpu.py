@@ -61,6 +61,9 @@ def _worker(rank, world, port, q):
         models = [None] * world
         dist.all_gather_object(models, params)
         if rank == 0:
+            # numpy copies travel by value (torch tensors would be shared through file
+            # descriptors that vanish when this process exits)
+            models = [{b: {k: v.numpy() for k, v in d.items()} for b, d in m.items()} for m in models]
             q.put(("ok", gathered, t, models))
     except Exception as e:  # report to the parent instead of hanging it
         q.put(("err", repr(e), None, None))
@@ -90,7 +93,7 @@ def test_two_ranks_equal_single_process():
         np.testing.assert_array_equal(merged_imgs[b], render_block(g, box, cams[b]))
     per_block = {}
     for d in models:
-        per_block.update(d)
+        per_block.update({b: {k: torch.as_tensor(v) for k, v in p.items()} for b, p in d.items()})
     boxes = [box for _, box in leaves]
     merged = merge_blocks([per_block[b] for b in range(len(leaves))], boxes)
     # every Gaussian lies in exactly one KD leaf: the merge is a permutation of the scene
