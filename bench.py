@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lobe", choices=["lobe", "reference"])
     ap.add_argument("--workload", default="medium", choices=["medium", "small", "city", "multi"])
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="WxH, or auto: tile shape and pixels per lane by the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multi-block measurement")
     ap.add_argument("--recompute", action="store_true")
@@ -217,16 +217,16 @@ def batched_vs_plain(reps=5):
     best, times = autotune(sets, cams, wl.items, wl.blocks, reps=reps, use_cache=False, dL_init=fill)
     batched_ms = _time(best.replay, reps, best.stream)
     pixels = best.batch.n_pixels
-    tile = best.tile
+    tile, best_px = best.tile, best.px
     n_isect = best.n_isect
     del best
     torch.cuda.empty_cache()
-    plain = PlainSteps(sets, cams, wl.items, wl.blocks, tile=tile)
+    plain = PlainSteps(sets, cams, wl.items, wl.blocks, tile=tile, px=best_px)
     for st in plain.steps:
         fill(st)
     plain_ms = _time(plain.run, reps, torch.cuda.current_stream())
     return {"workload": wl.name, "gaussians": sum(s.n for s in sets), "views": len(cams), "pixels": pixels,
-            "intersections": n_isect, "tile": list(tile), "autotune_ms": {k: round(v, 3) for k, v in times.items()},
+            "intersections": n_isect, "tile": list(tile), "px_per_lane": best_px or "default", "autotune_ms": {k: round(v, 3) for k, v in times.items()},
             "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
             "batched_mpix_s": round(pixels / batched_ms / 1e3, 1), "plain_mpix_s": round(pixels / plain_ms / 1e3, 1),
             "ratio": round(plain_ms / batched_ms, 3)}
@@ -254,12 +254,26 @@ def main():
     from paper_2510_01767_b300 import _abi
     from paper_2510_01767_b300.losses import loss_and_grad
 
-    tile = tuple(int(x) for x in args.tile.split("x"))
+    from paper_2510_01767_b300.batched import autotune, config_name
+
     wl = build_workload(args.workload, seed=rank)
-    wl.tile = tile
     sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
     batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
-    ctx = lobe.Context(tile=tile, recompute_T=args.recompute)
+    if args.workload == "city":
+        # visibility cropping over the block's camera set (Sec. 3.3), as a crop mask on the 4M inputs
+        sets[0].crop_mask = lobe.visibility_crop(lobe.Context(), batch)[0]
+        batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
+    tuning = None
+    if args.tile == "auto":
+        best, tuning = autotune(sets, [c.as_dict() for c in wl.cameras], wl.items, wl.blocks, reps=3, use_cache=False,
+                                recompute_T=args.recompute)
+        tile, px = best.tile, best.px
+        del best
+        torch.cuda.empty_cache()
+    else:
+        tile, px = tuple(int(x) for x in args.tile.split("x")), 0
+    wl.tile = tile
+    ctx = lobe.Context(tile=tile, recompute_T=args.recompute, px_fwd=px, px_bwd=px)
 
     # one-time: bins sized from a first pass, dL/dC of the training loss against a target
     proj, bins, img = lobe.forward(ctx, batch, sync=True)
@@ -456,7 +470,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(float(step_ms.mean()), 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "gaussians": sum(s.n for s in sets), "pixels": batch.n_pixels,
-                       "tile": list(tile), "sh_degree": 3, "intersections": n_isect, "visible": vis,
+                       "tile": list(tile), "px_per_lane": px or "default",
+                       "tuning_ms": ({k: round(v, 4) for k, v in tuning.items()} if tuning else None),
+                       "sh_degree": 3, "intersections": n_isect, "visible": vis,
+                       "visibility_crop": args.workload == "city",
                        "bwd_mode": "recompute" if args.recompute else "store",
                        "l2": "flushed between timed steps (2x126 MB write)",
                        "dL_dC": "L1+0.2(1-SSIM) vs perturbed-copy render, computed once before timing",

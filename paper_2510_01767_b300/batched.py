@@ -8,8 +8,10 @@ the adjoint, and the per-set parameter gradients summed over views in registers.
 the binning scratch is reserved up front and no stage synchronises with the host, the whole
 step is captured once in a CUDA graph and replayed as a single launch.
 
-``autotune`` picks the tile shape (8x8, 16x16, 32x16) by timing graph replays on the actual
-batch; results are cached per (GPU, batch signature) in ``~/.cache/lobe/autotune.json``.
+``autotune`` picks the tile shape (8x8, 16x16, 32x16) and the pixels each lane composites (a
+kernel knob: fewer means more warps per tile, more means fewer splat loads and reductions per
+pixel) by timing graph replays on the actual batch; results are cached per (GPU, batch
+signature) in ``~/.cache/lobe/autotune.json``.
 ``PlainSteps`` is the reference it is compared with: one view per call sequence, eager,
 each view projecting its block's Gaussians itself.
 """
@@ -25,14 +27,22 @@ import torch
 from . import raster as R
 
 TILES = ((8, 8), (16, 16), (32, 16))
+# (tile, pixels per lane) candidates; pixels per lane 0 = the library default for the tile
+CANDIDATES = (((8, 8), 1), ((8, 8), 2), ((16, 16), 2), ((16, 16), 4), ((32, 16), 4), ((32, 16), 8))
+
+
+def config_name(tile, px):
+    return f"{tile[0]}x{tile[1]}" + (f"/px{px}" if px else "")
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lobe", "autotune.json")
 
 
 class BatchedStep:
     def __init__(self, sets, cameras, items, blocks=(), tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0),
-                 recompute_T=False, slack=1.25, stream=None):
+                 recompute_T=False, slack=1.25, stream=None, px=0):
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        self.ctx = R.Context(tile=tile, sh_degree=sh_degree, bg=bg, recompute_T=recompute_T, stream=self.stream)
+        self.ctx = R.Context(tile=tile, sh_degree=sh_degree, bg=bg, recompute_T=recompute_T, stream=self.stream,
+                             px_fwd=px, px_bwd=px)
+        self.px = px
         self.batch = R.Batch(sets, cameras, items, blocks)
         self.tile = tuple(tile)
         with torch.cuda.stream(self.stream):
@@ -119,9 +129,13 @@ def signature(sets, cameras, items):
     return h.hexdigest()[:16]
 
 
-def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=True, dL_init=None, **kw):
-    """Returns (best BatchedStep captured in a graph, {tile: ms per step})."""
-    key = f"{torch.cuda.get_device_name()}|{signature(sets, cameras, items)}"
+def autotune(sets, cameras, items, blocks=(), tiles=None, reps=5, use_cache=True, dL_init=None,
+             candidates=CANDIDATES, **kw):
+    """Returns (best BatchedStep captured in a graph, {"<tile>/px<n>": ms per step}). ``tiles``
+    restricts the search to those tile shapes with the default pixels per lane."""
+    if tiles is not None:
+        candidates = tuple((tuple(t), 0) for t in tiles)
+    key = f"{torch.cuda.get_device_name()}|{signature(sets, cameras, items)}|{config_name_list(candidates)}"
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -129,19 +143,19 @@ def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=Tru
         except (OSError, ValueError):
             cache = {}
     if use_cache and key in cache:
-        tile = tuple(cache[key]["tile"])
-        st = BatchedStep(sets, cameras, items, blocks, tile=tile, **kw)
+        tile, px = tuple(cache[key]["tile"]), int(cache[key].get("px", 0))
+        st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, **kw)
         if dL_init is not None:
             dL_init(st)
         return st.capture(), cache[key]["times"]
     times, best, best_ms = {}, None, float("inf")
-    for tile in tiles:
-        st = BatchedStep(sets, cameras, items, blocks, tile=tile, **kw)
+    for tile, px in candidates:
+        st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, **kw)
         if dL_init is not None:
             dL_init(st)
         st.capture()
         ms = _time(st.replay, reps, st.stream)
-        times[f"{tile[0]}x{tile[1]}"] = ms
+        times[config_name(tile, px)] = ms
         if ms < best_ms:
             if best is not None:
                 del best
@@ -151,7 +165,11 @@ def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=Tru
         torch.cuda.empty_cache()
     if use_cache:
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        cache[key] = {"tile": list(best.tile), "times": times, "when": time.time()}
+        cache[key] = {"tile": list(best.tile), "px": best.px, "times": times, "when": time.time()}
         with open(CACHE, "w") as f:
             json.dump(cache, f)
     return best, times
+
+
+def config_name_list(candidates):
+    return ",".join(config_name(t, p) for t, p in candidates)
