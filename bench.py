@@ -226,7 +226,7 @@ def batched_vs_plain(reps=5):
         fill(st)
     plain_ms = _time(plain.run, reps, torch.cuda.current_stream())
     return {"workload": wl.name, "gaussians": sum(s.n for s in sets), "views": len(cams), "pixels": pixels,
-            "intersections": n_isect, "tile": list(tile), "px_per_lane": best_px or "default", "autotune_ms": {k: round(v, 3) for k, v in times.items()},
+            "intersections": n_isect, "tile": list(tile), "px_per_lane": list(best_px), "autotune_ms": {k: round(v, 3) for k, v in times.items()},
             "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
             "batched_mpix_s": round(pixels / batched_ms / 1e3, 1), "plain_mpix_s": round(pixels / plain_ms / 1e3, 1),
             "ratio": round(plain_ms / batched_ms, 3)}
@@ -259,9 +259,13 @@ def main():
     wl = build_workload(args.workload, seed=rank)
     sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
     batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
+    n_input = sum(s.n for s in sets)
     if args.workload == "city":
-        # visibility cropping over the block's camera set (Sec. 3.3), as a crop mask on the 4M inputs
-        sets[0].crop_mask = lobe.visibility_crop(lobe.Context(), batch)[0]
+        # visibility cropping (Sec. 3.3): once per block, before its fine training, the Gaussians
+        # no camera of the block sees are removed; every training step then renders the rest
+        mask = lobe.visibility_crop(lobe.Context(), batch)[0]
+        kept = lobe.crop_compact({k: getattr(sets[0], k) for k in lobe.PARAM_KEYS}, mask)
+        sets = [lobe.GaussianSet(**kept)]
         batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
     tuning = None
     if args.tile == "auto":
@@ -271,9 +275,9 @@ def main():
         del best
         torch.cuda.empty_cache()
     else:
-        tile, px = tuple(int(x) for x in args.tile.split("x")), 0
+        tile, px = tuple(int(x) for x in args.tile.split("x")), (0, 0)
     wl.tile = tile
-    ctx = lobe.Context(tile=tile, recompute_T=args.recompute, px_fwd=px, px_bwd=px)
+    ctx = lobe.Context(tile=tile, recompute_T=args.recompute, px_fwd=px[0], px_bwd=px[1])
 
     # one-time: bins sized from a first pass, dL/dC of the training loss against a target
     proj, bins, img = lobe.forward(ctx, batch, sync=True)
@@ -469,11 +473,13 @@ def main():
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(float(step_ms.mean()), 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "gaussians": sum(s.n for s in sets), "pixels": batch.n_pixels,
-                       "tile": list(tile), "px_per_lane": px or "default",
+            "config": {"workload": wl.name, "gaussians": sum(s.n for s in sets), "gaussians_input": n_input,
+                       "pixels": batch.n_pixels,
+                       "tile": list(tile), "px_per_lane": {"fwd": px[0] or "default", "bwd": px[1] or "default"},
                        "tuning_ms": ({k: round(v, 4) for k, v in tuning.items()} if tuning else None),
                        "sh_degree": 3, "intersections": n_isect, "visible": vis,
-                       "visibility_crop": args.workload == "city",
+                       "visibility_crop": ("applied once before the timed steps (Gaussians no view of the block "
+                                           "sees removed)") if args.workload == "city" else None,
                        "bwd_mode": "recompute" if args.recompute else "store",
                        "l2": "flushed between timed steps (2x126 MB write)",
                        "dL_dC": "L1+0.2(1-SSIM) vs perturbed-copy render, computed once before timing",
