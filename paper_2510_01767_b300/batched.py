@@ -27,21 +27,21 @@ import torch
 from . import raster as R
 
 TILES = ((8, 8), (16, 16), (32, 16))
-# (tile, pixels per lane) candidates; pixels per lane 0 = the library default for the tile
-CANDIDATES = (((8, 8), 1), ((8, 8), 2), ((16, 16), 2), ((16, 16), 4), ((32, 16), 4), ((32, 16), 8))
+PX_OPTIONS = {(8, 8): (1, 2), (16, 16): (2, 4, 8), (32, 16): (2, 4, 8)}  # pixels per lane per tile shape
 
 
-def config_name(tile, px):
-    return f"{tile[0]}x{tile[1]}" + (f"/px{px}" if px else "")
+def config_name(tile, px=(0, 0)):
+    return f"{tile[0]}x{tile[1]}" + (f"/f{px[0]}b{px[1]}" if px and px[0] else "")
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lobe", "autotune.json")
 
 
 class BatchedStep:
     def __init__(self, sets, cameras, items, blocks=(), tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0),
-                 recompute_T=False, slack=1.25, stream=None, px=0):
+                 recompute_T=False, slack=1.25, stream=None, px=(0, 0)):
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        px = (px, px) if isinstance(px, int) else tuple(px)
         self.ctx = R.Context(tile=tile, sh_degree=sh_degree, bg=bg, recompute_T=recompute_T, stream=self.stream,
-                             px_fwd=px, px_bwd=px)
+                             px_fwd=px[0], px_bwd=px[1])
         self.px = px
         self.batch = R.Batch(sets, cameras, items, blocks)
         self.tile = tuple(tile)
@@ -68,6 +68,26 @@ class BatchedStep:
         R.render_fwd(c, b, self.proj, self.bins, self.image)
         R.render_bwd(c, b, self.proj, self.bins, self.image, self.dL, self.grad2d)
         R.project_bwd(c, b, self.proj, self.grad2d, self.grads, accumulate=False)
+
+    def tune_px(self, options, reps=3):
+        """Times the composite and its adjoint at each pixels-per-lane option and keeps the
+        fastest for each (they are independent knobs). Returns (fwd, bwd)."""
+        c, b = self.ctx, self.batch
+        best = {}
+        with torch.cuda.stream(self.stream):
+            self.run()
+            for px in options:
+                c.configure(px=(px, px))
+                fwd = _time(lambda: R.render_fwd(c, b, self.proj, self.bins, self.image), reps, self.stream)
+                bwd = _time(lambda: R.render_bwd(c, b, self.proj, self.bins, self.image, self.dL, self.grad2d), reps,
+                            self.stream)
+                if fwd < best.get("f", (float("inf"), 0))[0]:
+                    best["f"] = (fwd, px)
+                if bwd < best.get("b", (float("inf"), 0))[0]:
+                    best["b"] = (bwd, px)
+        self.px = (best["f"][1], best["b"][1])
+        c.configure(px=self.px)
+        return self.px
 
     def capture(self, warmup=2):
         with torch.cuda.stream(self.stream):
@@ -129,13 +149,12 @@ def signature(sets, cameras, items):
     return h.hexdigest()[:16]
 
 
-def autotune(sets, cameras, items, blocks=(), tiles=None, reps=5, use_cache=True, dL_init=None,
-             candidates=CANDIDATES, **kw):
-    """Returns (best BatchedStep captured in a graph, {"<tile>/px<n>": ms per step}). ``tiles``
-    restricts the search to those tile shapes with the default pixels per lane."""
-    if tiles is not None:
-        candidates = tuple((tuple(t), 0) for t in tiles)
-    key = f"{torch.cuda.get_device_name()}|{signature(sets, cameras, items)}|{config_name_list(candidates)}"
+def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=True, dL_init=None, tune_px=True,
+             **kw):
+    """Returns (best BatchedStep captured in a graph, {"<tile>/f<px>b<px>": ms per step}): per tile
+    shape, the pixels per lane of the composite and of its adjoint are tuned separately, then
+    the whole step is timed as a graph replay."""
+    key = f"{torch.cuda.get_device_name()}|{signature(sets, cameras, items)}|{config_name_list(tiles)}|{int(tune_px)}"
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -143,19 +162,22 @@ def autotune(sets, cameras, items, blocks=(), tiles=None, reps=5, use_cache=True
         except (OSError, ValueError):
             cache = {}
     if use_cache and key in cache:
-        tile, px = tuple(cache[key]["tile"]), int(cache[key].get("px", 0))
+        tile, px = tuple(cache[key]["tile"]), tuple(cache[key].get("px", (0, 0)))
         st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, **kw)
         if dL_init is not None:
             dL_init(st)
         return st.capture(), cache[key]["times"]
     times, best, best_ms = {}, None, float("inf")
-    for tile, px in candidates:
-        st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, **kw)
+    for tile in tiles:
+        tile = tuple(tile)
+        st = BatchedStep(sets, cameras, items, blocks, tile=tile, **kw)
         if dL_init is not None:
             dL_init(st)
+        if tune_px:
+            st.tune_px(PX_OPTIONS.get(tile, (0,)), reps=max(2, reps // 2))
         st.capture()
         ms = _time(st.replay, reps, st.stream)
-        times[config_name(tile, px)] = ms
+        times[config_name(tile, st.px)] = ms
         if ms < best_ms:
             if best is not None:
                 del best
@@ -165,11 +187,11 @@ def autotune(sets, cameras, items, blocks=(), tiles=None, reps=5, use_cache=True
         torch.cuda.empty_cache()
     if use_cache:
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        cache[key] = {"tile": list(best.tile), "px": best.px, "times": times, "when": time.time()}
+        cache[key] = {"tile": list(best.tile), "px": list(best.px), "times": times, "when": time.time()}
         with open(CACHE, "w") as f:
             json.dump(cache, f)
     return best, times
 
 
-def config_name_list(candidates):
-    return ",".join(config_name(t, p) for t, p in candidates)
+def config_name_list(tiles):
+    return ",".join(f"{t[0]}x{t[1]}" for t in tiles)

@@ -168,10 +168,8 @@ __device__ __forceinline__ unsigned lanemask_lt()
 
 // ------------------------------------------------------------------ compositing step
 //
-// One (pixel, splat) evaluation, shared by the forward and both backward sweeps so that
-// the alpha-skip and early-stop decisions are bit-identical between them. Explicit
-// round-to-nearest intrinsics keep the compiler from contracting differently per kernel.
-// The staged splat holds the conic pre-scaled into the base-2 exponent domain:
+// Constants of the compositing step (render.cu). The staged splat holds the conic pre-scaled
+// into the base-2 exponent domain:
 //   A = -0.5 a log2(e), B = -b log2(e), C = -0.5 c log2(e)  =>  G = exp(-sigma) = 2^(A dx^2 + B dx dy + C dy^2)
 
 constexpr float LOG2E = 1.4426950408889634f;
@@ -179,28 +177,6 @@ constexpr float LN2 = 0.6931471805599453f;
 constexpr float ALPHA_MIN = 1.0f / 255.0f;
 constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_MIN = 1e-4f;
-
-struct Eval {
-    float dx, dy, G, alpha;
-    bool use;      // contributes (sigma >= 0 and alpha >= 1/255)
-    bool clamped;  // alpha hit the 0.99 clamp
-};
-
-__device__ __forceinline__ Eval eval_pair(float u, float v, float A, float B, float C, float o, float pxc,
-                                          float pyc)
-{
-    Eval r;
-    r.dx = __fsub_rn(u, pxc);
-    r.dy = __fsub_rn(v, pyc);
-    float t = __fmaf_rn(A, r.dx, __fmul_rn(B, r.dy));
-    float p2 = __fmaf_rn(r.dx, t, __fmul_rn(__fmul_rn(C, r.dy), r.dy));
-    r.G = ex2(p2);
-    float araw = __fmul_rn(o, r.G);
-    r.clamped = araw >= ALPHA_MAX;
-    r.alpha = fminf(ALPHA_MAX, araw);
-    r.use = (p2 <= 0.0f) && (r.alpha >= ALPHA_MIN);
-    return r;
-}
 
 // T after a contributor; the stop rule is `next_T(T, alpha) < T_MIN` (checked before adding)
 __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }

@@ -418,6 +418,213 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     }
 }
 
+// --------------------------------------------------------------------------- paired adjoint
+//
+// The same adjoint with a lane's pixels taken two at a time (pixel rows 2i and 2i+1 of its
+// column) in packed float32x2 arithmetic (add/sub/mul/fma .f32x2: one instruction for both
+// pixels, each half rounded exactly like the scalar operation). The kernels are issue-bound,
+// so halving the floating-point instructions of a contributing pixel pair is what counts.
+// Per-pixel decisions stay scalar and identical to the forward's (same dy, p2, ex2, o * G in
+// the same rounding); a pixel of the pair that does not use the splat gets G = 0, hence
+// alpha = 0, which leaves its T, B and every gradient term unchanged.
+
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float sum2(f2 v)
+{
+    float a, b;
+    upk(v, a, b);
+    return a + b;
+}
+
+template <int TW, int TH, int PX, bool RECOMPUTE>
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
+    k_render_bwd2(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                  const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
+                  const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
+{
+    static_assert(PX % 2 == 0, "pixels are paired");
+    constexpr int NP = PX / 2;
+    using G = Slab<TW, TH, PX>;
+    __shared__ WarpStage stage[G::WARPS];
+    WarpStage &st = stage[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = blockIdx.x;
+    const ItemParams &I = P.item[item_of_tile(P, t)];
+    const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
+    const int px = tx * TW + lane % TW;
+    const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
+    const float pxc = (float)px + 0.5f;
+    const int start = tile_start[t], end = tile_start[t + 1];
+    const SlabBox bx = slab_box<TW, TH, PX>(tx, ty, warp);
+    const long long HW = (long long)I.W * I.H;
+    float pyc[PX], g0[PX], g1[PX], g2[PX], T[PX];
+    int nc[PX];
+    bool inside[PX];
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        pyc[k] = (float)(py0 + k) + 0.5f;
+        inside[k] = px < I.W && py0 + k < I.H;
+        g0[k] = g1[k] = g2[k] = 0.0f;
+        T[k] = 1.0f;
+        nc[k] = 0;
+        if (inside[k]) {
+            const long long p = (long long)(py0 + k) * I.W + px;
+            const float *d = dL + 3 * I.pix_off;
+            g0[k] = d[p];
+            g1[k] = d[HW + p];
+            g2[k] = d[2 * HW + p];
+            if (!RECOMPUTE) {
+                T[k] = Tfin[I.pix_off + p];
+                nc[k] = ncin[I.pix_off + p];
+            }
+        }
+    }
+    if (RECOMPUTE) {
+        bool live[PX];
+        float c0[PX], c1[PX], c2[PX];
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            live[k] = inside[k];
+            c0[k] = c1[k] = c2[k] = 0.0f;
+        }
+        forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, c0, c1, c2, nc, st);
+    }
+    // per pixel pair: packed row centres, dL/dC, colour behind (from the background), T
+    f2 pyc2[NP], G0[NP], G1[NP], G2[NP], B0[NP], B1[NP], B2[NP], T2[NP];
+    const f2 bg0 = pk(P.bg[0], P.bg[0]), bg1 = pk(P.bg[1], P.bg[1]), bg2 = pk(P.bg[2], P.bg[2]);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        pyc2[i] = pk(pyc[2 * i], pyc[2 * i + 1]);
+        G0[i] = pk(g0[2 * i], g0[2 * i + 1]);
+        G1[i] = pk(g1[2 * i], g1[2 * i + 1]);
+        G2[i] = pk(g2[2 * i], g2[2 * i + 1]);
+        B0[i] = bg0;
+        B1[i] = bg1;
+        B2[i] = bg2;
+        T2[i] = pk(T[2 * i], T[2 * i + 1]);
+    }
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) m = max(m, nc[k]);
+    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+    const int stop = min(start + m, end);
+    const f2 one2 = pk(1.0f, 1.0f);
+
+    int top = stop, base = max(start, stop - 32);
+    Staged nx;
+    bool nh;
+    fetch(splat, ids, base + lane, top, bx, nx, nh);
+    while (top > start) {
+        st.s0[lane] = nx.s0;
+        st.s1[lane] = nx.s1;
+        st.s2[lane] = nx.s2;
+        st.id[lane] = nx.id;
+        unsigned hits = __ballot_sync(0xffffffffu, nh);
+        __syncwarp();
+        const int nbase = max(start, base - 32);
+        fetch(splat, ids, nbase + lane, base, bx, nx, nh);
+        while (hits) {  // back to front: highest position first
+            const int j = 31 - __clz(hits);
+            hits &= ~(1u << j);
+            const float4 q0 = st.s0[j], q1 = st.s1[j];
+            const float cb = st.s2[j].x, pmin = st.s2[j].y;
+            const int pos = base - start + j;
+            const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
+            const f2 v2 = pk(q0.y, q0.y), C2 = pk(q1.x, q1.x), a2 = pk(cl.a2, cl.a2), b1 = pk(cl.b1, cl.b1);
+            f2 du = 0, dv = 0, dA = 0, dB = 0, dC = 0, dop = 0, dr = 0, dg = 0, db = 0;  // 0 = (+0, +0)
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const bool ok0 = pos < nc[2 * i], ok1 = pos < nc[2 * i + 1];
+                if (!(ok0 || ok1)) continue;
+                const f2 dy2 = sub2(v2, pyc2[i]);
+                const f2 p2 = fma2(dy2, fma2(C2, dy2, b1), a2);
+                float pa, pb;
+                upk(p2, pa, pb);
+                const bool u0 = ok0 && pa <= 0.0f && pa >= pmin, u1 = ok1 && pb <= 0.0f && pb >= pmin;
+                if (!(u0 || u1)) continue;
+                any = true;
+                const float Ga = u0 ? ex2(pa) : 0.0f, Gb = u1 ? ex2(pb) : 0.0f;
+                float ra, rb;
+                upk(mul2(pk(q1.y, q1.y), pk(Ga, Gb)), ra, rb);  // o * G, as in the forward
+                const bool ka = ra >= ALPHA_MAX, kb = rb >= ALPHA_MAX;
+                const float aa = fminf(ALPHA_MAX, ra), ab = fminf(ALPHA_MAX, rb);
+                const f2 al = pk(aa, ab);
+                float oma, omb;
+                upk(sub2(one2, al), oma, omb);
+                const f2 Ti = mul2(T2[i], pk(__fdividef(1.0f, oma), __fdividef(1.0f, omb)));  // T in front
+                const f2 w = mul2(al, Ti);
+                dr = fma2(w, G0[i], dr);
+                dg = fma2(w, G1[i], dg);
+                db = fma2(w, G2[i], db);
+                const f2 d0 = sub2(pk(q1.z, q1.z), B0[i]), d1 = sub2(pk(q1.w, q1.w), B1[i]),
+                         d2 = sub2(pk(cb, cb), B2[i]);
+                const f2 da = mul2(Ti, fma2(G2[i], d2, fma2(G1[i], d1, mul2(G0[i], d0))));  // dL/dalpha
+                B0[i] = fma2(al, d0, B0[i]);
+                B1[i] = fma2(al, d1, B1[i]);
+                B2[i] = fma2(al, d2, B2[i]);
+                T2[i] = Ti;
+                // past the clamp alpha no longer depends on o or the exponent
+                dop = fma2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb), dop);
+                const f2 dp2 = mul2(da, pk(ka ? 0.0f : aa * LN2, kb ? 0.0f : ab * LN2));
+                const f2 dpy = mul2(dp2, dy2);
+                dA = fma2(dp2, pk(cl.dx * cl.dx, cl.dx * cl.dx), dA);
+                dB = fma2(dpy, pk(cl.dx, cl.dx), dB);
+                dC = fma2(dpy, dy2, dC);
+                du = fma2(dp2, fma2(pk(q0.w, q0.w), dy2, pk(2.f * q0.z * cl.dx, 2.f * q0.z * cl.dx)), du);
+                dv = fma2(dp2, pk(q0.w * cl.dx, q0.w * cl.dx), dv);
+                dv = fma2(pk(2.f * q1.x, 2.f * q1.x), dpy, dv);
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                const float vals[9] = {sum2(du), sum2(dv), sum2(dA), sum2(dB), sum2(dC),
+                                       sum2(dop), sum2(dr), sum2(dg), sum2(db)};
+                int idx;
+                const float tot = warp_reduce9(vals, idx);
+                if (idx >= 0) {
+                    // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
+                    const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
+                    red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
+                }
+            }
+        }
+        __syncwarp();
+        top = base;
+        base = nbase;
+    }
+}
+
 // --------------------------------------------------------------------------- launchers
 
 template <int TW, int TH, int PX>
@@ -436,12 +643,18 @@ static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *spla
 {
     count_launch();
     const int threads = 32 * Slab<TW, TH, PX>::WARPS;
-    if (recompute)
-        k_render_bwd<TW, TH, PX, true><<<P.n_tiles, threads, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts,
-                                                                      ids, rgb, nc, dL, g2d);
-    else
-        k_render_bwd<TW, TH, PX, false><<<P.n_tiles, threads, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), ts,
-                                                                       ids, rgb, nc, dL, g2d);
+    const float4 *sp = reinterpret_cast<const float4 *>(splat);
+    if constexpr (PX % 2 == 0) {  // pixel pairs in packed arithmetic
+        if (recompute)
+            k_render_bwd2<TW, TH, PX, true><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+        else
+            k_render_bwd2<TW, TH, PX, false><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+    } else {
+        if (recompute)
+            k_render_bwd<TW, TH, PX, true><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+        else
+            k_render_bwd<TW, TH, PX, false><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+    }
     return cudaGetLastError();
 }
 

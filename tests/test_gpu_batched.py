@@ -108,7 +108,7 @@ def test_autotune_picks_fastest(workload, tmp_path, monkeypatch):
     sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
     cams = [c.as_dict() for c in wl.cameras]
     best, times = autotune(sets, cams, wl.items, wl.blocks, reps=3, dL_init=fill_dL)
-    assert set(times) == {"8x8/px1", "8x8/px2", "16x16/px2", "16x16/px4", "32x16/px4", "32x16/px8"}
+    assert {k.split("/")[0] for k in times} == {"8x8", "16x16", "32x16"} and len(times) == 3
     assert times[batched.config_name(best.tile, best.px)] == min(times.values())
     again, t2 = autotune(sets, cams, wl.items, wl.blocks, reps=3, dL_init=fill_dL)  # from the cache
     assert again.tile == best.tile and again.px == best.px and t2 == times
