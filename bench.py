@@ -312,7 +312,7 @@ def main():
         lobe.render_bwd(ctx, batch, proj, bins, image, dL, grad2d)
         if ev:
             ev[4].record(stream)
-        lobe.project_bwd(ctx, batch, proj, grad2d, grads, accumulate=True)
+        lobe.project_bwd(ctx, batch, proj, grad2d, grads, accumulate=False)  # fresh gradients, as autograd returns
         if ev:
             ev[5].record(stream)
 
