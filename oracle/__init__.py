@@ -322,6 +322,50 @@ def visibility_crop(g, cams, tile=(16, 16), sh_degree=3) -> np.ndarray:
     return mask
 
 
+def render_depth(p: Projection, ids, tile_start, cam, tile=(16, 16), margins=MARGINS_NONE,
+                 pixel_flags=None) -> Image:
+    """Composite depth of fast camera selection (Sec. 3.2): D = sum_i d_i alpha_i T_i, the
+    blending equation with each Gaussian's camera-space depth d_i in place of its colour.
+    Returned as an Image whose rgb[0] (= rgb[1] = rgb[2]) is D, with the background 0."""
+    q = Projection(p.mean2d, p.conic, np.repeat(p.depth[:, None], 3, axis=1), p.opacity, p.depth, p.radius,
+                   p.rect, p.flags, p.radius_all)
+    return render_fwd(q, ids, tile_start, cam, tile, (0.0, 0.0, 0.0), margins, pixel_flags)
+
+
+def backproject(D, T, cam, normalize=False):
+    """World points of the pixels some Gaussian reached (T < 1), from the depth map D (divided
+    by the accumulated opacity 1 - T when normalize): camera-space (x, y, z) =
+    ((px + 0.5 - cx) D / fx, (py + 0.5 - cy) D / fy, D), world = the inverse of the
+    world->camera viewmat applied to it (R^T (p_c - t) for an orthonormal R). Returns
+    (points [H, W, 3], mask [H, W])."""
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    H, W = D.shape
+    mask = T < 1.0
+    d = D / np.where(mask, 1.0 - T, 1.0) if normalize else D
+    py, px = np.mgrid[0:H, 0:W].astype(np.float64)
+    pc = np.stack([(px + 0.5 - c["cx"]) / c["fx"] * d, (py + 0.5 - c["cy"]) / c["fy"] * d, d], axis=-1)
+    Vinv = np.linalg.inv(np.asarray(c["viewmat"], np.float64).reshape(4, 4))
+    return pc @ Vinv[:3, :3].T + Vinv[:3, 3], mask
+
+
+def fcs_coverage(D, T, cam, blocks, normalize=False, rel_margin=0.0):
+    """Fast camera selection counts (Sec. 3.2): per block box, the number of back-projected
+    points inside it (lo <= p < hi per axis), and the number of points N_p. With rel_margin >
+    0 also returns a per-pixel flag for points within rel_margin * (|coordinate| + 1) of a face
+    of some box (a float32 evaluation may put them on either side)."""
+    pts, mask = backproject(D, T, cam, normalize)
+    counts, flags = [], np.zeros(mask.shape, bool)
+    for b in blocks:
+        lo, hi = np.asarray(b.lo, np.float64), np.asarray(b.hi, np.float64)
+        inside = mask & np.all((pts >= lo) & (pts < hi), axis=-1)
+        counts.append(int(inside.sum()))
+        if rel_margin > 0:
+            tol = rel_margin * (np.abs(pts) + 1.0)
+            near = np.isfinite(lo) & (np.abs(pts - lo) < tol) | np.isfinite(hi) & (np.abs(pts - hi) < tol)
+            flags |= mask & np.any(near, axis=-1)
+    return np.array(counts, np.int64), int(mask.sum()), flags
+
+
 def sh_basis(dirs, degree=3):
     """Real SH basis [n,16] and its derivative [n,16,3] for each row of ``dirs``."""
     L = lib()

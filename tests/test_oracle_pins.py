@@ -394,3 +394,80 @@ def test_render_backward_colour_gradient_is_blend_weight():
         p2.color[i, 1] += 1.0
         im2 = oracle.render_fwd(p2, f.ids, f.tile_start, CAM128)
         np.testing.assert_allclose(g2d.color[i, 1], (im2.rgb[1] - f.image.rgb[1]).sum(), rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- fast camera selection
+
+def test_depth_composite_on_axis_closed_form():
+    """One isotropic Gaussian at depth z on the optical axis: D = z alpha(pixel) exactly
+    (a single contributor, T = 1 in front of it), and D / (1 - T_final) = z."""
+    s, z = 0.05, 4.0
+    g = one_gaussian((0, 0, z), (math.log(s),) * 3, logit=0.4)
+    p = oracle.project(g, CAM128)
+    ids, ts = oracle.bin_sort(p, CAM128)
+    img = oracle.render_depth(p, ids, ts, CAM128)
+    var = (128 * s / z) ** 2 + 0.3
+    o = 1 / (1 + math.exp(-0.4))
+    ys, xs = np.mgrid[0:128, 0:128]
+    alpha = np.minimum(0.99, o * np.exp(-((xs + 0.5 - 64) ** 2 + (ys + 0.5 - 64) ** 2) / (2 * var)))
+    r = p.radius[0]
+    t0, t1 = math.floor((64 - r) / 16), math.ceil((64 + r) / 16)
+    seen = (xs // 16 >= t0) & (xs // 16 < t1) & (ys // 16 >= t0) & (ys // 16 < t1) & (alpha >= 1 / 255)
+    np.testing.assert_allclose(img.rgb[0], np.where(seen, z * alpha, 0.0), atol=1e-13)
+    D = img.rgb[0][seen] / (1 - img.T_final[seen])
+    np.testing.assert_allclose(D, z, rtol=1e-12)
+
+
+def test_depth_of_two_layers_weights_front_and_back():
+    """Two concentric isotropic Gaussians at depths z1 < z2 on the axis: at the centre pixel
+    D = z1 a1 + z2 a2 (1 - a1)."""
+    g = one_gaussian((0, 0, 3.0), (math.log(0.2),) * 3, logit=0.0)
+    g2 = one_gaussian((0, 0, 6.0), (math.log(0.4),) * 3, logit=1.0)
+    both = {k: np.concatenate([g[k], g2[k]]) for k in g}
+    p = oracle.project(both, CAM128)
+    ids, ts = oracle.bin_sort(p, CAM128)
+    img = oracle.render_depth(p, ids, ts, CAM128)
+    rho2 = 0.5 ** 2 * 2  # pixel (64, 64) centre is (64.5, 64.5)
+    a1 = 0.5 * math.exp(-rho2 / (2 * ((128 * 0.2 / 3) ** 2 + 0.3)))
+    a2 = (1 / (1 + math.exp(-1))) * math.exp(-rho2 / (2 * ((128 * 0.4 / 6) ** 2 + 0.3)))
+    assert img.rgb[0][64, 64] == pytest.approx(3.0 * a1 + 6.0 * a2 * (1 - a1), rel=1e-12)
+
+
+def test_backprojection_inverts_the_pinhole():
+    """Back-projected points of a posed camera project back onto their pixel centres at
+    camera-space depth D."""
+    eye, target = np.array([3.0, -2.0, 5.0]), np.array([0.0, 0.5, 0.0])
+    cam = scenes.pinhole(40, 30, 50.0, cx=21.0, cy=14.5, viewmat=scenes.look_at(eye, target)).as_dict()
+    rng = np.random.default_rng(3)
+    D = rng.uniform(2.0, 9.0, (30, 40))
+    T = np.where(rng.uniform(size=(30, 40)) < 0.2, 1.0, rng.uniform(0.0, 0.9, (30, 40)))
+    pts, mask = oracle.backproject(D, T, cam)
+    assert np.array_equal(mask, T < 1.0)
+    V = np.asarray(cam["viewmat"], np.float64)
+    pc = pts @ V[:3, :3].T + V[:3, 3]
+    ys, xs = np.mgrid[0:30, 0:40]
+    np.testing.assert_allclose(pc[..., 2], D, rtol=1e-12)
+    np.testing.assert_allclose(cam["fx"] * pc[..., 0] / pc[..., 2] + cam["cx"], xs + 0.5, atol=1e-10)
+    np.testing.assert_allclose(cam["fy"] * pc[..., 1] / pc[..., 2] + cam["cy"], ys + 0.5, atol=1e-10)
+    # normalised depth divides by the accumulated opacity
+    ptsn, _ = oracle.backproject(D, T, cam, normalize=True)
+    pcn = ptsn @ V[:3, :3].T + V[:3, 3]
+    np.testing.assert_allclose(pcn[..., 2][mask], (D / (1 - T))[mask], rtol=1e-12)
+
+
+def test_coverage_of_a_wall_split_by_a_block_boundary():
+    """A camera facing a wall at depth z along +z (identity pose): the points left of the
+    principal point (x < 0 in the world) fall in the block x < 0 -- exactly the pixel columns
+    whose centres lie left of cx -- and the ratio V is that fraction."""
+    W, H, z = 64, 48, 7.0
+    cam = dict(viewmat=np.eye(4), fx=60.0, fy=60.0, cx=27.0, cy=24.0, width=W, height=H, near=0.01, far=1e10)
+    D = np.full((H, W), z)
+    T = np.zeros((H, W))
+    T[:, -5:] = 1.0  # five columns see nothing
+    left = scenes.AABB((-math.inf, -math.inf, -math.inf), (0.0, math.inf, math.inf))
+    right = scenes.AABB((0.0, -math.inf, -math.inf), (math.inf, math.inf, math.inf))
+    near = scenes.AABB((-math.inf, -math.inf, -math.inf), (math.inf, math.inf, z - 1))
+    counts, n, _ = oracle.fcs_coverage(D, T, cam, [left, right, near])
+    cols_left = int(np.sum(np.arange(W - 5) + 0.5 < 27.0))
+    assert n == H * (W - 5)
+    assert counts.tolist() == [H * cols_left, H * (W - 5 - cols_left), 0]
