@@ -14,6 +14,7 @@
  *   lobe_render_fwd   per-tile front-to-back compositing
  *   lobe_render_bwd   adjoint of the composite -> per-splat 2D gradients
  *   lobe_project_bwd  adjoint of the projection -> parameter gradients + SD statistics
+ *   lobe_render_depth, lobe_fcs_coverage   fast camera selection (Sec. 3.2)
  *
  * A "batch" is a list of items (Gaussian set, camera, block); one call processes every
  * item of the batch in one launch per stage. The plain single-view path is a batch of one.
@@ -240,6 +241,24 @@ lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *stream, const lo
 /* Front-to-back compositing of every tile of every item. */
 lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                             const lobe_bins *bins, const lobe_image *image);
+
+/* lobe_render_fwd plus the depth channel of fast camera selection (Sec. 3.2): depth[p] =
+ * sum_i d_i alpha_i T_i over the pixel's composite (d_i = the splat's camera-space depth; the
+ * paper's unnormalised compositing), same layout as T_final. The image is written as by
+ * lobe_render_fwd. depth must not be NULL when the batch has pixels. */
+lobe_status lobe_render_depth(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                              const lobe_bins *bins, const lobe_image *image, float *depth);
+
+/* Fast camera selection (Sec. 3.2): back-projects every pixel that some splat reached
+ * (T_final < 1) at depth D (depth[p], divided by 1 - T_final when normalize != 0) through its
+ * item's pinhole, p_c = ((x + 0.5 - cx) D / fx, (y + 0.5 - cy) D / fy, D), p_w = R^T (p_c - t),
+ * and counts the points inside each box (lo <= p_w < hi per axis): counts[item * n_blocks + b]
+ * and n_points[item] (device, overwritten). The visibility ratio of the paper is
+ * V(item, b) = counts / n_points; a camera is assigned to a block when V >= tau (0.1).
+ * n_blocks <= 64. Items' own blocks are ignored; any Gaussian set may be referenced. */
+lobe_status lobe_fcs_coverage(lobe_ctx *ctx, const lobe_batch *batch, const lobe_image *image, const float *depth,
+                              const lobe_aabb *blocks, int32_t n_blocks, int32_t normalize, uint32_t *counts,
+                              uint32_t *n_points);
 
 /* Adjoint of lobe_render_fwd. dL_drgb has the layout of image->rgb. Reads image->T_final
  * and image->n_contrib unless the context has recompute_T set (then only dL_drgb).

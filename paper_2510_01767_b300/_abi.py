@@ -97,6 +97,10 @@ SIGNATURES = {
     "lobe_project_bwd": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), vp,
                                         ctypes.POINTER(Grads), ctypes.c_int32]),
     "lobe_visibility_crop": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(vp)]),
+    "lobe_render_depth": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), ctypes.POINTER(Bins),
+                                         ctypes.POINTER(Image), vp]),
+    "lobe_fcs_coverage": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Image), vp, ctypes.POINTER(AABB),
+                                         ctypes.c_int32, ctypes.c_int32, vp, vp]),
 }
 
 _lib = None

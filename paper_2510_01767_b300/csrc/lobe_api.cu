@@ -437,8 +437,45 @@ lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
         return fail(ctx, LOBE_ERR_ARG, "inputs missing");
     if (!image || !image->rgb || !image->T_final || !image->n_contrib) return fail(ctx, LOBE_ERR_ARG, "image buffers missing");
     CUDA_TRY(launch_render_fwd(*H.p, proj->splat, bins->tile_start, bins->gauss_ids, image->rgb, image->T_final,
-                               image->n_contrib, ctx->stream),
+                               image->n_contrib, nullptr, ctx->stream),
              "render fwd");
+    return LOBE_OK;
+}
+
+lobe_status lobe_render_depth(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                              const lobe_bins *bins, const lobe_image *image, float *depth)
+{
+    BUILD_PARAMS(H);
+    if (!proj || (H.p->n_entries > 0 && !proj->splat) || !bins || !bins->gauss_ids || !bins->tile_start)
+        return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    if (!image || !image->rgb || !image->T_final || !image->n_contrib) return fail(ctx, LOBE_ERR_ARG, "image buffers missing");
+    if (!depth && H.p->n_pixels > 0) return fail(ctx, LOBE_ERR_ARG, "depth is NULL");
+    CUDA_TRY(launch_render_fwd(*H.p, proj->splat, bins->tile_start, bins->gauss_ids, image->rgb, image->T_final,
+                               image->n_contrib, depth, ctx->stream),
+             "render depth");
+    return LOBE_OK;
+}
+
+lobe_status lobe_fcs_coverage(lobe_ctx *ctx, const lobe_batch *batch, const lobe_image *image, const float *depth,
+                              const lobe_aabb *blocks, int32_t n_blocks, int32_t normalize, uint32_t *counts,
+                              uint32_t *n_points)
+{
+    BUILD_PARAMS(H);
+    if (n_blocks < 0 || n_blocks > FCS_MAX_BLOCKS)
+        return fail(ctx, LOBE_ERR_ARG, "n_blocks %d outside [0, %d]", n_blocks, FCS_MAX_BLOCKS);
+    if (n_blocks > 0 && !blocks) return fail(ctx, LOBE_ERR_ARG, "blocks is NULL");
+    if (!counts || !n_points) return fail(ctx, LOBE_ERR_ARG, "outputs missing");
+    if (H.p->n_pixels > 0 && (!image || !image->T_final || !depth)) return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    FcsBlocks B{};
+    B.n = n_blocks;
+    for (int b = 0; b < n_blocks; ++b)
+        for (int k = 0; k < 3; ++k) {
+            B.lo[b][k] = blocks[b].lo[k];
+            B.hi[b][k] = blocks[b].hi[k];
+        }
+    CUDA_TRY(launch_fcs_coverage(*H.p, B, depth, image ? image->T_final : nullptr, normalize ? 1 : 0, counts, n_points,
+                                 ctx->stream),
+             "fcs coverage");
     return LOBE_OK;
 }
 

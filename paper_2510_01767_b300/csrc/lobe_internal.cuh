@@ -210,7 +210,16 @@ cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
 cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, uint32_t *list,
                                uint32_t *count, unsigned long long *lb_slots, int *ctl, cudaStream_t);
 cudaError_t launch_render_fwd(const BatchParams &, const float *, const int *, const int *, float *, float *, int *,
-                              cudaStream_t);
+                              float *depth, cudaStream_t);
+
+// Block boxes of fast camera selection (kernel parameter).
+constexpr int FCS_MAX_BLOCKS = 64;
+struct FcsBlocks {
+    float lo[FCS_MAX_BLOCKS][3], hi[FCS_MAX_BLOCKS][3];
+    int n;
+};
+cudaError_t launch_fcs_coverage(const BatchParams &, const FcsBlocks &, const float *depth, const float *Tfin,
+                                int normalize, uint32_t *counts, uint32_t *n_points, cudaStream_t);
 cudaError_t launch_render_bwd(const BatchParams &, bool, const float *, const int *, const int *, const float *,
                               const int *, const float *, float *, cudaStream_t);
 cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int *radius, const int *tiles,

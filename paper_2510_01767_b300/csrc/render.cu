@@ -84,6 +84,7 @@ __device__ __forceinline__ PairEval pair_eval(const Column &cl, float v, float C
 struct Staged {
     float4 s0, s1;
     float2 s2;
+    float dep;  // camera-space depth (the depth channel of fast camera selection)
     int id;
 };
 
@@ -132,7 +133,9 @@ __device__ __forceinline__ void fetch(const float4 *__restrict__ splat, const in
         const float4 a = splat[3 * e], b = splat[3 * e + 1];
         s.s0 = make_float4(a.x, a.y, -0.5f * LOG2E * a.z, -LOG2E * a.w);
         s.s1 = make_float4(-0.5f * LOG2E * b.x, b.y, b.z, b.w);
-        s.s2 = make_float2(splat[3 * e + 2].x, -log2f(255.0f * b.y));
+        const float4 c = splat[3 * e + 2];
+        s.s2 = make_float2(c.x, -log2f(255.0f * b.y));
+        s.dep = c.y;
         s.id = e;
         hit = slab_reachable(bx, s.s0.x, s.s0.y, s.s0.z, s.s0.w, s.s1.x, s.s2.y);
     }
@@ -143,15 +146,18 @@ struct WarpStage {
     float4 s1[32];
     float2 s2[32];
     int id[32];
+    float dep[32];
 };
 
 // Front-to-back walk of [start, end) for a lane's PX pixels (forward, and the first sweep
-// of the recompute adjoint). live[k] must be false for pixels outside the image.
-template <int PX>
+// of the recompute adjoint). live[k] must be false for pixels outside the image. With DEPTH,
+// D[k] also accumulates sum_i d_i alpha_i T_i (the depth compositing of fast camera selection,
+// Sec. 3.2: the blending equation with each splat's camera-space depth in place of colour).
+template <int PX, bool DEPTH = false>
 __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, const int *__restrict__ ids, int start,
                                               int end, const SlabBox &bx, float pxc, const float (&pyc)[PX],
                                               bool (&live)[PX], float (&T)[PX], float (&C0)[PX], float (&C1)[PX],
-                                              float (&C2)[PX], int (&last)[PX], WarpStage &st)
+                                              float (&C2)[PX], int (&last)[PX], WarpStage &st, float *D = nullptr)
 {
     const int lane = threadIdx.x & 31;
     Staged nx;
@@ -165,6 +171,7 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
         st.s0[lane] = nx.s0;
         st.s1[lane] = nx.s1;
         st.s2[lane] = nx.s2;
+        if (DEPTH) st.dep[lane] = nx.dep;
         unsigned hits = __ballot_sync(0xffffffffu, nh);  // splats of the batch that can reach the slab
         __syncwarp();
         fetch(splat, ids, base + 32 + lane, end, bx, nx, nh);
@@ -173,6 +180,7 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
             hits &= hits - 1;
             const float4 q0 = st.s0[j], q1 = st.s1[j];
             const float cb = st.s2[j].x, pmin = st.s2[j].y;
+            const float dj = DEPTH ? st.dep[j] : 0.0f;
             const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
@@ -188,6 +196,7 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
                 C0[k] += q1.z * w;
                 C1[k] += q1.w * w;
                 C2[k] += cb * w;
+                if (DEPTH) D[k] += dj * w;
                 T[k] = Tn;
                 last[k] = base - start + j + 1;
             }
@@ -209,11 +218,11 @@ __device__ __forceinline__ SlabBox slab_box(int tx, int ty, int warp)
     return b;
 }
 
-template <int TW, int TH, int PX>
+template <int TW, int TH, int PX, bool DEPTH>
 __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     k_render_fwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                  const int *__restrict__ tile_start, const int *__restrict__ ids, float *__restrict__ rgb,
-                 float *__restrict__ Tout, int *__restrict__ ncout)
+                 float *__restrict__ Tout, int *__restrict__ ncout, float *__restrict__ depth)
 {
     using G = Slab<TW, TH, PX>;
     __shared__ WarpStage stage[G::WARPS];
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     const int px = tx * TW + lane % TW;
     const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
     const float pxc = (float)px + 0.5f;
-    float pyc[PX], T[PX], C0[PX], C1[PX], C2[PX];
+    float pyc[PX], T[PX], C0[PX], C1[PX], C2[PX], D[PX];
     int last[PX];
     bool live[PX], inside[PX];
 #pragma unroll
@@ -233,11 +242,11 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
         inside[k] = px < I.W && py0 + k < I.H;
         live[k] = inside[k];
         T[k] = 1.0f;
-        C0[k] = C1[k] = C2[k] = 0.0f;
+        C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
         last[k] = 0;
     }
-    forward_sweep<PX>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc, live,
-                      T, C0, C1, C2, last, stage[warp]);
+    forward_sweep<PX, DEPTH>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc,
+                             live, T, C0, C1, C2, last, stage[warp], D);
     const long long HW = (long long)I.W * I.H;
     float *out = rgb + 3 * I.pix_off;
 #pragma unroll
@@ -249,6 +258,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
         out[2 * HW + p] = C2[k] + T[k] * P.bg[2];
         Tout[I.pix_off + p] = T[k];
         ncout[I.pix_off + p] = last[k];
+        if (DEPTH) depth[I.pix_off + p] = D[k];
     }
 }
 
@@ -629,11 +639,16 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 
 template <int TW, int TH, int PX>
 static cudaError_t fwd_t(const BatchParams &P, const float *splat, const int *ts, const int *ids, float *rgb, float *T,
-                         int *nc, cudaStream_t st)
+                         int *nc, float *depth, cudaStream_t st)
 {
     count_launch();
-    k_render_fwd<TW, TH, PX><<<P.n_tiles, 32 * Slab<TW, TH, PX>::WARPS, 0, st>>>(
-        P, reinterpret_cast<const float4 *>(splat), ts, ids, rgb, T, nc);
+    const float4 *sp = reinterpret_cast<const float4 *>(splat);
+    if (depth)
+        k_render_fwd<TW, TH, PX, true><<<P.n_tiles, 32 * Slab<TW, TH, PX>::WARPS, 0, st>>>(P, sp, ts, ids, rgb, T, nc,
+                                                                                          depth);
+    else
+        k_render_fwd<TW, TH, PX, false><<<P.n_tiles, 32 * Slab<TW, TH, PX>::WARPS, 0, st>>>(P, sp, ts, ids, rgb, T, nc,
+                                                                                           nullptr);
     return cudaGetLastError();
 }
 
@@ -690,11 +705,11 @@ bool valid_px(int tw, int px)
     } while (0)
 
 cudaError_t launch_render_fwd(const BatchParams &P, const float *splat, const int *ts, const int *ids, float *rgb,
-                              float *T, int *nc, cudaStream_t st)
+                              float *T, int *nc, float *depth, cudaStream_t st)
 {
     if (P.n_tiles == 0) return cudaSuccess;
     const int px = P.px_fwd ? P.px_fwd : default_px(P.tw, false);
-    LOBE_PX_DISPATCH(fwd_t, P, splat, ts, ids, rgb, T, nc, st);
+    LOBE_PX_DISPATCH(fwd_t, P, splat, ts, ids, rgb, T, nc, depth, st);
 }
 
 cudaError_t launch_render_bwd(const BatchParams &P, bool recompute, const float *splat, const int *ts, const int *ids,

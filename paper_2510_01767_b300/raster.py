@@ -304,6 +304,40 @@ def render_fwd(ctx: Context, batch: Batch, proj: Projection, bins: Bins, out: Im
     return out
 
 
+def render_depth(ctx: Context, batch: Batch, proj: Projection, bins: Bins, out: Image | None = None,
+                 depth: torch.Tensor | None = None):
+    """render_fwd plus the composite depth of fast camera selection (Sec. 3.2): returns
+    (image, depth[pixels]) with depth = sum_i d_i alpha_i T_i per pixel."""
+    out = out if out is not None else empty_image(batch.n_pixels)
+    depth = depth if depth is not None else torch.empty(batch.n_pixels, dtype=torch.float32, device="cuda")
+    ctx._check(ctx.lib.lobe_render_depth(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()),
+                                         ctypes.byref(bins.c()), ctypes.byref(out.c()), _ptr(depth)))
+    return out, depth
+
+
+def fcs_coverage(ctx: Context, batch: Batch, image: Image, depth: torch.Tensor, blocks, normalize=False):
+    """Fast camera selection (Sec. 3.2): counts[item, block] of back-projected depth points
+    inside each block box and n_points[item] (pixels some splat reached). The visibility
+    ratio is V = counts / n_points."""
+    blocks = list(blocks)
+    arr = (A.AABB * max(1, len(blocks)))()
+    for i, b in enumerate(blocks):
+        arr[i] = aabb_struct(b)
+    n_items = len(batch.items)
+    counts = torch.empty((n_items, max(1, len(blocks))), dtype=torch.int32, device="cuda")
+    npts = torch.empty(n_items, dtype=torch.int32, device="cuda")
+    ctx._check(ctx.lib.lobe_fcs_coverage(ctx.handle, ctypes.byref(batch.c), ctypes.byref(image.c()), _ptr(depth), arr,
+                                         len(blocks), int(bool(normalize)), _ptr(counts), _ptr(npts)))
+    return counts[:, :len(blocks)], npts
+
+
+def fcs_select(counts: torch.Tensor, n_points: torch.Tensor, tau: float = 0.1):
+    """The paper's assignment C(b) = {c : V(c, b) >= tau}: returns (V [items, blocks], list of
+    item indices per block)."""
+    V = counts.double() / n_points.clamp(min=1).double()[:, None]
+    return V, [torch.nonzero(V[:, b] >= tau).flatten().tolist() for b in range(V.shape[1])]
+
+
 def render_bwd(ctx: Context, batch: Batch, proj: Projection, bins: Bins, image: Image | None,
                dL_drgb: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     _require_cuda(dL_drgb, "dL_drgb")
