@@ -53,8 +53,10 @@ def parse():
     ap.add_argument("--impl", default="lobe", choices=["lobe", "reference"])
     ap.add_argument("--workload", default="medium", choices=["medium", "small", "city", "multi"])
     ap.add_argument("--tile", default="auto", help="WxH, or auto: tile shape and pixels per lane by the autotuner")
+    ap.add_argument("--px", default="0,0", help="with --tile WxH: pixels per lane of the composite and its adjoint")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multi-block measurement")
+    ap.add_argument("--no-fcs", action="store_true", help="skip the fast-camera-selection measurement")
     ap.add_argument("--recompute", action="store_true")
     return ap.parse_args()
 
@@ -232,6 +234,61 @@ def batched_vs_plain(reps=5):
             "ratio": round(plain_ms / batched_ms, 3)}
 
 
+def fcs_benchmark(reps=5):
+    """Fast camera selection (Sec. 3.2) over a coarse model: a 2M-Gaussian city, 16 KD blocks
+    and 64 aerial cameras of 800x600, 16 cameras per batch: project, bin, composite with the
+    depth channel, back-project and count per block. Returns a dict for the JSON line."""
+    import torch
+    import paper_2510_01767_b300 as lobe
+
+    g = scenes.city_layout(11, 2_000_000)
+    blocks = [box for _, box in scenes.kd_median_leaves(g.means, 4)]
+    rng = np.random.default_rng(12)
+    cams = [scenes.aerial_camera((rng.uniform(-200, 200), rng.uniform(-200, 200), 0.0), rng.uniform(120, 180),
+                                 rng.uniform(35, 60), rng.uniform(0, 360), 800, 600, 880.0) for _ in range(64)]
+    sets = [lobe.GaussianSet.from_numpy(g)]
+    per = 16
+    batches = [lobe.Batch(sets, cams[i:i + per], [(0, c, -1) for c in range(len(cams[i:i + per]))])
+               for i in range(0, len(cams), per)]
+    ctx = lobe.Context(tile=(16, 16))
+    state = []
+    for b in batches:  # bins sized once
+        proj, bins, _ = lobe.forward(ctx, b, sync=True)
+        ctx.reserve(b.n_entries, int(bins.count * 1.25) + 4096, b.tiles((16, 16))[0])
+        bins = lobe.raster.empty_bins(int(bins.count * 1.25) + 4096, b.tiles((16, 16))[0])
+        state.append((b, proj, bins, lobe.raster.empty_image(b.n_pixels),
+                      torch.empty(b.n_pixels, dtype=torch.float32, device="cuda")))
+    stream = torch.cuda.current_stream()
+
+    def run():
+        out = []
+        for b, proj, bins, img, depth in state:
+            lobe.project(ctx, b, proj)
+            lobe.bin_sort(ctx, b, proj, bins, sync=False)
+            lobe.render_depth(ctx, b, proj, bins, img, depth)
+            out.append(lobe.fcs_coverage(ctx, b, img, depth, blocks))
+        return out
+
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        res = run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    counts = torch.cat([c for c, _ in res]).cpu()
+    npts = torch.cat([n for _, n in res]).cpu()
+    V, assign = lobe.fcs_select(counts, npts, tau=0.1)
+    pixels = sum(b.n_pixels for b, *_ in state)
+    return {"workload": "fcs_city_2M_64cams_800x600_16blocks", "cameras": len(cams), "blocks": len(blocks),
+            "ms": round(ms, 3), "cameras_per_s": round(len(cams) / ms * 1e3, 1),
+            "mpix_s": round(pixels / ms / 1e3, 1),
+            "cameras_per_block": [len(a) for a in assign]}
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -275,7 +332,7 @@ def main():
         del best
         torch.cuda.empty_cache()
     else:
-        tile, px = tuple(int(x) for x in args.tile.split("x")), (0, 0)
+        tile, px = tuple(int(x) for x in args.tile.split("x")), tuple(int(x) for x in args.px.split(","))
     wl.tile = tile
     ctx = lobe.Context(tile=tile, recompute_T=args.recompute, px_fwd=px[0], px_bwd=px[1])
 
@@ -467,6 +524,10 @@ def main():
         del proj, bins, image, grad2d, grads, flush
         torch.cuda.empty_cache()
         bvp = batched_vs_plain()
+    fcs = None
+    if world == 1 and not args.no_fcs:
+        torch.cuda.empty_cache()
+        fcs = fcs_benchmark()
 
     if rank == 0:
         line = {
@@ -493,6 +554,7 @@ def main():
             "stages": stages,
             "cpu_baseline": cpu,
             "batched_vs_plain": bvp,
+            "fast_camera_selection": fcs,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
