@@ -478,8 +478,9 @@ __device__ __forceinline__ float sum2(f2 v)
     return a + b;
 }
 
+// At most 128 registers a thread (occupancy: the kernel is latency- as much as issue-bound).
 template <int TW, int TH, int PX, bool RECOMPUTE>
-__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 32 * Slab<TW, TH, PX>::WARPS))
     k_render_bwd2(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                   const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
                   const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
