@@ -366,6 +366,51 @@ def fcs_coverage(D, T, cam, blocks, normalize=False, rel_margin=0.0):
     return np.array(counts, np.int64), int(mask.sum()), flags
 
 
+def densify(params, acc, cnt, normals, grad_threshold, max_clone_log_scale, prune_logit, n_split,
+            split_log_shrink):
+    """Selective densification (Sec. 3.3) with the adaptive density control of the 3DGS
+    procedure (appendix "3DGS Training"). Per Gaussian: pruned when its opacity logit is below
+    prune_logit; else, when it has SD views (cnt > 0, so its mean was inside the block) and
+    its mean gradient acc / cnt reaches grad_threshold, cloned (an exact copy follows it) if
+    its largest log-scale is at most max_clone_log_scale, split otherwise into n_split
+    children with means mu + R(q) (exp(log_s) * z_k) (z_k = normals[g, k]) and log-scales
+    log_s - split_log_shrink; else kept. Outputs follow their sources' order. The decisions
+    are taken in float32, the precision of the statistic and the parameters; the children's
+    geometry in FP64. Returns (dict of float64 arrays, source index per output)."""
+    f32 = np.float32
+    ls = np.asarray(params["log_scales"], f32)
+    lg = np.asarray(params["opacity_logits"], f32)
+    acc32 = np.asarray(acc, f32)
+    cnt = np.asarray(cnt, np.int64)
+    n = lg.shape[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mean_grad = np.where(cnt > 0, acc32 / np.maximum(cnt, 1).astype(f32), f32(0))
+    prune = lg < f32(prune_logit)
+    dens = ~prune & (cnt > 0) & (mean_grad >= f32(grad_threshold))
+    clone = dens & (ls.max(axis=1) <= f32(max_clone_log_scale))
+    split = dens & ~clone
+    k_out = np.where(prune, 0, np.where(clone, 2, np.where(split, n_split, 1)))
+    source = np.repeat(np.arange(n), k_out)
+    first = np.concatenate([[0], np.cumsum(k_out)[:-1]])
+    k = np.arange(source.shape[0]) - first[source]
+    out = {key: np.asarray(params[key], np.float64)[source].copy() for key in
+           ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    child = split[source]
+    if child.any():
+        g = source[child]
+        q = np.asarray(params["quats"], np.float64)[g]
+        q = q / np.linalg.norm(q, axis=1, keepdims=True)
+        r, x, y, z = q.T
+        R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - r * z), 2 * (x * z + r * y),
+                      2 * (x * y + r * z), 1 - 2 * (x * x + z * z), 2 * (y * z - r * x),
+                      2 * (x * z - r * y), 2 * (y * z + r * x), 1 - 2 * (x * x + y * y)], axis=1).reshape(-1, 3, 3)
+        s = np.exp(np.asarray(params["log_scales"], np.float64)[g])
+        zk = np.asarray(normals, np.float64)[g, k[child]]
+        out["means"][child] = np.asarray(params["means"], np.float64)[g] + np.einsum("nij,nj->ni", R, s * zk)
+        out["log_scales"][child] = np.asarray(params["log_scales"], np.float64)[g] - split_log_shrink
+    return out, source
+
+
 def sh_basis(dirs, degree=3):
     """Real SH basis [n,16] and its derivative [n,16,3] for each row of ``dirs``."""
     L = lib()

@@ -471,3 +471,67 @@ def test_coverage_of_a_wall_split_by_a_block_boundary():
     cols_left = int(np.sum(np.arange(W - 5) + 0.5 < 27.0))
     assert n == H * (W - 5)
     assert counts.tolist() == [H * cols_left, H * (W - 5 - cols_left), 0]
+
+
+# ----------------------------------------------------------------------------- densification
+
+def dens_set(n=5):
+    rng = np.random.default_rng(0)
+    return dict(means=rng.standard_normal((n, 3)).astype(np.float32),
+                log_scales=np.full((n, 3), -3.0, np.float32), quats=np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+                opacity_logits=np.zeros(n, np.float32), sh=rng.standard_normal((n, 16, 3)).astype(np.float32))
+
+
+def test_densify_branches_and_order():
+    """One Gaussian per branch: pruned (transparent), cloned (large gradient, small), split
+    (large gradient, large), kept (small gradient), and a large-gradient Gaussian outside the
+    block (no SD views), which is kept."""
+    p = dens_set(5)
+    p["opacity_logits"][0] = -6.0             # opacity 0.0025 < 0.005
+    p["log_scales"][2] = [-1.0, -3.0, -3.0]   # larger than the clone limit
+    acc = np.float32([1.0, 0.003, 0.003, 0.0001, 0.0])
+    cnt = np.int32([1, 3, 3, 1, 0])
+    acc[4] = 5.0                              # no views inside the block: cnt = 0
+    normals = np.zeros((5, 2, 3), np.float32)
+    out, src = oracle.densify(p, acc, cnt, normals, 2e-4, math.log(0.1), math.log(0.005 / 0.995), 2, math.log(1.6))
+    assert src.tolist() == [1, 1, 2, 2, 3, 4]
+    np.testing.assert_array_equal(out["means"][0], out["means"][1])  # the clone is an exact copy
+    np.testing.assert_allclose(out["log_scales"][2], np.float64([-1.0, -3.0, -3.0]) - math.log(1.6), rtol=1e-15)
+    np.testing.assert_allclose(out["means"][2], p["means"][2], rtol=1e-15)  # z = 0: the parent's mean
+    np.testing.assert_array_equal(out["sh"][5], p["sh"][4].astype(np.float64))
+
+
+def test_split_child_is_the_rotated_scaled_draw():
+    """A 90-degree turn about z with scales (2, 1, 0.5): the draw z = (1, 0, 0) lands at
+    mu + (0, 2, 0), z = (0, 0, 1) at mu + (0, 0, 0.5)."""
+    p = dens_set(1)
+    c, s = math.cos(math.pi / 4), math.sin(math.pi / 4)
+    p["quats"][0] = [c, 0, 0, s]
+    p["log_scales"][0] = np.log([2.0, 1.0, 0.5])
+    normals = np.float32([[[1, 0, 0], [0, 0, 1]]])
+    out, src = oracle.densify(p, np.float32([1.0]), np.int32([1]), normals, 2e-4, math.log(0.1), -20.0, 2, math.log(1.6))
+    assert src.tolist() == [0, 0]
+    np.testing.assert_allclose(out["means"][0] - p["means"][0], [0, 2, 0], atol=1e-6)
+    np.testing.assert_allclose(out["means"][1] - p["means"][0], [0, 0, 0.5], atol=1e-6)
+
+
+def test_split_children_follow_the_gaussian():
+    """Children drawn with many standard normals have the parent's covariance R S^2 R^T (the
+    split samples from the Gaussian itself)."""
+    rng = np.random.default_rng(5)
+    m = 200_000
+    p = dens_set(1)
+    q = rng.standard_normal(4)
+    p["quats"][0] = q / np.linalg.norm(q)
+    p["log_scales"][0] = np.log([0.3, 0.1, 0.05])
+    normals = rng.standard_normal((1, m, 3)).astype(np.float32)
+    p1 = {k: np.repeat(v, 1, axis=0) for k, v in p.items()}
+    out, _ = oracle.densify(p1, np.float32([1.0]), np.int32([1]), normals, 2e-4, -10.0, -20.0, m, 0.0)
+    d = out["means"] - p["means"][0]
+    qn = p["quats"][0].astype(np.float64)
+    r, x, y, z = qn / np.linalg.norm(qn)
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - r * z), 2 * (x * z + r * y)],
+                  [2 * (x * y + r * z), 1 - 2 * (x * x + z * z), 2 * (y * z - r * x)],
+                  [2 * (x * z - r * y), 2 * (y * z + r * x), 1 - 2 * (x * x + y * y)]])
+    Sig = R @ np.diag([0.3, 0.1, 0.05]) ** 2 @ R.T
+    np.testing.assert_allclose(np.cov(d.T), Sig, atol=0.01 * 0.09)
