@@ -15,6 +15,7 @@
  *   lobe_render_bwd   adjoint of the composite -> per-splat 2D gradients
  *   lobe_project_bwd  adjoint of the projection -> parameter gradients + SD statistics
  *   lobe_render_depth, lobe_fcs_coverage   fast camera selection (Sec. 3.2)
+ *   lobe_densify      selective densification (Sec. 3.3) with 3DGS density control
  *
  * A "batch" is a list of items (Gaussian set, camera, block); one call processes every
  * item of the batch in one launch per stage. The plain single-view path is a batch of one.
@@ -174,6 +175,27 @@ typedef struct {
     int32_t *sd_cnt; /* [n] or NULL */
 } lobe_grads;
 
+/* Adaptive density control of the 3DGS procedure (appendix "3DGS Training"), restricted to
+ * the block by selective densification (Sec. 3.3): only Gaussians with a nonzero SD count
+ * (seen with their mean inside the block) may clone or split. Defaults of 3DGS in brackets. */
+typedef struct {
+    float grad_threshold;      /* mean SD gradient norm acc/cnt at or above which a Gaussian densifies [2e-4] */
+    float max_clone_log_scale; /* largest max(log-scale) that clones rather than splits [log(0.01 * extent)] */
+    float prune_logit;         /* Gaussians whose opacity logit is below this are removed [logit(0.005)] */
+    int32_t n_split;           /* children of a split Gaussian, 1..4 [2] */
+    float split_log_shrink;    /* subtracted from the children's log-scales [log(0.8 * n_split)] */
+} lobe_densify_params;
+
+/* Output parameter arrays (device, caller-owned), room for `capacity` Gaussians. */
+typedef struct {
+    float *means;          /* [capacity][3] */
+    float *log_scales;     /* [capacity][3] */
+    float *quats;          /* [capacity][4], 16-byte aligned */
+    float *opacity_logits; /* [capacity] */
+    float *sh;             /* [capacity][16][3], 16-byte aligned */
+    int64_t capacity;
+} lobe_params_out;
+
 int32_t lobe_abi_version(void);
 
 /* Number of CUDA kernels this library has enqueued since it was loaded (all contexts,
@@ -259,6 +281,18 @@ lobe_status lobe_render_depth(lobe_ctx *ctx, const lobe_batch *batch, const lobe
 lobe_status lobe_fcs_coverage(lobe_ctx *ctx, const lobe_batch *batch, const lobe_image *image, const float *depth,
                               const lobe_aabb *blocks, int32_t n_blocks, int32_t normalize, uint32_t *counts,
                               uint32_t *n_points);
+
+/* Selective densification (Sec. 3.3) with 3DGS adaptive density control: classifies every
+ * Gaussian of `set` (prune / clone / split / keep, see lobe_densify_params) from its SD
+ * statistic sd_acc / sd_cnt and writes the resulting set to `out`, in source order (a kept
+ * Gaussian once, a clone twice, a split one as n_split children), and source[o] = the index
+ * of output o's source Gaussian (nullable). normals[g][k][3] (device) are the caller's
+ * standard normal draws for child k of Gaussian g (read only for split Gaussians). Child k's
+ * mean is mu + R(q) (exp(log_s) * normals[g][k]). Synchronises; the output count is stored in
+ * *n_out_host (non-NULL); LOBE_ERR_CAPACITY (nothing written) when it exceeds out->capacity. */
+lobe_status lobe_densify(lobe_ctx *ctx, const lobe_gaussians *set, const float *sd_acc, const int32_t *sd_cnt,
+                         const float *normals, const lobe_densify_params *prm, const lobe_params_out *out,
+                         int32_t *source, int64_t *n_out_host);
 
 /* Adjoint of lobe_render_fwd. dL_drgb has the layout of image->rgb. Reads image->T_final
  * and image->n_contrib unless the context has recompute_T set (then only dL_drgb).

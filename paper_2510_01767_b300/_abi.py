@@ -72,6 +72,16 @@ class Grads(ctypes.Structure):
                 ("sd_acc", vp), ("sd_cnt", vp)]
 
 
+class DensifyParams(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("max_clone_log_scale", ctypes.c_float),
+                ("prune_logit", ctypes.c_float), ("n_split", ctypes.c_int32), ("split_log_shrink", ctypes.c_float)]
+
+
+class ParamsOut(ctypes.Structure):
+    _fields_ = [("means", vp), ("log_scales", vp), ("quats", vp), ("opacity_logits", vp), ("sh", vp),
+                ("capacity", ctypes.c_int64)]
+
+
 # name -> (restype, argtypes); the exported symbols of liblobe.so (checked by the tests)
 SIGNATURES = {
     "lobe_abi_version": (ctypes.c_int32, []),
@@ -97,6 +107,8 @@ SIGNATURES = {
     "lobe_project_bwd": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), vp,
                                         ctypes.POINTER(Grads), ctypes.c_int32]),
     "lobe_visibility_crop": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(vp)]),
+    "lobe_densify": (ctypes.c_int, [vp, ctypes.POINTER(Gaussians), vp, vp, vp, ctypes.POINTER(DensifyParams),
+                                    ctypes.POINTER(ParamsOut), vp, ctypes.POINTER(ctypes.c_int64)]),
     "lobe_render_depth": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), ctypes.POINTER(Bins),
                                          ctypes.POINTER(Image), vp]),
     "lobe_fcs_coverage": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Image), vp, ctypes.POINTER(AABB),

@@ -8,7 +8,7 @@
 #include <cstring>
 #include <new>
 
-#include "lobe_internal.cuh"
+#include "lookback.cuh"
 
 
 #include <atomic>
@@ -528,6 +528,43 @@ lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_
     CUDA_TRY(launch_project_bwd(P, proj->splat, proj->radius, grad2d, accumulate ? 1 : 0, ctx->bins.dkB,
                                 ctx->bins.scalars + 8, ctx->bins.scan_slots, ctx->bins.ctl, ctx->stream),
              "project bwd");
+    return LOBE_OK;
+}
+
+lobe_status lobe_densify(lobe_ctx *ctx, const lobe_gaussians *set, const float *sd_acc, const int32_t *sd_cnt,
+                         const float *normals, const lobe_densify_params *prm, const lobe_params_out *out,
+                         int32_t *source, int64_t *n_out_host)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    if (!set || !prm || !out || !n_out_host) return fail(ctx, LOBE_ERR_ARG, "arguments missing");
+    const long long n = set->n;
+    if (n < 0 || out->capacity < 0) return fail(ctx, LOBE_ERR_ARG, "negative size");
+    if (n > 0 && (!set->means || !set->log_scales || !set->quats || !set->opacity_logits || !set->sh || !sd_acc ||
+                  !sd_cnt || !normals))
+        return fail(ctx, LOBE_ERR_ARG, "input pointers missing");
+    if (out->capacity > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh))
+        return fail(ctx, LOBE_ERR_ARG, "output pointers missing");
+    if (prm->n_split < 1 || prm->n_split > 4) return fail(ctx, LOBE_ERR_ARG, "n_split %d outside [1, 4]", prm->n_split);
+    if (!aligned16(set->quats) || !aligned16(set->sh) || !aligned16(out->quats) || !aligned16(out->sh))
+        return fail(ctx, LOBE_ERR_ARG, "quats/sh misaligned");
+    if (n > (long long)UINT32_MAX / 4) return fail(ctx, LOBE_ERR_ARG, "too many Gaussians");
+    // per-Gaussian action (1 byte) and output count/offset (4 bytes) live in the entry scratch
+    if (!ctx->entry_mem || ctx->max_entries < n) {
+        lobe_status s = grow_entries(ctx, n);
+        if (s != LOBE_OK) return s;
+    }
+    uint8_t *action = reinterpret_cast<uint8_t *>(ctx->bins.offs);
+    uint32_t *offs = ctx->bins.vis_pos, *total = ctx->bins.scalars + 9;
+    CUDA_TRY(launch_densify_count(n, *set, sd_acc, sd_cnt, *prm, action, offs, total,
+                                  LB{ctx->bins.scan_slots, ctx->bins.ctl, ST_DENSIFY}, ctx->stream),
+             "densify count");
+    uint32_t n_out = 0;
+    CUDA_TRY(cudaMemcpyAsync(&n_out, total, sizeof n_out, cudaMemcpyDeviceToHost, ctx->stream), "densify count read");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "densify sync");
+    *n_out_host = (int64_t)n_out;
+    if ((long long)n_out > out->capacity)
+        return fail(ctx, LOBE_ERR_CAPACITY, "%u outputs exceed capacity %lld", n_out, (long long)out->capacity);
+    CUDA_TRY(launch_densify_emit(n, *set, action, offs, total, normals, *prm, *out, source, ctx->stream), "densify emit");
     return LOBE_OK;
 }
 

@@ -218,6 +218,13 @@ struct FcsBlocks {
     float lo[FCS_MAX_BLOCKS][3], hi[FCS_MAX_BLOCKS][3];
     int n;
 };
+struct LB;
+cudaError_t launch_densify_count(long long n, const lobe_gaussians &in, const float *acc, const int *cnt,
+                                 const lobe_densify_params &prm, uint8_t *action, uint32_t *n_out, uint32_t *total,
+                                 LB lb, cudaStream_t st);
+cudaError_t launch_densify_emit(long long n, const lobe_gaussians &in, const uint8_t *action, const uint32_t *off,
+                                const uint32_t *total, const float *normals, const lobe_densify_params &prm,
+                                const lobe_params_out &out, int *source, cudaStream_t st);
 cudaError_t launch_fcs_coverage(const BatchParams &, const FcsBlocks &, const float *depth, const float *Tfin,
                                 int normalize, uint32_t *counts, uint32_t *n_points, cudaStream_t);
 cudaError_t launch_render_bwd(const BatchParams &, bool, const float *, const int *, const int *, const float *,

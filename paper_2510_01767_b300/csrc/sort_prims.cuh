@@ -9,128 +9,12 @@
 
 namespace lobe {
 
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 16;                       // per lane, warp-striped
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 4096 elements per tile
 constexpr int RS_WARPS = 8;
 constexpr int RS_THREADS = RS_WARPS * 32;
 constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // elements ranked and staged per tile
 constexpr int RS_MAX_BLOCKS = 1184;             // 8 per SM on 148 SMs
 constexpr int BIN_THREADS = 256;
-
-// ------------------------------------------------------------------ single-pass exclusive scan
-//
-// out[i] = sum_{j<i} in(j) for i < n, n read from device memory when n_dev is given (the launch
-// shape then depends only on an upper bound, so the call is graph-capturable). Each block scans
-// one 4096-element tile (warp-striped, coalesced) and gets the tile's offset by look-back. The
-// block of the last tile writes the grand total to total32/total64 (nullable) and the count the
-// next stage may use to n_use: the total, or 0 with a latched capacity error when it exceeds
-// `capacity` (< 0: unlimited). In-place use (out == the loaded array) is safe: each element is
-// read and later written by the same thread. The block with ticket 0 zeroes zero_words words at
-// zero_buf (accumulators of later kernels).
-
-struct LoadVisible {  // 1 where a projected entry touches at least one tile
-    const int *tiles;
-    __device__ uint32_t operator()(long long i) const { return tiles[i] > 0 ? 1u : 0u; }
-};
-struct LoadPlain {
-    const uint32_t *src;
-    __device__ uint32_t operator()(long long i) const { return src[i]; }
-};
-
-template <class L>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(L load, const uint32_t *n_dev, long long n_host, uint32_t *out,
-                                                       uint32_t *total32, long long *total64, uint32_t *n_use,
-                                                       long long capacity, LB lb, int bump, uint32_t *zero_buf,
-                                                       int zero_words)
-{
-    __shared__ int s_tile;
-    __shared__ uint32_t s_gen, s_prefix;
-    __shared__ uint32_t s_warp[SCAN_THREADS / 32 + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        int t;
-        uint32_t g;
-        lb_take(lb.ctl, lb.stage, bump != 0, t, g);
-        s_tile = t;
-        s_gen = g;
-    }
-    __syncthreads();
-    const int tile = s_tile;
-    if (tile == 0)
-        for (int i = threadIdx.x; i < zero_words; i += SCAN_THREADS) zero_buf[i] = 0u;
-    const long long n = n_dev ? (long long)*n_dev : n_host;
-    const long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (tile >= (ntiles > 0 ? ntiles : 1)) return;
-    const uint32_t tag = lb_tag(s_gen, lb.stage);
-    // warp w owns elements [t0 + w * 512, t0 + (w + 1) * 512), lane-striped per round
-    const long long w0 = (long long)tile * SCAN_TILE + (long long)warp * (32 * SCAN_ITEMS);
-    uint32_t x[SCAN_ITEMS];
-#pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-        const long long i = w0 + r * 32 + lane;
-        x[r] = i < n ? load(i) : 0u;
-    }
-    uint32_t carry = 0;  // warp-exclusive running sum
-#pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-        uint32_t inc = x[r];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-        x[r] = carry + inc - x[r];
-        carry += tot;
-    }
-    uint32_t wex;
-    const uint32_t agg = block_exclusive_scan<SCAN_THREADS>(lane == 0 ? carry : 0u, wex, s_warp);
-    wex = __shfl_sync(0xffffffffu, wex, 0);
-    if (warp == 0) {
-        unsigned long long *slot = lb.slots + tile;
-        uint32_t prefix = 0;
-        if (tile == 0) {
-            if (lane == 0) lb_publish(slot, tag, LB_INC, agg);
-        } else {
-            if (lane == 0) lb_publish(slot, tag, LB_AGG, agg);
-            prefix = lb_exclusive_warp(lb.slots, tile, tag, lb.ctl);
-            if (lane == 0) lb_publish(slot, tag, LB_INC, prefix + agg);
-        }
-        if (lane == 0) s_prefix = prefix;
-        if (lane == 0 && tile == (ntiles > 0 ? ntiles - 1 : 0)) {
-            const uint32_t total = prefix + agg;
-            if (total32) *total32 = total;
-            if (total64) *total64 = (long long)total;
-            if (n_use) {
-                const bool over = capacity >= 0 && (long long)total > capacity;
-                *n_use = over ? 0u : total;
-                if (over) set_status(lb.ctl, STATUS_CAPACITY);
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t base = s_prefix + wex;
-#pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-        const long long i = w0 + r * 32 + lane;
-        if (i < n) out[i] = base + x[r];
-    }
-}
-
-template <class L>
-static void scan(L load, const uint32_t *n_dev, long long n_max, uint32_t *out, uint32_t *total32, long long *total64,
-                 uint32_t *n_use, long long capacity, LB lb, cudaStream_t st, bool bump = false,
-                 uint32_t *zero_buf = nullptr, int zero_words = 0)
-{
-    long long nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb < 1) nb = 1;
-    const long long n_host = n_dev ? 0 : n_max;
-    count_launch();
-    k_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, out, total32, total64, n_use, capacity, lb,
-                                                  bump ? 1 : 0, zero_buf, zero_words);
-}
 
 // ------------------------------------------------------------------ compaction of visible splats
 

@@ -331,6 +331,36 @@ def fcs_coverage(ctx: Context, batch: Batch, image: Image, depth: torch.Tensor, 
     return counts[:, :len(blocks)], npts
 
 
+def densify(ctx: Context, g: GaussianSet, sd_acc: torch.Tensor, sd_cnt: torch.Tensor, normals: torch.Tensor | None = None,
+            grad_threshold=2e-4, percent_dense=0.01, scene_extent=1.0, min_opacity=0.005, n_split=2,
+            generator: torch.Generator | None = None):
+    """Selective densification (Sec. 3.3) with the 3DGS density control: returns (the new
+    GaussianSet, source index of every output Gaussian). Gaussians outside the block have
+    sd_cnt = 0 and never clone or split. ``normals`` [n, n_split, 3] are the split children's
+    standard normal draws (drawn here from ``generator`` when not given)."""
+    n = g.n
+    if normals is None:
+        normals = torch.randn((n, n_split, 3), device="cuda", generator=generator)
+    _require_cuda(normals, "normals")
+    _require_cuda(sd_acc, "sd_acc")
+    _require_cuda(sd_cnt, "sd_cnt", torch.int32)
+    prm = A.DensifyParams(float(grad_threshold), float(math.log(percent_dense * scene_extent)),
+                          float(math.log(min_opacity / (1 - min_opacity))), int(n_split), float(math.log(0.8 * n_split)))
+    src = A.Gaussians(g.means.data_ptr(), g.log_scales.data_ptr(), g.quats.data_ptr(), g.opacity_logits.data_ptr(),
+                      g.sh.data_ptr(), None, n)
+    cap = n * max(2, n_split)
+    out = {k: torch.empty((cap,) + tuple(getattr(g, k).shape[1:]), dtype=torch.float32, device="cuda")
+           for k in PARAM_KEYS}
+    source = torch.empty(cap, dtype=torch.int32, device="cuda")
+    po = A.ParamsOut(out["means"].data_ptr(), out["log_scales"].data_ptr(), out["quats"].data_ptr(),
+                     out["opacity_logits"].data_ptr(), out["sh"].data_ptr(), cap)
+    n_out = ctypes.c_int64(0)
+    ctx._check(ctx.lib.lobe_densify(ctx.handle, ctypes.byref(src), _ptr(sd_acc), _ptr(sd_cnt), _ptr(normals),
+                                    ctypes.byref(prm), ctypes.byref(po), _ptr(source), ctypes.byref(n_out)))
+    m = int(n_out.value)
+    return GaussianSet(**{k: v[:m].contiguous() for k, v in out.items()}), source[:m]
+
+
 def fcs_select(counts: torch.Tensor, n_points: torch.Tensor, tau: float = 0.1):
     """The paper's assignment C(b) = {c : V(c, b) >= tau}: returns (V [items, blocks], list of
     item indices per block)."""
