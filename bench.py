@@ -289,6 +289,37 @@ def fcs_benchmark(reps=5):
             "cameras_per_block": [len(a) for a in assign]}
 
 
+def densify_benchmark(reps=5):
+    """Selective densification (Sec. 3.3) of a 2M-Gaussian block with a synthetic SD statistic
+    (60% of the Gaussians inside the block): classify, scan, emit. Returns a dict."""
+    import torch
+    import paper_2510_01767_b300 as lobe
+
+    rng = np.random.default_rng(21)
+    n = 2_000_000
+    g = scenes.uniform_gaussians(rng, n, 10.0, 5.0, 50.0, logscale_shift=math.log(10.0))
+    g.opacity_logits[:] = rng.normal(0.0, 3.0, n).astype(np.float32)
+    cnt = np.where(rng.uniform(size=n) < 0.6, rng.integers(1, 8, n), 0).astype(np.int32)
+    acc = (rng.exponential(2e-4, n) * np.maximum(cnt, 1)).astype(np.float32)
+    gs = lobe.GaussianSet.from_numpy(g)
+    acc_t, cnt_t = torch.as_tensor(acc).cuda(), torch.as_tensor(cnt).cuda()
+    normals = torch.randn((n, 2, 3), device="cuda")
+    ctx = lobe.Context()
+    for _ in range(2):
+        out, _ = lobe.densify(ctx, gs, acc_t, cnt_t, normals, scene_extent=20.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out, _ = lobe.densify(ctx, gs, acc_t, cnt_t, normals, scene_extent=20.0)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    # bytes: parameters + statistic read, outputs written (236 B a Gaussian each way)
+    gb = (n * (236 + 8) + out.n * 236) / 1e9
+    return {"workload": "densify_2M", "gaussians_in": n, "gaussians_out": out.n, "ms": round(ms, 3),
+            "gaussians_per_s": round(n / ms * 1e3, 1), "achieved_gbs": round(gb / ms * 1e3, 1),
+            "note": "host-timed around the call (it synchronises once to size the output)"}
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -524,10 +555,12 @@ def main():
         del proj, bins, image, grad2d, grads, flush
         torch.cuda.empty_cache()
         bvp = batched_vs_plain()
-    fcs = None
+    fcs = dens = None
     if world == 1 and not args.no_fcs:
         torch.cuda.empty_cache()
         fcs = fcs_benchmark()
+        torch.cuda.empty_cache()
+        dens = densify_benchmark()
 
     if rank == 0:
         line = {
@@ -555,6 +588,7 @@ def main():
             "cpu_baseline": cpu,
             "batched_vs_plain": bvp,
             "fast_camera_selection": fcs,
+            "selective_densification": dens,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
