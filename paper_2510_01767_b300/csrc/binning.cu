@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(256) k_super_area(const __grid_constant__ Batc
                                                     uint32_t *__restrict__ info0, uint32_t *__restrict__ info1,
                                                     uint32_t *__restrict__ info2)
 {
+    pdl_wait();
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= *V_dev) return;
     const uint32_t e = order[k];
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) k_super_dup(int S, const uint32_t *V_dev,
                                                    const uint32_t *__restrict__ info2, const uint32_t *n_sp_use,
                                                    uint32_t *__restrict__ skeys, uint32_t *__restrict__ svals)
 {
+    pdl_wait();
     __shared__ int s_idx[DUP_PAIRS + DUP_PAIRS / 32];  // padded: position j lives at j + j / 32
     __shared__ uint32_t s_k[2];
     __shared__ int s_wmax[8];
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(256) k_super_dup(int S, const uint32_t *V_dev,
 __global__ void __launch_bounds__(256) k_key_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
                                                     long long n_max, int shift, int n_keys, uint32_t *__restrict__ start)
 {
+    pdl_wait();
     const long long n = *n_dev < n_max ? (long long)*n_dev : n_max;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += (long long)gridDim.x * blockDim.x) {
         const long long prev = k > 0 ? (long long)(keys[k - 1] >> shift) : -1;
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(256) k_chunk_map(const uint32_t *__restrict__ 
                                                    const uint32_t *__restrict__ chunk_base, int n_super,
                                                    uint4 *__restrict__ work)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_super) return;
     const uint32_t b0 = chunk_base[s], b1 = chunk_base[s + 1], p0 = super_start[s], p1 = super_start[s + 1];
@@ -205,6 +209,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__r
                                                              const uint32_t *__restrict__ chunk_base, int n_super,
                                                              uint32_t *__restrict__ cnt)
 {
+    pdl_wait();
     constexpr int NT = S * S;
     __shared__ uint32_t wc[BIN_THREADS / 32][NT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -242,6 +247,7 @@ __global__ void __launch_bounds__(256) k_chunk_prefix(const __grid_constant__ Ba
                                                       const uint32_t *__restrict__ chunk_base, uint32_t *__restrict__ cnt,
                                                       uint32_t *__restrict__ tile_count)
 {
+    pdl_wait();
     constexpr int NT = S * S, G = 256 / NT;
     __shared__ uint32_t part[G][NT];
     const int s = blockIdx.x, t = threadIdx.x % NT, g = threadIdx.x / NT;
@@ -282,6 +288,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
                                                             const int *__restrict__ tile_start, const uint32_t *n_use,
                                                             int *__restrict__ gauss_ids)
 {
+    pdl_wait();
     constexpr int NT = S * S;
     __shared__ uint32_t wc[BIN_THREADS / 32][NT];
     __shared__ uint32_t base[NT];
@@ -341,6 +348,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
 __global__ void __launch_bounds__(256) k_clear_on_overflow(const uint32_t *n_use, const long long *total, int n_tiles,
                                                            int *__restrict__ tile_start)
 {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t <= n_tiles && *n_use == 0 && *total != 0) tile_start[t] = 0;
 }
@@ -367,12 +375,12 @@ cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int 
     scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, V, nullptr, nullptr, -1, lb_of(b, ST_SCAN_VISIBLE), st, true);
     if (n > 0) {
         count_launch();
-        k_compact<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tiles, splat, b.vis_pos, b.dkA, b.dvA);
+        launch_pdl(k_compact, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, tiles, splat, b.vis_pos, b.dkA, b.dvA);
     }
     radix_sort(V, n, 0, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.counts, lb_of(b, ST_DEPTH_PASS), st);
     if (n > 0) {
         count_launch();
-        k_super_area<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, V, b.vis_pos, splat, radius, b.offs, b.dkA,
+        launch_pdl(k_super_area, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, P, V, b.vis_pos, splat, radius, b.offs, b.dkA,
                                                                   b.dvA, b.dkB);  // free after the depth sort
     }
     scan(LoadPlain{b.offs}, V, n, b.offs, sp_total, nullptr, n_sp, pair_capacity, lb_of(b, ST_SCAN_OFFS), st);
@@ -390,7 +398,7 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
     {
         count_launch();
         const long long nb = (pair_capacity + DUP_PAIRS - 1) / DUP_PAIRS;
-        k_super_dup<<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>(P.S, V, b.vis_pos, b.offs, b.dkA, b.dvA, b.dkB, n_sp,
+        launch_pdl(k_super_dup, dim3((unsigned)(nb < 1 ? 1 : nb)), dim3(256), 0, st, P.S, V, b.vis_pos, b.offs, b.dkA, b.dvA, b.dkB, n_sp,
                                                                  b.skA, b.svA);
     }
     int nbits = 0;
@@ -404,7 +412,7 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
     b.sp_ids = vfinal;
     count_launch();
     const long long rblocks = (pair_capacity + 1 + 255) / 256;
-    k_key_ranges<<<(unsigned)(rblocks < 2368 ? rblocks : 2368), 256, 0, st>>>(kfinal, n_sp, pair_capacity, KEY_SHIFT,
+    launch_pdl(k_key_ranges, dim3((unsigned)(rblocks < 2368 ? rblocks : 2368)), dim3(256), 0, st, kfinal, n_sp, pair_capacity, KEY_SHIFT,
                                                                                 P.n_super, b.super_start);
     // chunk work items: chunk_base[s] = first work item of super-tile s, chunk_base[n_super] = total
     scan(LoadChunks{b.super_start}, nullptr, P.n_super, b.chunk_base, b.chunk_base + P.n_super, nullptr, nullptr, -1,
@@ -413,15 +421,15 @@ cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *
     uint32_t *ts = reinterpret_cast<uint32_t *>(tile_start);
     if (P.n_super > 0) {
         count_launch(3);
-        k_chunk_map<<<(P.n_super + 255) / 256, 256, 0, st>>>(b.super_start, b.chunk_base, P.n_super, b.work);
+        launch_pdl(k_chunk_map, dim3((P.n_super + 255) / 256), dim3(256), 0, st, b.super_start, b.chunk_base, P.n_super, b.work);
         if (P.S == 8) {
-            k_chunk_count<8><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.work, b.chunk_base,
+            launch_pdl(k_chunk_count<8>, dim3(persistent_grid(work_max)), dim3(BIN_THREADS), 0, st, b.sp_keys, b.work, b.chunk_base,
                                                                                 P.n_super, b.chunk_cnt);
-            k_chunk_prefix<8><<<P.n_super, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
+            launch_pdl(k_chunk_prefix<8>, dim3(P.n_super), dim3(256), 0, st, P, b.chunk_base, b.chunk_cnt, ts);
         } else {
-            k_chunk_count<4><<<persistent_grid(work_max), BIN_THREADS, 0, st>>>(b.sp_keys, b.work, b.chunk_base,
+            launch_pdl(k_chunk_count<4>, dim3(persistent_grid(work_max)), dim3(BIN_THREADS), 0, st, b.sp_keys, b.work, b.chunk_base,
                                                                                 P.n_super, b.chunk_cnt);
-            k_chunk_prefix<4><<<P.n_super, 256, 0, st>>>(P, b.chunk_base, b.chunk_cnt, ts);
+            launch_pdl(k_chunk_prefix<4>, dim3(P.n_super), dim3(256), 0, st, P, b.chunk_base, b.chunk_cnt, ts);
         }
     }
     // the scan's grand total lands in tile_start[n_tiles] and in the caller's n_isect
@@ -441,14 +449,14 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
         count_launch();
         const unsigned grid = persistent_grid(b.work_max);
         if (P.S == 8)
-            k_chunk_emit<8><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.work, b.chunk_base,
+            launch_pdl(k_chunk_emit<8>, dim3(grid), dim3(BIN_THREADS), 0, st, P, b.sp_keys, b.sp_ids, b.work, b.chunk_base,
                                                           b.chunk_cnt, tile_start, n_use, gauss_ids);
         else
-            k_chunk_emit<4><<<grid, BIN_THREADS, 0, st>>>(P, b.sp_keys, b.sp_ids, b.work, b.chunk_base,
+            launch_pdl(k_chunk_emit<4>, dim3(grid), dim3(BIN_THREADS), 0, st, P, b.sp_keys, b.sp_ids, b.work, b.chunk_base,
                                                           b.chunk_cnt, tile_start, n_use, gauss_ids);
     }
     count_launch();
-    k_clear_on_overflow<<<(P.n_tiles + 1 + 255) / 256, 256, 0, st>>>(n_use, n_isect_dev, P.n_tiles, tile_start);
+    launch_pdl(k_clear_on_overflow, dim3((P.n_tiles + 1 + 255) / 256), dim3(256), 0, st, n_use, n_isect_dev, P.n_tiles, tile_start);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) k_densify_classify(long long n, const flo
                                                           lobe_densify_params prm, uint8_t *__restrict__ action,
                                                           uint32_t *__restrict__ n_out)
 {
+    pdl_wait();
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     uint8_t a = DENS_KEEP;
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(256) k_densify_emit(long long n, lobe_gaussian
                                                       const float *__restrict__ normals, lobe_densify_params prm,
                                                       lobe_params_out out, int *__restrict__ source)
 {
+    pdl_wait();
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n || (long long)*total > out.capacity) return;
     const uint8_t a = action[g];
@@ -96,7 +98,7 @@ cudaError_t launch_densify_count(long long n, const lobe_gaussians &in, const fl
 {
     if (n > 0) {
         count_launch();
-        k_densify_classify<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in.log_scales, in.opacity_logits, acc, cnt,
+        launch_pdl(k_densify_classify, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, in.log_scales, in.opacity_logits, acc, cnt,
                                                                         prm, action, n_out);
     }
     scan(LoadPlain{n_out}, nullptr, n, n_out, total, nullptr, nullptr, -1, lb, st, true);
@@ -109,7 +111,7 @@ cudaError_t launch_densify_emit(long long n, const lobe_gaussians &in, const uin
 {
     if (n == 0) return cudaSuccess;
     count_launch();
-    k_densify_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, action, off, total, normals, prm, out, source);
+    launch_pdl(k_densify_emit, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, in, action, off, total, normals, prm, out, source);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) k_fcs_coverage(const __grid_constant__ Ba
                                                       const float *__restrict__ Tfin, int normalize,
                                                       uint32_t *__restrict__ counts, uint32_t *__restrict__ n_points)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = p < P.n_pixels;
@@ -71,7 +72,7 @@ cudaError_t launch_fcs_coverage(const BatchParams &P, const FcsBlocks &B, const 
     if (e == cudaSuccess) e = cudaMemsetAsync(n_points, 0, sizeof(uint32_t) * (size_t)P.n_items, st);
     if (e != cudaSuccess || P.n_pixels == 0) return e;
     count_launch();
-    k_fcs_coverage<<<(unsigned)((P.n_pixels + 255) / 256), 256, 0, st>>>(P, B, depth, Tfin, normalize, counts,
+    launch_pdl(k_fcs_coverage, dim3((unsigned)((P.n_pixels + 255) / 256)), dim3(256), 0, st, P, B, depth, Tfin, normalize, counts,
                                                                          n_points);
     return cudaGetLastError();
 }

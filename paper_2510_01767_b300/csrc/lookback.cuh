@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(L load, const uint32_t *n
                                                        long long capacity, LB lb, int bump, uint32_t *zero_buf,
                                                        int zero_words)
 {
+    pdl_wait();
     __shared__ int s_tile;
     __shared__ uint32_t s_gen, s_prefix;
     __shared__ uint32_t s_warp[SCAN_THREADS / 32 + 1];
@@ -265,7 +266,7 @@ static void scan(L load, const uint32_t *n_dev, long long n_max, uint32_t *out, 
     if (nb < 1) nb = 1;
     const long long n_host = n_dev ? 0 : n_max;
     count_launch();
-    k_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, n_dev, n_host, out, total32, total64, n_use, capacity, lb,
+    launch_pdl(k_scan<L>, dim3((unsigned)nb), dim3(SCAN_THREADS), 0, st, load, n_dev, n_host, out, total32, total64, n_use, capacity, lb,
                                                   bump ? 1 : 0, zero_buf, zero_words);
 }
 

@@ -181,6 +181,7 @@ __device__ __forceinline__ bool project_cam(const BatchParams &P, const ItemPara
 __global__ void __launch_bounds__(256, 4) k_project_fwd(const __grid_constant__ BatchParams P, float4 *__restrict__ splat,
                                                      int *__restrict__ radius, int *__restrict__ tiles)
 {
+    pdl_wait();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P.n_gauss) return;
     const int s = set_of_gauss(P, t);
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(256, 4) k_project_fwd(const __grid_constant__ 
 
 __global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ BatchParams P)
 {
+    pdl_wait();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P.n_gauss) return;
     const int s = set_of_gauss(P, t);
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_project_bwd_list(const __grid_co
                                                                  uint32_t *__restrict__ list, uint32_t *__restrict__ count,
                                                                  LB lb)
 {
+    pdl_wait();
     __shared__ int s_tile;
     __shared__ uint32_t s_gen, s_prefix;
     __shared__ uint32_t s_warp[PL_THREADS / 32 + 1];
@@ -362,6 +365,7 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
                   const int *__restrict__ radius, const float4 *__restrict__ grad2d, int accumulate,
                   const uint32_t *__restrict__ list, const uint32_t *__restrict__ count)
 {
+    pdl_wait();
     __shared__ float s_sh[PB_THREADS * PB_ROW];
     __shared__ float s_gsh[PB_THREADS * PB_ROW];
     __shared__ const float *s_src[PB_THREADS];  // the Gaussian's SH coefficients
@@ -596,7 +600,7 @@ cudaError_t launch_project_fwd(const BatchParams &P, float *splat, int *radius, 
     if (P.n_gauss == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
     count_launch();
-    k_project_fwd<<<blocks, 256, 0, st>>>(P, reinterpret_cast<float4 *>(splat), radius, tiles);
+    launch_pdl(k_project_fwd, dim3(blocks), dim3(256), 0, st, P, reinterpret_cast<float4 *>(splat), radius, tiles);
     return cudaGetLastError();
 }
 
@@ -605,7 +609,7 @@ cudaError_t launch_visibility(const BatchParams &P, cudaStream_t st)
     if (P.n_gauss == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
     count_launch();
-    k_visibility<<<blocks, 256, 0, st>>>(P);
+    launch_pdl(k_visibility, dim3(blocks), dim3(256), 0, st, P);
     return cudaGetLastError();
 }
 
@@ -616,10 +620,10 @@ cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const i
     if (P.n_gauss == 0) return cudaSuccess;
     count_launch(2);
     const unsigned lblocks = (unsigned)((P.n_gauss + PL_TILE - 1) / PL_TILE);
-    k_project_bwd_list<<<lblocks, PL_THREADS, 0, st>>>(P, radius, accumulate, list, count,
+    launch_pdl(k_project_bwd_list, dim3(lblocks), dim3(PL_THREADS), 0, st, P, radius, accumulate, list, count,
                                                        LB{lb_slots, ctl, ST_PBWD_LIST});
     const unsigned blocks = (unsigned)((P.n_gauss + PB_THREADS - 1) / PB_THREADS);
-    k_project_bwd<<<blocks, PB_THREADS, 0, st>>>(P, reinterpret_cast<const float4 *>(splat), radius,
+    launch_pdl(k_project_bwd, dim3(blocks), dim3(PB_THREADS), 0, st, P, reinterpret_cast<const float4 *>(splat), radius,
                                                  reinterpret_cast<const float4 *>(grad2d), accumulate, list, count);
     return cudaGetLastError();
 }

@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
                  const int *__restrict__ tile_start, const int *__restrict__ ids, float *__restrict__ rgb,
                  float *__restrict__ Tout, int *__restrict__ ncout, float *__restrict__ depth)
 {
+    pdl_wait();
     using G = Slab<TW, TH, PX>;
     __shared__ WarpStage stage[G::WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
                  const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
                  const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
 {
+    pdl_wait();
     using G = Slab<TW, TH, PX>;
     __shared__ WarpStage stage[G::WARPS];
     WarpStage &st = stage[threadIdx.x >> 5];
@@ -485,6 +487,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 3
                   const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
                   const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
 {
+    pdl_wait();
     static_assert(PX % 2 == 0, "pixels are paired");
     constexpr int NP = PX / 2;
     using G = Slab<TW, TH, PX>;
@@ -645,10 +648,10 @@ static cudaError_t fwd_t(const BatchParams &P, const float *splat, const int *ts
     count_launch();
     const float4 *sp = reinterpret_cast<const float4 *>(splat);
     if (depth)
-        k_render_fwd<TW, TH, PX, true><<<P.n_tiles, 32 * Slab<TW, TH, PX>::WARPS, 0, st>>>(P, sp, ts, ids, rgb, T, nc,
+        launch_pdl(k_render_fwd<TW, TH, PX, true>, dim3(P.n_tiles), dim3(32 * Slab<TW, TH, PX>::WARPS), 0, st, P, sp, ts, ids, rgb, T, nc,
                                                                                           depth);
     else
-        k_render_fwd<TW, TH, PX, false><<<P.n_tiles, 32 * Slab<TW, TH, PX>::WARPS, 0, st>>>(P, sp, ts, ids, rgb, T, nc,
+        launch_pdl(k_render_fwd<TW, TH, PX, false>, dim3(P.n_tiles), dim3(32 * Slab<TW, TH, PX>::WARPS), 0, st, P, sp, ts, ids, rgb, T, nc,
                                                                                            nullptr);
     return cudaGetLastError();
 }
@@ -662,14 +665,14 @@ static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *spla
     const float4 *sp = reinterpret_cast<const float4 *>(splat);
     if constexpr (PX % 2 == 0) {  // pixel pairs in packed arithmetic
         if (recompute)
-            k_render_bwd2<TW, TH, PX, true><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+            launch_pdl(k_render_bwd2<TW, TH, PX, true>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
         else
-            k_render_bwd2<TW, TH, PX, false><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+            launch_pdl(k_render_bwd2<TW, TH, PX, false>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
     } else {
         if (recompute)
-            k_render_bwd<TW, TH, PX, true><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+            launch_pdl(k_render_bwd<TW, TH, PX, true>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
         else
-            k_render_bwd<TW, TH, PX, false><<<P.n_tiles, threads, 0, st>>>(P, sp, ts, ids, rgb, nc, dL, g2d);
+            launch_pdl(k_render_bwd<TW, TH, PX, false>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
     }
     return cudaGetLastError();
 }

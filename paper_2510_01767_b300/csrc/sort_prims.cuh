@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(256) k_compact(long long n_entries, const int 
                                                  const float *__restrict__ splat, const uint32_t *__restrict__ pos,
                                                  uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals)
 {
+    pdl_wait();
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_entries || tiles[e] <= 0) return;
     uint32_t p = pos[e];
@@ -59,6 +60,7 @@ template <int DIG>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_count(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
                                                             int shift, int nbits, uint32_t *__restrict__ counts)
 {
+    pdl_wait();
     __shared__ uint32_t h[RS_WARPS][DIG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = lane; d < DIG; d += 32) h[warp][d] = 0;
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t *__
                                                               const uint32_t *n_dev, int shift, int nbits,
                                                               const uint32_t *__restrict__ offsets)
 {
+    pdl_wait();
     constexpr int DPT = DIG / RS_THREADS;
     __shared__ uint32_t s_k[RS_TILE];
     __shared__ uint32_t s_v[RS_TILE];
@@ -224,13 +227,13 @@ static void radix_sort(const uint32_t *n_dev, long long n_max, int shift0, int n
         lb.stage = stage0 + p;
         count_launch(2);
         if (bits <= 8) {
-            k_radix_count<256><<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift0 + lo, bits, counts);
+            launch_pdl(k_radix_count<256>, dim3(nb), dim3(RS_THREADS), 0, st, ks, n_dev, shift0 + lo, bits, counts);
             scan(LoadPlain{counts}, nullptr, 256LL * nb, counts, nullptr, nullptr, nullptr, -1, lb, st);
-            k_radix_scatter<256><<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
+            launch_pdl(k_radix_scatter<256>, dim3(nb), dim3(RS_THREADS), 0, st, ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
         } else {
-            k_radix_count<512><<<nb, RS_THREADS, 0, st>>>(ks, n_dev, shift0 + lo, bits, counts);
+            launch_pdl(k_radix_count<512>, dim3(nb), dim3(RS_THREADS), 0, st, ks, n_dev, shift0 + lo, bits, counts);
             scan(LoadPlain{counts}, nullptr, 512LL * nb, counts, nullptr, nullptr, nullptr, -1, lb, st);
-            k_radix_scatter<512><<<nb, RS_THREADS, 0, st>>>(ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
+            launch_pdl(k_radix_scatter<512>, dim3(nb), dim3(RS_THREADS), 0, st, ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
         }
     }
 }
