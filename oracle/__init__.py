@@ -491,3 +491,64 @@ def set_dict(gs) -> dict:
     if hasattr(gs, "arrays"):
         gs = gs.arrays()
     return {k: np.asarray(v, np.float64) for k, v in gs.items()}
+
+
+# ----------------------------------------------------------------------------- KD partition
+
+def kd_partition(centers, root, n_blocks, cams_points, tau=0.1, q_lo=0.1, q_hi=0.9, steps=3):
+    """Load-balanced KD-tree partition with cutline refinement (Alg. 1, Sec. 3.1), written as
+    plain loops. ``centers`` [N, 3] are the coarse Gaussian centres, ``root`` the scene box,
+    ``cams_points`` one entry per camera: the world points back-projected from its depth map
+    (fast camera selection, Sec. 3.2). A box's camera set holds the cameras of its parent with
+    V = (points inside the box) / (all the camera's points) >= tau; its workload is the set's
+    size. The leaf with the largest workload (earliest created among equals) is split along
+    the longer of its x / y extents (of the centres inside it) at a percentile q of those
+    centres' coordinates, starting at the median and moved by bisection toward the lighter
+    side for ``steps`` rounds inside [q_lo, q_hi]; the children of the last evaluated cut are
+    kept. Boxes are half-open: lo <= p < hi. Returns [(lo, hi, camera index list)] in
+    creation order of the leaves."""
+    centers = np.asarray(centers, np.float64)
+
+    def inside(pts, lo, hi):
+        return np.all((pts >= lo) & (pts < hi), axis=-1)
+
+    def cams_of(lo, hi, parent_cams):
+        out = []
+        for c in parent_cams:
+            pts = cams_points[c]
+            if len(pts) and inside(pts, lo, hi).sum() / len(pts) >= tau:
+                out.append(c)
+        return out
+
+    lo0 = np.array(root.lo, np.float64)
+    hi0 = np.array(root.hi, np.float64)
+    leaves = [(lo0, hi0, cams_of(lo0, hi0, list(range(len(cams_points)))), 0)]
+    serial = 1
+    while len(leaves) < n_blocks:
+        best = 0
+        for i in range(1, len(leaves)):
+            if len(leaves[i][2]) > len(leaves[best][2]) or \
+                    (len(leaves[i][2]) == len(leaves[best][2]) and leaves[i][3] < leaves[best][3]):
+                best = i
+        lo, hi, cams, _ = leaves.pop(best)
+        pts = centers[inside(centers, lo, hi)]
+        ext = [pts[:, d].max() - pts[:, d].min() if len(pts) else 0.0 for d in (0, 1)]
+        a = 0 if ext[0] >= ext[1] else 1
+        coords = np.sort(pts[:, a])
+        qlo, qhi, q = q_lo, q_hi, 0.5
+        for _ in range(steps):
+            cut = float(np.quantile(coords, q)) if len(coords) else 0.5 * (lo[a] + hi[a])
+            hl, lr = hi.copy(), lo.copy()
+            hl[a] = cut
+            lr[a] = cut
+            cl, cr = cams_of(lo, hl, cams), cams_of(lr, hi, cams)
+            if len(cl) > len(cr):
+                qhi, q = q, 0.5 * (qlo + q)
+            elif len(cr) > len(cl):
+                qlo, q = q, 0.5 * (qhi + q)
+            else:
+                break
+        leaves.append((lo, hl, cl, serial))
+        leaves.append((lr, hi, cr, serial + 1))
+        serial += 2
+    return [(lo, hi, cams) for lo, hi, cams, _ in leaves]

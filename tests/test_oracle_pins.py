@@ -535,3 +535,40 @@ def test_split_children_follow_the_gaussian():
                   [2 * (x * z - r * y), 2 * (y * z + r * x), 1 - 2 * (x * x + y * y)]])
     Sig = R @ np.diag([0.3, 0.1, 0.05]) ** 2 @ R.T
     np.testing.assert_allclose(np.cov(d.T), Sig, atol=0.01 * 0.09)
+
+
+# ----------------------------------------------------------------------------- KD partition
+
+def test_kd_partition_bisection_closed_form():
+    """Ten cameras, camera k seeing only the point x = k: the median cut (x = 5) leaves 4 / 6
+    cameras, the bisection moves right to q = 0.7 (x = 7: 6 / 4), back to q = 0.6 (x = 6:
+    5 / 5) and stops there."""
+    xs = np.linspace(0.0, 10.0, 1001)
+    centers = np.stack([xs, np.linspace(0.0, 1.0, 1001), np.zeros(1001)], 1)
+    cams = [np.array([[k + 0.0, 0.5, 0.0]]) for k in range(1, 11)]
+    root = scenes.AABB((-math.inf,) * 3, (math.inf,) * 3)
+    leaves = oracle.kd_partition(centers, root, 2, cams)
+    (lo0, hi0, c0), (lo1, hi1, c1) = leaves
+    assert hi0[0] == pytest.approx(6.0) and lo1[0] == pytest.approx(6.0)
+    assert c0 == [0, 1, 2, 3, 4] and c1 == [5, 6, 7, 8, 9]
+
+
+def test_kd_partition_invariants():
+    """n_blocks leaves that split the root: every centre in exactly one leaf; the split axis
+    follows the longer extent and the cut stays inside the [10%, 90%] percentiles."""
+    rng = np.random.default_rng(4)
+    centers = np.stack([rng.uniform(-40, 40, 20000), rng.uniform(-10, 10, 20000), np.zeros(20000)], 1)
+    cams = [np.stack([rng.normal(cx, 8, 300), rng.normal(cy, 3, 300), np.zeros(300)], 1)
+            for cx, cy in zip(rng.uniform(-40, 40, 24), rng.uniform(-10, 10, 24))]
+    root = scenes.AABB((-math.inf,) * 3, (math.inf,) * 3)
+    leaves = oracle.kd_partition(centers, root, 6, cams)
+    assert len(leaves) == 6
+    owner = np.zeros(len(centers), int)
+    for lo, hi, cs in leaves:
+        owner += np.all((centers >= lo) & (centers < hi), axis=1)
+        assert set(cs) <= set(range(24))
+    assert np.all(owner == 1)
+    # two leaves: the cut is along x (80 m against 20 m of extent), near the centres' median
+    (lo0, hi0, _), (lo1, hi1, _) = oracle.kd_partition(centers, root, 2, cams)
+    assert np.isinf(hi0[1]) and np.isfinite(hi0[0]) and hi0[0] == lo1[0]
+    assert np.quantile(centers[:, 0], 0.1) <= hi0[0] <= np.quantile(centers[:, 0], 0.9)
