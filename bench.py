@@ -283,10 +283,23 @@ def fcs_benchmark(reps=5):
     npts = torch.cat([n for _, n in res]).cpu()
     V, assign = lobe.fcs_select(counts, npts, tau=0.1)
     pixels = sum(b.n_pixels for b, *_ in state)
+    # the load-balanced KD partition into 16 blocks over the same depth maps (Alg. 1)
+    from paper_2510_01767_b300.partition import CameraDepths, kd_partition, workloads
+    depths = CameraDepths.from_maps(ctx, cams, torch.cat([d for *_, d in state]),
+                                    torch.cat([img.T_final for _, _, _, img, _ in state]))
+    root = scenes.AABB((-math.inf,) * 3, (math.inf,) * 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    leaves = kd_partition(g.means, root, 16, depths)
+    part_ms = (time.perf_counter() - t0) * 1e3
+    median = kd_partition(g.means, root, 16, depths, steps=1)  # no refinement: median cuts
     return {"workload": "fcs_city_2M_64cams_800x600_16blocks", "cameras": len(cams), "blocks": len(blocks),
             "ms": round(ms, 3), "cameras_per_s": round(len(cams) / ms * 1e3, 1),
             "mpix_s": round(pixels / ms / 1e3, 1),
-            "cameras_per_block": [len(a) for a in assign]}
+            "cameras_per_block": [len(a) for a in assign],
+            "kd_partition": {"blocks": 16, "ms": round(part_ms, 1), "workloads": workloads(leaves),
+                             "max_workload": max(workloads(leaves)),
+                             "max_workload_median_cuts": max(workloads(median))}}
 
 
 def densify_benchmark(reps=5):
