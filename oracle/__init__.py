@@ -493,6 +493,49 @@ def set_dict(gs) -> dict:
     return {k: np.asarray(v, np.float64) for k, v in gs.items()}
 
 
+# ----------------------------------------------------------------------------- Adam
+
+ADAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def adam(params, grads, exp_avg, exp_avg_sq, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, rows=None):
+    """One Adam update (Kingma and Ba, Algorithm 1) of a Gaussian set, the optimizer of the
+    3DGS procedure the fine-training follows (appendix "3DGS Training"). With g the gradient
+    and t = step (>= 1, the index of this update), per element:
+        m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+        p <- p - lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+    lr is a dict of per-group rates: means, log_scales, quats, opacity_logits, sh_dc (the
+    degree-0 coefficients sh[:, 0, :]) and sh_rest (sh[:, 1:, :]). With ``rows`` (bool [n])
+    only those Gaussians change, parameters and moments alike (the sparse variant of coarse
+    training, appendix "3DGS Training"); without, every Gaussian does (standard Adam, a zero
+    gradient still decays the moments and moves the parameter). All dicts map ADAM_KEYS to
+    arrays of the set's shapes. Returns new float64 dicts (params, exp_avg, exp_avg_sq)."""
+    t = int(step)
+    if t < 1:
+        raise ValueError("step must be >= 1")
+    bc1 = 1.0 - beta1 ** t
+    bc2 = 1.0 - beta2 ** t
+    out_p, out_m, out_v = {}, {}, {}
+    for key in ADAM_KEYS:
+        p = np.asarray(params[key], np.float64)
+        g = np.asarray(grads[key], np.float64)
+        m = beta1 * np.asarray(exp_avg[key], np.float64) + (1.0 - beta1) * g
+        v = beta2 * np.asarray(exp_avg_sq[key], np.float64) + (1.0 - beta2) * g * g
+        if key == "sh":
+            rate = np.full(p.shape[1:], float(lr["sh_rest"]))
+            rate[0, :] = float(lr["sh_dc"])
+        else:
+            rate = float(lr[key])
+        p_new = p - rate * (m / bc1) / (np.sqrt(v / bc2) + eps)
+        if rows is not None:
+            keep = ~np.asarray(rows, bool).reshape((-1,) + (1,) * (p.ndim - 1))
+            p_new = np.where(keep, p, p_new)
+            m = np.where(keep, np.asarray(exp_avg[key], np.float64), m)
+            v = np.where(keep, np.asarray(exp_avg_sq[key], np.float64), v)
+        out_p[key], out_m[key], out_v[key] = p_new, m, v
+    return out_p, out_m, out_v
+
+
 # ----------------------------------------------------------------------------- KD partition
 
 def kd_partition(centers, root, n_blocks, cams_points, tau=0.1, q_lo=0.1, q_hi=0.9, steps=3):

@@ -572,3 +572,78 @@ def test_kd_partition_invariants():
     (lo0, hi0, _), (lo1, hi1, _) = oracle.kd_partition(centers, root, 2, cams)
     assert np.isinf(hi0[1]) and np.isfinite(hi0[0]) and hi0[0] == lo1[0]
     assert np.quantile(centers[:, 0], 0.1) <= hi0[0] <= np.quantile(centers[:, 0], 0.9)
+
+
+# ----------------------------------------------------------------------------- Adam
+
+ADAM_LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=5e-2, sh_dc=2.5e-3, sh_rest=2.5e-3 / 20)
+
+
+def adam_state(rng, n, scale=1.0):
+    shapes = dict(means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity_logits=(n,), sh=(n, 16, 3))
+    return {k: rng.standard_normal(s) * scale for k, s in shapes.items()}
+
+
+def test_adam_constant_gradient_closed_form():
+    """From zero moments under a constant gradient g the bias corrections are exact:
+    m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so every step moves p by lr g / (|g| + eps)."""
+    rng = np.random.default_rng(0)
+    p0, g = adam_state(rng, 5), adam_state(rng, 5, 1e-3)
+    p, m, v = p0, {k: np.zeros_like(a) for k, a in p0.items()}, {k: np.zeros_like(a) for k, a in p0.items()}
+    for t in range(1, 6):
+        p, m, v = oracle.adam(p, g, m, v, t, ADAM_LR, eps=1e-8)
+    for k in oracle.ADAM_KEYS:
+        rate = np.full(p0[k].shape[1:], ADAM_LR["sh_rest"]) if k == "sh" else ADAM_LR[k]
+        if k == "sh":
+            rate[0, :] = ADAM_LR["sh_dc"]
+        np.testing.assert_allclose(p[k], p0[k] - 5 * rate * g[k] / (np.abs(g[k]) + 1e-8), rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(m[k], (1 - 0.9 ** 5) * g[k], rtol=1e-12)
+        np.testing.assert_allclose(v[k], (1 - 0.999 ** 5) * g[k] ** 2, rtol=1e-12)
+
+
+def test_adam_matches_torch_optim():
+    """Four steps of random gradients against torch.optim.Adam (library routine) in float64,
+    one parameter group per learning rate (the SH split into its degree-0 and other bands)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    n = 7
+    p = adam_state(rng, n)
+    tp = {k: torch.tensor(a, requires_grad=True) for k, a in p.items() if k != "sh"}
+    tp["sh_dc"] = torch.tensor(p["sh"][:, :1, :], requires_grad=True)
+    tp["sh_rest"] = torch.tensor(p["sh"][:, 1:, :], requires_grad=True)
+    opt = torch.optim.Adam([{"params": [tp[k]], "lr": ADAM_LR[k]} for k in tp], betas=(0.9, 0.999), eps=1e-15)
+    m = {k: np.zeros_like(a) for k, a in p.items()}
+    v = {k: np.zeros_like(a) for k, a in p.items()}
+    for t in range(1, 5):
+        g = adam_state(rng, n, 10.0 ** rng.uniform(-6, 0))
+        g["means"][0] = 0.0  # a row without gradient this step still moves (momentum)
+        for k in tp:
+            src = g["sh"][:, :1, :] if k == "sh_dc" else g["sh"][:, 1:, :] if k == "sh_rest" else g[k]
+            tp[k].grad = torch.tensor(src)
+        opt.step()
+        p, m, v = oracle.adam(p, g, m, v, t, ADAM_LR)
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        np.testing.assert_allclose(p[k], tp[k].detach().numpy(), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(p["sh"][:, :1], tp["sh_dc"].detach().numpy(), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(p["sh"][:, 1:], tp["sh_rest"].detach().numpy(), rtol=1e-12, atol=1e-15)
+    st = opt.state[tp["quats"]]
+    np.testing.assert_allclose(m["quats"], st["exp_avg"].numpy(), rtol=1e-12)
+    np.testing.assert_allclose(v["quats"], st["exp_avg_sq"].numpy(), rtol=1e-12)
+
+
+def test_adam_sparse_rows_leave_the_others_untouched():
+    """Sparse variant: rows outside the mask keep parameters and moments bit for bit; rows in
+    it get exactly the dense update."""
+    rng = np.random.default_rng(2)
+    n = 9
+    p, g, m = adam_state(rng, n), adam_state(rng, n, 0.1), adam_state(rng, n, 0.01)
+    v = {k: np.abs(a) * 0.01 for k, a in adam_state(rng, n).items()}
+    rows = rng.uniform(size=n) < 0.5
+    rows[0], rows[1] = True, False
+    sp, sm, sv = oracle.adam(p, g, m, v, 7, ADAM_LR, rows=rows)
+    dp, dm, dv = oracle.adam(p, g, m, v, 7, ADAM_LR)
+    for k in oracle.ADAM_KEYS:
+        for got, dense, before in ((sp, dp, p), (sm, dm, m), (sv, dv, v)):
+            np.testing.assert_array_equal(got[k][~rows], before[k][~rows])
+            np.testing.assert_array_equal(got[k][rows], dense[k][rows])
+            assert np.all(dense[k][~rows] != before[k][~rows])
