@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--px", default="0,0", help="with --tile WxH: pixels per lane of the composite and its adjoint")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multi-block measurement")
-    ap.add_argument("--no-fcs", action="store_true", help="skip the fast-camera-selection measurement")
+    ap.add_argument("--no-fcs", action="store_true", help="skip the fast-camera-selection, densification and Adam measurements")
     ap.add_argument("--recompute", action="store_true")
     return ap.parse_args()
 
@@ -333,6 +333,86 @@ def densify_benchmark(reps=5):
             "note": "host-timed around the call (it synchronises once to size the output)"}
 
 
+ADAM_BYTES = 59 * 4 * 7  # per Gaussian: p, g, m, v read, p, m, v written (59 floats each)
+
+
+def adam_benchmark(ctx, batch, proj, grad2d, hbm_peak, reps=10):
+    """Adam (appendix "3DGS Training") on the bench's set: the projection adjoint followed by the
+    standalone update, the two fused (standard and sparse Adam), the standalone update alone
+    (HBM roofline), torch's fused Adam on the same tensors for context, and the standalone
+    update over a 4M-Gaussian set (a whole coarse city model before visibility cropping).
+    CUDA events around each variant, L2 flushed before each rep. Returns a dict."""
+    import torch
+    import paper_2510_01767_b300 as lobe
+
+    sets = [lobe.GaussianSet(**{k: getattr(s, k).clone() for k in lobe.PARAM_KEYS}, crop_mask=s.crop_mask)
+            for s in batch.sets]
+    cb = lobe.Batch(sets, batch.cameras, batch.items, batch.blocks)
+    n = sum(s.n for s in sets)
+    opts = [lobe.Adam(s) for s in sets]
+    grads = lobe.zero_grads(cb, sd=False)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    def unfused():
+        lobe.project_bwd(ctx, cb, proj, grad2d, grads)
+        for o, gr in zip(opts, grads):
+            o.step(ctx, gr)
+
+    def adam_only():
+        for o, gr in zip(opts, grads):
+            o.step(ctx, gr)
+
+    t_unfused = timed(unfused)
+    t_adj = timed(lambda: lobe.project_bwd(ctx, cb, proj, grad2d, grads))
+    t_dense = timed(lambda: lobe.project_bwd_adam(ctx, cb, proj, grad2d, opts, sparse=False))
+    t_sparse = timed(lambda: lobe.project_bwd_adam(ctx, cb, proj, grad2d, opts, sparse=True))
+    t_adam = timed(adam_only)
+    # torch's fused Adam (library kernels) on the same tensors, one group per array
+    tparams = [getattr(s, k) for s in sets for k in lobe.PARAM_KEYS]
+    for tp, gr in zip(tparams, [g[k] for g in grads for k in lobe.PARAM_KEYS]):
+        tp.grad = gr
+    topt = torch.optim.Adam([{"params": [tp]} for tp in tparams], lr=1e-3, eps=1e-15, fused=True)
+    t_torch = timed(topt.step)
+    for tp in tparams:
+        tp.grad = None
+    del topt
+    # the whole coarse model: 4M Gaussians
+    big_n = 4_000_000
+    big = lobe.GaussianSet(**{k: torch.randn((big_n,) + tuple(getattr(sets[0], k).shape[1:]), device="cuda")
+                              for k in lobe.PARAM_KEYS})
+    big_g = {k: torch.randn_like(getattr(big, k)) * 1e-3 for k in lobe.PARAM_KEYS}
+    big_opt = lobe.Adam(big)
+    t_big = timed(lambda: big_opt.step(ctx, big_g))
+    del big, big_g, big_opt
+    torch.cuda.empty_cache()
+    gbs = ADAM_BYTES * n / 1e9 / (t_adam / 1e3)
+    gbs_big = ADAM_BYTES * big_n / 1e9 / (t_big / 1e3)
+    return {"workload": f"{batch.sets[0].n}-gaussian set of the step", "gaussians": n,
+            "adjoint_then_adam_ms": round(t_unfused, 4), "adjoint_ms": round(t_adj, 4),
+            "fused_adjoint_adam_ms": round(t_dense, 4), "fused_adjoint_sparse_adam_ms": round(t_sparse, 4),
+            "fused_saving": round(1.0 - t_dense / t_unfused, 4),
+            "adam_ms": round(t_adam, 4), "torch_fused_adam_ms": round(t_torch, 4),
+            "adam_roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": round(hbm_peak, 1), "unit": "GB/s",
+                              "frac": round(gbs / hbm_peak, 4), "bytes_per_gaussian": ADAM_BYTES},
+            "adam_4M": {"gaussians": big_n, "ms": round(t_big, 4), "achieved_gbs": round(gbs_big, 1),
+                        "frac": round(gbs_big / hbm_peak, 4)}}
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -563,6 +643,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    adam = None
+    if world == 1 and not args.no_fcs:
+        adam = adam_benchmark(ctx, batch, proj, grad2d, hbm_peak)
     bvp = None
     if world == 1 and not args.no_batched:
         del proj, bins, image, grad2d, grads, flush
@@ -602,6 +685,7 @@ def main():
             "batched_vs_plain": bvp,
             "fast_camera_selection": fcs,
             "selective_densification": dens,
+            "adam": adam,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

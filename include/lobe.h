@@ -309,6 +309,63 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
 lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                              const float *grad2d, const lobe_grads *grads, int32_t accumulate);
 
+/* Mutable SoA arrays of one Gaussian set (device, caller-owned), in the shapes of
+ * lobe_gaussians: means [n][3], log_scales [n][3], quats [n][4], opacity_logits [n],
+ * sh [n][16][3]. Every pointer 16-byte aligned. */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+} lobe_param_arrays;
+
+/* Adam (Kingma and Ba, Algorithm 1), the optimizer of the 3DGS procedure that the per-block
+ * fine-training follows (appendix "3DGS Training"). Per element, with t = step:
+ *   m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2,
+ *   p <- p - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps),
+ * computed in float32 (the bias corrections in double on the host). Learning rates per
+ * group; sh_dc is the degree-0 band sh[g][0][0..2], sh_rest the other 45 floats. 3DGS values
+ * in brackets. */
+typedef struct {
+    float lr_means;       /* [1.6e-4 * scene extent, decayed] */
+    float lr_log_scales;  /* [5e-3] */
+    float lr_quats;       /* [1e-3] */
+    float lr_opacity;     /* [5e-2] */
+    float lr_sh_dc;       /* [2.5e-3] */
+    float lr_sh_rest;     /* [2.5e-3 / 20] */
+    double beta1, beta2;  /* [0.9, 0.999]; double, so that 1 - beta is exact to float32 rounding */
+    float eps;            /* [1e-15] */
+    int64_t step;         /* t >= 1: the index of this update (the caller counts) */
+} lobe_adam_params;
+
+/* Parameters (updated in place) and the two moment buffers of one set, all in the same
+ * layout; moments start at zero. */
+typedef struct {
+    lobe_param_arrays param;
+    lobe_param_arrays exp_avg;    /* m */
+    lobe_param_arrays exp_avg_sq; /* v */
+} lobe_adam_state;
+
+/* One Adam update of a set of n Gaussians from the gradients `grad` (device, read only).
+ * rows (device uint8 [n], nullable): when given, only Gaussians with rows[g] != 0 change,
+ * parameters and moments alike (the sparse Adam of coarse training, appendix "3DGS
+ * Training"); NULL updates every Gaussian (standard Adam). Asynchronous on the ctx stream. */
+lobe_status lobe_adam(lobe_ctx *ctx, int64_t n, const lobe_adam_state *state, const lobe_param_arrays *grad,
+                      const uint8_t *rows, const lobe_adam_params *prm);
+
+/* lobe_project_bwd fused with the Adam update: the adjoint of the batch (summed over each
+ * set's items, as lobe_project_bwd with accumulate = 0) is applied to states[s] with the
+ * hyper-parameters prm[s] (one of each per set; states[s].param must be the arrays of
+ * batch->sets[s]) without being written out. sparse = 1
+ * changes only the Gaussians some item of the batch sees (sparse Adam); sparse = 0 applies
+ * standard Adam to every Gaussian of every set (zero gradient for the unseen ones). sd
+ * (nullable; one per set, only sd_acc / sd_cnt read) receives the selective-densification
+ * statistic as in lobe_project_bwd. Asynchronous on the ctx stream. */
+lobe_status lobe_project_bwd_adam(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                                  const float *grad2d, const lobe_grads *sd, const lobe_adam_state *states,
+                                  const lobe_adam_params *prm, int32_t sparse);
+
 /* Visibility cropping (Sec. 3.3): for every set, mask[s][g] |= 1 when Gaussian g is visible
  * (passes the culling rules, crop mask ignored) from at least one item of that set.
  * masks[s] are device pointers (uint8 [n]); they are OR-ed into, not cleared. */

@@ -82,6 +82,21 @@ class ParamsOut(ctypes.Structure):
                 ("capacity", ctypes.c_int64)]
 
 
+class ParamArrays(ctypes.Structure):
+    _fields_ = [("means", vp), ("log_scales", vp), ("quats", vp), ("opacity_logits", vp), ("sh", vp)]
+
+
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr_means", ctypes.c_float), ("lr_log_scales", ctypes.c_float), ("lr_quats", ctypes.c_float),
+                ("lr_opacity", ctypes.c_float), ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_float),
+                ("step", ctypes.c_int64)]
+
+
+class AdamState(ctypes.Structure):
+    _fields_ = [("param", ParamArrays), ("exp_avg", ParamArrays), ("exp_avg_sq", ParamArrays)]
+
+
 # name -> (restype, argtypes); the exported symbols of liblobe.so (checked by the tests)
 SIGNATURES = {
     "lobe_abi_version": (ctypes.c_int32, []),
@@ -113,6 +128,11 @@ SIGNATURES = {
                                          ctypes.POINTER(Image), vp]),
     "lobe_fcs_coverage": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Image), vp, ctypes.POINTER(AABB),
                                          ctypes.c_int32, ctypes.c_int32, vp, vp]),
+    "lobe_adam": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(AdamState), ctypes.POINTER(ParamArrays), vp,
+                                 ctypes.POINTER(AdamParams)]),
+    "lobe_project_bwd_adam": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), vp,
+                                             ctypes.POINTER(Grads), ctypes.POINTER(AdamState),
+                                             ctypes.POINTER(AdamParams), ctypes.c_int32]),
 }
 
 _lib = None

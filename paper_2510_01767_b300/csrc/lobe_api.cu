@@ -531,6 +531,125 @@ lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_
     return LOBE_OK;
 }
 
+// ------------------------------------------------------------------ Adam
+
+static bool adam_arrays_ok(const lobe_param_arrays &a)
+{
+    return a.means && a.log_scales && a.quats && a.opacity_logits && a.sh && aligned16(a.means) &&
+           aligned16(a.log_scales) && aligned16(a.quats) && aligned16(a.opacity_logits) && aligned16(a.sh);
+}
+
+static void adam_set(const lobe_adam_state &st, AdamSet &z)
+{
+    const lobe_param_arrays *arr[3] = {&st.param, &st.exp_avg, &st.exp_avg_sq};
+    float **dst[3] = {z.p, z.m, z.v};
+    for (int i = 0; i < 3; ++i) {
+        dst[i][0] = arr[i]->means;
+        dst[i][1] = arr[i]->log_scales;
+        dst[i][2] = arr[i]->quats;
+        dst[i][3] = arr[i]->opacity_logits;
+        dst[i][4] = arr[i]->sh;
+    }
+}
+
+static lobe_status adam_constants(lobe_ctx *ctx, const lobe_adam_params *prm, AdamK &k)
+{
+    if (!prm) return fail(ctx, LOBE_ERR_ARG, "adam parameters missing");
+    if (prm->step < 1) return fail(ctx, LOBE_ERR_ARG, "adam step %lld < 1", (long long)prm->step);
+    if (!(prm->beta1 >= 0.0 && prm->beta1 < 1.0 && prm->beta2 >= 0.0 && prm->beta2 < 1.0) || !(prm->eps >= 0.f))
+        return fail(ctx, LOBE_ERR_ARG, "adam betas outside [0, 1) or eps negative");
+    const double t = (double)prm->step;
+    const double bc1 = 1.0 - std::pow(prm->beta1, t), bc2 = 1.0 - std::pow(prm->beta2, t);
+    if (!(bc1 > 0.0 && bc2 > 0.0)) return fail(ctx, LOBE_ERR_ARG, "adam bias correction is zero");
+    k.b1 = (float)prm->beta1;
+    k.b2 = (float)prm->beta2;
+    k.omb1 = (float)(1.0 - prm->beta1);
+    k.omb2 = (float)(1.0 - prm->beta2);
+    k.eps = prm->eps;
+    k.rsb2 = (float)(1.0 / std::sqrt(bc2));
+    const float lr[AG_COUNT] = {prm->lr_means, prm->lr_log_scales, prm->lr_quats,
+                                prm->lr_opacity, prm->lr_sh_dc, prm->lr_sh_rest};
+    for (int i = 0; i < AG_COUNT; ++i) k.ss[i] = (float)((double)lr[i] / bc1);
+    return LOBE_OK;
+}
+
+lobe_status lobe_adam(lobe_ctx *ctx, int64_t n, const lobe_adam_state *state, const lobe_param_arrays *grad,
+                      const uint8_t *rows, const lobe_adam_params *prm)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    if (n < 0) return fail(ctx, LOBE_ERR_ARG, "negative size");
+    AdamK k;
+    lobe_status st = adam_constants(ctx, prm, k);
+    if (st != LOBE_OK) return st;
+    if (n == 0) return LOBE_OK;
+    if (!state || !grad) return fail(ctx, LOBE_ERR_ARG, "state or gradients missing");
+    if (!adam_arrays_ok(state->param) || !adam_arrays_ok(state->exp_avg) || !adam_arrays_ok(state->exp_avg_sq) ||
+        !adam_arrays_ok(*grad))
+        return fail(ctx, LOBE_ERR_ARG, "adam arrays missing or not 16-byte aligned");
+    AdamSet z;
+    adam_set(*state, z);
+    const float *g[5] = {grad->means, grad->log_scales, grad->quats, grad->opacity_logits, grad->sh};
+    CUDA_TRY(launch_adam(n, z, g, rows, rows ? 1 : 0, k, ctx->stream), "adam");
+    return LOBE_OK;
+}
+
+lobe_status lobe_project_bwd_adam(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
+                                  const float *grad2d, const lobe_grads *sd, const lobe_adam_state *states,
+                                  const lobe_adam_params *prm, int32_t sparse)
+{
+    BUILD_PARAMS(H);
+    BatchParams &P = *H.p;
+    AdamBatch *A = new (std::nothrow) AdamBatch;
+    if (!A) return fail(ctx, LOBE_ERR_OOM, "host parameter block");
+    struct Free {
+        AdamBatch *a;
+        ~Free() { delete a; }
+    } free_a{A};
+    memset(A, 0, sizeof *A);
+    if (!prm) return fail(ctx, LOBE_ERR_ARG, "adam parameters missing");
+    for (int s = 0; s < P.n_sets; ++s) {
+        lobe_status st = adam_constants(ctx, prm + s, A->k[s]);
+        if (st != LOBE_OK) return st;
+    }
+    if (!states || (P.n_entries > 0 && (!proj || !proj->splat || !proj->radius || !grad2d)))
+        return fail(ctx, LOBE_ERR_ARG, "inputs missing");
+    for (int s = 0; s < P.n_sets; ++s) {
+        const lobe_adam_state &z = states[s];
+        const lobe_gaussians &G = batch->sets[s];
+        if (P.set[s].n > 0) {
+            if (!adam_arrays_ok(z.param) || !adam_arrays_ok(z.exp_avg) || !adam_arrays_ok(z.exp_avg_sq))
+                return fail(ctx, LOBE_ERR_ARG, "set %d: adam arrays missing or not 16-byte aligned", s);
+            if (z.param.means != G.means || z.param.log_scales != G.log_scales || z.param.quats != G.quats ||
+                z.param.opacity_logits != G.opacity_logits || z.param.sh != G.sh)
+                return fail(ctx, LOBE_ERR_ARG, "set %d: adam parameters are not the batch's set", s);
+        }
+        adam_set(z, A->set[s]);
+        if (sd) {
+            if ((sd[s].sd_acc == nullptr) != (sd[s].sd_cnt == nullptr))
+                return fail(ctx, LOBE_ERR_ARG, "set %d: sd_acc/sd_cnt mismatch", s);
+            P.set[s].sd_acc = sd[s].sd_acc;
+            P.set[s].sd_cnt = sd[s].sd_cnt;
+        }
+    }
+    if (!ctx->entry_mem || ctx->max_entries < P.n_entries || max_scan_length(ctx->max_entries) < P.n_gauss) {
+        lobe_status s = grow_entries(ctx, P.n_entries > P.n_gauss ? P.n_entries : P.n_gauss);
+        if (s != LOBE_OK) return s;
+    }
+    // standard Adam: the list kernel records who is seen (one byte per Gaussian, in the
+    // binning scratch) for the zero-gradient pass over the others
+    uint8_t *seen = reinterpret_cast<uint8_t *>(ctx->bins.offs);
+    if (!sparse)
+        for (int s = 0; s < P.n_sets; ++s) P.set[s].vis_mask = seen + P.set[s].gauss_off;
+    CUDA_TRY(launch_project_bwd(P, proj->splat, proj->radius, grad2d, 1, ctx->bins.dkB, ctx->bins.scalars + 8,
+                                ctx->bins.scan_slots, ctx->bins.ctl, ctx->stream, A),
+             "project bwd + adam");
+    if (!sparse)
+        for (int s = 0; s < P.n_sets; ++s)
+            CUDA_TRY(launch_adam(P.set[s].n, A->set[s], nullptr, seen + P.set[s].gauss_off, 2, A->k[s], ctx->stream),
+                     "adam (unseen Gaussians)");
+    return LOBE_OK;
+}
+
 lobe_status lobe_densify(lobe_ctx *ctx, const lobe_gaussians *set, const float *sd_acc, const int32_t *sd_cnt,
                          const float *normals, const lobe_densify_params *prm, const lobe_params_out *out,
                          int32_t *source, int64_t *n_out_host)

@@ -183,6 +183,60 @@ constexpr float T_MIN = 1e-4f;
 // T after a contributor; the stop rule is `next_T(T, alpha) < T_MIN` (checked before adding)
 __device__ __forceinline__ float next_T(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
 
+// ------------------------------------------------------------------ Adam
+//
+// One Adam update (Kingma and Ba) per element, in float32: with 1 - b1, 1 - b2,
+// ss = lr / (1 - b1^t) and rsb2 = 1 / sqrt(1 - b2^t) formed on the host in double (from
+// double betas: 1 - 0.999f would be off by 1.3e-5),
+//   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,  p <- p - ss m / (sqrt(v) rsb2 + eps),
+// which is p - lr m_hat / (sqrt(v_hat) + eps) with the bias-corrected moments. The fused
+// projection adjoint and the standalone kernel share this step.
+
+// learning-rate groups of a Gaussian set (the SH split into its degree-0 and other bands)
+enum AdamGroup { AG_MEANS = 0, AG_LOG_SCALES, AG_QUATS, AG_OPACITY, AG_SH_DC, AG_SH_REST, AG_COUNT };
+
+struct AdamK {
+    float b1, b2, omb1, omb2, eps, rsb2;
+    float ss[AG_COUNT];
+};
+
+// The square root and the division take the PTX approximations (sqrt.approx.f32: relative
+// error at most 2^-23; div.approx.f32: at most 2 ulp for a denominator in [2^-126, 2^126],
+// which eps >= 1e-15 and any finite moment keep): one instruction each instead of the
+// correctly rounded sequences, which would triple the update's instruction count.
+__device__ __forceinline__ float adam_sqrt(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void adam_step(const AdamK &k, float ss, float g, float &p, float &m, float &v)
+{
+    m = fmaf(k.b1, m, k.omb1 * g);
+    v = fmaf(k.b2, v, k.omb2 * (g * g));
+    p = p - ss * __fdividef(m, fmaf(adam_sqrt(v), k.rsb2, k.eps));
+}
+
+// zero gradient (a Gaussian no item sees, under standard Adam)
+__device__ __forceinline__ void adam_decay(const AdamK &k, float ss, float &p, float &m, float &v)
+{
+    m = k.b1 * m;
+    v = k.b2 * v;
+    p = p - ss * __fdividef(m, fmaf(adam_sqrt(v), k.rsb2, k.eps));
+}
+
+// the parameters and moments of one set, in the order means, log_scales, quats, opacity, sh
+struct AdamSet {
+    float *p[5], *m[5], *v[5];
+};
+
+// fused adjoint + Adam: per set of the batch
+struct AdamBatch {
+    AdamSet set[LOBE_MAX_SETS];
+    AdamK k[LOBE_MAX_SETS];
+};
+
 // ------------------------------------------------------------------ scratch and launchers
 
 // Scratch of the binning stage (context-owned, or carved from any device buffer). The
@@ -239,7 +293,13 @@ void count_launch(int n = 1);
 cudaError_t launch_project_fwd(const BatchParams &, float *, int *, int *, cudaStream_t);
 cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
 cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, uint32_t *list,
-                               uint32_t *count, unsigned long long *lb_slots, int *ctl, cudaStream_t);
+                               uint32_t *count, unsigned long long *lb_slots, int *ctl, cudaStream_t,
+                               const AdamBatch *adam = nullptr);
+// Standalone Adam over one set: mode 0 every row, 1 rows with rows[r] != 0 (sparse), 2 rows
+// with rows[r] == 0 and a zero gradient (grad unused: the Gaussians no item saw, after the
+// fused adjoint has updated the others).
+cudaError_t launch_adam(long long n, const AdamSet &s, const float *const grad[5], const uint8_t *rows, int mode,
+                        const AdamK &k, cudaStream_t);
 cudaError_t launch_render_fwd(const BatchParams &, const float *, const int *, const int *, float *, float *, int *,
                               float *depth, cudaStream_t);
 

@@ -264,15 +264,19 @@ __global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ Batc
 //   colour = max(0, SH + 0.5): masked where the raw value is negative; the view direction
 //   mu - campos carries a gradient to mu through the normalisation.
 // The adjoint runs in two kernels. The first visits every Gaussian once: it appends each one
-// that some item sees to a list (one atomic per warp; the list's order does not matter, every
-// Gaussian's result is computed on its own) and, unless accumulating, zeroes the gradients of
-// the others. The second walks the list, so every lane of every warp does the chain rule
+// that some item sees to a list and, unless accumulating, zeroes the gradients of the others.
+// The second walks the list, so every lane of every warp does the chain rule
 // (culled Gaussians, often most of a large set, cost no issue slots there). Per-view
 // contributions to dL/dSigma (6 values), dL/dmu and dL/dlogit are summed in registers over the
 // set's items, the 48 SH gradients in a padded shared-memory row per thread; the Sigma -> (s, q)
 // step runs once per Gaussian. A block of the second kernel takes 64 listed Gaussians, stages
 // their SH coefficients into shared memory (192 contiguous bytes per Gaussian) and writes their
 // SH gradients back the same way.
+// The fused variant (k_project_bwd_adam) ends in the Adam update of each listed Gaussian
+// instead: parameters and moments are read and written where the gradients would have been
+// written, and the gradients stay in registers and shared memory. Gaussians off the list keep
+// parameters and moments (sparse Adam); for standard Adam the first kernel records who is seen
+// and a zero-gradient Adam pass updates the others afterwards.
 
 constexpr int PB_THREADS = 64;
 constexpr int PB_ROW = 49;  // odd row stride: the per-thread rows fall in distinct banks
@@ -319,6 +323,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_project_bwd_list(const __grid_co
             const long long g = t - S.gauss_off;
             for (int k = 0; k < S.item_count && !vis[r]; ++k)
                 vis[r] = radius[P.item[P.set_items[S.item_begin + k]].entry_off + g] > 0;
+            if (S.vis_mask != nullptr) S.vis_mask[g] = vis[r] ? 1 : 0;  // fused standard Adam: who is seen
             if (!vis[r] && !accumulate) {
                 for (int i = 0; i < 3; ++i) {
                     S.g_means[3 * g + i] = 0.f;
@@ -360,16 +365,22 @@ __global__ void __launch_bounds__(PL_THREADS) k_project_bwd_list(const __grid_co
         if (vis[r]) list[base + rank[r]] = (uint32_t)(w0 + r * 32 + lane);
 }
 
-__global__ void __launch_bounds__(PB_THREADS, 8)
-    k_project_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
-                  const int *__restrict__ radius, const float4 *__restrict__ grad2d, int accumulate,
-                  const uint32_t *__restrict__ list, const uint32_t *__restrict__ count)
+// ADAM: instead of writing the gradients, apply the Adam update of the Gaussian's set in
+// place (A), so that a Gaussian's gradient never leaves the kernel (the sparse step: only
+// listed Gaussians change).
+template <bool ADAM>
+__device__ __forceinline__ void project_bwd_body(const BatchParams &P, const float4 *__restrict__ splat,
+                                                 const int *__restrict__ radius, const float4 *__restrict__ grad2d,
+                                                 int accumulate, const uint32_t *__restrict__ list,
+                                                 const uint32_t *__restrict__ count, const AdamBatch *A)
 {
     pdl_wait();
     __shared__ float s_sh[PB_THREADS * PB_ROW];
     __shared__ float s_gsh[PB_THREADS * PB_ROW];
     __shared__ const float *s_src[PB_THREADS];  // the Gaussian's SH coefficients
-    __shared__ float *s_dst[PB_THREADS];        // and its SH gradients
+    __shared__ float *s_dst[PB_THREADS];        // and its SH gradients (ADAM: its SH, updated in place)
+    __shared__ float *s_m[ADAM ? PB_THREADS : 1], *s_v[ADAM ? PB_THREADS : 1];  // ADAM: its SH moments
+    __shared__ int s_set[ADAM ? PB_THREADS : 1];                                  // ADAM: its set
     const uint32_t nv = *count;
     const long long b0 = (long long)blockIdx.x * PB_THREADS;
     if (b0 >= (long long)nv) return;
@@ -383,13 +394,37 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
     if (any) {
         load_world(S, g, w);  // in flight while the block stages its SH coefficients
         s_src[threadIdx.x] = S.sh + 48 * g;
-        s_dst[threadIdx.x] = S.g_sh + 48 * g;
+        if constexpr (ADAM) {
+            s_dst[threadIdx.x] = A->set[s].p[4] + 48 * g;
+            s_m[threadIdx.x] = A->set[s].m[4] + 48 * g;
+            s_v[threadIdx.x] = A->set[s].v[4] + 48 * g;
+            s_set[threadIdx.x] = s;
+        } else {
+            s_dst[threadIdx.x] = S.g_sh + 48 * g;
+        }
         // the first item's per-entry inputs, toward L2 meanwhile
         const long long e0 = P.item[P.set_items[S.item_begin]].entry_off + g;
         asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e0));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e0 + 2));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(splat + 3 * e0 + 1));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(radius + e0));
+        if constexpr (ADAM) {
+            // this Gaussian's Adam state, toward L2 while the adjoint computes: the SH moments
+            // (192 bytes each, at most three 128-byte lines) and the other arrays' entries
+            const AdamSet &Z = A->set[s];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Z.m[4] + 48 * g + 32 * i));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Z.v[4] + 48 * g + 32 * i));
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int w = a < 2 ? 3 : a == 2 ? 4 : 1;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Z.p[a] + w * g));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Z.m[a] + w * g));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Z.v[a] + w * g));
+            }
+        }
     }
     float *gsh = s_gsh + threadIdx.x * PB_ROW;
     const float *shr = s_sh + threadIdx.x * PB_ROW;
@@ -551,7 +586,43 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
         }
     }
     // ---- write the per-Gaussian parameters
-    if (any) {
+    if (ADAM && any) {
+        const AdamSet &Z = A->set[s];
+        const AdamK &k = A->k[s];
+        // every load first (none waits on a store), then the updates and the stores
+        float pm[3], mm[3], vm[3], pl[3], ml[3], vl[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            pm[i] = Z.p[0][3 * g + i]; mm[i] = Z.m[0][3 * g + i]; vm[i] = Z.v[0][3 * g + i];
+            pl[i] = Z.p[1][3 * g + i]; ml[i] = Z.m[1][3 * g + i]; vl[i] = Z.v[1][3 * g + i];
+        }
+        float4 pq = reinterpret_cast<float4 *>(Z.p[2])[g], mq = reinterpret_cast<float4 *>(Z.m[2])[g],
+               vq = reinterpret_cast<float4 *>(Z.v[2])[g];
+        float po = Z.p[3][g], mo = Z.m[3][g], vo = Z.v[3][g];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            adam_step(k, k.ss[AG_MEANS], gmu[i], pm[i], mm[i], vm[i]);
+            adam_step(k, k.ss[AG_LOG_SCALES], gls[i], pl[i], ml[i], vl[i]);
+        }
+        adam_step(k, k.ss[AG_QUATS], gq[0], pq.x, mq.x, vq.x);
+        adam_step(k, k.ss[AG_QUATS], gq[1], pq.y, mq.y, vq.y);
+        adam_step(k, k.ss[AG_QUATS], gq[2], pq.z, mq.z, vq.z);
+        adam_step(k, k.ss[AG_QUATS], gq[3], pq.w, mq.w, vq.w);
+        adam_step(k, k.ss[AG_OPACITY], glogit, po, mo, vo);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Z.p[0][3 * g + i] = pm[i]; Z.m[0][3 * g + i] = mm[i]; Z.v[0][3 * g + i] = vm[i];
+            Z.p[1][3 * g + i] = pl[i]; Z.m[1][3 * g + i] = ml[i]; Z.v[1][3 * g + i] = vl[i];
+        }
+        reinterpret_cast<float4 *>(Z.p[2])[g] = pq;
+        reinterpret_cast<float4 *>(Z.m[2])[g] = mq;
+        reinterpret_cast<float4 *>(Z.v[2])[g] = vq;
+        Z.p[3][g] = po; Z.m[3][g] = mo; Z.v[3][g] = vo;
+        if (S.sd_acc != nullptr && sd_cnt > 0) {
+            S.sd_acc[g] += sd_acc;
+            S.sd_cnt[g] += sd_cnt;
+        }
+    } else if (any) {
         if (accumulate) {
             for (int i = 0; i < 3; ++i) {
                 S.g_means[3 * g + i] += gmu[i];
@@ -575,6 +646,44 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
         }
     }
     __syncthreads();
+    if constexpr (ADAM) {
+        // ---- Adam on the block's SH: 12 float4 per Gaussian, consecutive threads take
+        // consecutive chunks of one Gaussian's 192 bytes; in two halves of 6 chunks a thread,
+        // each with all its loads (parameter, m, v) issued before the first update
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4 P4[6], M4[6], V4[6];
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const int j = threadIdx.x + (6 * h + r) * PB_THREADS;
+                if (j < nblk * 12) {
+                    const int gi = j / 12, c = j - gi * 12;
+                    P4[r] = reinterpret_cast<const float4 *>(s_dst[gi])[c];
+                    M4[r] = reinterpret_cast<const float4 *>(s_m[gi])[c];
+                    V4[r] = reinterpret_cast<const float4 *>(s_v[gi])[c];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const int j = threadIdx.x + (6 * h + r) * PB_THREADS;
+                if (j < nblk * 12) {
+                    const int gi = j / 12, c = j - gi * 12;
+                    const AdamK &k = A->k[s_set[gi]];
+                    const float *gv = s_gsh + gi * PB_ROW + 4 * c;
+                    // the first three floats of a Gaussian's 48 are its degree-0 band
+                    const float sa = c == 0 ? k.ss[AG_SH_DC] : k.ss[AG_SH_REST];
+                    adam_step(k, sa, gv[0], P4[r].x, M4[r].x, V4[r].x);
+                    adam_step(k, sa, gv[1], P4[r].y, M4[r].y, V4[r].y);
+                    adam_step(k, sa, gv[2], P4[r].z, M4[r].z, V4[r].z);
+                    adam_step(k, k.ss[AG_SH_REST], gv[3], P4[r].w, M4[r].w, V4[r].w);
+                    reinterpret_cast<float4 *>(s_dst[gi])[c] = P4[r];
+                    reinterpret_cast<float4 *>(s_m[gi])[c] = M4[r];
+                    reinterpret_cast<float4 *>(s_v[gi])[c] = V4[r];
+                }
+            }
+        }
+        return;
+    }
     // ---- SH gradients of the block's Gaussians: 12 float4 per Gaussian, consecutive threads
     // take consecutive chunks of one Gaussian's 192 bytes
 #pragma unroll
@@ -591,6 +700,23 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
         }
         *dst = a;
     }
+}
+
+__global__ void __launch_bounds__(PB_THREADS, 8)
+    k_project_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                  const int *__restrict__ radius, const float4 *__restrict__ grad2d, int accumulate,
+                  const uint32_t *__restrict__ list, const uint32_t *__restrict__ count)
+{
+    project_bwd_body<false>(P, splat, radius, grad2d, accumulate, list, count, nullptr);
+}
+
+__global__ void __launch_bounds__(PB_THREADS, 8)
+    k_project_bwd_adam(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
+                       const int *__restrict__ radius, const float4 *__restrict__ grad2d,
+                       const uint32_t *__restrict__ list, const uint32_t *__restrict__ count,
+                       const __grid_constant__ AdamBatch A)
+{
+    project_bwd_body<true>(P, splat, radius, grad2d, 1, list, count, &A);
 }
 
 // --------------------------------------------------------------------------- launchers
@@ -615,7 +741,7 @@ cudaError_t launch_visibility(const BatchParams &P, cudaStream_t st)
 
 cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const int *radius, const float *grad2d,
                                int accumulate, uint32_t *list, uint32_t *count, unsigned long long *lb_slots, int *ctl,
-                               cudaStream_t st)
+                               cudaStream_t st, const AdamBatch *adam)
 {
     if (P.n_gauss == 0) return cudaSuccess;
     count_launch(2);
@@ -623,8 +749,12 @@ cudaError_t launch_project_bwd(const BatchParams &P, const float *splat, const i
     launch_pdl(k_project_bwd_list, dim3(lblocks), dim3(PL_THREADS), 0, st, P, radius, accumulate, list, count,
                                                        LB{lb_slots, ctl, ST_PBWD_LIST});
     const unsigned blocks = (unsigned)((P.n_gauss + PB_THREADS - 1) / PB_THREADS);
-    launch_pdl(k_project_bwd, dim3(blocks), dim3(PB_THREADS), 0, st, P, reinterpret_cast<const float4 *>(splat), radius,
-                                                 reinterpret_cast<const float4 *>(grad2d), accumulate, list, count);
+    if (adam)
+        launch_pdl(k_project_bwd_adam, dim3(blocks), dim3(PB_THREADS), 0, st, P, reinterpret_cast<const float4 *>(splat),
+                   radius, reinterpret_cast<const float4 *>(grad2d), list, count, *adam);
+    else
+        launch_pdl(k_project_bwd, dim3(blocks), dim3(PB_THREADS), 0, st, P, reinterpret_cast<const float4 *>(splat),
+                   radius, reinterpret_cast<const float4 *>(grad2d), accumulate, list, count);
     return cudaGetLastError();
 }
 

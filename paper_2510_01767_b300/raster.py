@@ -361,6 +361,74 @@ def densify(ctx: Context, g: GaussianSet, sd_acc: torch.Tensor, sd_cnt: torch.Te
     return GaussianSet(**{k: v[:m].contiguous() for k, v in out.items()}), source[:m]
 
 
+# learning rates of the 3DGS procedure (means: times the scene extent, decayed by the caller)
+ADAM_LR_3DGS = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=5e-2, sh_dc=2.5e-3, sh_rest=2.5e-3 / 20)
+
+
+def _arrays(d) -> A.ParamArrays:
+    get = (lambda k: getattr(d, k)) if isinstance(d, GaussianSet) else (lambda k: d[k])
+    for k in PARAM_KEYS:
+        _require_cuda(get(k), k)
+    return A.ParamArrays(*(get(k).data_ptr() for k in PARAM_KEYS))
+
+
+class Adam:
+    """Adam state of one Gaussian set: the two moment buffers in the set's layout, the
+    per-group learning rates (ADAM_LR_3DGS keys) and the step count. ``step`` applies an
+    update from given gradients (lobe_adam); ``project_bwd_adam`` fuses it into the
+    projection adjoint. The set's tensors are updated in place."""
+
+    def __init__(self, g: GaussianSet, lr=None, betas=(0.9, 0.999), eps=1e-15):
+        self.set = g
+        self.lr = dict(ADAM_LR_3DGS if lr is None else lr)
+        self.betas = (float(betas[0]), float(betas[1]))
+        self.eps = float(eps)
+        self.exp_avg = {k: torch.zeros_like(getattr(g, k)) for k in PARAM_KEYS}
+        self.exp_avg_sq = {k: torch.zeros_like(getattr(g, k)) for k in PARAM_KEYS}
+        self.t = 0
+
+    def _state(self) -> A.AdamState:
+        return A.AdamState(_arrays(self.set), _arrays(self.exp_avg), _arrays(self.exp_avg_sq))
+
+    def _params(self, t) -> A.AdamParams:
+        lr = self.lr
+        return A.AdamParams(lr["means"], lr["log_scales"], lr["quats"], lr["opacity_logits"], lr["sh_dc"],
+                            lr["sh_rest"], self.betas[0], self.betas[1], self.eps, int(t))
+
+    def step(self, ctx: Context, grads: dict, rows: torch.Tensor | None = None):
+        """One update from grads (dict of PARAM_KEYS tensors); with rows (uint8 [n]) only
+        the rows marked nonzero change (sparse Adam)."""
+        if rows is not None:
+            _require_cuda(rows, "rows", torch.uint8)
+        st, ga = self._state(), _arrays(grads)
+        ctx._check(ctx.lib.lobe_adam(ctx.handle, self.set.n, ctypes.byref(st), ctypes.byref(ga), _ptr(rows),
+                                     ctypes.byref(self._params(self.t + 1))))
+        self.t += 1
+
+
+def project_bwd_adam(ctx: Context, batch: Batch, proj: Projection, grad2d: torch.Tensor, optimizers, sd=None,
+                     sparse: bool = False):
+    """The projection adjoint fused with Adam: optimizers[s] (an Adam of batch.sets[s]) takes
+    one step with the batch's gradients, which are never written out. sparse: only the
+    Gaussians some item sees change; otherwise every Gaussian of every set does (standard
+    Adam). sd: optional list of dicts with sd_acc / sd_cnt (accumulated)."""
+    if len(optimizers) != len(batch.sets) or any(o.set is not g for o, g in zip(optimizers, batch.sets)):
+        raise ValueError("one Adam per set of the batch, in order")
+    _require_cuda(grad2d, "grad2d")
+    states = (A.AdamState * len(optimizers))(*[o._state() for o in optimizers])
+    prms = (A.AdamParams * len(optimizers))(*[o._params(o.t + 1) for o in optimizers])
+    sdarr = None
+    if sd is not None:
+        sdarr = (A.Grads * len(batch.sets))()
+        for i, d in enumerate(sd):
+            sdarr[i].sd_acc = d["sd_acc"].data_ptr() if d.get("sd_acc") is not None else None
+            sdarr[i].sd_cnt = d["sd_cnt"].data_ptr() if d.get("sd_cnt") is not None else None
+    ctx._check(ctx.lib.lobe_project_bwd_adam(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()), _ptr(grad2d),
+                                             sdarr, states, prms, int(bool(sparse))))
+    for o in optimizers:
+        o.t += 1
+
+
 def fcs_select(counts: torch.Tensor, n_points: torch.Tensor, tau: float = 0.1):
     """The paper's assignment C(b) = {c : V(c, b) >= tau}: returns (V [items, blocks], list of
     item indices per block)."""
