@@ -44,9 +44,33 @@ class Rasterizer:
 
     def batch(self, params, cameras):
         g = R.GaussianSet(*[p.detach().contiguous() for p in params], crop_mask=self.crop_mask)
+        return self.batch_of(g, cameras)
+
+    def batch_of(self, g: R.GaussianSet, cameras):
         blocks = [self.block] if self.block is not None else []
         items = [(0, i, 0 if blocks else -1) for i in range(len(cameras))]
         return R.Batch([g], cameras, items, blocks)
+
+    def train_step(self, opt: R.Adam, cameras, loss_fn, sparse: bool = False):
+        """One training step with the Adam update fused into the projection adjoint: render
+        the views of ``cameras`` from opt.set, loss_fn(list of [3,H,W] views) -> scalar tensor
+        (differentiated by torch on the images only), render adjoint, then the fused projection
+        adjoint + Adam (standard, or sparse: only the Gaussians some view sees change). The SD
+        statistics accumulate as in ``rasterize``. Returns the loss (detached)."""
+        if isinstance(cameras, dict) or hasattr(cameras, "as_dict"):
+            cameras = [cameras]
+        if opt.set.crop_mask is not self.crop_mask:
+            opt.set.crop_mask = self.crop_mask
+        batch = self.batch_of(opt.set, list(cameras))
+        proj, bins, img = R.forward(self.ctx, batch, sync=True)
+        self.last_bins = bins
+        rgb = img.rgb.detach().requires_grad_(True)
+        loss = loss_fn(batch.image_views(rgb))
+        (d_rgb,) = torch.autograd.grad(loss, rgb)
+        g2d = R.render_bwd(self.ctx, batch, proj, bins, None if self.ctx.recompute_T else img, d_rgb.contiguous())
+        sd = [{"sd_acc": self.sd_acc, "sd_cnt": self.sd_cnt}] if self.sd_acc.shape[0] == opt.set.n else None
+        R.project_bwd_adam(self.ctx, batch, proj, g2d, [opt], sd=sd, sparse=sparse)
+        return loss.detach()
 
 
 class LobeRasterize(torch.autograd.Function):

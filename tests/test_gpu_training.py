@@ -5,7 +5,8 @@ autograd.Function, with the selective-densification statistics accumulated on th
 Pins: the loss over eight fixed probe views, taken every 100 steps, does not rise and ends
 well below its start; the PSNR of the fitted set against the targets rises; Gaussians the
 views see collect SD statistics and the others none. The per-step time of the last 400 steps
-(rasterizer forward + backward, loss, fused Adam) is printed."""
+(rasterizer forward + backward, loss, Adam) is printed. Two optimizers: torch's fused Adam on
+the autograd.Function's gradients, and the library's Adam fused into the projection adjoint."""
 import math
 import time
 
@@ -36,18 +37,33 @@ def psnr(ps, cams, targets, n):
     return -10 * math.log10(mse)
 
 
-def test_fit_2m_city_block_64_views_500_steps():
+@pytest.fixture(scope="module")
+def city_fit():
     gt, init, cams, block = scenes.training_scene(n=2_000_000, n_views=64, width=1280, height=720)
     gtp = params_of(gt, requires_grad=False)
     with torch.no_grad():
         r = lobe.Rasterizer(gt.n)
         targets = [lobe.rasterize(*gtp, c.as_dict(), r).clone() for c in cams]
     del gtp
-    ps = params_of(init)
-    raster = lobe.Rasterizer(init.n, tile=(16, 16), block=block)
     extent = float(np.linalg.norm(gt.means.max(0) - gt.means.min(0)))
+    return init, cams, block, targets, extent
+
+
+@pytest.mark.parametrize("optimizer", ["torch_adam", "fused_adam"])
+def test_fit_2m_city_block_64_views_500_steps(city_fit, optimizer):
+    """torch_adam: rasterize (autograd.Function) + loss + torch's fused Adam; fused_adam: the
+    library's training step, whose projection adjoint applies the Adam update itself."""
+    init, cams, block, targets, extent = city_fit
+    raster = lobe.Rasterizer(init.n, tile=(16, 16), block=block)
     lrs = [1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3]  # means, log-scales, quats, opacity, SH (3DGS defaults)
-    opt = torch.optim.Adam([{"params": [p], "lr": lr} for p, lr in zip(ps, lrs)], eps=1e-15, fused=True)
+    if optimizer == "torch_adam":
+        ps = params_of(init)
+        opt = torch.optim.Adam([{"params": [p], "lr": lr} for p, lr in zip(ps, lrs)], eps=1e-15, fused=True)
+    else:
+        gs = lobe.GaussianSet(*params_of(init, requires_grad=False))
+        ps = [getattr(gs, k) for k in KEYS]
+        opt = lobe.Adam(gs, lr=dict(zip(("means", "log_scales", "quats", "opacity_logits", "sh_dc"), lrs),
+                                    sh_rest=lrs[4]), eps=1e-15)
     probe, probe_t = cams[::8], targets[::8]
 
     def probe_loss():
@@ -65,11 +81,14 @@ def test_fit_2m_city_block_64_views_500_steps():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
         k = int(order[it])
-        img = lobe.rasterize(*ps, cams[k].as_dict(), raster)
-        loss = l1_ssim_loss(img, targets[k])
-        opt.zero_grad(set_to_none=True)
-        loss.backward()
-        opt.step()
+        if optimizer == "torch_adam":
+            img = lobe.rasterize(*ps, cams[k].as_dict(), raster)
+            loss = l1_ssim_loss(img, targets[k])
+            opt.zero_grad(set_to_none=True)
+            loss.backward()
+            opt.step()
+        else:
+            raster.train_step(opt, cams[k].as_dict(), lambda views: l1_ssim_loss(views[0], targets[k]))
         if it % 100 == 99:
             if it > 100:
                 torch.cuda.synchronize()
@@ -80,7 +99,8 @@ def test_fit_2m_city_block_64_views_500_steps():
     torch.cuda.synchronize()
     step_ms = (time.perf_counter() - t0) / 400 * 1e3
     c = np.array(checkpoints)
-    print(f"\n{step_ms:.2f} ms per step (last 400 of 500); probe loss every 100 steps: {np.round(c, 4).tolist()}")
+    print(f"\n{optimizer}: {step_ms:.2f} ms per step (last 400 of 500); probe loss every 100 steps: "
+          f"{np.round(c, 4).tolist()}")
     assert np.all(c[1:] <= c[:-1] * 1.03), c
     assert c[-1] < 0.75 * c[0], c
     psnr1 = psnr(ps, probe, probe_t, init.n)
