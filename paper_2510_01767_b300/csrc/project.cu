@@ -189,8 +189,15 @@ __global__ void __launch_bounds__(256, 4) k_project_fwd(const __grid_constant__ 
     const long long g = t - S.gauss_off;
     const bool cropped = S.crop != nullptr && S.crop[g] == 0;
     World w;
-    if (!cropped) load_world(S, g, w);
     const float4 *shg = reinterpret_cast<const float4 *>(S.sh + 48 * g);
+    if (!cropped) {
+        // the SH coefficients toward L2 while the geometry is loaded and projected: their loads
+        // below then wait on L2 rather than on DRAM (a culled Gaussian's lines are wasted reads)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(shg));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(shg + 6));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(shg + 11));
+        load_world(S, g, w);
+    }
     const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
     float opacity = 0.0f;
     bool first = true;
