@@ -577,7 +577,10 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 3
             const int pos = base - start + j;
             const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
             const f2 v2 = pk(q0.y, q0.y), C2 = pk(q1.x, q1.x), a2 = pk(cl.a2, cl.a2), b1 = pk(cl.b1, cl.b1);
-            f2 du = 0, dv = 0, dA = 0, dB = 0, dC = 0, dop = 0, dr = 0, dg = 0, db = 0;  // 0 = (+0, +0)
+            const f2 oln2 = pk(q1.y * LN2, q1.y * LN2);
+            // per lane: S1 = sum dL/dp2, S2 = sum dL/dp2 dy, S3 = sum dL/dp2 dy^2 over its pixels; dx
+            // is the lane's own, so the exponent's gradients follow from these three after the loop
+            f2 S1 = 0, S2 = 0, S3 = 0, dop = 0, dr = 0, dg = 0, db = 0;  // 0 = (+0, +0)
             bool any = false;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
@@ -610,20 +613,21 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 3
                 B1[i] = fma2(al, d1, B1[i]);
                 B2[i] = fma2(al, d2, B2[i]);
                 T2[i] = Ti;
-                // past the clamp alpha no longer depends on o or the exponent
-                dop = fma2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb), dop);
-                const f2 dp2 = mul2(da, pk(ka ? 0.0f : aa * LN2, kb ? 0.0f : ab * LN2));
+                // past the clamp alpha no longer depends on o or the exponent: dL/do = da G and
+                // dL/dp2 = da o G ln2 (alpha = o G below the clamp)
+                const f2 t = mul2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb));
+                dop = add2(dop, t);
+                const f2 dp2 = mul2(t, oln2);
                 const f2 dpy = mul2(dp2, dy2);
-                dA = fma2(dp2, pk(cl.dx * cl.dx, cl.dx * cl.dx), dA);
-                dB = fma2(dpy, pk(cl.dx, cl.dx), dB);
-                dC = fma2(dpy, dy2, dC);
-                du = fma2(dp2, fma2(pk(q0.w, q0.w), dy2, pk(2.f * q0.z * cl.dx, 2.f * q0.z * cl.dx)), du);
-                dv = fma2(dp2, pk(q0.w * cl.dx, q0.w * cl.dx), dv);
-                dv = fma2(pk(2.f * q1.x, 2.f * q1.x), dpy, dv);
+                S1 = add2(S1, dp2);
+                S2 = add2(S2, dpy);
+                S3 = fma2(dpy, dy2, S3);
             }
             if (__any_sync(0xffffffffu, any)) {
-                const float vals[9] = {sum2(du), sum2(dv), sum2(dA), sum2(dB), sum2(dC),
-                                       sum2(dop), sum2(dr), sum2(dg), sum2(db)};
+                // p2 = A dx^2 + B dx dy + C dy^2 with dx = u - x, dy = v - y
+                const float s1 = sum2(S1), s2 = sum2(S2), dx = cl.dx;
+                const float vals[9] = {fmaf(q0.w, s2, 2.f * q0.z * dx * s1), fmaf(q0.w * dx, s1, 2.f * q1.x * s2),
+                                       dx * dx * s1, dx * s2, sum2(S3), sum2(dop), sum2(dr), sum2(dg), sum2(db)};
                 int idx;
                 const float tot = warp_reduce9(vals, idx);
                 if (idx >= 0) {
