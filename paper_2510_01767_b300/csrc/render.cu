@@ -141,6 +141,48 @@ __device__ __forceinline__ void fetch(const float4 *__restrict__ splat, const in
     }
 }
 
+// Packed float32x2 arithmetic (add/sub/mul/fma .f32x2: one instruction for two values, each
+// half rounded exactly like the scalar operation).
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float sum2(f2 v)
+{
+    float a, b;
+    upk(v, a, b);
+    return a + b;
+}
+
 struct WarpStage {
     float4 s0[32];
     float4 s1[32];
@@ -182,17 +224,35 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
             const float cb = st.s2[j].x, pmin = st.s2[j].y;
             const float dj = DEPTH ? st.dep[j] : 0.0f;
             const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
+            // the exponent of every pixel: in pairs (packed) when PX is even -- the same rounding
+            // as pair_eval and as the paired adjoint
+            float pv[PX];
+            if constexpr (PX % 2 == 0) {
+                const f2 v2 = pk(q0.y, q0.y), Cq = pk(q1.x, q1.x), a2 = pk(cl.a2, cl.a2), b1 = pk(cl.b1, cl.b1);
+#pragma unroll
+                for (int i = 0; i < PX / 2; ++i) {
+                    const f2 dy2 = sub2(v2, pk(pyc[2 * i], pyc[2 * i + 1]));
+                    upk(fma2(dy2, fma2(Cq, dy2, b1), a2), pv[2 * i], pv[2 * i + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < PX; ++k) {
+                    const float dy = __fsub_rn(q0.y, pyc[k]);
+                    pv[k] = __fmaf_rn(dy, __fmaf_rn(q1.x, dy, cl.b1), cl.a2);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
                 if (!live[k]) continue;
-                const PairEval r = pair_eval(cl, q0.y, q1.x, q1.y, pmin, pyc[k]);
-                if (!r.use) continue;
-                const float Tn = next_T(T[k], r.alpha);
+                const float p2 = pv[k];
+                if (!(p2 <= 0.0f && p2 >= pmin)) continue;  // sigma < 0 or alpha < 1/255: skipped
+                const float alpha = fminf(ALPHA_MAX, __fmul_rn(q1.y, ex2(p2)));
+                const float Tn = next_T(T[k], alpha);
                 if (Tn < T_MIN) {
                     live[k] = false;
                     continue;
                 }
-                const float w = r.alpha * T[k];
+                const float w = alpha * T[k];
                 C0[k] += q1.z * w;
                 C1[k] += q1.w * w;
                 C2[k] += cb * w;
@@ -439,46 +499,6 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 // Per-pixel decisions stay scalar and identical to the forward's (same dy, p2, ex2, o * G in
 // the same rounding); a pixel of the pair that does not use the splat gets G = 0, hence
 // alpha = 0, which leaves its T, B and every gradient term unchanged.
-
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ float sum2(f2 v)
-{
-    float a, b;
-    upk(v, a, b);
-    return a + b;
-}
 
 // At most 128 registers a thread (occupancy: the kernel is latency- as much as issue-bound).
 template <int TW, int TH, int PX, bool RECOMPUTE>
