@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_visibility(const __grid_constant__ Batc
 constexpr int PB_THREADS = 64;
 constexpr int PB_ROW = 49;  // odd row stride: the per-thread rows fall in distinct banks
 
-constexpr int PL_THREADS = 256, PL_ITEMS = 16, PL_TILE = PL_THREADS * PL_ITEMS;  // 4096 Gaussians per tile
+constexpr int PL_THREADS = 1024, PL_ITEMS = 4, PL_TILE = PL_THREADS * PL_ITEMS;  // 4096 Gaussians per tile
 
 // List (ascending, so neighbours in the list share cache sectors) of the Gaussians some item
 // sees, by a single-pass compaction with decoupled look-back; the last tile writes the count.
