@@ -227,11 +227,37 @@ def batched_vs_plain(reps=5):
     for st in plain.steps:
         fill(st)
     plain_ms = _time(plain.run, reps, torch.cuda.current_stream())
+    del plain
+    torch.cuda.empty_cache()
+    # the per-view path of a training loop: the autograd.Function view by view (each forward
+    # synchronises once to size its bins), parameters as leaf tensors; host-timed, since the
+    # device idles during the synchronisations
+    params = [[getattr(s, k).clone().requires_grad_(True) for k in lobe.PARAM_KEYS] for s in sets]
+    rasters = {(si, b): lobe.Rasterizer(sets[si].n, tile=tile, block=wl.blocks[b] if b >= 0 else None)
+               for si, _, b in wl.items}
+    dls = [torch.randn((3, cams[c]["height"], cams[c]["width"]), generator=gen, device="cuda") for _, c, _ in wl.items]
+
+    def per_view():
+        for (si, c, b), dl in zip(wl.items, dls):
+            lobe.rasterize(*params[si], cams[c], rasters[(si, b)]).backward(dl)
+
+    per_view()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        per_view()
+    torch.cuda.synchronize()
+    autograd_ms = (time.perf_counter() - t0) / reps * 1e3
+    del params, rasters, dls
+    torch.cuda.empty_cache()
     return {"workload": wl.name, "gaussians": sum(s.n for s in sets), "views": len(cams), "pixels": pixels,
             "intersections": n_isect, "tile": list(tile), "px_per_lane": list(best_px), "autotune_ms": {k: round(v, 3) for k, v in times.items()},
             "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
             "batched_mpix_s": round(pixels / batched_ms / 1e3, 1), "plain_mpix_s": round(pixels / plain_ms / 1e3, 1),
-            "ratio": round(plain_ms / batched_ms, 3)}
+            "ratio": round(plain_ms / batched_ms, 3),
+            "autograd_per_view_ms": round(autograd_ms, 3), "ratio_vs_autograd_per_view": round(autograd_ms / batched_ms, 3),
+            "note": "ratio: against the eager one-view-per-call library path (no host synchronisation); "
+                    "ratio_vs_autograd_per_view: against the autograd.Function called view by view (host-timed)"}
 
 
 def fcs_benchmark(reps=5):
