@@ -275,3 +275,58 @@ def test_fused_equals_adjoint_then_adam(sparse):
         assert torch.equal(sf[s][1], su[s][1])
         torch.testing.assert_close(sf[s][0], su[s][0], rtol=1e-6, atol=0)
     record("fused vs unfused adam, means (/1e-5 rel)", worst)
+
+
+@pytest.mark.parametrize("sparse", [True, False])
+def test_fused_adam_with_crop_mask_and_empty_set(sparse):
+    """A cropped set next to an empty one: cropped Gaussians are culled, so sparse Adam leaves
+    them (and everything unseen) bit for bit while standard Adam decays them; the empty set is a
+    no-op; the seen Gaussians move as the adjoint followed by lobe_adam moves them."""
+    rng = np.random.default_rng(3)
+    g_np = scenes.uniform_gaussians(rng, 5_003, 1.0, 2.0, 6.0)
+    crop = (rng.uniform(size=g_np.n) < 0.5).astype(np.uint8)
+    empty = scenes.uniform_gaussians(rng, 0, 1.0, 2.0, 6.0)
+    cams = [scenes.pinhole(96, 64, 80.0), scenes.pinhole(64, 64, 60.0)]
+    items = [(0, 0, -1), (0, 1, -1), (1, 1, -1)]
+
+    def run(fused):
+        sets = [lobe.GaussianSet.from_numpy(g_np), lobe.GaussianSet.from_numpy(empty)]
+        sets[0].crop_mask = torch.as_tensor(crop).cuda()
+        batch = lobe.Batch(sets, cams, items)
+        ctx = lobe.Context(tile=(16, 16))
+        proj, bins, img = lobe.forward(ctx, batch)
+        dL = torch.as_tensor(np.random.default_rng(8).standard_normal(3 * batch.n_pixels), dtype=torch.float32).cuda()
+        g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
+        opts = [lobe.Adam(s, lr=LR, betas=(B1, B2), eps=EPS) for s in sets]
+        m0 = {k: torch.as_tensor(np.random.default_rng(2).standard_normal(shapes(g_np.n)[k]) * 1e-3,
+                                 dtype=torch.float32).cuda() for k in KEYS}
+        opts[0].exp_avg = {k: v.clone() for k, v in m0.items()}
+        opts[0].exp_avg_sq = {k: (v * v * 3).contiguous() for k, v in m0.items()}
+        opts[0].t = 4
+        seen = ((proj.radius[0:g_np.n] > 0) | (proj.radius[g_np.n:2 * g_np.n] > 0))
+        if fused:
+            lobe.project_bwd_adam(ctx, batch, proj, g2d, opts, sparse=sparse)
+        else:
+            grads = lobe.project_bwd(ctx, batch, proj, g2d)
+            opts[0].step(ctx, grads[0], seen.to(torch.uint8) if sparse else None)
+        torch.cuda.synchronize()
+        return {k: getattr(sets[0], k).clone() for k in KEYS}, seen
+
+    pf, seen = run(True)
+    pu, _ = run(False)
+    seen = seen.cpu().numpy()
+    cropped = crop == 0
+    assert not np.any(seen & cropped)  # the crop mask culls
+    assert seen.sum() > 100 and (~seen & ~cropped).sum() >= 0
+    p0 = {k: np.asarray(getattr(g_np, k)) for k in KEYS}
+    for k in KEYS:
+        a, b = pf[k].cpu().numpy(), pu[k].cpu().numpy()
+        if k == "means":
+            np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-7)
+        else:
+            np.testing.assert_array_equal(a, b)
+        moved = np.any((a != p0[k]).reshape(g_np.n, -1), axis=1)
+        if sparse:
+            assert not np.any(moved[~seen]), k  # unseen rows keep their bits
+        else:
+            assert np.all(moved[~seen]), k  # standard Adam moves them by their momentum
