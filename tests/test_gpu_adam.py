@@ -317,7 +317,7 @@ def test_fused_adam_with_crop_mask_and_empty_set(sparse):
     seen = seen.cpu().numpy()
     cropped = crop == 0
     assert not np.any(seen & cropped)  # the crop mask culls
-    assert seen.sum() > 100 and (~seen & ~cropped).sum() >= 0
+    assert seen.sum() > 100 and (~seen).sum() > 100
     p0 = {k: np.asarray(getattr(g_np, k)) for k in KEYS}
     for k in KEYS:
         a, b = pf[k].cpu().numpy(), pu[k].cpu().numpy()
