@@ -110,14 +110,15 @@ typedef struct {
     int32_t n_items;
 } lobe_batch;
 
-/* Context configuration. tile_w x tile_h must be one of 8x8, 16x16, 32x16. */
+/* Context configuration. tile_w x tile_h must be one of 8x8, 16x8, 16x16, 32x16. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t sh_degree;  /* active SH degree, 0..3 */
     float bg[3];        /* background colour */
     int32_t recompute_T; /* 1: render_bwd re-derives the per-pixel state (T_final, n_contrib)
                             with a forward sweep instead of reading the saved one */
-    int32_t px_fwd;      /* pixels per lane in render_fwd: 0 = default; 2, 4, 8 (8x8 tiles: 1, 2) */
+    int32_t px_fwd;      /* pixels per lane in render_fwd: 0 = default; 2, 4, 8 (16x8 tiles: 1, 2, 4;
+                            8x8 tiles: 1, 2) */
     int32_t px_bwd;      /* pixels per lane in render_bwd: same choices */
     int32_t reserved[5];
 } lobe_config;

@@ -8,7 +8,7 @@ the adjoint, and the per-set parameter gradients summed over views in registers.
 the binning scratch is reserved up front and no stage synchronises with the host, the whole
 step is captured once in a CUDA graph and replayed as a single launch.
 
-``autotune`` picks the tile shape (8x8, 16x16, 32x16) and the pixels each lane composites (a
+``autotune`` picks the tile shape (8x8, 16x8, 16x16, 32x16) and the pixels each lane composites (a
 kernel knob: fewer means more warps per tile, more means fewer splat loads and reductions per
 pixel) by timing graph replays on the actual batch; results are cached per (GPU, batch
 signature) in ``~/.cache/lobe/autotune.json``.
@@ -26,8 +26,8 @@ import torch
 
 from . import raster as R
 
-TILES = ((8, 8), (16, 16), (32, 16))
-PX_OPTIONS = {(8, 8): (1, 2), (16, 16): (2, 4, 8), (32, 16): (2, 4, 8)}  # pixels per lane per tile shape
+TILES = ((8, 8), (16, 8), (16, 16), (32, 16))
+PX_OPTIONS = {(8, 8): (1, 2), (16, 8): (1, 2, 4), (16, 16): (2, 4, 8), (32, 16): (2, 4, 8)}  # pixels per lane per tile shape
 
 
 def config_name(tile, px=(0, 0)):

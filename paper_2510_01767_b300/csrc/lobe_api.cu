@@ -55,16 +55,16 @@ static lobe_status cuda_fail(lobe_ctx *ctx, cudaError_t e, const char *where)
 
 static bool valid_tile(int tw, int th)
 {
-    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 16);
+    return (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 16);
 }
 
 static lobe_status check_config(lobe_ctx *ctx, const lobe_config *cfg)
 {
     if (!cfg) return fail(ctx, LOBE_ERR_ARG, "config is NULL");
     if (!valid_tile(cfg->tile_w, cfg->tile_h))
-        return fail(ctx, LOBE_ERR_ARG, "tile %dx%d not one of 8x8, 16x16, 32x16", cfg->tile_w, cfg->tile_h);
+        return fail(ctx, LOBE_ERR_ARG, "tile %dx%d not one of 8x8, 16x8, 16x16, 32x16", cfg->tile_w, cfg->tile_h);
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3) return fail(ctx, LOBE_ERR_ARG, "sh_degree %d not in 0..3", cfg->sh_degree);
-    if (!valid_px(cfg->tile_w, cfg->px_fwd) || !valid_px(cfg->tile_w, cfg->px_bwd))
+    if (!valid_px(cfg->tile_w, cfg->tile_h, cfg->px_fwd) || !valid_px(cfg->tile_w, cfg->tile_h, cfg->px_bwd))
         return fail(ctx, LOBE_ERR_ARG, "pixels per lane %d/%d not supported with %dx%d tiles", cfg->px_fwd, cfg->px_bwd,
                     cfg->tile_w, cfg->tile_h);
     return LOBE_OK;

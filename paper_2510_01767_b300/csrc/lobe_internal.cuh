@@ -65,8 +65,8 @@ struct BatchParams {
     float bg[3];
 };
 
-int default_px(int tw, bool backward);
-bool valid_px(int tw, int px);
+int default_px(int tw, int th, bool backward);
+bool valid_px(int tw, int th, int px);
 
 // Super-tile edge (in tiles) of the two-level binning: 64 px for 8x8 and 16x16 tiles.
 __host__ __device__ inline int super_edge(int tw) { return tw == 8 ? 8 : 4; }

@@ -701,26 +701,34 @@ static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *spla
     return cudaGetLastError();
 }
 
-// Pixels per lane: a config knob (0 = default). 16x16 and 32x16 tiles take 2, 4 or 8; 8x8 tiles
-// take 1 or 2. Fewer pixels per lane = more warps per tile (finer early termination in the
-// forward); more = fewer splat loads and cross-lane reductions per pixel (the adjoint).
-int default_px(int tw, bool backward)
+// Pixels per lane: a config knob (0 = default). 16x16 and 32x16 tiles take 2, 4 or 8; 16x8
+// tiles 1, 2 or 4; 8x8 tiles 1 or 2. Fewer pixels per lane = more warps per tile (finer early
+// termination in the forward); more = fewer splat loads and cross-lane reductions per pixel
+// (the adjoint).
+int default_px(int tw, int th, bool backward)
 {
     (void)backward;  // measured on B300: 4 is best or within 1% for both passes at 16x16 and 32x16
-    return tw == 8 ? 2 : 4;
+    return tw == 8 ? 2 : (th == 8 ? 2 : 4);
 }
 
-bool valid_px(int tw, int px)
+bool valid_px(int tw, int th, int px)
 {
-    return px == 0 || (tw == 8 ? (px == 1 || px == 2) : (px == 2 || px == 4 || px == 8));
+    if (px == 0) return true;
+    if (tw == 8) return px == 1 || px == 2;
+    if (th == 8) return px == 1 || px == 2 || px == 4;
+    return px == 2 || px == 4 || px == 8;
 }
 
 #define LOBE_PX_DISPATCH(FN, ...)                                                                  \
     do {                                                                                          \
-        if (P.tw == 16) {                                                                         \
+        if (P.tw == 16 && P.th == 16) {                                                           \
             if (px == 2) return FN<16, 16, 2>(__VA_ARGS__);                                       \
             if (px == 4) return FN<16, 16, 4>(__VA_ARGS__);                                       \
             if (px == 8) return FN<16, 16, 8>(__VA_ARGS__);                                       \
+        } else if (P.tw == 16 && P.th == 8) {                                                     \
+            if (px == 1) return FN<16, 8, 1>(__VA_ARGS__);                                        \
+            if (px == 2) return FN<16, 8, 2>(__VA_ARGS__);                                        \
+            if (px == 4) return FN<16, 8, 4>(__VA_ARGS__);                                        \
         } else if (P.tw == 32) {                                                                  \
             if (px == 2) return FN<32, 16, 2>(__VA_ARGS__);                                       \
             if (px == 4) return FN<32, 16, 4>(__VA_ARGS__);                                       \
@@ -736,7 +744,7 @@ cudaError_t launch_render_fwd(const BatchParams &P, const float *splat, const in
                               float *T, int *nc, float *depth, cudaStream_t st)
 {
     if (P.n_tiles == 0) return cudaSuccess;
-    const int px = P.px_fwd ? P.px_fwd : default_px(P.tw, false);
+    const int px = P.px_fwd ? P.px_fwd : default_px(P.tw, P.th, false);
     LOBE_PX_DISPATCH(fwd_t, P, splat, ts, ids, rgb, T, nc, depth, st);
 }
 
@@ -746,7 +754,7 @@ cudaError_t launch_render_bwd(const BatchParams &P, bool recompute, const float 
     cudaError_t err = P.n_entries > 0 ? cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)P.n_entries, st)
                                       : cudaSuccess;
     if (err != cudaSuccess || P.n_tiles == 0) return err;
-    const int px = P.px_bwd ? P.px_bwd : default_px(P.tw, true);
+    const int px = P.px_bwd ? P.px_bwd : default_px(P.tw, P.th, true);
     LOBE_PX_DISPATCH(bwd_t, P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
 }
 

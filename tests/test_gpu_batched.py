@@ -85,7 +85,7 @@ def test_graph_follows_parameter_updates(workload):
     torch.testing.assert_close(st.image.rgb, eager.image.rgb, rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("tile", [(8, 8), (32, 16)])
+@pytest.mark.parametrize("tile", [(8, 8), (16, 8), (32, 16)])
 def test_batched_other_tiles_match_16(workload, tile):
     wl = workload
     sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
@@ -108,7 +108,7 @@ def test_autotune_picks_fastest(workload, tmp_path, monkeypatch):
     sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
     cams = [c.as_dict() for c in wl.cameras]
     best, times = autotune(sets, cams, wl.items, wl.blocks, reps=3, dL_init=fill_dL)
-    assert {k.split("/")[0] for k in times} == {"8x8", "16x16", "32x16"} and len(times) == 3
+    assert {k.split("/")[0] for k in times} == {"8x8", "16x8", "16x16", "32x16"} and len(times) == 4
     assert times[batched.config_name(best.tile, best.px)] == min(times.values())
     again, t2 = autotune(sets, cams, wl.items, wl.blocks, reps=3, dL_init=fill_dL)  # from the cache
     assert again.tile == best.tile and again.px == best.px and t2 == times

@@ -84,8 +84,10 @@ def test_project_matches_oracle(small, posed):
 
 # ----------------------------------------------------------------------------- bin + sort
 
-def test_bin_sort_bit_exact_on_oracle_projection(small):
+@pytest.mark.parametrize("tile", [(16, 16), (16, 8)])
+def test_bin_sort_bit_exact_on_oracle_projection(small, tile):
     wl, g = small
+    wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
     cam = wl.cameras[0].as_dict()
     p = oracle.project(g, cam, wl.tile).rounded()
     ids, ts = oracle.bin_sort(p, cam, wl.tile)
@@ -142,7 +144,7 @@ def stage_inputs(wl, g, cam):
     return p, ids, ts
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 16)])
 def test_render_fwd_matches_oracle(small, tile):
     wl, g = small
     wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
@@ -165,9 +167,11 @@ def test_render_fwd_matches_oracle(small, tile):
     np.testing.assert_array_equal(nc[ok], img.n_contrib[ok])
 
 
-@pytest.mark.parametrize("recompute", [False, True])
-def test_render_bwd_matches_oracle(small, recompute):
+@pytest.mark.parametrize("recompute, tile, px", [(False, (16, 16), 0), (True, (16, 16), 0), (False, (16, 8), 1),
+                                                  (False, (16, 8), 4), (True, (16, 8), 4)])
+def test_render_bwd_matches_oracle(small, recompute, tile, px):
     wl, g = small
+    wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
     cam = wl.cameras[0].as_dict()
     p, ids, ts = stage_inputs(wl, g, cam)
     bg = (0.1, 0.2, 0.3)
@@ -175,7 +179,7 @@ def test_render_bwd_matches_oracle(small, recompute):
     dL = np.random.default_rng(3).standard_normal((3, 128, 128)) * (img.flags == 0)[None]
     dL = dL.astype(np.float32).astype(np.float64)
     want = oracle_grad2d_array(oracle.render_bwd(p, ids, ts, cam, dL, wl.tile, bg))
-    ctx = ctx_for(wl, bg=bg, recompute_T=recompute)
+    ctx = ctx_for(wl, bg=bg, recompute_T=recompute, px_fwd=px, px_bwd=px)
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, wl.tile)
     bins = lobe.bin_sort(ctx, batch, gp)
