@@ -98,15 +98,15 @@ def sparse_dL(cam, wins, pixel_ok, seed=3):
     return dL * pixel_ok[None]
 
 
-def run_single(wl, crop=None, n_win=3):
+def run_single(wl, crop=None, n_win=3, tile=None, px=(0, 0)):
     g = wl.sets[0]
     cam = wl.cameras[0].as_dict()
-    tile = wl.tile
+    tile = tuple(tile or wl.tile)
     sets = [lobe.GaussianSet.from_numpy(g)]
     if crop is not None:
         sets[0].crop_mask = torch.as_tensor(crop).cuda()
     batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
-    ctx = lobe.Context(tile=tile)  # default pixels per lane, as in bench.py
+    ctx = lobe.Context(tile=tile, px_fwd=px[0], px_bwd=px[1])
     proj, bins, img = lobe.forward(ctx, batch)
     rgb = img.rgb.view(3, cam["height"], cam["width"]).cpu().numpy()
     g64 = oracle.set_dict(g)
@@ -157,11 +157,16 @@ def run_single(wl, crop=None, n_win=3):
         assert err <= 1e-3, (k, err)
 
 
-def test_fullsize_medium_200k_1600x1066():
-    run_single(scenes.medium_scene())
+# tile shape and pixels per lane: the defaults, and the configuration bench.py's autotuner picks
+# for the workload (32x16 tiles with 4 / 8 pixels per lane for the medium view, 8x8 with 1 / 2
+# for the city block)
+@pytest.mark.parametrize("tile, px", [((16, 16), (0, 0)), ((32, 16), (4, 8))])
+def test_fullsize_medium_200k_1600x1066(tile, px):
+    run_single(scenes.medium_scene(), tile=tile, px=px)
 
 
-def test_fullsize_city_block_with_visibility_crop():
+@pytest.mark.parametrize("tile, px", [((16, 16), (0, 0)), ((8, 8), (1, 2))])
+def test_fullsize_city_block_with_visibility_crop(tile, px):
     wl = scenes.city_block_scene(n=4_000_000)
     # the block's visibility crop (Sec. 3.3) from the GPU, checked against the oracle's
     sets = [lobe.GaussianSet.from_numpy(wl.sets[0])]
@@ -173,7 +178,7 @@ def test_fullsize_city_block_with_visibility_crop():
     ok = (flags & (oracle.F_GUARD | oracle.F_RECT | oracle.F_RADIUS)) == 0
     np.testing.assert_array_equal(crop[ok], want[ok])
     assert 0.05 < want.mean() < 0.95
-    run_single(wl, crop=crop)
+    run_single(wl, crop=crop, tile=tile, px=px)
 
 
 def test_fullsize_multi_block_batched_graph_items():
