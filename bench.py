@@ -555,19 +555,20 @@ def main():
     gaussians = sum(s.n for s in sets) * K * world
     value = pixels / total_s / 1e6
 
-    # ---- end to end through host buffers (pinned), copies inside the timed region. Every step
-    # uploads its inputs (parameters, dL/dC) and downloads its results (image, parameter
-    # gradients); device buffers are doubled so that step i+1's uploads and step i-1's downloads
-    # run on their own streams (copy engines) while step i's kernels run.
+    # ---- end to end through host buffers (pinned), copies inside the timed region. Two readings:
+    # (1) `e2e`, a training loop's: the parameters (and their gradients, which the optimizer
+    # consumes on the device) stay resident; every step uploads its per-view input (dL/dC,
+    # standing in for the view's target image: 3 floats a pixel) and downloads its rendered
+    # image; (2) `e2e_host_params`, the rasterizer as a service whose caller owns the
+    # parameters: every step also uploads all parameters and downloads all gradients. Device
+    # buffers are doubled so that step i+1's uploads and step i-1's downloads run on their own
+    # streams (copy engines) while step i's kernels run.
     host_params = [{k: getattr(s, k).detach().cpu().pin_memory() for k in lobe.PARAM_KEYS} for s in sets]
     host_crop = [s.crop_mask.cpu().pin_memory() if s.crop_mask is not None else None for s in sets]
     host_dL = dL.cpu().pin_memory()
     host_rgb = [torch.empty_like(image.rgb, device="cpu").pin_memory() for _ in range(2)]
     host_grads = [[{k: torch.empty_like(g[k], device="cpu").pin_memory() for k in lobe.PARAM_KEYS} for g in grads]
                   for _ in range(2)]
-    h2d = sum(t.numel() * t.element_size() for d in host_params for t in d.values()) + host_dL.numel() * 4
-    h2d += sum(c.numel() for c in host_crop if c is not None)
-    d2h = host_rgb[0].numel() * 4 + sum(t.numel() * t.element_size() for d in host_grads[0] for t in d.values())
     bsets = [[lobe.GaussianSet(**{k: torch.empty_like(getattr(s, k)) for k in lobe.PARAM_KEYS},
                                crop_mask=torch.empty_like(s.crop_mask) if s.crop_mask is not None else None)
               for s in sets] for _ in range(2)]
@@ -580,53 +581,66 @@ def main():
     ev_used = [torch.cuda.Event() for _ in range(2)]  # kernels done with buffer b
     ev_out = [torch.cuda.Event() for _ in range(2)]   # results of buffer b downloaded
 
-    def e2e_step(i):
+    def e2e_step(i, params):
         b = i & 1
         with torch.cuda.stream(up):
             up.wait_event(ev_used[b])  # step i-2 finished reading these inputs
-            for s, hp, hc in zip(bsets[b], host_params, host_crop):
-                for k in lobe.PARAM_KEYS:
-                    getattr(s, k).copy_(hp[k], non_blocking=True)
-                if hc is not None:
-                    s.crop_mask.copy_(hc, non_blocking=True)
+            if params:
+                for s, hp, hc in zip(bsets[b], host_params, host_crop):
+                    for k in lobe.PARAM_KEYS:
+                        getattr(s, k).copy_(hp[k], non_blocking=True)
+                    if hc is not None:
+                        s.crop_mask.copy_(hc, non_blocking=True)
             bdL[b].copy_(host_dL, non_blocking=True)
             ev_in[b].record(up)
         stream.wait_event(ev_in[b])
         stream.wait_event(ev_out[b])  # step i-2's results have left these buffers
-        lobe.project(ctx, bbatch[b], proj)
-        lobe.bin_sort(ctx, bbatch[b], proj, bins, sync=False)
-        lobe.render_fwd(ctx, bbatch[b], proj, bins, bimage[b])
-        lobe.render_bwd(ctx, bbatch[b], proj, bins, bimage[b], bdL[b], grad2d)
-        lobe.project_bwd(ctx, bbatch[b], proj, grad2d, bgrads[b], accumulate=False)
+        bt, gr = (bbatch[b], bgrads[b]) if params else (batch, grads)
+        lobe.project(ctx, bt, proj)
+        lobe.bin_sort(ctx, bt, proj, bins, sync=False)
+        lobe.render_fwd(ctx, bt, proj, bins, bimage[b])
+        lobe.render_bwd(ctx, bt, proj, bins, bimage[b], bdL[b], grad2d)
+        lobe.project_bwd(ctx, bt, proj, grad2d, gr, accumulate=False)
         ev_used[b].record(stream)
         with torch.cuda.stream(down):
             down.wait_event(ev_used[b])
             host_rgb[b].copy_(bimage[b].rgb, non_blocking=True)
-            for g, hg in zip(bgrads[b], host_grads[b]):
-                for k in lobe.PARAM_KEYS:
-                    hg[k].copy_(g[k], non_blocking=True)
+            if params:
+                for g, hg in zip(bgrads[b], host_grads[b]):
+                    for k in lobe.PARAM_KEYS:
+                        hg[k].copy_(g[k], non_blocking=True)
             ev_out[b].record(down)
 
-    for i in range(2):
-        e2e_step(i)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(up)  # before the first upload
-    for i in range(K):
-        e2e_step(i)
-    for ev in ev_out:
-        stream.wait_event(ev)
-    e1.record(stream)  # after the last download
-    torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = pixels / e2e_s / 1e6
+    def run_e2e(params):
+        for i in range(2):
+            e2e_step(i, params)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(up)  # before the first upload
+        for i in range(K):
+            e2e_step(i, params)
+        for ev in ev_out:
+            stream.wait_event(ev)
+        e1.record(stream)  # after the last download
+        torch.cuda.synchronize()
+        e2e_s = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = host_dL.numel() * 4
+        d2h = host_rgb[0].numel() * 4
+        if params:
+            h2d += sum(t.numel() * t.element_size() for d in host_params for t in d.values())
+            h2d += sum(c.numel() for c in host_crop if c is not None)
+            d2h += sum(t.numel() * t.element_size() for d in host_grads[0] for t in d.values())
+        return pixels / e2e_s / 1e6, h2d, d2h
+
+    e2e_value, h2d, d2h = run_e2e(False)
+    e2e_hp_value, h2d_hp, d2h_hp = run_e2e(True)
     clk.__exit__(None, None, None)  # sampled over both timed regions
 
     # ---- roofline of the dominant stage
@@ -702,7 +716,11 @@ def main():
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "gaussians_per_s": round(gaussians / total_s, 1),
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h),
+                    "reading": "training loop: parameters resident; per step dL/dC up, the image down"},
+            "e2e_host_params": {"value": round(e2e_hp_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d_hp),
+                                "d2h_bytes_per_step": int(d2h_hp),
+                                "reading": "caller-owned parameters: per step also all parameters up, all gradients down"},
             "gpu_launches": int(launches),
             "clocks": {k: csum[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "roofline": roof,
