@@ -1,6 +1,6 @@
 """Shared test helpers: moving oracle data to the GPU path's layouts and comparing results.
 
-Tolerances (spec bar): image max-abs error 1e-4 on pixels whose compositing decisions
+Tolerances (the parity bar): image max-abs error 1e-4 on pixels whose compositing decisions
 are not marginal; gradient relative error 1e-3, measured per element as
 |gpu - oracle| / max(|oracle|, 1e-3 * max|oracle of that tensor|) -- the floor keeps
 near-zero elements of a float32 sum over thousands of pixels from dominating the ratio.
@@ -25,7 +25,7 @@ def record(name, value):
 
 
 def assert_img_close(gpu, orc, name):
-    """Max-abs image error (spec bar 1e-4), recorded under `name`."""
+    """Max-abs image error (parity bar 1e-4), recorded under `name`."""
     d = float(np.abs(np.asarray(gpu, np.float64) - np.asarray(orc, np.float64)).max()) if np.size(orc) else 0.0
     record(name, d)
     assert d <= IMG_ATOL, f"{name}: max-abs error {d:.3e} > {IMG_ATOL}"
