@@ -310,6 +310,13 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
 lobe_status lobe_project_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                              const float *grad2d, const lobe_grads *grads, int32_t accumulate);
 
+/* Self-test of the bounded device-side waits (failure detection without a GPU fault): one
+ * warp waits, on the ctx stream, for a look-back word that nothing publishes; after the wait
+ * limit (a few seconds of polling) it latches the timeout status and returns. The next
+ * lobe_get_status returns LOBE_ERR_TIMEOUT (and clears it); the context stays usable. Returns
+ * LOBE_OK once the kernel is enqueued. */
+lobe_status lobe_selftest_wait(lobe_ctx *ctx);
+
 /* Mutable SoA arrays of one Gaussian set (device, caller-owned), in the shapes of
  * lobe_gaussians: means [n][3], log_scales [n][3], quats [n][4], opacity_logits [n],
  * sh [n][16][3]. Every pointer 16-byte aligned. */

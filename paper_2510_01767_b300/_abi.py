@@ -128,6 +128,7 @@ SIGNATURES = {
                                          ctypes.POINTER(Image), vp]),
     "lobe_fcs_coverage": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Image), vp, ctypes.POINTER(AABB),
                                          ctypes.c_int32, ctypes.c_int32, vp, vp]),
+    "lobe_selftest_wait": (ctypes.c_int, [vp]),
     "lobe_adam": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(AdamState), ctypes.POINTER(ParamArrays), vp,
                                  ctypes.POINTER(AdamParams)]),
     "lobe_project_bwd_adam": (ctypes.c_int, [vp, ctypes.POINTER(Batch), ctypes.POINTER(Projected), vp,

@@ -334,6 +334,13 @@ lobe_status lobe_get_status(lobe_ctx *ctx)
     return LOBE_OK;
 }
 
+lobe_status lobe_selftest_wait(lobe_ctx *ctx)
+{
+    if (!ctx) return LOBE_ERR_ARG;
+    CUDA_TRY(launch_selftest_wait(ctx->status, ctx->stream), "wait self-test");
+    return LOBE_OK;
+}
+
 // Parameter blocks are ~13 KB: keep them off the host stack of the caller's thread.
 struct ParamHolder {
     BatchParams *p;

@@ -295,6 +295,9 @@ cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
 cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, uint32_t *list,
                                uint32_t *count, unsigned long long *lb_slots, int *ctl, cudaStream_t,
                                const AdamBatch *adam = nullptr);
+// One warp waits on a look-back word nothing publishes until its spin limit latches
+// STATUS_TIMEOUT in ctl[0] (the bounded-wait self-test).
+cudaError_t launch_selftest_wait(int *ctl, cudaStream_t st);
 // Standalone Adam over one set: mode 0 every row, 1 rows with rows[r] != 0 (sparse), 2 rows
 // with rows[r] == 0 and a zero gradient (grad unused: the Gaussians no item saw, after the
 // fused adjoint has updated the others).
