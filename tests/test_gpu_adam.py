@@ -11,6 +11,7 @@ sparse variant of the coarse training) against the FP64 oracle.
 * Fused against unfused on the GPU (the adjoint's gradients through lobe_adam), sparse and
   standard, on a multi-set, multi-view batch.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -330,3 +331,31 @@ def test_fused_adam_with_crop_mask_and_empty_set(sparse):
             assert not np.any(moved[~seen]), k  # unseen rows keep their bits
         else:
             assert np.all(moved[~seen]), k  # standard Adam moves them by their momentum
+
+
+def test_fused_adam_rejects_foreign_parameters():
+    """The fused step updates the batch's own arrays: an Adam state over other tensors is an
+    argument error (nothing launched), as is a missing optimizer."""
+    rng = np.random.default_rng(4)
+    g_np = scenes.uniform_gaussians(rng, 1_000, 1.0, 2.0, 6.0)
+    gs = lobe.GaussianSet.from_numpy(g_np)
+    other = lobe.GaussianSet.from_numpy(g_np)
+    batch = lobe.Batch([gs], [scenes.pinhole(64, 64, 60.0)], [(0, 0, -1)])
+    ctx = lobe.Context(tile=(16, 16))
+    proj, bins, img = lobe.forward(ctx, batch)
+    g2d = lobe.render_bwd(ctx, batch, proj, bins, img, torch.ones(3 * 64 * 64, device="cuda"))
+    with pytest.raises(ValueError):
+        lobe.project_bwd_adam(ctx, batch, proj, g2d, [lobe.Adam(other)])
+    with pytest.raises(ValueError):
+        lobe.project_bwd_adam(ctx, batch, proj, g2d, [])
+    # the C ABI checks the same (the binding's check bypassed)
+    opt = lobe.Adam(other)
+    states = (lobe.raster.A.AdamState * 1)(opt._state())
+    prms = (lobe.raster.A.AdamParams * 1)(opt._params(1))
+    before_means, before_sh = gs.means.clone(), gs.sh.clone()
+    code = ctx.lib.lobe_project_bwd_adam(ctx.handle, ctypes.byref(batch.c), ctypes.byref(proj.c()),
+                                         ctypes.c_void_p(g2d.data_ptr()), None, states, prms, 0)
+    assert code == lobe.raster.A.ERR_ARG
+    torch.cuda.synchronize()
+    assert torch.equal(gs.means, before_means) and torch.equal(gs.sh, before_sh)
+    ctx.status()
