@@ -82,6 +82,35 @@ def test_project_matches_oracle(small, posed):
                                                       (p.rect[ok, 3] - p.rect[ok, 1]), 0))
 
 
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_lower_sh_degrees_match_oracle(small, deg):
+    """Active SH degree below 3: the colour uses the first (deg + 1)^2 bands only, and the
+    adjoint writes zero gradients for the others."""
+    wl, g = small
+    cam = wl.cameras[0].as_dict()
+    ctx = ctx_for(wl, sh_degree=deg)
+    batch = make_batch(wl)
+    proj = lobe.project(ctx, batch)
+    p = oracle.project(g, cam, wl.tile, sh_degree=deg, margins=oracle.MARGINS_E2E)
+    s = proj.splat.cpu().numpy().astype(np.float64)
+    ok = ((p.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) == 0) & (p.radius > 0)
+    assert ok.sum() > 500
+    np.testing.assert_allclose(np.abs(s[ok, 6:9]), p.color[ok], atol=2e-5)
+    f = oracle.forward(g, cam, wl.tile, sh_degree=deg, margins=oracle.MARGINS_STAGE)
+    dL = np.random.default_rng(6).standard_normal((3, 128, 128)) * (f.pixel_flags == 0)[None]
+    g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
+    g2d_r = oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
+                            (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity)))
+    want = oracle.project_bwd(g, cam, g2d_r, wl.tile, sh_degree=deg)
+    grads = lobe.project_bwd(ctx, batch, proj, dev(oracle_grad2d_array(g2d_r)))
+    okg = (f.proj.flags == 0) & (f.proj.radius > 0)
+    nb = (deg + 1) ** 2
+    gsh = grads[0]["sh"].cpu().numpy()
+    assert_grad_close(gsh[okg, :nb], want.sh[okg, :nb], f"sh degree {deg}")
+    assert np.all(gsh[:, nb:] == 0)
+    assert_grad_close(grads[0]["means"].cpu().numpy()[okg], want.means[okg], f"means sh degree {deg}")
+
+
 # ----------------------------------------------------------------------------- bin + sort
 
 @pytest.mark.parametrize("tile", [(16, 16), (16, 8)])
