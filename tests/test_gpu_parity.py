@@ -278,6 +278,46 @@ def test_end_to_end_small(small, recompute):
         assert_grad_close(gr[k][okg], getattr(pg, k)[okg], k)
 
 
+def test_project_bwd_sums_views_like_oracle(small):
+    """One set seen by two cameras: the GPU adjoint sums its per-view contributions in registers
+    and counts the SD statistic per view; the oracle runs each view's adjoint and adds them."""
+    wl, g = small
+    cam0 = wl.cameras[0].as_dict()
+    cam1 = dict(cam0, viewmat=scenes.look_at((0.7, -0.5, -0.6), (0.0, 0.0, 4.0), up=(0, -1, 0)))
+    cams = [cam0, cam1]
+    box = scenes.AABB((-0.6, -0.4, -math.inf), (0.5, 0.7, math.inf))
+    wl2 = scenes.Workload(wl.name, wl.sets, [scenes.Camera(**c) for c in cams], [box], [(0, 0, 0), (0, 1, 0)],
+                          wl.tile)
+    want = None
+    g2ds, flags = [], np.zeros(g["means"].shape[0], np.int32)
+    for v, cam in enumerate(cams):
+        f = oracle.forward(g, cam, wl.tile, margins=oracle.MARGINS_STAGE)
+        dL = np.random.default_rng(10 + v).standard_normal((3, 128, 128)) * (f.pixel_flags == 0)[None]
+        g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
+        g2d_r = oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
+                                (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity)))
+        pb = oracle.project_bwd(g, cam, g2d_r, wl.tile, aabb=box)
+        want = pb if want is None else oracle.ParamGrads(*(a + b for a, b in zip(
+            (want.means, want.log_scales, want.quats, want.opacity_logits, want.sh, want.sd_acc, want.sd_cnt),
+            (pb.means, pb.log_scales, pb.quats, pb.opacity_logits, pb.sh, pb.sd_acc, pb.sd_cnt))))
+        g2ds.append(oracle_grad2d_array(g2d_r))
+        flags |= f.proj.flags
+    ctx = ctx_for(wl2)
+    batch = make_batch(wl2)
+    proj = lobe.project(ctx, batch)
+    grads = lobe.zero_grads(batch)
+    lobe.project_bwd(ctx, batch, proj, dev(np.concatenate(g2ds)), grads, accumulate=True)
+    gr = {k: v.cpu().numpy() for k, v in grads[0].items()}
+    rad = proj.radius.cpu().numpy().reshape(2, -1)
+    ok = (flags == 0) & (rad > 0).any(axis=0)
+    assert ok.sum() > 500 and ((rad > 0).all(axis=0) & ok).sum() > 100  # many seen by both views
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert_grad_close(gr[k][ok], getattr(want, k)[ok], k + " (two views)")
+    np.testing.assert_array_equal(gr["sd_cnt"][ok], want.sd_cnt[ok])
+    assert want.sd_cnt[ok].max() == 2
+    assert_grad_close(gr["sd_acc"][ok], want.sd_acc[ok], "sd_acc (two views)")
+
+
 def test_batched_equals_plain():
     rng = np.random.default_rng(21)
     sets = [scenes.uniform_gaussians(rng, 800, 1.0, 2.0, 6.0), scenes.uniform_gaussians(rng, 500, 1.0, 2.0, 6.0)]
