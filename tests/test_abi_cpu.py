@@ -106,3 +106,18 @@ def test_product_path_fails_loudly_without_cuda():
     import paper_2510_01767_b300 as lobe
     with pytest.raises(RuntimeError, match="CUDA"):
         lobe.Context()
+
+
+def test_batch_limits(L):
+    """LOBE_MAX_SETS sets and LOBE_MAX_ITEMS items pass; one more of either is an argument error."""
+    from paper_2510_01767_b300 import _abi as A
+    cfg = A.Config(16, 16, 3)
+    out = (ctypes.c_int64 * 3)()
+    n_sets, n_items = 16, 64
+    b, keep = _batch(A, [(64, 48)] * 4, [10] * n_sets, [(i % n_sets, i % 4) for i in range(n_items)])
+    assert L.lobe_batch_sizes(ctypes.byref(cfg), ctypes.byref(b), out) == 0
+    assert out[0] == n_items * 10
+    b, keep = _batch(A, [(64, 48)] * 4, [10] * n_sets, [(i % n_sets, i % 4) for i in range(n_items + 1)])
+    assert L.lobe_batch_sizes(ctypes.byref(cfg), ctypes.byref(b), out) == A.ERR_ARG
+    b, keep = _batch(A, [(64, 48)] * 4, [10] * (n_sets + 1), [(i % (n_sets + 1), 0) for i in range(n_sets + 1)])
+    assert L.lobe_batch_sizes(ctypes.byref(cfg), ctypes.byref(b), out) == A.ERR_ARG

@@ -336,6 +336,39 @@ def test_batched_equals_plain():
         torch.testing.assert_close(rgbs[i], b1.image_views(im1.rgb)[0], rtol=0, atol=0)
 
 
+def test_largest_batch_matches_single_item_runs():
+    """The largest batch (16 sets, 64 items of uneven size): every item's image equals that
+    item rendered alone, bit for bit, and the summed adjoint of each set equals the sum of its
+    items' single-item adjoints within float32 summation order."""
+    rng = np.random.default_rng(33)
+    sets = [scenes.uniform_gaussians(rng, int(rng.integers(50, 400)), 1.0, 2.0, 6.0) for _ in range(16)]
+    cams = [scenes.pinhole(72, 40, 60.0), scenes.pinhole(33, 65, 50.0), scenes.pinhole(48, 48, 45.0, cx=20.0),
+            scenes.pinhole(64, 32, 70.0, viewmat=scenes.look_at((0.2, 0.1, -0.3), (0, 0, 4.0), up=(0, -1, 0)))]
+    items = [(i % 16, (i // 16 + i) % 4, -1) for i in range(64)]
+    wl = scenes.Workload("max", sets, cams, [], items, (16, 16))
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    proj, bins, img = lobe.forward(ctx, batch)
+    dL = torch.as_tensor(np.random.default_rng(2).standard_normal(3 * batch.n_pixels), dtype=torch.float32).cuda()
+    g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
+    grads = lobe.project_bwd(ctx, batch, proj, g2d)
+    rgbs = batch.image_views(img.rgb)
+    dls = batch.image_views(dL)
+    summed = [{k: torch.zeros_like(v) for k, v in g.items()} for g in grads]
+    for i, (si, ci, _) in enumerate(items):
+        one = scenes.Workload("o", [sets[si]], [cams[ci]], [], [(0, 0, -1)], (16, 16))
+        b1 = make_batch(one)
+        p1, bn1, im1 = lobe.forward(ctx, b1)
+        torch.testing.assert_close(rgbs[i], b1.image_views(im1.rgb)[0], rtol=0, atol=0)
+        g1 = lobe.project_bwd(ctx, b1, p1, lobe.render_bwd(ctx, b1, p1, bn1, im1, dls[i].reshape(-1).contiguous()))
+        for k in summed[si]:
+            summed[si][k] += g1[0][k]
+    for g, s in zip(grads, summed):
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            a, b = g[k].double(), s[k].double()
+            assert float((a - b).abs().max()) <= 1e-4 * max(float(b.abs().max()), 1e-12), k
+
+
 def test_visibility_crop_matches_oracle():
     wl = scenes.small_scene()
     # two oblique views that each see only part of the scene
