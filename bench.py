@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--px", default="0,0", help="with --tile WxH: pixels per lane of the composite and its adjoint")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multi-block measurement")
-    ap.add_argument("--no-fcs", action="store_true", help="skip the fast-camera-selection, densification and Adam measurements")
+    ap.add_argument("--no-fcs", action="store_true", help="skip the fast-camera-selection, densification, Adam and training-step measurements")
     ap.add_argument("--recompute", action="store_true")
     return ap.parse_args()
 
@@ -439,6 +439,61 @@ def adam_benchmark(ctx, batch, proj, grad2d, hbm_peak, reps=10):
                         "frac": round(gbs_big / hbm_peak, 4)}}
 
 
+def training_benchmark(steps=60, warm=20):
+    """A training step of the per-block fine training (config-5 style): a 2M-Gaussian city block
+    fitted to 16 target views at 1280x720 with L1 + 0.2 (1 - SSIM), one view a step, 3DGS
+    learning rates. Per-step time (a) through the autograd.Function with torch's fused Adam and
+    (b) through Rasterizer.train_step, whose projection adjoint applies the Adam update itself.
+    Host-timed over `steps` steps after `warm` (each step synchronises once to size its bins).
+    Returns a dict."""
+    import torch
+    import paper_2510_01767_b300 as lobe
+    from paper_2510_01767_b300.losses import l1_ssim_loss
+
+    gt, init, cams, block = scenes.training_scene(n=2_000_000, n_views=16)
+    keys = lobe.PARAM_KEYS
+    with torch.no_grad():
+        r = lobe.Rasterizer(gt.n)
+        gtp = [torch.as_tensor(gt.arrays()[k]).cuda().contiguous() for k in keys]
+        targets = [lobe.rasterize(*gtp, c.as_dict(), r).clone() for c in cams]
+        del gtp, r
+    extent = float(np.linalg.norm(gt.means.max(0) - gt.means.min(0)))
+    lrs = [1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3]
+    order = np.random.default_rng(0).permutation(np.arange(steps + warm) % len(cams))
+    out = {"workload": "city_block_2M_16views_1280x720", "gaussians": init.n, "steps": steps}
+    for variant in ("torch_adam", "fused_adam"):
+        raster = lobe.Rasterizer(init.n, tile=(16, 16), block=block)
+        ps = [torch.as_tensor(init.arrays()[k]).cuda().contiguous() for k in keys]
+        if variant == "torch_adam":
+            ps = [p.requires_grad_(True) for p in ps]
+            opt = torch.optim.Adam([{"params": [p], "lr": lr} for p, lr in zip(ps, lrs)], eps=1e-15, fused=True)
+        else:
+            gs = lobe.GaussianSet(*ps)
+            opt = lobe.Adam(gs, lr=dict(zip(("means", "log_scales", "quats", "opacity_logits", "sh_dc"), lrs),
+                                        sh_rest=lrs[4]), eps=1e-15)
+        losses = []
+        for it in range(steps + warm):
+            if it == warm:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            k = int(order[it])
+            if variant == "torch_adam":
+                loss = l1_ssim_loss(lobe.rasterize(*ps, cams[k].as_dict(), raster), targets[k])
+                opt.zero_grad(set_to_none=True)
+                loss.backward()
+                opt.step()
+            else:
+                loss = raster.train_step(opt, cams[k].as_dict(), lambda v: l1_ssim_loss(v[0], targets[k]))
+            if it in (0, steps + warm - 1):
+                losses.append(round(float(loss), 5))
+        torch.cuda.synchronize()
+        out[variant + "_ms_per_step"] = round((time.perf_counter() - t0) / steps * 1e3, 3)
+        out[variant + "_loss_first_last"] = losses
+        del raster, ps, opt
+        torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -691,12 +746,14 @@ def main():
         del proj, bins, image, grad2d, grads, flush
         torch.cuda.empty_cache()
         bvp = batched_vs_plain()
-    fcs = dens = None
+    fcs = dens = train = None
     if world == 1 and not args.no_fcs:
         torch.cuda.empty_cache()
         fcs = fcs_benchmark()
         torch.cuda.empty_cache()
         dens = densify_benchmark()
+        torch.cuda.empty_cache()
+        train = training_benchmark()
 
     if rank == 0:
         line = {
@@ -730,6 +787,7 @@ def main():
             "fast_camera_selection": fcs,
             "selective_densification": dens,
             "adam": adam,
+            "training_step": train,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
