@@ -605,14 +605,14 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 3
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const bool ok0 = pos < nc[2 * i], ok1 = pos < nc[2 * i + 1];
-                if (!(ok0 || ok1)) continue;
+                if (NP == 1 && !(ok0 || ok1)) continue;  // several pairs: branch-free, so the pairs interleave
                 const f2 dy2 = sub2(v2, pyc2[i]);
                 const f2 p2 = fma2(dy2, fma2(C2, dy2, b1), a2);
                 float pa, pb;
                 upk(p2, pa, pb);
                 const bool u0 = ok0 && pa <= 0.0f && pa >= pmin, u1 = ok1 && pb <= 0.0f && pb >= pmin;
-                if (!(u0 || u1)) continue;
-                any = true;
+                if (NP == 1 && !(u0 || u1)) continue;
+                any |= u0 || u1;  // a pair neither pixel uses has alpha = 0 and leaves everything unchanged
                 const float Ga = u0 ? ex2(pa) : 0.0f, Gb = u1 ? ex2(pb) : 0.0f;
                 float ra, rb;
                 upk(mul2(pk(q1.y, q1.y), pk(Ga, Gb)), ra, rb);  // o * G, as in the forward
@@ -632,7 +632,14 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 3
                 B0[i] = fma2(al, d0, B0[i]);
                 B1[i] = fma2(al, d1, B1[i]);
                 B2[i] = fma2(al, d2, B2[i]);
-                T2[i] = Ti;
+                if (NP == 1) {
+                    T2[i] = Ti;
+                } else {  // an unused pixel keeps its T exactly (the reciprocal of 1 - 0 is approximate)
+                    float t0, t1, n0, n1;
+                    upk(T2[i], t0, t1);
+                    upk(Ti, n0, n1);
+                    T2[i] = pk(u0 ? n0 : t0, u1 ? n1 : t1);
+                }
                 // past the clamp alpha no longer depends on o or the exponent: dL/do = da G and
                 // dL/dp2 = da o G ln2 (alpha = o G below the clamp)
                 const f2 t = mul2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb));

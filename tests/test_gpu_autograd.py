@@ -67,8 +67,11 @@ def test_store_and_recompute_backward_agree():
         img = lobe.rasterize(*ps, cam, raster)
         (img * dL).sum().backward()
         grads.append([p.grad.cpu().numpy() for p in ps])
+    # the two runs differ only by the order of the float32 atomic additions of the per-splat 2D
+    # gradients (a few ulps of sums over up to thousands of pixels); relative to the 1e-3 floor
+    # of the smallest elements that reaches ~1e-4, so allow 3e-4 (a third of the parity bar)
     for a, b, k in zip(grads[0], grads[1], KEYS):
-        assert grad_rel_err(a, b) <= 1e-4, k  # float32 atomic summation order differs
+        assert grad_rel_err(a, b) <= 3e-4, k
 
 
 def test_multi_view_gradient_is_sum_of_single_views():
