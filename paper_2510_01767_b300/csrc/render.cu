@@ -243,22 +243,41 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
             }
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
-                if (!live[k]) continue;
-                const float p2 = pv[k];
-                if (!(p2 <= 0.0f && p2 >= pmin)) continue;  // sigma < 0 or alpha < 1/255: skipped
-                const float alpha = fminf(ALPHA_MAX, __fmul_rn(q1.y, ex2(p2)));
-                const float Tn = next_T(T[k], alpha);
-                if (Tn < T_MIN) {
-                    live[k] = false;
-                    continue;
+                if constexpr (PX == 1) {
+                    if (!live[k]) continue;
+                    const float p2 = pv[k];
+                    if (!(p2 <= 0.0f && p2 >= pmin)) continue;  // sigma < 0 or alpha < 1/255: skipped
+                    const float alpha = fminf(ALPHA_MAX, __fmul_rn(q1.y, ex2(p2)));
+                    const float Tn = next_T(T[k], alpha);
+                    if (Tn < T_MIN) {
+                        live[k] = false;
+                        continue;
+                    }
+                    const float w = alpha * T[k];
+                    C0[k] += q1.z * w;
+                    C1[k] += q1.w * w;
+                    C2[k] += cb * w;
+                    if (DEPTH) D[k] += dj * w;
+                    T[k] = Tn;
+                    last[k] = base - start + j + 1;
+                } else {
+                    // several pixels a lane: branch-free, so the pixels' chains interleave; a
+                    // pixel that skips or stops gets weight 0 and keeps T and last exactly
+                    const float p2 = pv[k];
+                    const bool use = live[k] && p2 <= 0.0f && p2 >= pmin;
+                    const float alpha = use ? fminf(ALPHA_MAX, __fmul_rn(q1.y, ex2(p2))) : 0.0f;
+                    const float Tn = next_T(T[k], alpha);
+                    const bool stop = use && Tn < T_MIN;
+                    const bool upd = use && !stop;
+                    live[k] = live[k] && !stop;
+                    const float w = upd ? alpha * T[k] : 0.0f;
+                    C0[k] += q1.z * w;
+                    C1[k] += q1.w * w;
+                    C2[k] += cb * w;
+                    if (DEPTH) D[k] += dj * w;
+                    T[k] = upd ? Tn : T[k];
+                    last[k] = upd ? base - start + j + 1 : last[k];
                 }
-                const float w = alpha * T[k];
-                C0[k] += q1.z * w;
-                C1[k] += q1.w * w;
-                C2[k] += cb * w;
-                if (DEPTH) D[k] += dj * w;
-                T[k] = Tn;
-                last[k] = base - start + j + 1;
             }
         }
         __syncwarp();

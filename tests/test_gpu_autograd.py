@@ -89,8 +89,8 @@ def test_multi_view_gradient_is_sum_of_single_views():
         (lobe.rasterize(*qs, c, lobe.Rasterizer(500, tile=wl.tile)) * dL[i]).sum().backward()
         for a, q in zip(acc, qs):
             a += q.grad
-    for a, b, k in zip(both, acc, KEYS):
-        assert grad_rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 1e-4, k
+    for a, b, k in zip(both, acc, KEYS):  # float32 atomic order, as in the store/recompute test
+        assert grad_rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 3e-4, k
 
 
 def test_sd_statistics_only_inside_block():
