@@ -358,7 +358,8 @@ typedef struct {
 /* One Adam update of a set of n Gaussians from the gradients `grad` (device, read only).
  * rows (device uint8 [n], nullable): when given, only Gaussians with rows[g] != 0 change,
  * parameters and moments alike (the sparse Adam of coarse training, appendix "3DGS
- * Training"); NULL updates every Gaussian (standard Adam). Asynchronous on the ctx stream. */
+ * Training"); NULL updates every Gaussian (standard Adam). Asynchronous on the ctx stream.
+ * n is at most 357,564,416 (LOBE_ERR_ARG beyond). */
 lobe_status lobe_adam(lobe_ctx *ctx, int64_t n, const lobe_adam_state *state, const lobe_param_arrays *grad,
                       const uint8_t *rows, const lobe_adam_params *prm);
 

@@ -589,6 +589,7 @@ lobe_status lobe_adam(lobe_ctx *ctx, int64_t n, const lobe_adam_state *state, co
     lobe_status st = adam_constants(ctx, prm, k);
     if (st != LOBE_OK) return st;
     if (n == 0) return LOBE_OK;
+    if (12 * n > (1ll << 32) - (1ll << 22)) return fail(ctx, LOBE_ERR_ARG, "adam: more than 357M Gaussians in one set");
     if (!state || !grad) return fail(ctx, LOBE_ERR_ARG, "state or gradients missing");
     if (!adam_arrays_ok(state->param) || !adam_arrays_ok(state->exp_avg) || !adam_arrays_ok(state->exp_avg_sq) ||
         !adam_arrays_ok(*grad))
@@ -623,6 +624,8 @@ lobe_status lobe_project_bwd_adam(lobe_ctx *ctx, const lobe_batch *batch, const 
     for (int s = 0; s < P.n_sets; ++s) {
         const lobe_adam_state &z = states[s];
         const lobe_gaussians &G = batch->sets[s];
+        if (12 * P.set[s].n > (1ll << 32) - (1ll << 22))
+            return fail(ctx, LOBE_ERR_ARG, "set %d: adam takes at most 357M Gaussians a set", s);
         if (P.set[s].n > 0) {
             if (!adam_arrays_ok(z.param) || !adam_arrays_ok(z.exp_avg) || !adam_arrays_ok(z.exp_avg_sq))
                 return fail(ctx, LOBE_ERR_ARG, "set %d: adam arrays missing or not 16-byte aligned", s);
