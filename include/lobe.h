@@ -120,7 +120,10 @@ typedef struct {
     int32_t px_fwd;      /* pixels per lane in render_fwd: 0 = default; 2, 4, 8 (16x8 tiles: 1, 2, 4;
                             8x8 tiles: 1, 2) */
     int32_t px_bwd;      /* pixels per lane in render_bwd: same choices */
-    int32_t reserved[5];
+    int32_t bin_general; /* 1: lobe_bin_sort always takes the general multi-kernel path; 0: batches of
+                            at most 4096 entries and 4096 tiles (tiles x entries <= 2^20) are binned
+                            by one CTA in one launch (the same result bit for bit) */
+    int32_t reserved[4];
 } lobe_config;
 
 /* Sizes implied by a batch under a config: out[0] = projected entries (sum over items of

@@ -377,6 +377,23 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
         return fail(ctx, LOBE_ERR_ARG, "projected buffers missing");
     if (!bins || !bins->gauss_ids || !bins->tile_start || !bins->n_isect || bins->capacity < 0)
         return fail(ctx, LOBE_ERR_ARG, "bins missing");
+    if (!ctx->cfg.bin_general && bin_small_fits(P)) {  // one CTA, no scratch
+        long long *n_isect = reinterpret_cast<long long *>(bins->n_isect);
+        CUDA_TRY(launch_bin_small(P, proj->splat, proj->radius, proj->tiles_touched, bins->gauss_ids,
+                                  bins->tile_start, n_isect, bins->capacity, ctx->status, ctx->stream),
+                 "bin small");
+        if (sync) {
+            long long total = 0;
+            CUDA_TRY(cudaMemcpyAsync(&total, n_isect, sizeof total, cudaMemcpyDeviceToHost, ctx->stream), "n_isect read");
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream), "n_isect sync");
+            *n_isect_host = total;
+            if (total > bins->capacity) {  // the caller is told synchronously instead
+                CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status clear");
+                return fail(ctx, LOBE_ERR_CAPACITY, "%lld pairs exceed capacity %lld", total, (long long)bins->capacity);
+            }
+        }
+        return LOBE_OK;
+    }
     if (P.n_super > max_super_tiles())
         return fail(ctx, LOBE_ERR_ARG, "%d super-tiles (64x64-pixel blocks) exceed %lld", P.n_super, max_super_tiles());
     if (P.n_tiles > max_scan_length(0))

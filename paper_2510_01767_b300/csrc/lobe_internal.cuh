@@ -295,6 +295,12 @@ cudaError_t launch_visibility(const BatchParams &, cudaStream_t);
 cudaError_t launch_project_bwd(const BatchParams &, const float *, const int *, const float *, int, uint32_t *list,
                                uint32_t *count, unsigned long long *lb_slots, int *ctl, cudaStream_t,
                                const AdamBatch *adam = nullptr);
+// Binning of a small batch (<= 4096 entries and tiles, tiles x entries <= 2^20) in one CTA,
+// bit-identical to the general path: tile_start, gauss_ids, n_isect; capacity overflow latched.
+bool bin_small_fits(const BatchParams &P);
+cudaError_t launch_bin_small(const BatchParams &P, const float *splat, const int *radius, const int *tiles,
+                             int *gauss_ids, int *tile_start, long long *n_isect, long long capacity, int *status,
+                             cudaStream_t st);
 // One warp waits on a look-back word nothing publishes until its spin limit latches
 // STATUS_TIMEOUT in ctl[0] (the bounded-wait self-test).
 cudaError_t launch_selftest_wait(int *ctl, cudaStream_t st);

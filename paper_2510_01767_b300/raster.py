@@ -139,7 +139,7 @@ class Context:
     """A lobe_ctx bound to a CUDA stream (the current torch stream by default)."""
 
     def __init__(self, tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0), recompute_T=False, stream=None, px_fwd=0,
-                 px_bwd=0):
+                 px_bwd=0, bin_general=False):
         if not torch.cuda.is_available():
             raise RuntimeError("the lobe rasterizer needs a CUDA device (no CPU fallback)")
         self.lib = A.lib()
@@ -148,6 +148,7 @@ class Context:
         self.bg = tuple(float(b) for b in bg)
         self.recompute_T = bool(recompute_T)
         self.px = (int(px_fwd), int(px_bwd))
+        self.bin_general = bool(bin_general)  # never the one-CTA binning of small batches
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = ctypes.c_void_p()
         A.check(self.lib.lobe_ctx_create(ctypes.byref(self.handle), ctypes.c_void_p(self.stream.cuda_stream),
@@ -161,6 +162,7 @@ class Context:
         c.bg[:] = list(self.bg)
         c.recompute_T = int(self.recompute_T)
         c.px_fwd, c.px_bwd = self.px
+        c.bin_general = int(self.bin_general)
         return c
 
     def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None, px=None):

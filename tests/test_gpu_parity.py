@@ -14,8 +14,8 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import (IMG_ATOL, assert_grad_close, assert_img_close, oracle_grad2d_array, rect_tiles,
-                           splat_array)
+from tests.helpers import (IMG_ATOL, assert_grad_close, assert_img_close, oracle_grad2d_array, rect_of,
+                           rect_tiles, splat_array)
 
 pytestmark = pytest.mark.gpu
 
@@ -113,14 +113,15 @@ def test_lower_sh_degrees_match_oracle(small, deg):
 
 # ----------------------------------------------------------------------------- bin + sort
 
+@pytest.mark.parametrize("general", [False, True])  # the one-CTA path for small batches, and the general one
 @pytest.mark.parametrize("tile", [(16, 16), (16, 8)])
-def test_bin_sort_bit_exact_on_oracle_projection(small, tile):
+def test_bin_sort_bit_exact_on_oracle_projection(small, tile, general):
     wl, g = small
     wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
     cam = wl.cameras[0].as_dict()
     p = oracle.project(g, cam, wl.tile).rounded()
     ids, ts = oracle.bin_sort(p, cam, wl.tile)
-    ctx = ctx_for(wl)
+    ctx = ctx_for(wl, bin_general=general)
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, wl.tile)
     bins = lobe.bin_sort(ctx, batch, gp)
@@ -171,6 +172,50 @@ def stage_inputs(wl, g, cam):
     p = oracle.project(g, cam, wl.tile).rounded()
     ids, ts = oracle.bin_sort(p, cam, wl.tile)
     return p, ids, ts
+
+
+def test_small_batch_binning_equals_general_and_oracle():
+    """Two sets, four items of ragged sizes, 16x8 tiles (a small batch): the one-CTA binning and
+    the general multi-kernel binning give identical pairs, tile starts and counts, and every
+    item's lists equal the oracle's for that item."""
+    rng = np.random.default_rng(17)
+    sets = [scenes.uniform_gaussians(rng, 900, 1.0, 2.0, 6.0), scenes.uniform_gaussians(rng, 700, 1.0, 2.0, 6.0)]
+    cams = [scenes.pinhole(150, 97, 120.0), scenes.pinhole(64, 64, 60.0, cx=20.0),
+            scenes.pinhole(101, 130, 100.0, viewmat=scenes.look_at((0.3, 0.2, -0.2), (0, 0, 4.0), up=(0, -1, 0)))]
+    items = [(0, 0, -1), (1, 1, -1), (0, 2, -1), (1, 0, -1)]
+    tile = (16, 8)
+    wl = scenes.Workload("sb", sets, cams, [], items, tile)
+    batch = make_batch(wl)
+    assert batch.n_entries <= 4096 and batch.tiles(tile)[0] <= 4096
+    got = []
+    for general in (False, True):
+        ctx = ctx_for(wl, bin_general=general)
+        proj = lobe.project(ctx, batch)
+        bins = lobe.bin_sort(ctx, batch, proj)
+        got.append((bins.count, bins.ids().cpu().numpy(), bins.tile_start.cpu().numpy(), proj))
+    assert got[0][0] == got[1][0]
+    np.testing.assert_array_equal(got[0][1], got[1][1])
+    np.testing.assert_array_equal(got[0][2], got[1][2])
+    # per item against the oracle, on the GPU's own projection (exact integer rectangles)
+    proj = got[0][3]
+    sp, rad = proj.splat.cpu().numpy(), proj.radius.cpu().numpy()
+    _, toffs = batch.tiles(tile)
+    ids, ts = got[0][1], got[0][2]
+    for i, (si, ci, _) in enumerate(items):
+        e0 = batch.entry_off[i]
+        n = sets[si].n
+        cam = cams[ci].as_dict()
+        pg = oracle.Projection(sp[e0:e0 + n, 0:2].astype(np.float64), sp[e0:e0 + n, 2:5].astype(np.float64),
+                               sp[e0:e0 + n, 6:9].astype(np.float64), sp[e0:e0 + n, 5].astype(np.float64),
+                               sp[e0:e0 + n, 9].astype(np.float64), rad[e0:e0 + n].copy(),
+                               rect_of(sp[e0:e0 + n, 0:2], rad[e0:e0 + n], cam, tile), np.zeros(n, np.int32),
+                               rad[e0:e0 + n].copy())
+        want_ids, want_ts = oracle.bin_sort(pg, cam, tile)
+        t0 = toffs[i]
+        nt = len(want_ts) - 1
+        for t in range(nt):
+            a = ids[ts[t0 + t]:ts[t0 + t + 1]] - e0
+            np.testing.assert_array_equal(a, want_ids[want_ts[t]:want_ts[t + 1]])
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 16)])
@@ -439,9 +484,10 @@ def test_ragged_image_matches_oracle():
     assert_img_close(rgb[:, ok], f.image.rgb[:, ok], "image ragged (end to end)")
 
 
-def test_capacity_overflow_is_reported_without_sync():
+@pytest.mark.parametrize("general", [False, True])
+def test_capacity_overflow_is_reported_without_sync(general):
     wl = scenes.small_scene()
-    ctx = ctx_for(wl)
+    ctx = ctx_for(wl, bin_general=general)
     batch = make_batch(wl)
     proj = lobe.project(ctx, batch)
     ctx.reserve(batch.n_entries, 1 << 16, batch.tiles(wl.tile)[0])
