@@ -1,0 +1,26 @@
+"""Host-side logic without a GPU: the camera assignment of fast camera selection (Sec. 3.2)
+from per-block counts, and the autotuner's configuration names."""
+import numpy as np
+import torch
+
+from paper_2510_01767_b300 import batched
+from paper_2510_01767_b300.raster import fcs_select
+
+
+def test_fcs_select_assigns_cameras_at_tau():
+    """V[c, b] = counts / points; camera c joins block b when V >= tau (0.1 in the paper);
+    a camera without points joins nothing."""
+    counts = torch.tensor([[50, 5, 45], [0, 0, 0], [10, 10, 80], [1, 99, 0]], dtype=torch.int32)
+    npts = torch.tensor([100, 0, 100, 100], dtype=torch.int32)
+    V, assign = fcs_select(counts, npts, tau=0.1)
+    np.testing.assert_allclose(V.numpy(), [[0.5, 0.05, 0.45], [0, 0, 0], [0.1, 0.1, 0.8], [0.01, 0.99, 0.0]])
+    assert assign == [[0, 2], [2, 3], [0, 2]]
+    _, strict = fcs_select(counts, npts, tau=0.5)
+    assert strict == [[0], [3], [2]]
+
+
+def test_autotune_configuration_names():
+    assert batched.config_name((8, 8), (1, 2)) == "8x8/f1b2"
+    assert batched.config_name((32, 16), (4, 8)) == "32x16/f4b8"
+    for tile, pxs in batched.PX_OPTIONS.items():
+        assert tile in batched.TILES and len(pxs) >= 2
