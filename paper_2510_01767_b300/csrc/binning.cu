@@ -5,7 +5,8 @@
 // 200k-splat view) while each pixel uses only its first few hundred entries, so the sort
 // dominates. Here the same order is reached without sorting the pairs at all:
 //
-//   1. compact the visible splats and sort them by depth (a few hundred thousand keys);
+//   1. compact the visible splats and sort them by depth (a few hundred thousand keys; four
+//      one-launch radix passes);
 //   2. duplicate them per SUPER-tile (S x S tiles, 64 px) in depth order -- the key carries the
 //      super-tile id (bits 16..31) and the splat's tile rectangle relative to that super-tile
 //      (4 x 4 bits) -- and stably sort those few million pairs by super-tile id: each
@@ -372,12 +373,15 @@ cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int 
 {
     const long long n = P.n_entries;
     uint32_t *V = b.scalars, *n_sp = b.scalars + 1, *sp_total = b.scalars + 4;
-    scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, V, nullptr, nullptr, -1, lb_of(b, ST_SCAN_VISIBLE), st, true);
+    scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, V, nullptr, nullptr, -1, lb_of(b, ST_SCAN_VISIBLE), st, true,
+         b.os_hist, 4 * 256);
     if (n > 0) {
         count_launch();
-        launch_pdl(k_compact, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, tiles, splat, b.vis_pos, b.dkA, b.dvA);
+        launch_pdl(k_compact_hist, dim3((unsigned)((n + CH_SPAN - 1) / CH_SPAN)), dim3(CH_THREADS), 0, st, n, tiles, splat,
+                   b.vis_pos, b.dkA, b.dvA, b.os_hist);
     }
-    radix_sort(V, n, 0, 32, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.counts, lb_of(b, ST_DEPTH_PASS), st);
+    onesweep_sort32(V, n, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.os_hist, b.os_slots, lb_of(b, ST_DEPTH_PASS),
+                    st);
     if (n > 0) {
         count_launch();
         launch_pdl(k_super_area, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, P, V, b.vis_pos, splat, radius, b.offs, b.dkA,
@@ -463,7 +467,8 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
 // ------------------------------------------------------------------ scratch layout
 //
 // entry part: 6 arrays of max_entries words, radix digit counts, scalars, the scans' look-back
-//             words (one per 4096 elements of the longest scan)
+//             words (one per 4096 elements of the longest scan), the depth keys' four digit
+//             histograms, the depth sort's look-back words (256 per 2048 entries)
 // pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong), the chunk work table
 //             (16 B per chunk), per-chunk tile counts
 // super part: super-tile list starts and chunk bases (max_super + 1 words each)
@@ -476,7 +481,8 @@ size_t entry_scratch_bytes(long long max_entries)
 {
     size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
     return 6 * words_rounded(e) + words_rounded((size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS) + words_rounded(16) +
-           slots_rounded(scan_slots(max_scan_length(max_entries)));
+           slots_rounded(scan_slots(max_scan_length(max_entries))) + words_rounded(4 * 256) +
+           slots_rounded(onesweep_slots(max_entries));
 }
 
 size_t pair_scratch_bytes(long long max_pairs, long long max_super)
@@ -522,6 +528,8 @@ void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch 
     b.counts = c.take((size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS);
     b.scalars = c.take(16);
     b.scan_slots = c.take_slots(scan_slots(max_scan_length(max_entries)));
+    b.os_hist = c.take(4 * 256);
+    b.os_slots = c.take_slots(onesweep_slots(max_entries));
     b.ctl = ctl;
     b.status = ctl;
 }

@@ -248,6 +248,8 @@ struct BinScratch {
     uint32_t *counts;   // radix digit counts per block [256][blocks], scanned in place
     uint32_t *scalars;  // [0] visible splats, [1] usable super pairs, [2] usable pairs, [4] super pairs
     unsigned long long *scan_slots;                    // decoupled look-back words of the scans
+    uint32_t *os_hist;                                 // [4][256] digit histograms of the depth keys
+    unsigned long long *os_slots;                      // depth sort look-back words [tiles][256]
     uint32_t *skA, *svA, *skB, *svB;                   // [max_pairs]
     uint32_t *sp_keys, *sp_ids;                        // sorted super pairs (one of the A/B arrays)
     uint4 *work;                                       // per chunk: (super-tile, first pair, end pair)

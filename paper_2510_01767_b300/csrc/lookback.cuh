@@ -29,7 +29,7 @@ constexpr int CTL_WORDS = 2 + LB_STAGES;
 
 enum : int {  // look-back stages (each scan has its own ticket counter and tag)
     ST_SCAN_VISIBLE = 0,
-    ST_DEPTH_PASS = 1,  // .. 4: digit-count scans of the depth sort
+    ST_DEPTH_PASS = 1,  // .. 4: the depth sort's onesweep passes
     ST_SCAN_OFFS = 5,
     ST_SUPER_PASS = 6,  // .. 7: digit-count scans of the super-tile sort
     ST_SCAN_CHUNKS = 8,

@@ -1,10 +1,14 @@
 // sort_prims.cuh -- device primitives of the binning stage (included by binning.cu only):
 // a single-pass exclusive scan with a device-side length (decoupled look-back, lookback.cuh),
-// compaction of visible splats, and a stable LSD radix sort of (key, value) pairs (per pass:
-// digit counts per block, their scan, a block-chunked scatter). Radix passes are
-// block-chunked: each block owns a contiguous chunk, ranks 2048-element tiles of it with warp
-// ballots, reorders each tile by digit in shared memory, and writes runs of equal digits with
-// coalesced stores. Every result is deterministic.
+// compaction of visible splats with the digit histograms of their depth keys, and two stable
+// LSD radix sorts of (key, value) pairs:
+//   - radix_sort: per pass, digit counts per block, their scan, a block-chunked scatter (three
+//     launches a pass; any digit width up to 9 bits);
+//   - onesweep_sort32: all 32 bits in four 8-bit passes of one launch each, the digit offsets
+//     of earlier tiles found by per-digit look-back (Adinets & Merrill, "Onesweep: A Faster
+//     Least Significant Digit Radix Sort for GPUs", 2022).
+// Both rank 2048-element tiles with warp ballots, reorder each tile by digit in shared memory
+// and write runs of equal digits with coalesced stores. Every result is deterministic.
 #include "lookback.cuh"
 
 namespace lobe {
@@ -18,17 +22,51 @@ constexpr int BIN_THREADS = 256;
 
 // ------------------------------------------------------------------ compaction of visible splats
 
-// keys = fp32 depth bits (positive depths order like unsigned ints), values = entry id
-__global__ void __launch_bounds__(256) k_compact(long long n_entries, const int *__restrict__ tiles,
-                                                 const float *__restrict__ splat, const uint32_t *__restrict__ pos,
-                                                 uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals)
+// keys = fp32 depth bits (positive depths order like unsigned ints), values = entry id; each
+// block compacts CH_SPAN consecutive entries and adds its keys' digit counts to the four 8-bit
+// digit histograms of the depth sort: hist[p * 256 + d] = visible keys with (key >> 8p) & 255
+// == d (hist is zeroed by the visible-splat scan that runs before).
+constexpr int CH_THREADS = 256;
+constexpr int CH_ITEMS = 8;
+constexpr int CH_SPAN = CH_THREADS * CH_ITEMS;
+
+__global__ void __launch_bounds__(CH_THREADS) k_compact_hist(long long n_entries, const int *__restrict__ tiles,
+                                                             const float *__restrict__ splat,
+                                                             const uint32_t *__restrict__ pos,
+                                                             uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
+                                                             uint32_t *__restrict__ hist)
 {
     pdl_wait();
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_entries || tiles[e] <= 0) return;
-    uint32_t p = pos[e];
-    dkeys[p] = __float_as_uint(splat[12 * e + 9]);
-    dvals[p] = (uint32_t)e;
+    __shared__ uint32_t h[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += CH_THREADS) h[i] = 0;
+    const long long e0 = (long long)blockIdx.x * CH_SPAN + threadIdx.x;
+    bool vis[CH_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CH_ITEMS; ++j) {
+        const long long e = e0 + j * CH_THREADS;
+        vis[j] = e < n_entries && tiles[e] > 0;
+    }
+    uint32_t key[CH_ITEMS], dst[CH_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CH_ITEMS; ++j) {
+        const long long e = e0 + j * CH_THREADS;
+        key[j] = vis[j] ? __float_as_uint(splat[12 * e + 9]) : 0u;
+        dst[j] = vis[j] ? pos[e] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CH_ITEMS; ++j) {
+        if (!vis[j]) continue;
+        dkeys[dst[j]] = key[j];
+        dvals[dst[j]] = (uint32_t)(e0 + j * CH_THREADS);
+        atomicAdd(&h[key[j] & 255u], 1u);
+        atomicAdd(&h[256 + ((key[j] >> 8) & 255u)], 1u);
+        atomicAdd(&h[512 + ((key[j] >> 16) & 255u)], 1u);
+        atomicAdd(&h[768 + (key[j] >> 24)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += CH_THREADS)
+        if (h[i]) atomicAdd(hist + i, h[i]);
 }
 
 // ------------------------------------------------------------------ radix sort (LSD, <= 9 bits/pass)
@@ -235,6 +273,182 @@ static void radix_sort(const uint32_t *n_dev, long long n_max, int shift0, int n
             scan(LoadPlain{counts}, nullptr, 512LL * nb, counts, nullptr, nullptr, nullptr, -1, lb, st);
             launch_pdl(k_radix_scatter<512>, dim3(nb), dim3(RS_THREADS), 0, st, ks, vs, kd, vd, n_dev, shift0 + lo, bits, counts);
         }
+    }
+}
+
+// ------------------------------------------------------------------ onesweep (one launch a pass)
+
+// The sum of one digit's counts over tiles [0, tile), for the calling thread alone: the words
+// slots[j * 256 + d] of tiles j = tile - 1, tile - 2, ... are read eight at a time (independent
+// loads) and summed down to the nearest inclusive word; a word not yet published ends the
+// window and is polled again (at most LB_SPIN_LIMIT times, then STATUS_TIMEOUT is latched).
+// A timed-out sum only undercounts, so the scatter that uses it stays in bounds.
+__device__ __forceinline__ uint32_t lb_exclusive_digit(const unsigned long long *slots, int tile, int d, uint32_t tag,
+                                                       int *status)
+{
+    constexpr int W = 8;
+    uint32_t sum = 0;
+    int j = tile - 1, spins = 0;
+    while (j >= 0) {
+        unsigned long long w[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) w[q] = j - q >= 0 ? lb_load(slots + (long long)(j - q) * 256 + d) : 0ull;
+        int used = 0;
+        bool stop = false, blocked = false;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (stop || blocked || j - q < 0) continue;
+            if ((uint32_t)(w[q] >> 34) != tag) {
+                blocked = true;
+                continue;
+            }
+            sum += (uint32_t)w[q];
+            ++used;
+            stop = ((uint32_t)(w[q] >> 32) & 3u) == LB_INC;
+        }
+        if (stop) break;
+        j -= used;
+        if (blocked) {
+            if (++spins > LB_SPIN_LIMIT) {
+                set_status(status, STATUS_TIMEOUT);
+                break;
+            }
+            __nanosleep(40);
+        }
+    }
+    return sum;
+}
+
+// One pass of the stable LSD sort by the 8-bit digit at `shift`. The block with ticket t ranks
+// tile t (keys [t * 2048, (t + 1) * 2048)) by digit as k_radix_scatter does, publishes its 256
+// digit counts (slots[t * 256 + d], aggregate first, inclusive once known), gets per digit the
+// keys of earlier tiles by look-back, and scatters: a key of digit d goes to start(d) + (digit-d
+// keys of earlier tiles) + (its rank among the tile's digit-d keys), start being the exclusive
+// scan of the whole key set's digit histogram `hist`. Tiles go in ticket order, so every wait
+// is on a block that is already running.
+__global__ void __launch_bounds__(RS_THREADS) k_onesweep(const uint32_t *__restrict__ kin,
+                                                         const uint32_t *__restrict__ vin,
+                                                         uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                         const uint32_t *n_dev, int shift,
+                                                         const uint32_t *__restrict__ hist,
+                                                         unsigned long long *slots, LB lb)
+{
+    pdl_wait();
+    __shared__ uint32_t s_k[RS_TILE];
+    __shared__ uint32_t s_v[RS_TILE];
+    __shared__ uint32_t wcnt[RS_WARPS][256];
+    __shared__ uint32_t local_off[256], grun[256];
+    __shared__ uint32_t scan_sm[RS_THREADS / 32 + 1];
+    __shared__ int s_tile;
+    __shared__ uint32_t s_gen;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    if (tid == 0) {
+        int t;
+        uint32_t g;
+        lb_take(lb.ctl, lb.stage, false, t, g);
+        s_tile = t;
+        s_gen = g;
+    }
+    for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
+    __syncthreads();
+    const int tile = s_tile;
+    const long long n = *n_dev;
+    const long long tb = (long long)tile * RS_TILE;
+    if (tb >= n) return;
+    const long long hi = n - tb < RS_TILE ? n : tb + RS_TILE;
+    const uint32_t tag = lb_tag(s_gen, lb.stage);
+    const unsigned lt = lanemask_lt();
+    const uint32_t hcount = hist[tid];
+    uint32_t k[RS_ITEMS], v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
+    bool ok[RS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const long long i = tb + warp * (32 * RS_ITEMS) + j * 32 + lane;
+        ok[j] = i < hi;
+        k[j] = ok[j] ? kin[i] : 0u;
+        v[j] = ok[j] ? vin[i] : 0u;
+    }
+    // rank within the warp's 256 consecutive elements, in order
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        dg[j] = (k[j] >> shift) & 255u;
+        const unsigned valid = __ballot_sync(0xffffffffu, ok[j]);
+        const unsigned peers = warp_peers(dg[j], 8, valid);
+        const int leader = ok[j] ? __ffs(peers) - 1 : lane;
+        uint32_t base = (ok[j] && lane == leader) ? wcnt[warp][dg[j]] : 0u;
+        base = __shfl_sync(0xffffffffu, base, leader);
+        rk[j] = base + __popc(peers & lt);
+        __syncwarp();
+        if (ok[j] && lane == leader) wcnt[warp][dg[j]] = base + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread tid = digit: exclusive prefix over warps, the tile's count, its look-back
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = cnt;
+        cnt += c;
+    }
+    unsigned long long *slot = slots + (long long)tile * 256 + tid;
+    lb_publish(slot, tag, tile == 0 ? LB_INC : LB_AGG, cnt);
+    uint32_t before = 0;
+    if (tile > 0) {
+        before = lb_exclusive_digit(slots, tile, tid, tag, lb.ctl);
+        lb_publish(slot, tag, LB_INC, before + cnt);
+    }
+    uint32_t ex, start;
+    block_exclusive_scan<RS_THREADS>(cnt, ex, scan_sm);
+    local_off[tid] = ex;
+    block_exclusive_scan<RS_THREADS>(hcount, start, scan_sm);
+    grun[tid] = start + before;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        if (ok[j]) {
+            const uint32_t p = local_off[dg[j]] + wcnt[warp][dg[j]] + rk[j];
+            s_k[p] = k[j];
+            s_v[p] = v[j];
+        }
+    }
+    __syncthreads();
+    const int n_tile = (int)(hi - tb);
+    for (int i = tid; i < n_tile; i += RS_THREADS) {
+        const uint32_t key = s_k[i];
+        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t g = grun[d] + (uint32_t)i - local_off[d];
+        if ((long long)g < n) {
+            kout[g] = key;
+            vout[g] = s_v[i];
+        }
+    }
+}
+
+// Look-back words of the onesweep passes for up to n keys (256 per 2048-key tile).
+static inline long long onesweep_slots(long long n) { return ((n > 0 ? n : 1) + RS_TILE - 1) / RS_TILE * 256; }
+
+// Stable sort of the first *n_dev (<= n_max) pairs (kA, vA) by all 32 key bits: four onesweep
+// passes A -> B -> A -> B -> (kf, vf); (kf, vf) must not alias (kB, vB). hist holds the four
+// digit histograms of the keys; pass p takes its tickets and tags from stage lb.stage + p.
+static void onesweep_sort32(const uint32_t *n_dev, long long n_max, uint32_t *kA, uint32_t *vA, uint32_t *kB,
+                            uint32_t *vB, uint32_t *kf, uint32_t *vf, const uint32_t *hist,
+                            unsigned long long *slots, LB lb, cudaStream_t st)
+{
+    const long long tiles = (n_max + RS_TILE - 1) / RS_TILE;
+    const unsigned grid = (unsigned)(tiles < 1 ? 1 : tiles);
+    const int stage0 = lb.stage;
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t *ks = (p & 1) ? kB : kA, *vs = (p & 1) ? vB : vA;
+        uint32_t *kd = (p & 1) ? kA : kB, *vd = (p & 1) ? vA : vB;
+        if (p == 3) {
+            kd = kf;
+            vd = vf;
+        }
+        lb.stage = stage0 + p;
+        count_launch();
+        launch_pdl(k_onesweep, dim3(grid), dim3(RS_THREADS), 0, st, ks, vs, kd, vd, n_dev, 8 * p, hist + 256 * p,
+                   slots, lb);
     }
 }
 
