@@ -290,14 +290,21 @@ def test_fused_adam_with_crop_mask_and_empty_set(sparse):
     cams = [scenes.pinhole(96, 64, 80.0), scenes.pinhole(64, 64, 60.0)]
     items = [(0, 0, -1), (0, 1, -1), (1, 1, -1)]
 
-    def run(fused):
+    def make_sets():
         sets = [lobe.GaussianSet.from_numpy(g_np), lobe.GaussianSet.from_numpy(empty)]
         sets[0].crop_mask = torch.as_tensor(crop).cuda()
+        return sets
+
+    # one forward and render adjoint for both paths (its atomics sum in no fixed order)
+    ctx = lobe.Context(tile=(16, 16))
+    batch0 = lobe.Batch(make_sets(), cams, items)
+    proj, bins, img = lobe.forward(ctx, batch0)
+    dL = torch.as_tensor(np.random.default_rng(8).standard_normal(3 * batch0.n_pixels), dtype=torch.float32).cuda()
+    g2d = lobe.render_bwd(ctx, batch0, proj, bins, img, dL)
+
+    def run(fused):
+        sets = make_sets()
         batch = lobe.Batch(sets, cams, items)
-        ctx = lobe.Context(tile=(16, 16))
-        proj, bins, img = lobe.forward(ctx, batch)
-        dL = torch.as_tensor(np.random.default_rng(8).standard_normal(3 * batch.n_pixels), dtype=torch.float32).cuda()
-        g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
         opts = [lobe.Adam(s, lr=LR, betas=(B1, B2), eps=EPS) for s in sets]
         m0 = {k: torch.as_tensor(np.random.default_rng(2).standard_normal(shapes(g_np.n)[k]) * 1e-3,
                                  dtype=torch.float32).cuda() for k in KEYS}
