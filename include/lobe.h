@@ -253,11 +253,15 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
  * written). The call synchronises again at the end and stores the (splat, tile) pair count
  * in *n_isect_host (nullable); more pairs than bins->capacity gives LOBE_ERR_CAPACITY and
  * bins describing empty tiles.
- * The first call on a device looks up the array's device address (and may load the
- * library's kernels); make that first call before any stream capture. All calls share the
- * one array: calls whose work overlaps on the GPU (other threads, other streams) race and
- * must be serialised by the caller. Other errors: LOBE_ERR_ARG (bad arguments),
- * LOBE_ERR_CUDA (a CUDA call failed). */
+ * The first call on a device (and the first after that device's context was destroyed and
+ * created again) looks up the array's device address (and may load the library's kernels);
+ * make that first call before any stream capture. All calls share the one array: calls
+ * whose work overlaps on the GPU (other threads, other streams) race and must be serialised
+ * by the caller. At each of its two synchronisations the call also reads the status word
+ * that the kernels latch in the array (cleared at the start of every call):
+ * LOBE_ERR_TIMEOUT when a bounded device-side wait gave up (the bins are then undefined),
+ * LOBE_ERR_CAPACITY when an overflow was latched. Other errors: LOBE_ERR_ARG (bad
+ * arguments), LOBE_ERR_CUDA (a CUDA call failed). */
 #define LOBE_NOALLOC_MAX_ENTRIES 262144
 #define LOBE_NOALLOC_MAX_TILES 65536
 #define LOBE_NOALLOC_MAX_PAIRS 524288

@@ -19,8 +19,12 @@ constexpr size_t kScratchBytes = size_t(20) << 20;
 constexpr size_t kStatusBytes = CTL_BYTES;  // status word + look-back control block
 constexpr int kMaxDevices = 64;
 
+struct DeviceSlot {
+    unsigned long long ctx_id;  // driver context the address belongs to (0: not looked up yet)
+    void *addr;                 // device address of the array in that context
+};
 std::mutex g_mu;
-void *g_addr[kMaxDevices];  // device address of the array, per device, set on first use
+DeviceSlot g_slot[kMaxDevices];
 
 }  // namespace
 
@@ -28,26 +32,65 @@ void *g_addr[kMaxDevices];  // device address of the array, per device, set on f
 // name only stands in for the symbol; kernels get the address looked up below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Once per device, with that device current: the array's device address.
+// Unique id of the calling thread's current driver context (driver entry points fetched
+// through the runtime, so the library needs no link against the driver library). 0 when the
+// driver cannot tell, in which case the address is looked up on every call.
+static unsigned long long current_context_id()
+{
+    typedef int (*GetCurrent)(void **);
+    typedef int (*GetId)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || ctx == nullptr || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Set-up, once per device (again only if that device's context was destroyed and created
+// anew, e.g. after cudaDeviceReset, since the array may then sit elsewhere), with the device
+// current: the array's device address.
 static lobe_status scratch_address(void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LOBE_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return LOBE_ERR_STATE;
+    const unsigned long long id = current_context_id();  // 0 before the runtime made a context current
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_addr[dev] == nullptr) {
+    DeviceSlot &s = g_slot[dev];
+    if (s.addr == nullptr || id == 0 || s.ctx_id != id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return LOBE_ERR_CUDA;
-        g_addr[dev] = p;
+        s.addr = p;
+        s.ctx_id = current_context_id();  // the lookup has made the device's context current
     }
-    *out = g_addr[dev];
+    *out = s.addr;
     return LOBE_OK;
+}
+
+// Status latched by the kernels in the array's control block -> the call's return code.
+static lobe_status device_status(int code)
+{
+    return code == STATUS_TIMEOUT ? LOBE_ERR_TIMEOUT : (code == STATUS_CAPACITY ? LOBE_ERR_CAPACITY : LOBE_OK);
 }
 
 extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *stream, const lobe_batch *batch,
                                              const lobe_projected *proj, const lobe_bins *bins, int64_t *n_isect_host)
 {
-    // the parameter block (~15 KB) lives in per-thread static storage, not on the heap
+    // the parameter block (~15 KB) is host memory: per-thread storage, set up once per host
+    // thread on its first call (no device memory is allocated, here or anywhere in this call)
     static thread_local BatchParams P;
     lobe_status s = lobe_internal_build_params(cfg, batch, P);
     if (s != LOBE_OK) return s;
@@ -82,9 +125,13 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
     if (bin_super_count(P, proj->splat, proj->radius, proj->tiles_touched, b, kMaxPairs, st) != cudaSuccess)
         return LOBE_ERR_CUDA;
     uint32_t n_sp = 0;
+    int code = STATUS_OK;
     if (cudaMemcpyAsync(&n_sp, b.scalars + 4, sizeof n_sp, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&code, status, sizeof code, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return LOBE_ERR_CUDA;
+    // a bounded wait that gave up leaves the counts undefined: report it, bins not written
+    if (device_status(code) != LOBE_OK) return device_status(code);
     if ((long long)n_sp > kMaxPairs) return LOBE_ERR_CAPACITY;
 
     long long *n_isect = reinterpret_cast<long long *>(bins->n_isect);
@@ -94,8 +141,11 @@ extern "C" lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *strea
         return LOBE_ERR_CUDA;
     long long total = 0;
     if (cudaMemcpyAsync(&total, n_isect, sizeof total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&code, status, sizeof code, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return LOBE_ERR_CUDA;
     if (n_isect_host) *n_isect_host = total;
+    // the device's own verdict first: a timed-out wait (LOBE_ERR_TIMEOUT) or a latched overflow
+    if (device_status(code) != LOBE_OK) return device_status(code);
     return total > bins->capacity ? LOBE_ERR_CAPACITY : LOBE_OK;
 }

@@ -82,3 +82,60 @@ def test_noalloc_rejects_batches_beyond_its_limits():
                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
                                          ctypes.byref(batch.c), ctypes.byref(proj.c()), ctypes.byref(out.c()), None)
     assert code == A.ERR_CAPACITY
+
+
+def call_noalloc(ctx, batch, proj, out):
+    n = ctypes.c_int64(-1)
+    code = A.lib().lobe_bin_sort_noalloc(ctypes.byref(ctx._config()),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                         ctypes.byref(batch.c), ctypes.byref(proj.c()), ctypes.byref(out.c()),
+                                         ctypes.byref(n))
+    torch.cuda.synchronize()
+    return code, n.value
+
+
+def test_noalloc_lists_match_the_oracle():
+    """One small view binned by the allocation-free call against the oracle's (tile, depth,
+    index) sort of the same float32 splats: the lists and tile ranges bit for bit."""
+    import oracle
+
+    wl = scenes.small_scene(seed=3)
+    sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
+    batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
+    ctx = lobe.Context(tile=wl.tile)
+    proj = lobe.project(ctx, batch)
+    n_tiles, _ = batch.tiles(wl.tile)
+    out = lobe.raster.empty_bins(1 << 16, n_tiles)
+    code, n = call_noalloc(ctx, batch, proj, out)
+    assert code == A.OK, A.STATUS_NAMES.get(code, code)
+    sp = proj.splat.cpu().numpy().astype(np.float64)
+    radius = proj.radius.cpu().numpy()
+    p = oracle.Projection(sp[:, 0:2], sp[:, 2:5], sp[:, 6:9], sp[:, 5], sp[:, 9], radius,
+                          np.zeros((len(radius), 4), np.int32), np.zeros(len(radius), np.int32), radius)
+    ids, ts = oracle.bin_sort(p, wl.cameras[0].as_dict(), wl.tile)
+    assert n == len(ids) > 0
+    np.testing.assert_array_equal(out.gauss_ids[:n].cpu().numpy(), ids)
+    np.testing.assert_array_equal(out.tile_start.cpu().numpy(), ts)
+
+
+def test_noalloc_reports_overflow_then_recovers():
+    """Bins one pair too small: LOBE_ERR_CAPACITY with the true pair count and every tile
+    empty. The next call, on the same shared array (whose status word the overflow latched),
+    must then bin bit-exactly like lobe_bin_sort again."""
+    wl = scenes.small_scene(seed=4)
+    sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
+    batch = lobe.Batch(sets, wl.cameras, wl.items, wl.blocks)
+    ctx = lobe.Context(tile=wl.tile)
+    proj = lobe.project(ctx, batch)
+    ref = lobe.bin_sort(ctx, batch, proj)
+    n_tiles, _ = batch.tiles(wl.tile)
+    small = lobe.raster.empty_bins(ref.count - 1, n_tiles)
+    small.tile_start.fill_(-7)
+    code, n = call_noalloc(ctx, batch, proj, small)
+    assert code == A.ERR_CAPACITY
+    assert n == ref.count
+    assert int(small.tile_start.abs().max().item()) == 0
+    out = lobe.raster.empty_bins(ref.count, n_tiles)
+    code, n = call_noalloc(ctx, batch, proj, out)
+    assert code == A.OK, A.STATUS_NAMES.get(code, code)
+    check_equal(ref, out, n)
