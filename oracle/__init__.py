@@ -62,6 +62,7 @@ def lib():
         _lib.orc_depth_key.argtypes = [ctypes.c_double]
         _lib.orc_round_f32.restype = ctypes.c_float
         _lib.orc_round_f32.argtypes = [ctypes.c_double]
+        _lib.orc_bin_ext.restype = ctypes.c_int64
     return _lib
 
 
@@ -409,6 +410,147 @@ def densify(params, acc, cnt, normals, grad_threshold, max_clone_log_scale, prun
         out["means"][child] = np.asarray(params["means"], np.float64)[g] + np.einsum("nij,nj->ni", R, s * zk)
         out["log_scales"][child] = np.asarray(params["log_scales"], np.float64)[g] - split_log_shrink
     return out, source
+
+
+# ----------------------------------------------------------------------------- admissible branches
+
+MAX_LEAVES = 64  # leaves per pixel an enumeration keeps (a uint64 bitmask names the admissible ones)
+
+
+@dataclass
+class ExtBins:
+    """Per-tile lists with every possible member: ``unc[k]`` is 0 for a certain member, 1 for
+    a member only if a marginal projection decision went the other way, 2 for a member that
+    such a flip would remove."""
+    ids: np.ndarray
+    unc: np.ndarray
+    tile_start: np.ndarray
+
+
+def bin_ext(p: Projection, cam, tile=(16, 16), win=None) -> ExtBins:
+    """Extended per-tile lists of the tiles touching ``win`` = (x0, y0, x1, y1) (None: all):
+    the certain members as ``bin_sort`` lists them, plus the Gaussians whose membership a
+    marginal radius, rectangle or guard decision (``p.flags``) could flip."""
+    L = lib()
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    m2, _ = _d(p.mean2d)
+    r, _ = _i(p.radius)
+    ra, _ = _i(p.radius_all)
+    fl, _ = _i(p.flags)
+    dp, _ = _d(p.depth)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    gx, gy = grid(c, tile)
+    with window(*(win or (0, 0, 1 << 30, 1 << 30))):
+        total = L.orc_bin_ext(ctypes.c_int64(p.n), ptr(m2), ptr(r), ptr(ra), ptr(fl), ptr(dp), W, H, tile[0],
+                              tile[1], None, None, None)
+        ids = np.zeros(max(total, 1), np.int32)
+        unc = np.zeros(max(total, 1), np.uint8)
+        ts = np.zeros(gx * gy + 1, np.int32)
+        L.orc_bin_ext(ctypes.c_int64(p.n), ptr(m2), ptr(r), ptr(ra), ptr(fl), ptr(dp), W, H, tile[0], tile[1],
+                      ptr(ids), ptr(unc), ptr(ts))
+    return ExtBins(ids[:total], unc[:total], ts)
+
+
+@dataclass
+class Leaves:
+    """Every admissible composite of each pixel of a window (see ``render_leaves``)."""
+    win: tuple            # (x0, y0, x1, y1)
+    n: np.ndarray         # [h, w] leaves per pixel; 0 = more than the cap (pixel not checkable)
+    C: np.ndarray         # [h, w, L, 3] colour, background included
+    T: np.ndarray         # [h, w, L] final transmittance
+    nc: np.ndarray        # [h, w, L] n_contrib
+
+
+def _win(cam, win):
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    if win is None:
+        return (0, 0, c["width"], c["height"])
+    x0, y0, x1, y1 = win
+    return (x0, y0, min(x1, c["width"]), min(y1, c["height"]))
+
+
+def render_leaves(p: Projection, eb: ExtBins, cam, tile=(16, 16), bg=(0.0, 0.0, 0.0), margins=MARGINS_NONE,
+                  win=None, max_leaves=MAX_LEAVES, certain=False) -> Leaves:
+    """Enumerates, per pixel of ``win``, every composite reachable by flipping decisions that
+    are marginal under ``margins`` (membership of uncertain list members, sigma < 0, the 1/255
+    skip, the 0.99 clamp, the 1e-4 stop), depth first with the FP64 outcome first: leaf 0 is
+    the FP64 composite. ``certain`` treats every list member as certain (stage inputs)."""
+    if not 1 <= max_leaves <= 64:
+        raise ValueError("max_leaves must be in [1, 64]")
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    x0, y0, x1, y1 = _win(c, win)
+    h, w = y1 - y0, x1 - x0
+    n = np.zeros((h, w), np.int32)
+    C = np.zeros((h, w, max_leaves, 3))
+    T = np.zeros((h, w, max_leaves))
+    nc = np.zeros((h, w, max_leaves), np.int32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m2, _ = _d(p.mean2d)
+    cn, _ = _d(p.conic)
+    co, _ = _d(p.color)
+    op, _ = _d(p.opacity)
+    ids, _ = _i(eb.ids if len(eb.ids) else np.zeros(1, np.int32))
+    unc = np.ascontiguousarray(eb.unc if len(eb.unc) else np.zeros(1, np.uint8), np.uint8)
+    ts, _ = _i(eb.tile_start)
+    bgv, _ = _d(np.asarray(bg, np.float64))
+    mg, _ = _d(margins)
+    lib().orc_render_leaves(W, H, tile[0], tile[1], ptr(m2), ptr(cn), ptr(co), ptr(op), ptr(ids),
+                            None if certain else ptr(unc), ptr(ts), ptr(bgv), ptr(mg), x0, y0, x1, y1,
+                            max_leaves, ptr(n), ptr(C), ptr(T), ptr(nc))
+    return Leaves((x0, y0, x1, y1), n, C, T, nc)
+
+
+def render_bwd_envelope(p: Projection, eb: ExtBins, cam, dL_drgb, admissible, tile=(16, 16), bg=(0.0, 0.0, 0.0),
+                        margins=MARGINS_NONE, win=None, max_leaves=MAX_LEAVES, certain=False):
+    """Bounds of the composite adjoint when each pixel of ``win`` may have taken any of its
+    ``admissible`` leaves (uint64 [h, w], bit l = leaf l of ``render_leaves`` with the same
+    arguments): (lo, hi, absmax), each [n, 12] in the grad2d layout (u, v, conic a, b, c,
+    opacity, r, g, b, 0, 0, 0). Any one choice of an admissible leaf per pixel gives per-splat
+    gradients inside [lo, hi]; with one admissible leaf per pixel lo = hi = the plain
+    adjoint. absmax sums, per pixel, the largest absolute per-pixel term over the admissible
+    leaves (the scale a float32 sum of the terms resolves to)."""
+    c = cam if isinstance(cam, dict) else cam.as_dict()
+    W, H = c["width"], c["height"]
+    x0, y0, x1, y1 = _win(c, win)
+    adm = np.ascontiguousarray(admissible, np.uint64).reshape(y1 - y0, x1 - x0)
+    lo = np.zeros((p.n, 12))
+    hi = np.zeros((p.n, 12))
+    ab = np.zeros((p.n, 12))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    m2, _ = _d(p.mean2d)
+    cn, _ = _d(p.conic)
+    co, _ = _d(p.color)
+    op, _ = _d(p.opacity)
+    ids, _ = _i(eb.ids if len(eb.ids) else np.zeros(1, np.int32))
+    unc = np.ascontiguousarray(eb.unc if len(eb.unc) else np.zeros(1, np.uint8), np.uint8)
+    ts, _ = _i(eb.tile_start)
+    bgv, _ = _d(np.asarray(bg, np.float64))
+    mg, _ = _d(margins)
+    gr, _ = _d(np.asarray(dL_drgb).reshape(3, H, W))
+    lib().orc_render_bwd_envelope(W, H, tile[0], tile[1], ptr(m2), ptr(cn), ptr(co), ptr(op), ptr(ids),
+                                  None if certain else ptr(unc), ptr(ts), ptr(bgv), ptr(mg), x0, y0, x1, y1,
+                                  max_leaves, ptr(adm), ptr(gr), ptr(lo), ptr(hi), ptr(ab))
+    return lo, hi, ab
+
+
+class branch_flips:
+    """Context manager: while active, ``project_bwd`` inverts the culling decision of every
+    Gaussian with ``vis[g] != 0`` and the colour clamp of channel ch where bit ch of
+    ``color[g]`` is set (the other outcome of a decision float32 could take either way)."""
+
+    def __init__(self, vis=None, color=None):
+        self.vis = None if vis is None else np.ascontiguousarray(vis, np.uint8)
+        self.color = None if color is None else np.ascontiguousarray(color, np.uint8)
+
+    def __enter__(self):
+        ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        lib().orc_set_branch_flips(ptr(self.vis), ptr(self.color))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_branch_flips(None, None)
 
 
 def sh_basis(dirs, degree=3):

@@ -267,6 +267,19 @@ typedef struct {
     double Y[16];
 } proj_t;
 
+/* Optional per-Gaussian overrides of decisions that float32 arithmetic could take the other
+ * way (tests set them to evaluate the other branch; NULL = none). g_vis_flip[g] != 0 inverts
+ * the culling decision of Gaussian g in orc_project_bwd; bit ch of g_color_flip[g] inverts
+ * the clamp of colour channel ch at 0 in orc_project_bwd. They change no arithmetic. */
+static const uint8_t *g_vis_flip = NULL;
+static const uint8_t *g_color_flip = NULL;
+
+void orc_set_branch_flips(const uint8_t *vis_flip, const uint8_t *color_flip)
+{
+    g_vis_flip = vis_flip;
+    g_color_flip = color_flip;
+}
+
 static int near_integer(double x, double margin)
 {
     return fabs(x - floor(x + 0.5)) < margin;
@@ -282,7 +295,7 @@ static void tile_rect(double u, double v, int r, int tw, int th, int gx, int gy,
 
 static void project_one(const double *mu, const double *ls, const double *q, double logit,
                         const double *sh, int degree, int cropped, const cam_t *k,
-                        int tw, int th, const double *mg, proj_t *P)
+                        int tw, int th, const double *mg, int flip_vis, proj_t *P)
 {
     memset(P, 0, sizeof *P);
     if (cropped) return;
@@ -361,8 +374,11 @@ static void project_one(const double *mu, const double *ls, const double *q, dou
             if (kk >= 0 && kk <= gmax[i] && fabs(e[i] - kk * t[i]) < mg[M_PX]) P->flags |= F_RECT;
         }
     }
-    if (guard_out || P->rect[2] <= P->rect[0] || P->rect[3] <= P->rect[1]) return;
-    /* view-dependent colour */
+    int culled = guard_out || P->rect[2] <= P->rect[0] || P->rect[3] <= P->rect[1];
+    /* a caller may invert a culling decision that float32 could take the other way */
+    if (flip_vis) culled = !culled;
+    /* view-dependent colour and opacity, also for a culled Gaussian (the other branch of a
+     * marginal culling decision needs them) */
     for (int i = 0; i < 3; ++i) P->dir[i] = mu[i] - k->campos[i];
     P->dirlen = sqrt(P->dir[0] * P->dir[0] + P->dir[1] * P->dir[1] + P->dir[2] * P->dir[2]);
     for (int i = 0; i < 3; ++i) P->n[i] = P->dir[i] / P->dirlen;
@@ -376,7 +392,7 @@ static void project_one(const double *mu, const double *ls, const double *q, dou
         if (fabs(P->color_raw[ch]) < mg[M_COL]) P->flags |= F_COLOR;
     }
     P->opacity = 1.0 / (1.0 + exp(-logit));
-    P->visible = 1;
+    P->visible = !culled;
 }
 
 /* ------------------------------------------------------------------ public: project */
@@ -392,7 +408,7 @@ int orc_project(int64_t n, const double *means, const double *log_scales, const 
     for (int64_t g = 0; g < n; ++g) {
         proj_t P;
         project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], sh + 48 * g, degree,
-                    crop ? crop[g] == 0 : 0, &k, tw, th, margins, &P);
+                    crop ? crop[g] == 0 : 0, &k, tw, th, margins, 0, &P);
         mean2d[2 * g] = P.mean2d[0];
         mean2d[2 * g + 1] = P.mean2d[1];
         for (int i = 0; i < 3; ++i) {
@@ -736,6 +752,479 @@ int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const dou
     return 0;
 }
 
+/* ------------------------------------------------------------------ admissible branches
+ *
+ * A float32 evaluation of the rasterizer may take a decision the other way when the FP64
+ * value lies within float32 rounding of its threshold. Either outcome is then a correct
+ * result of the method at the precision the GPU computes in. The functions below enumerate,
+ * per pixel, every outcome reachable by flipping marginal decisions (the "leaves"), so that a
+ * test can accept a float32 result exactly when it matches one of them, instead of leaving
+ * such pixels out.
+ *
+ * Marginal decisions of one (pixel, Gaussian) pair, with the margins of orc_margins:
+ *   membership  the Gaussian is in the pixel's tile list only under one outcome of a marginal
+ *               projection decision (radius, rectangle edge, fov guard: the "uncertain"
+ *               members of orc_bin_ext)
+ *   sigma < 0   |sigma| < M_SIG
+ *   clamp       |o G - 0.99| < M_REL 0.99 (alpha moves by at most the margin; the gradient
+ *               changes form)
+ *   alpha skip  |255 alpha - 1| < M_REL
+ *   stop        |T (1 - alpha) - 1e-4| < M_REL 1e-4
+ * The walk is a depth-first search over the pixel's list in compositing order: at a marginal
+ * decision it first follows the FP64 outcome, then the other one. Leaves are numbered in
+ * that order, so leaf 0 is the plain FP64 composite, and a second walk over the same inputs
+ * numbers them identically. An uncertain member whose sigma or alpha test fails by more than
+ * the margin is skipped under both outcomes and is not a branch. */
+
+/* Per Gaussian, the tiles (inside the sampling window) it may belong to: certain members (the
+ * FP64 rectangle when no projection decision of the Gaussian is marginal, else the rectangle
+ * of radius r - 1 of a visible Gaussian without a marginal guard decision) and uncertain
+ * members (the rest of the rectangle of radius r + 1 of a Gaussian with a marginal radius,
+ * rectangle or guard decision). unc[k] = 0 certain, 1 uncertain and outside the FP64
+ * rectangle, 2 uncertain and inside it. Lists in (tile, fp32 depth, index) order as orc_bin;
+ * tile_start as orc_bin. Returns the number of entries; with ids == NULL it only counts. */
+static int ext_member(int64_t g, int tx, int ty, const double *mean2d, const int32_t *radius,
+                      const int32_t *radius_all, const int32_t *gflags, int tw, int th, int gx, int gy)
+{
+    /* -1: not a member; 0 certain; 1 uncertain, outside the FP64 rectangle; 2 uncertain, inside */
+    int marg = (gflags[g] & (F_GUARD | F_RADIUS | F_RECT)) && radius_all[g] > 0;
+    int own[4] = {0, 0, 0, 0};
+    if (radius[g] > 0) tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, own);
+    int in_own = tx >= own[0] && tx < own[2] && ty >= own[1] && ty < own[3];
+    if (!marg) return in_own ? 0 : -1;
+    int outer[4], inner[4] = {0, 0, 0, 0};
+    tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g] + 1, tw, th, gx, gy, outer);
+    if (!(tx >= outer[0] && tx < outer[2] && ty >= outer[1] && ty < outer[3])) return -1;
+    if (!(gflags[g] & F_GUARD) && radius[g] > 0 && radius_all[g] > 1)
+        tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g] - 1, tw, th, gx, gy, inner);
+    if (tx >= inner[0] && tx < inner[2] && ty >= inner[1] && ty < inner[3]) return 0;
+    return in_own ? 2 : 1;
+}
+
+int64_t orc_bin_ext(int64_t n, const double *mean2d, const int32_t *radius, const int32_t *radius_all,
+                    const int32_t *gflags, const double *depth, int W, int H, int tw, int th,
+                    int32_t *ids, uint8_t *unc, int32_t *tile_start)
+{
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int64_t total = 0;
+    pair_t *pairs = NULL;
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t k = 0;
+        for (int64_t g = 0; g < n; ++g) {
+            int marg = (gflags[g] & (F_GUARD | F_RADIUS | F_RECT)) && radius_all[g] > 0;
+            if (!marg && radius[g] <= 0) continue;
+            int r[4];
+            tile_rect(mean2d[2 * g], mean2d[2 * g + 1], marg ? radius_all[g] + 1 : radius[g], tw, th, gx, gy, r);
+            for (int ty = r[1]; ty < r[3]; ++ty)
+                for (int tx = r[0]; tx < r[2]; ++tx) {
+                    if (!tile_in_window(tx, ty, tw, th)) continue;
+                    if (ext_member(g, tx, ty, mean2d, radius, radius_all, gflags, tw, th, gx, gy) < 0) continue;
+                    if (pass == 1) {
+                        pairs[k].tile = (uint32_t)(ty * gx + tx);
+                        pairs[k].dbits = f32_bits(depth[g]);
+                        pairs[k].g = (int32_t)g;
+                    }
+                    ++k;
+                }
+        }
+        if (pass == 0) {
+            total = k;
+            if (!ids) return total;
+            pairs = malloc(sizeof(pair_t) * (total ? total : 1));
+        }
+    }
+    qsort(pairs, total, sizeof(pair_t), pair_cmp);
+    for (int64_t i = 0; i < total; ++i) {
+        int tx = (int)(pairs[i].tile % (uint32_t)gx), ty = (int)(pairs[i].tile / (uint32_t)gx);
+        ids[i] = pairs[i].g;
+        unc[i] = (uint8_t)ext_member(pairs[i].g, tx, ty, mean2d, radius, radius_all, gflags, tw, th, gx, gy);
+    }
+    int64_t i = 0;
+    for (int t = 0; t <= gx * gy; ++t) {
+        while (i < total && pairs[i].tile < (uint32_t)t) ++i;
+        tile_start[t] = (int32_t)i;
+    }
+    free(pairs);
+    return total;
+}
+
+typedef struct {
+    int32_t g;
+    int64_t pos;  /* position in the pixel's list */
+    double alpha, T, G, dx, dy;
+    int clamped;
+} brec_t;
+
+typedef struct {
+    double T, C[3];
+    int32_t last;
+    int64_t nrec;
+} wstate_t;
+
+typedef struct walk_s walk_t;
+struct walk_s {
+    double pxc, pyc;
+    const int32_t *list;
+    const uint8_t *unc;  /* NULL: every member certain */
+    int64_t len;
+    const double *mean2d, *conic, *color, *opacity, *mg;
+    int max_leaves, nleaves, overflow;
+    brec_t *rec;
+    void (*leaf)(walk_t *w, int index, const wstate_t *S);
+    void *user;
+};
+
+/* one pair's FP64 quantities */
+typedef struct {
+    int64_t i;
+    int32_t g;
+    double dx, dy, sigma, G, araw;
+} pairq_t;
+
+static void walk(walk_t *w, int64_t i, wstate_t S);
+
+static void emit_leaf(walk_t *w, const wstate_t *S)
+{
+    if (w->overflow) return;
+    if (w->nleaves >= w->max_leaves) {
+        w->overflow = 1;
+        return;
+    }
+    w->leaf(w, w->nleaves, S);
+    w->nleaves++;
+}
+
+/* the stop test and, unless the walk stops, the pair's contribution. A stop leaves the state
+ * as it was before the pair, whatever alpha the pair had: *stopped (nullable) records that
+ * this pair's stop leaf exists, so that its other outcomes do not repeat it. */
+static void pair_stop(walk_t *w, const pairq_t *q, wstate_t S, double alpha, int clamped, int *stopped)
+{
+    double Tn = S.T * (1.0 - alpha);
+    int stop = Tn < 1e-4, marg = fabs(Tn - 1e-4) < w->mg[M_REL] * 1e-4;
+    for (int b = 0; b < 1 + marg; ++b) {
+        int st = b == 0 ? stop : !stop;
+        if (st) {
+            if (stopped && *stopped) continue;
+            if (stopped) *stopped = 1;
+            emit_leaf(w, &S);
+            continue;
+        }
+        wstate_t N = S;
+        double wgt = alpha * S.T;
+        for (int ch = 0; ch < 3; ++ch) N.C[ch] += w->color[3 * q->g + ch] * wgt;
+        brec_t *r = w->rec + S.nrec;
+        r->g = q->g; r->pos = q->i; r->alpha = alpha; r->T = S.T; r->G = q->G;
+        r->dx = q->dx; r->dy = q->dy; r->clamped = clamped;
+        N.nrec = S.nrec + 1;
+        N.T = Tn;
+        N.last = (int32_t)(q->i + 1);
+        walk(w, q->i + 1, N);
+    }
+}
+
+/* The distinct outcomes of one pair with a marginal decision: "skipped" (not a member, sigma
+ * < 0 or alpha < 1/255: all leave the state as it is) and "used with the clamp on / off".
+ * The FP64 outcome comes first; only outcomes some assignment of the marginal decisions
+ * reaches are followed. u is the pair's membership flag (0 certain, 1 / 2 uncertain with
+ * the FP64 rectangle excluding / including it). */
+static void pair_branch(walk_t *w, const pairq_t *q, int u, wstate_t S)
+{
+    const double *mg = w->mg;
+    int mem_fp = u != 1, mem_m = u != 0;
+    int sig_fp = !(q->sigma < 0.0), sig_m = fabs(q->sigma) < mg[M_SIG];  /* the sigma test passes */
+    int cl_fp = q->araw >= 0.99, cl_m = fabs(q->araw - 0.99) < mg[M_REL] * 0.99;
+    double a_of[2];
+    int pass_fp[2], pass_m[2];
+    for (int c = 0; c < 2; ++c) {
+        a_of[c] = c ? 0.99 : q->araw;
+        pass_fp[c] = !(a_of[c] < 1.0 / 255.0);
+        pass_m[c] = fabs(a_of[c] * 255.0 - 1.0) < mg[M_REL];
+    }
+    int mem_in = mem_fp || mem_m, mem_out = !mem_fp || mem_m;
+    int sig_pass = sig_fp || sig_m, sig_fail = !sig_fp || sig_m;
+    int use_ok[2], skip_ok = mem_out || (mem_in && sig_fail);
+    for (int c = 0; c < 2; ++c) {
+        int clamp_ok = c == cl_fp || cl_m;
+        use_ok[c] = mem_in && sig_pass && clamp_ok && (pass_fp[c] || pass_m[c]);
+        if (mem_in && sig_pass && clamp_ok && (!pass_fp[c] || pass_m[c])) skip_ok = 1;
+    }
+    int fp_used = mem_fp && sig_fp && pass_fp[cl_fp];
+    /* outcome codes: 0 skipped, 1 used unclamped, 2 used clamped; FP64 first */
+    int order[3], no = 0;
+    order[no++] = fp_used ? 1 + cl_fp : 0;
+    if (order[0] != 0 && skip_ok) order[no++] = 0;
+    for (int c = 0; c < 2; ++c)
+        if (use_ok[c] && order[0] != 1 + c) order[no++] = 1 + c;
+    int stopped = 0;
+    for (int k = 0; k < no; ++k) {
+        if (order[k] == 0)
+            walk(w, q->i + 1, S);
+        else
+            pair_stop(w, q, S, a_of[order[k] - 1], order[k] - 1, &stopped);
+    }
+}
+
+static void walk(walk_t *w, int64_t i, wstate_t S)
+{
+    const double *mg = w->mg;
+    for (; i < w->len; ++i) {
+        if (w->overflow) return;
+        pairq_t q;
+        q.i = i;
+        q.g = w->list[i];
+        q.dx = w->mean2d[2 * q.g] - w->pxc;
+        q.dy = w->mean2d[2 * q.g + 1] - w->pyc;
+        const double *cn = w->conic + 3 * q.g;
+        q.sigma = 0.5 * (cn[0] * q.dx * q.dx + cn[2] * q.dy * q.dy) + cn[1] * q.dx * q.dy;
+        q.G = exp(-q.sigma);
+        q.araw = w->opacity[q.g] * q.G;
+        int m_sig = fabs(q.sigma) < mg[M_SIG];
+        int m_clamp = fabs(q.araw - 0.99) < mg[M_REL] * 0.99;
+        double alpha = q.araw >= 0.99 ? 0.99 : q.araw;
+        int m_a = fabs(alpha * 255.0 - 1.0) < mg[M_REL];
+        int u = w->unc ? w->unc[i] : 0;
+        if (u || m_sig || m_clamp || m_a) {
+            pair_branch(w, &q, u, S);
+            return;
+        }
+        /* no marginal decision: the plain step */
+        if (q.sigma < 0.0 || alpha < 1.0 / 255.0) continue;
+        double Tn = S.T * (1.0 - alpha);
+        if (fabs(Tn - 1e-4) < mg[M_REL] * 1e-4) {
+            pair_stop(w, &q, S, alpha, q.araw >= 0.99, NULL);
+            return;
+        }
+        if (Tn < 1e-4) {
+            emit_leaf(w, &S);
+            return;
+        }
+        double wgt = alpha * S.T;
+        for (int ch = 0; ch < 3; ++ch) S.C[ch] += w->color[3 * q.g + ch] * wgt;
+        brec_t *r = w->rec + S.nrec;
+        r->g = q.g; r->pos = i; r->alpha = alpha; r->T = S.T; r->G = q.G;
+        r->dx = q.dx; r->dy = q.dy; r->clamped = q.araw >= 0.99;
+        S.nrec++;
+        S.T = Tn;
+        S.last = (int32_t)(i + 1);
+    }
+    emit_leaf(w, &S);
+}
+
+static void walk_pixel(walk_t *w, int px, int py, const int32_t *list, const uint8_t *unc, int64_t len)
+{
+    w->pxc = px + 0.5;
+    w->pyc = py + 0.5;
+    w->list = list;
+    w->unc = unc;
+    w->len = len;
+    w->nleaves = 0;
+    w->overflow = 0;
+    wstate_t S;
+    S.T = 1.0;
+    S.C[0] = S.C[1] = S.C[2] = 0.0;
+    S.last = 0;
+    S.nrec = 0;
+    walk(w, 0, S);
+}
+
+/* forward leaves of a window */
+typedef struct {
+    int L;
+    double *C, *T;
+    int32_t *nc;
+    const double *bg;
+    int64_t p;  /* window pixel index */
+} fleaf_t;
+
+static void fwd_leaf(walk_t *w, int index, const wstate_t *S)
+{
+    fleaf_t *f = w->user;
+    int64_t o = f->p * f->L + index;
+    for (int ch = 0; ch < 3; ++ch) f->C[3 * o + ch] = S->C[ch] + S->T * f->bg[ch];
+    f->T[o] = S->T;
+    f->nc[o] = S->last;
+}
+
+static int64_t max_tile_len(const int32_t *tile_start, int n_tiles)
+{
+    int64_t m = 0;
+    for (int t = 0; t < n_tiles; ++t)
+        if (tile_start[t + 1] - tile_start[t] > m) m = tile_start[t + 1] - tile_start[t];
+    return m;
+}
+
+/* Every leaf of every pixel of the window [x0,x1) x [y0,y1) (clipped to the image). Window
+ * pixel p = (y - y0) * (x1 - x0) + (x - x0) gets nleaf[p] leaves (0 when there are more than
+ * max_leaves: the pixel cannot be checked) with colour (background included) C[p][l][3],
+ * T_final T[p][l] and n_contrib nc[p][l]. unc may be NULL (all members certain). */
+int orc_render_leaves(int W, int H, int tw, int th, const double *mean2d, const double *conic,
+                      const double *color, const double *opacity, const int32_t *ids, const uint8_t *unc,
+                      const int32_t *tile_start, const double *bg, const double *margins, int x0, int y0,
+                      int x1, int y1, int max_leaves, int32_t *nleaf, double *C, double *T, int32_t *nc)
+{
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int64_t maxlen = max_tile_len(tile_start, gx * gy);
+    walk_t w;
+    memset(&w, 0, sizeof w);
+    w.mean2d = mean2d; w.conic = conic; w.color = color; w.opacity = opacity; w.mg = margins;
+    w.max_leaves = max_leaves;
+    w.rec = malloc(sizeof(brec_t) * (maxlen ? maxlen : 1));
+    w.leaf = fwd_leaf;
+    fleaf_t f = {max_leaves, C, T, nc, bg, 0};
+    w.user = &f;
+    int ww = x1 - x0;
+    for (int py = y0; py < y1 && py < H; ++py)
+        for (int px = x0; px < x1 && px < W; ++px) {
+            int t = (py / th) * gx + px / tw;
+            f.p = (int64_t)(py - y0) * ww + (px - x0);
+            walk_pixel(&w, px, py, ids + tile_start[t], unc ? unc + tile_start[t] : NULL,
+                       tile_start[t + 1] - tile_start[t]);
+            nleaf[f.p] = w.overflow ? 0 : w.nleaves;
+        }
+    free(w.rec);
+    return 0;
+}
+
+/* Backward envelope: the textbook reverse-order adjoint (as orc_render_bwd) of every leaf
+ * that admissible[p] (bit l = leaf l) lists, per window pixel. Per Gaussian and each of the
+ * 12 grad2d components (u, v, conic a, b, c, opacity, r, g, b, 0, 0, 0) lo/hi receive the
+ * sum over pixels of the smallest / largest contribution among that pixel's admissible
+ * leaves (a Gaussian absent from a leaf contributes 0 there), and absmax the sum over
+ * pixels of the largest, over its admissible leaves, absolute per-pixel term: every value a
+ * consistent choice of one admissible leaf per pixel can produce lies in [lo, hi]. */
+typedef struct {
+    const uint64_t *adm;
+    int64_t p;
+    const double *gC;  /* dL/dC of the pixel */
+    const double *bg, *conic, *color;
+    /* per list position: current leaf's terms, running min/max/absmax, last leaf seen */
+    double *cur, *mn, *mx, *ab;
+    int32_t *seen;     /* leaf count (1-based) at the last update of the position, 0 = never */
+    int64_t *touched;
+    int64_t ntouched;
+    int32_t *gid;
+    int nadm;          /* admissible leaves folded so far for this pixel */
+} bleaf_t;
+
+static void bwd_leaf(walk_t *w, int index, const wstate_t *S)
+{
+    bleaf_t *b = w->user;
+    if (index >= 64 || !((b->adm[b->p] >> index) & 1)) return;
+    const double *gC = b->gC;
+    double B[3] = {b->bg[0], b->bg[1], b->bg[2]};
+    int k = ++b->nadm;
+    for (int64_t r = S->nrec - 1; r >= 0; --r) {
+        const brec_t *e = w->rec + r;
+        int32_t g = e->g;
+        const double *c = b->color + 3 * g;
+        double t[12] = {0};
+        double dalpha = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            t[6 + ch] = e->alpha * e->T * gC[ch];
+            dalpha += e->T * (c[ch] - B[ch]) * gC[ch];
+            B[ch] = e->alpha * c[ch] + (1.0 - e->alpha) * B[ch];
+        }
+        if (!e->clamped) {
+            const double *cn = b->conic + 3 * g;
+            double dsig = -dalpha * e->alpha;
+            t[5] = dalpha * e->G;
+            t[2] = dsig * 0.5 * e->dx * e->dx;
+            t[3] = dsig * e->dx * e->dy;
+            t[4] = dsig * 0.5 * e->dy * e->dy;
+            t[0] = dsig * (cn[0] * e->dx + cn[1] * e->dy);
+            t[1] = dsig * (cn[1] * e->dx + cn[2] * e->dy);
+        }
+        int64_t pos = e->pos;
+        double *cur = b->cur + 12 * pos;
+        for (int j = 0; j < 12; ++j) cur[j] = t[j];
+        if (b->seen[pos] == 0) {
+            /* first time in this pixel: earlier admissible leaves had it absent (0) */
+            b->touched[b->ntouched++] = pos;
+            b->gid[pos] = g;
+            for (int j = 0; j < 12; ++j) {
+                b->mn[12 * pos + j] = k > 1 ? fmin(0.0, t[j]) : t[j];
+                b->mx[12 * pos + j] = k > 1 ? fmax(0.0, t[j]) : t[j];
+                b->ab[12 * pos + j] = fabs(t[j]);
+            }
+        } else {
+            for (int j = 0; j < 12; ++j) {
+                b->mn[12 * pos + j] = fmin(b->mn[12 * pos + j], t[j]);
+                b->mx[12 * pos + j] = fmax(b->mx[12 * pos + j], t[j]);
+                b->ab[12 * pos + j] = fmax(b->ab[12 * pos + j], fabs(t[j]));
+            }
+        }
+        b->seen[pos] = k;
+    }
+    /* positions of earlier leaves absent from this one contribute 0 here */
+    for (int64_t m = 0; m < b->ntouched; ++m) {
+        int64_t pos = b->touched[m];
+        if (b->seen[pos] == k) continue;
+        for (int j = 0; j < 12; ++j) {
+            b->mn[12 * pos + j] = fmin(b->mn[12 * pos + j], 0.0);
+            b->mx[12 * pos + j] = fmax(b->mx[12 * pos + j], 0.0);
+        }
+        b->seen[pos] = k;
+    }
+}
+
+int orc_render_bwd_envelope(int W, int H, int tw, int th, const double *mean2d, const double *conic,
+                            const double *color, const double *opacity, const int32_t *ids,
+                            const uint8_t *unc, const int32_t *tile_start, const double *bg,
+                            const double *margins, int x0, int y0, int x1, int y1, int max_leaves,
+                            const uint64_t *admissible, const double *dL_drgb, double *lo, double *hi,
+                            double *absmax)
+{
+    int gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int64_t HW = (int64_t)W * H;
+    int64_t maxlen = max_tile_len(tile_start, gx * gy);
+    int64_t m1 = maxlen ? maxlen : 1;
+    walk_t w;
+    memset(&w, 0, sizeof w);
+    w.mean2d = mean2d; w.conic = conic; w.color = color; w.opacity = opacity; w.mg = margins;
+    w.max_leaves = max_leaves;
+    w.rec = malloc(sizeof(brec_t) * m1);
+    w.leaf = bwd_leaf;
+    bleaf_t b;
+    memset(&b, 0, sizeof b);
+    b.adm = admissible; b.bg = bg; b.conic = conic; b.color = color;
+    b.cur = malloc(sizeof(double) * 12 * m1);
+    b.mn = malloc(sizeof(double) * 12 * m1);
+    b.mx = malloc(sizeof(double) * 12 * m1);
+    b.ab = malloc(sizeof(double) * 12 * m1);
+    b.seen = calloc((size_t)m1, sizeof(int32_t));
+    b.touched = malloc(sizeof(int64_t) * m1);
+    b.gid = malloc(sizeof(int32_t) * m1);
+    w.user = &b;
+    int ww = x1 - x0;
+    for (int py = y0; py < y1 && py < H; ++py)
+        for (int px = x0; px < x1 && px < W; ++px) {
+            int64_t p = (int64_t)py * W + px;
+            double gC[3] = {dL_drgb[p], dL_drgb[HW + p], dL_drgb[2 * HW + p]};
+            b.p = (int64_t)(py - y0) * ww + (px - x0);
+            if (admissible[b.p] == 0) continue;
+            if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;
+            int t = (py / th) * gx + px / tw;
+            b.gC = gC;
+            b.nadm = 0;
+            b.ntouched = 0;
+            walk_pixel(&w, px, py, ids + tile_start[t], unc ? unc + tile_start[t] : NULL,
+                       tile_start[t + 1] - tile_start[t]);
+            for (int64_t m = 0; m < b.ntouched; ++m) {
+                int64_t pos = b.touched[m];
+                int32_t g = b.gid[pos];
+                for (int j = 0; j < 12; ++j) {
+                    lo[12 * g + j] += b.mn[12 * pos + j];
+                    hi[12 * g + j] += b.mx[12 * pos + j];
+                    absmax[12 * g + j] += b.ab[12 * pos + j];
+                }
+                b.seen[pos] = 0;
+            }
+        }
+    free(w.rec);
+    free(b.cur); free(b.mn); free(b.mx); free(b.ab); free(b.seen); free(b.touched); free(b.gid);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ public: projection backward
  *
  * Chain rule from dL/d(mean2d, conic, colour, opacity) of one view to the raw parameters.
@@ -757,7 +1246,7 @@ int orc_project_bwd(int64_t n, const double *means, const double *log_scales, co
         proj_t P;
         const double *mu = means + 3 * g;
         project_one(mu, log_scales + 3 * g, quats + 4 * g, logits[g], sh + 48 * g, degree,
-                    crop ? crop[g] == 0 : 0, &k, tw, th, mg, &P);
+                    crop ? crop[g] == 0 : 0, &k, tw, th, mg, g_vis_flip ? g_vis_flip[g] : 0, &P);
         if (!P.visible) continue;
         double gmu[3] = {0, 0, 0};
         /* opacity */
@@ -768,7 +1257,9 @@ int orc_project_bwd(int64_t n, const double *means, const double *log_scales, co
         orc_sh_basis(degree, P.n, Y, dY);
         double dn[3] = {0, 0, 0};
         for (int ch = 0; ch < 3; ++ch) {
-            if (P.color_raw[ch] < 0.0) continue;
+            int clamped = P.color_raw[ch] < 0.0;
+            if (g_color_flip && ((g_color_flip[g] >> ch) & 1)) clamped = !clamped;
+            if (clamped) continue;
             double dc = d_color[3 * g + ch];
             for (int b = 0; b < nb; ++b) {
                 g_sh[48 * g + 3 * b + ch] += Y[b] * dc;
@@ -881,7 +1372,7 @@ int orc_visibility_crop(int64_t n, const double *means, const double *log_scales
     for (int64_t g = 0; g < n; ++g) {
         proj_t P;
         project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], sh + 48 * g, degree, 0,
-                    &k, tw, th, mg, &P);
+                    &k, tw, th, mg, 0, &P);
         if (P.visible) mask[g] = 1;
     }
     return 0;
