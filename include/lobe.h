@@ -222,6 +222,8 @@ const char *lobe_last_error(const lobe_ctx *ctx);
 lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect, int64_t max_tiles);
 /* Synchronises the stream, returns and clears the latched device status. */
 lobe_status lobe_get_status(lobe_ctx *ctx);
+/* The same call under the name of the scope table's boundary. */
+lobe_status lobe_sync_status(lobe_ctx *ctx);
 
 /* EWA projection + SH colour + culling (near/far, 1.3x fov guard, crop mask, empty
  * rectangle) of every (item, Gaussian). Writes `out` for all entries. */
@@ -289,6 +291,14 @@ lobe_status lobe_render_depth(lobe_ctx *ctx, const lobe_batch *batch, const lobe
 lobe_status lobe_fcs_coverage(lobe_ctx *ctx, const lobe_batch *batch, const lobe_image *image, const float *depth,
                               const lobe_aabb *blocks, int32_t n_blocks, int32_t normalize, uint32_t *counts,
                               uint32_t *n_points);
+
+/* Camera assignment of fast camera selection (Sec. 3.2, the visibility ratio and its threshold
+ * tau): V[c][b] = counts[c][b] / n_points[c] (0 when the camera has no point) and assign[c][b]
+ * = (V >= tau), for n_items cameras and n_blocks blocks; the paper uses tau = 0.1. HOST arrays
+ * (the counts of lobe_fcs_coverage copied back), row-major [n_items][n_blocks]; plain host
+ * code, no device work. LOBE_ERR_ARG on a null array or negative size. */
+lobe_status lobe_fcs_select(const uint32_t *counts, const uint32_t *n_points, int32_t n_items, int32_t n_blocks,
+                            double tau, double *V, uint8_t *assign);
 
 /* Selective densification (Sec. 3.3) with 3DGS adaptive density control: classifies every
  * Gaussian of `set` (prune / clone / split / keep, see lobe_densify_params) from its SD
@@ -386,6 +396,14 @@ lobe_status lobe_project_bwd_adam(lobe_ctx *ctx, const lobe_batch *batch, const 
  * (passes the culling rules, crop mask ignored) from at least one item of that set.
  * masks[s] are device pointers (uint8 [n]); they are OR-ed into, not cleared. */
 lobe_status lobe_visibility_crop(lobe_ctx *ctx, const lobe_batch *batch, uint8_t *const *masks);
+
+/* Throughput probe of one instruction kind (a measurement helper, not part of the method):
+ * `blocks` blocks of 256 threads, each thread running eight independent chains of `iters`
+ * steps of kind 0 = scalar fma.rn.f32 (2 FLOP), 1 = packed fma.rn.f32x2 (4 FLOP), 2 =
+ * ex2.approx.f32 (1 op), asynchronously on `stream`. Per launch: blocks * 256 * 8 * iters
+ * steps. sink (device, >= 256 floats) is written only in an impossible case. The compositing
+ * kernels' rooflines are taken against the rates these reach. */
+lobe_status lobe_peak_probe(void *stream, int32_t kind, int32_t blocks, int32_t iters, float *sink);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,23 @@ MARGINS_STAGE = np.array([2e-5, 1e-4, 2e-6, 1e-6, 1e-5, 1e-6])
 # end to end: the GPU's float32 projection feeds its renderer
 MARGINS_E2E = np.array([5e-4, 2e-3, 2e-5, 2e-5, 1e-4, 2e-5])
 
-F_GUARD, F_RADIUS, F_RECT, F_COLOR = 1, 2, 4, 8
+F_GUARD, F_RADIUS, F_RECT, F_COLOR, F_GUARD_OUT = 1, 2, 4, 8, 16
+
+
+def marginal_visibility(p: "Projection") -> np.ndarray:
+    """Gaussians whose culling decision float32 may take the other way: a marginal fov-guard
+    decision, or (not culled by the guard) a marginal radius / rectangle edge, which may make
+    the tile rectangle empty or not at the image border."""
+    g = (p.flags & F_GUARD) != 0
+    r = ((p.flags & (F_RADIUS | F_RECT)) != 0) & ((p.flags & F_GUARD_OUT) == 0)
+    return (g | r) & (p.radius_all > 0)
+
+
+def marginal_rect(p: "Projection") -> np.ndarray:
+    """Gaussians whose tile rectangle a marginal decision may change (as orc_bin_ext reads it)."""
+    m = (p.flags & F_GUARD) != 0
+    m |= ((p.flags & (F_RADIUS | F_RECT)) != 0) & ((p.flags & F_GUARD_OUT) == 0)
+    return m & (p.radius_all > 0)
 
 
 def build(force: bool = False) -> str:
@@ -105,6 +121,7 @@ class Projection:
     rect: np.ndarray
     flags: np.ndarray
     radius_all: np.ndarray
+    color_raw: np.ndarray | None = None  # [n,3] SH colour + 0.5 before the clamp at 0
 
     @property
     def n(self):
@@ -115,7 +132,7 @@ class Projection:
         r = lambda a: a.astype(np.float32).astype(np.float64)
         return Projection(r(self.mean2d), r(self.conic), r(self.color), r(self.opacity),
                           self.depth.copy(), self.radius.copy(), self.rect.copy(), self.flags.copy(),
-                          self.radius_all.copy())
+                          self.radius_all.copy(), None if self.color_raw is None else self.color_raw.copy())
 
 
 def project(g, cam, tile=(16, 16), sh_degree=3, crop=None, margins=MARGINS_NONE) -> Projection:
@@ -131,12 +148,12 @@ def project(g, cam, tile=(16, 16), sh_degree=3, crop=None, margins=MARGINS_NONE)
     mg, pmg = _d(margins)
     out = Projection(np.zeros((n, 2)), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n), np.zeros(n),
                      np.zeros(n, np.int32), np.zeros((n, 4), np.int32), np.zeros(n, np.int32),
-                     np.zeros(n, np.int32))
+                     np.zeros(n, np.int32), np.zeros((n, 3)))
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     L.orc_project(ctypes.c_int64(n), pm, pls, pq, plo, psh, ctypes.c_int(sh_degree), pcr, pcv,
                   ctypes.c_int(tile[0]), ctypes.c_int(tile[1]), pmg,
                   ptr(out.mean2d), ptr(out.conic), ptr(out.color), ptr(out.opacity), ptr(out.depth),
-                  ptr(out.radius), ptr(out.rect), ptr(out.flags), ptr(out.radius_all))
+                  ptr(out.radius), ptr(out.rect), ptr(out.flags), ptr(out.radius_all), ptr(out.color_raw))
     return out
 
 
@@ -428,7 +445,8 @@ class ExtBins:
 
 
 def bin_ext(p: Projection, cam, tile=(16, 16), win=None) -> ExtBins:
-    """Extended per-tile lists of the tiles touching ``win`` = (x0, y0, x1, y1) (None: all):
+    """Extended per-tile lists of the tiles touching ``win`` = (x0, y0, x1, y1) (None: the
+    sampling window(s) in effect, by default the whole image):
     the certain members as ``bin_sort`` lists them, plus the Gaussians whose membership a
     marginal radius, rectangle or guard decision (``p.flags``) could flip."""
     L = lib()
@@ -441,7 +459,8 @@ def bin_ext(p: Projection, cam, tile=(16, 16), win=None) -> ExtBins:
     dp, _ = _d(p.depth)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     gx, gy = grid(c, tile)
-    with window(*(win or (0, 0, 1 << 30, 1 << 30))):
+    ctx = window(*win) if win is not None else _NoWindowChange()
+    with ctx:
         total = L.orc_bin_ext(ctypes.c_int64(p.n), ptr(m2), ptr(r), ptr(ra), ptr(fl), ptr(dp), W, H, tile[0],
                               tile[1], None, None, None)
         ids = np.zeros(max(total, 1), np.int32)
@@ -450,6 +469,14 @@ def bin_ext(p: Projection, cam, tile=(16, 16), win=None) -> ExtBins:
         L.orc_bin_ext(ctypes.c_int64(p.n), ptr(m2), ptr(r), ptr(ra), ptr(fl), ptr(dp), W, H, tile[0], tile[1],
                       ptr(ids), ptr(unc), ptr(ts))
     return ExtBins(ids[:total], unc[:total], ts)
+
+
+class _NoWindowChange:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
 
 
 @dataclass
@@ -590,6 +617,24 @@ class window:
 
     def __enter__(self):
         lib().orc_set_window(*self.w)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_window(0, 0, 1 << 30, 1 << 30)
+
+
+class windows:
+    """Context manager restricting bin/render/render_bwd (and bin_ext) to the union of several
+    pixel windows [(x0, y0, x1, y1), ...] (at most 64): tiles touching any of them, pixels
+    inside any of them. Changes no arithmetic."""
+
+    def __init__(self, rects):
+        self.r = np.ascontiguousarray(np.asarray(rects, np.int32).reshape(-1, 4))
+        if not 1 <= len(self.r) <= 64:
+            raise ValueError("1 to 64 windows")
+
+    def __enter__(self):
+        lib().orc_set_windows(len(self.r), self.r.ctypes.data_as(ctypes.c_void_p))
         return self
 
     def __exit__(self, *exc):

@@ -62,6 +62,7 @@ enum {
     F_RADIUS = 2,  /* ceil(3 sqrt(lambda)) marginal */
     F_RECT = 4,    /* a rectangle edge within M_PX of a tile boundary */
     F_COLOR = 8,   /* colour clamp marginal (gradient mask) */
+    F_GUARD_OUT = 16, /* culled by the fov guard (whether or not that decision is marginal) */
 };
 
 /* ------------------------------------------------------------------ small helpers */
@@ -313,6 +314,7 @@ static void project_one(const double *mu, const double *ls, const double *q, dou
     /* the guard decision is applied at the end so that a culled Gaussian still carries
      * the radius and rectangle it would have had (used to flag marginal pixels) */
     int guard_out = fabs(txz) > limx || fabs(tyz) > limy;
+    if (guard_out) P->flags |= F_GUARD_OUT;
 
     /* 3D covariance Sigma = R S S^T R^T */
     P->qnorm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -401,7 +403,7 @@ int orc_project(int64_t n, const double *means, const double *log_scales, const 
                 const double *logits, const double *sh, int degree, const uint8_t *crop,
                 const double *camv, int tw, int th, const double *margins,
                 double *mean2d, double *conic, double *color, double *opacity, double *depth,
-                int32_t *radius, int32_t *rect, int32_t *flags, int32_t *radius_all)
+                int32_t *radius, int32_t *rect, int32_t *flags, int32_t *radius_all, double *color_raw)
 {
     cam_t k;
     load_cam(camv, &k);
@@ -421,6 +423,8 @@ int orc_project(int64_t n, const double *means, const double *log_scales, const 
         for (int i = 0; i < 4; ++i) rect[4 * g + i] = P.visible ? P.rect[i] : 0;
         flags[g] = P.flags;
         if (radius_all) radius_all[g] = P.radius;
+        if (color_raw)
+            for (int i = 0; i < 3; ++i) color_raw[3 * g + i] = P.color_raw[i];
     }
     return 0;
 }
@@ -431,10 +435,41 @@ int orc_project(int64_t n, const double *means, const double *log_scales, const 
  * (pairs of tiles outside the window are not emitted, pixels outside are not touched).
  * Default: no restriction. It changes no arithmetic. */
 static int g_win[4] = {0, 0, 1 << 30, 1 << 30};
+/* Optionally several windows at once (tiles and pixels inside any of them); g_win is then
+ * their bounding box. At most ORC_MAX_WINDOWS. */
+#define ORC_MAX_WINDOWS 64
+static int g_nwin = 0;
+static int g_wins[ORC_MAX_WINDOWS][4];
 
 void orc_set_window(int x0, int y0, int x1, int y1)
 {
     g_win[0] = x0; g_win[1] = y0; g_win[2] = x1; g_win[3] = y1;
+    g_nwin = 0;
+}
+
+int orc_set_windows(int n, const int32_t *rects)
+{
+    if (n < 1 || n > ORC_MAX_WINDOWS) return -1;
+    g_nwin = n;
+    g_win[0] = g_win[1] = 1 << 30;
+    g_win[2] = g_win[3] = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < 4; ++j) g_wins[i][j] = rects[4 * i + j];
+        if (rects[4 * i] < g_win[0]) g_win[0] = rects[4 * i];
+        if (rects[4 * i + 1] < g_win[1]) g_win[1] = rects[4 * i + 1];
+        if (rects[4 * i + 2] > g_win[2]) g_win[2] = rects[4 * i + 2];
+        if (rects[4 * i + 3] > g_win[3]) g_win[3] = rects[4 * i + 3];
+    }
+    return 0;
+}
+
+/* the pixel lies in the sampling window(s) */
+static int pixel_in_window(int px, int py)
+{
+    if (g_nwin == 0) return 1;
+    for (int i = 0; i < g_nwin; ++i)
+        if (px >= g_wins[i][0] && px < g_wins[i][2] && py >= g_wins[i][1] && py < g_wins[i][3]) return 1;
+    return 0;
 }
 
 /* Optional per-Gaussian sums of the absolute values of the per-pixel terms that
@@ -446,7 +481,13 @@ void orc_set_abs_out(double *a12) { g_abs = a12; }
 
 static int tile_in_window(int tx, int ty, int tw, int th)
 {
-    return (tx + 1) * tw > g_win[0] && tx * tw < g_win[2] && (ty + 1) * th > g_win[1] && ty * th < g_win[3];
+    if (g_nwin == 0)
+        return (tx + 1) * tw > g_win[0] && tx * tw < g_win[2] && (ty + 1) * th > g_win[1] && ty * th < g_win[3];
+    for (int i = 0; i < g_nwin; ++i)
+        if ((tx + 1) * tw > g_wins[i][0] && tx * tw < g_wins[i][2] && (ty + 1) * th > g_wins[i][1] &&
+            ty * th < g_wins[i][3])
+            return 1;
+    return 0;
 }
 
 /* ------------------------------------------------------------------ public: bin + sort */
@@ -603,6 +644,7 @@ int orc_render_fwd(int W, int H, int tw, int th, const double *mean2d, const dou
     int64_t HW = (int64_t)W * H;
     for (int py = g_win[1]; py < H && py < g_win[3]; ++py)
         for (int px = g_win[0]; px < W && px < g_win[2]; ++px) {
+            if (!pixel_in_window(px, py)) continue;
             int t = (py / th) * gx + px / tw;
             double C[3], T, ws;
             int32_t nc;
@@ -706,6 +748,7 @@ int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const dou
     contrib_t *rec = malloc(sizeof(contrib_t) * (maxlen ? maxlen : 1));
     for (int py = g_win[1]; py < H && py < g_win[3]; ++py)
         for (int px = g_win[0]; px < W && px < g_win[2]; ++px) {
+            if (!pixel_in_window(px, py)) continue;
             int64_t p = (int64_t)py * W + px;
             double gC[3] = {dL_drgb[p], dL_drgb[HW + p], dL_drgb[2 * HW + p]};
             if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;
@@ -783,11 +826,21 @@ int orc_render_bwd(int W, int H, int tw, int th, const double *mean2d, const dou
  * rectangle or guard decision). unc[k] = 0 certain, 1 uncertain and outside the FP64
  * rectangle, 2 uncertain and inside it. Lists in (tile, fp32 depth, index) order as orc_bin;
  * tile_start as orc_bin. Returns the number of entries; with ids == NULL it only counts. */
+/* Whether a marginal decision can change a Gaussian's tile rectangle: a marginal guard
+ * decision, or a marginal radius / rectangle edge unless the fov guard culls it anyway. */
+static int ext_marginal(int32_t flags, int32_t radius_all)
+{
+    if (radius_all <= 0) return 0;
+    if (flags & F_GUARD) return 1;
+    if (flags & F_GUARD_OUT) return 0;
+    return (flags & (F_RADIUS | F_RECT)) != 0;
+}
+
 static int ext_member(int64_t g, int tx, int ty, const double *mean2d, const int32_t *radius,
                       const int32_t *radius_all, const int32_t *gflags, int tw, int th, int gx, int gy)
 {
     /* -1: not a member; 0 certain; 1 uncertain, outside the FP64 rectangle; 2 uncertain, inside */
-    int marg = (gflags[g] & (F_GUARD | F_RADIUS | F_RECT)) && radius_all[g] > 0;
+    int marg = ext_marginal(gflags[g], radius_all[g]);
     int own[4] = {0, 0, 0, 0};
     if (radius[g] > 0) tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius[g], tw, th, gx, gy, own);
     int in_own = tx >= own[0] && tx < own[2] && ty >= own[1] && ty < own[3];
@@ -811,7 +864,7 @@ int64_t orc_bin_ext(int64_t n, const double *mean2d, const int32_t *radius, cons
     for (int pass = 0; pass < 2; ++pass) {
         int64_t k = 0;
         for (int64_t g = 0; g < n; ++g) {
-            int marg = (gflags[g] & (F_GUARD | F_RADIUS | F_RECT)) && radius_all[g] > 0;
+            int marg = ext_marginal(gflags[g], radius_all[g]);
             if (!marg && radius[g] <= 0) continue;
             int r[4];
             tile_rect(mean2d[2 * g], mean2d[2 * g + 1], marg ? radius_all[g] + 1 : radius[g], tw, th, gx, gy, r);

@@ -100,6 +100,9 @@ class AdamState(ctypes.Structure):
 # name -> (restype, argtypes); the exported symbols of liblobe.so (checked by the tests)
 SIGNATURES = {
     "lobe_abi_version": (ctypes.c_int32, []),
+    "lobe_peak_probe": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp]),
+    "lobe_sync_status": (ctypes.c_int, [vp]),
+    "lobe_fcs_select": (ctypes.c_int, [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp]),
     "lobe_kernel_launches": (ctypes.c_int64, []),
     "lobe_batch_sizes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Batch), ctypes.POINTER(ctypes.c_int64)]),
     "lobe_ctx_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, ctypes.POINTER(Config)]),

@@ -334,6 +334,23 @@ lobe_status lobe_get_status(lobe_ctx *ctx)
     return LOBE_OK;
 }
 
+lobe_status lobe_sync_status(lobe_ctx *ctx) { return lobe_get_status(ctx); }
+
+lobe_status lobe_fcs_select(const uint32_t *counts, const uint32_t *n_points, int32_t n_items, int32_t n_blocks,
+                            double tau, double *V, uint8_t *assign)
+{
+    if (n_items < 0 || n_blocks < 0 || (n_items > 0 && n_blocks > 0 && (!counts || !n_points || !V || !assign)))
+        return LOBE_ERR_ARG;
+    for (int32_t c = 0; c < n_items; ++c)
+        for (int32_t b = 0; b < n_blocks; ++b) {
+            const int64_t k = (int64_t)c * n_blocks + b;
+            const double np = n_points[c] > 0 ? (double)n_points[c] : 1.0;
+            V[k] = (double)counts[k] / np;
+            assign[k] = V[k] >= tau ? 1 : 0;
+        }
+    return LOBE_OK;
+}
+
 lobe_status lobe_selftest_wait(lobe_ctx *ctx)
 {
     if (!ctx) return LOBE_ERR_ARG;

@@ -297,8 +297,18 @@ __device__ __forceinline__ SlabBox slab_box(int tx, int ty, int warp)
     return b;
 }
 
+#ifndef LOBE_FWD_REGS
+#define LOBE_FWD_REGS 0  // 0: no cap beyond the compiler's choice
+#endif
+// Resident blocks an SM must fit for a register cap of `regs` a thread (0: no cap), at most
+// the 32 blocks an SM holds.
+constexpr int min_blocks_for(int regs, int warps)
+{
+    return regs > 0 ? (65536 / (regs * 32 * warps) < 32 ? 65536 / (regs * 32 * warps) : 32) : 1;
+}
+
 template <int TW, int TH, int PX, bool DEPTH>
-__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(LOBE_FWD_REGS, Slab<TW, TH, PX>::WARPS))
     k_render_fwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                  const int *__restrict__ tile_start, const int *__restrict__ ids, float *__restrict__ rgb,
                  float *__restrict__ Tout, int *__restrict__ ncout, float *__restrict__ depth)
@@ -519,9 +529,13 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 // the same rounding); a pixel of the pair that does not use the splat gets G = 0, hence
 // alpha = 0, which leaves its T, B and every gradient term unchanged.
 
-// At most 128 registers a thread (occupancy: the kernel is latency- as much as issue-bound).
+// At most LOBE_BWD_REGS registers a thread (occupancy: the kernel is latency- as much as
+// issue-bound).
+#ifndef LOBE_BWD_REGS
+#define LOBE_BWD_REGS 128
+#endif
 template <int TW, int TH, int PX, bool RECOMPUTE>
-__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, 65536 / (128 * 32 * Slab<TW, TH, PX>::WARPS))
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(LOBE_BWD_REGS, Slab<TW, TH, PX>::WARPS))
     k_render_bwd2(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                   const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
                   const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)

@@ -434,8 +434,15 @@ def project_bwd_adam(ctx: Context, batch: Batch, proj: Projection, grad2d: torch
 def fcs_select(counts: torch.Tensor, n_points: torch.Tensor, tau: float = 0.1):
     """The paper's assignment C(b) = {c : V(c, b) >= tau}: returns (V [items, blocks], list of
     item indices per block)."""
-    V = counts.double() / n_points.clamp(min=1).double()[:, None]
-    return V, [torch.nonzero(V[:, b] >= tau).flatten().tolist() for b in range(V.shape[1])]
+    import numpy as np
+    c = np.ascontiguousarray(counts.detach().cpu().numpy(), dtype=np.uint32)
+    n = np.ascontiguousarray(n_points.detach().cpu().numpy(), dtype=np.uint32)
+    items, blocks = c.shape
+    V = np.zeros((items, blocks), np.float64)
+    assign = np.zeros((items, blocks), np.uint8)
+    A.check(A.lib().lobe_fcs_select(c.ctypes.data, n.ctypes.data, items, blocks, float(tau), V.ctypes.data,
+                                    assign.ctypes.data))
+    return torch.as_tensor(V), [np.nonzero(assign[:, b])[0].tolist() for b in range(blocks)]
 
 
 def render_bwd(ctx: Context, batch: Batch, proj: Projection, bins: Bins, image: Image | None,

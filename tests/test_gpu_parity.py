@@ -2,9 +2,11 @@
 
 Stage tests feed every GPU stage the oracle's own upstream result rounded to float32, so
 the comparison isolates one kernel's arithmetic; end-to-end tests chain the GPU stages.
-Pixels (and, for gradients, their dL/dC) whose compositing decisions are marginal under
-float32 (alpha at 1/255, T at 1e-4, the 0.99 clamp, a radius or rectangle edge at a
-boundary) are excluded; their count is bounded in each test.
+Where float32 may take a decision either way (alpha at 1/255, T at 1e-4, the 0.99 clamp,
+sigma < 0, a radius, rectangle edge or fov guard at its boundary, the colour clamp) the
+oracle enumerates every outcome: each GPU pixel must match one of its pixel's admissible
+results, and the gradients must lie in the envelope of the adjoints of the outcomes the
+GPU's own forward matched (tests/helpers.py). No pixel or Gaussian is left out.
 """
 import math
 
@@ -14,7 +16,8 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import (IMG_ATOL, assert_grad_close, assert_img_close, oracle_grad2d_array, rect_of,
+from tests.helpers import (IMG_ATOL, add_envelopes, assert_envelope, assert_grad_close, assert_params_in_envelope,
+                           check_lists_admissible, match_image, oracle_grad2d_array, param_envelope, rect_of,
                            rect_tiles, splat_array)
 
 pytestmark = pytest.mark.gpu
@@ -50,8 +53,6 @@ def ctx_for(wl, **kw):
     return lobe.Context(tile=wl.tile, **kw)
 
 
-# ----------------------------------------------------------------------------- project
-
 @pytest.mark.parametrize("posed", [False, True])
 def test_project_matches_oracle(small, posed):
     wl, g = small
@@ -66,18 +67,27 @@ def test_project_matches_oracle(small, posed):
     p = oracle.project(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
     rad = proj.radius.cpu().numpy()
     s = proj.splat.cpu().numpy().astype(np.float64)
-    marg = (p.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) != 0
-    ok = ~marg
-    np.testing.assert_array_equal(rad[ok], p.radius[ok])
-    vis = ok & (p.radius > 0)
+    check_projection_admissible(p, rad, s, proj.tiles.cpu().numpy(), cam, wl.tile)
+
+
+def check_projection_admissible(p, rad, s, tiles, cam, tile):
+    """Radius, culling and tile count of every Gaussian: the oracle's, or (where its radius,
+    rectangle or guard decision is marginal) a radius within one of it or culled; the splat
+    values of every Gaussian the GPU keeps; the tile count of the GPU's own exact rectangle."""
+    marg = oracle.marginal_rect(p) | oracle.marginal_visibility(p)
+    np.testing.assert_array_equal(rad[~marg], p.radius[~marg])
+    alt_ok = (rad == p.radius) | (rad == 0) | (np.abs(rad - p.radius_all) <= 1)
+    assert np.all(alt_ok[marg]), "a marginal Gaussian's radius is outside the admissible set"
+    vis = rad > 0
     assert vis.sum() > 500
     np.testing.assert_allclose(s[vis, 0:2], p.mean2d[vis], rtol=1e-5, atol=2e-4)
     np.testing.assert_allclose(s[vis, 2:5], p.conic[vis], rtol=2e-4, atol=1e-7)
     np.testing.assert_allclose(s[vis, 5], p.opacity[vis], rtol=1e-5, atol=1e-7)
-    np.testing.assert_allclose(s[vis, 6:9], p.color[vis], atol=2e-5)
+    np.testing.assert_allclose(np.abs(s[vis, 6:9]), p.color[vis], atol=2e-5)
     # depth key: float32 rounding of the double-precision z, bit for bit
     np.testing.assert_array_equal(s[vis, 9].astype(np.float32), p.depth[vis].astype(np.float32))
-    tiles = proj.tiles.cpu().numpy()
+    np.testing.assert_array_equal(tiles, rect_tiles(s[:, 0:2], rad, cam, tile))
+    ok = ~marg
     np.testing.assert_array_equal(tiles[ok], np.where(p.radius[ok] > 0, (p.rect[ok, 2] - p.rect[ok, 0]) *
                                                       (p.rect[ok, 3] - p.rect[ok, 1]), 0))
 
@@ -93,22 +103,22 @@ def test_lower_sh_degrees_match_oracle(small, deg):
     proj = lobe.project(ctx, batch)
     p = oracle.project(g, cam, wl.tile, sh_degree=deg, margins=oracle.MARGINS_E2E)
     s = proj.splat.cpu().numpy().astype(np.float64)
-    ok = ((p.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) == 0) & (p.radius > 0)
+    rad = proj.radius.cpu().numpy()
+    ok = rad > 0
     assert ok.sum() > 500
     np.testing.assert_allclose(np.abs(s[ok, 6:9]), p.color[ok], atol=2e-5)
-    f = oracle.forward(g, cam, wl.tile, sh_degree=deg, margins=oracle.MARGINS_STAGE)
-    dL = np.random.default_rng(6).standard_normal((3, 128, 128)) * (f.pixel_flags == 0)[None]
+    f = oracle.forward(g, cam, wl.tile, sh_degree=deg)
+    dL = np.random.default_rng(6).standard_normal((3, 128, 128))
     g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
-    g2d_r = oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
-                            (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity)))
-    want = oracle.project_bwd(g, cam, g2d_r, wl.tile, sh_degree=deg)
-    grads = lobe.project_bwd(ctx, batch, proj, dev(oracle_grad2d_array(g2d_r)))
-    okg = (f.proj.flags == 0) & (f.proj.radius > 0)
+    g2d_r = oracle_grad2d_array(oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
+                                                (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity))))
+    env = param_envelope(g, cam, p, g2d_r, g2d_r, wl.tile, sh_degree=deg)
+    grads = lobe.project_bwd(ctx, batch, proj, dev(g2d_r))
     nb = (deg + 1) ** 2
     gsh = grads[0]["sh"].cpu().numpy()
-    assert_grad_close(gsh[okg, :nb], want.sh[okg, :nb], f"sh degree {deg}")
+    assert_envelope(gsh[:, :nb], env["sh"][0][:, :nb], env["sh"][1][:, :nb], f"sh degree {deg}")
     assert np.all(gsh[:, nb:] == 0)
-    assert_grad_close(grads[0]["means"].cpu().numpy()[okg], want.means[okg], f"means sh degree {deg}")
+    assert_envelope(grads[0]["means"].cpu().numpy(), env["means"][0], env["means"][1], f"means sh degree {deg}")
 
 
 # ----------------------------------------------------------------------------- bin + sort
@@ -225,7 +235,8 @@ def test_render_fwd_matches_oracle(small, tile):
     cam = wl.cameras[0].as_dict()
     p, ids, ts = stage_inputs(wl, g, cam)
     bg = (0.1, 0.2, 0.3)
-    img = oracle.render_fwd(p, ids, ts, cam, tile, bg, oracle.MARGINS_STAGE)
+    eb = oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts)
+    lv = oracle.render_leaves(p, eb, cam, tile, bg, oracle.MARGINS_STAGE, certain=True)
     ctx = ctx_for(wl, bg=bg)
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, tile)
@@ -234,11 +245,7 @@ def test_render_fwd_matches_oracle(small, tile):
     rgb = out.rgb.view(3, 128, 128).cpu().numpy()
     T = out.T_final.view(128, 128).cpu().numpy()
     nc = out.n_contrib.view(128, 128).cpu().numpy()
-    ok = img.flags == 0
-    assert ok.mean() > 0.99
-    assert_img_close(rgb[:, ok], img.rgb[:, ok], "image small (stage)")
-    assert_img_close(T[ok], img.T_final[ok], "T_final small (stage)")
-    np.testing.assert_array_equal(nc[ok], img.n_contrib[ok])
+    match_image(lv, rgb, T, nc, "image small (stage)")
 
 
 @pytest.mark.parametrize("recompute, tile, px", [(False, (16, 16), 0), (True, (16, 16), 0), (False, (16, 8), 1),
@@ -249,78 +256,74 @@ def test_render_bwd_matches_oracle(small, recompute, tile, px):
     cam = wl.cameras[0].as_dict()
     p, ids, ts = stage_inputs(wl, g, cam)
     bg = (0.1, 0.2, 0.3)
-    img = oracle.render_fwd(p, ids, ts, cam, wl.tile, bg, oracle.MARGINS_STAGE)
-    dL = np.random.default_rng(3).standard_normal((3, 128, 128)) * (img.flags == 0)[None]
-    dL = dL.astype(np.float32).astype(np.float64)
-    want = oracle_grad2d_array(oracle.render_bwd(p, ids, ts, cam, dL, wl.tile, bg))
+    eb = oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts)
+    lv = oracle.render_leaves(p, eb, cam, wl.tile, bg, oracle.MARGINS_STAGE, certain=True)
+    dL = np.random.default_rng(3).standard_normal((3, 128, 128)).astype(np.float32).astype(np.float64)
     ctx = ctx_for(wl, bg=bg, recompute_T=recompute, px_fwd=px, px_bwd=px)
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, wl.tile)
     bins = lobe.bin_sort(ctx, batch, gp)
     out = lobe.render_fwd(ctx, batch, gp, bins)
+    adm = match_image(lv, out.rgb.view(3, 128, 128).cpu().numpy(), out.T_final.view(128, 128).cpu().numpy(),
+                      out.n_contrib.view(128, 128).cpu().numpy(), "image small (stage, before the adjoint)")
+    lo, hi, _ = oracle.render_bwd_envelope(p, eb, cam, dL, adm, wl.tile, bg, oracle.MARGINS_STAGE, certain=True)
     g2d = lobe.render_bwd(ctx, batch, gp, bins, out, dev(dL).reshape(-1)).cpu().numpy()
     vis = p.radius > 0
     for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
                        ("color", slice(6, 9))]:
-        assert_grad_close(g2d[vis, cols], want[vis, cols], name)
+        assert_envelope(g2d[vis, cols], lo[vis, cols], hi[vis, cols], name)
     assert np.all(g2d[:, 9:] == 0)
 
 
 def test_project_bwd_matches_oracle(small):
     wl, g = small
     cam = wl.cameras[0].as_dict()
-    f = oracle.forward(g, cam, wl.tile, margins=oracle.MARGINS_STAGE)
-    dL = np.random.default_rng(4).standard_normal((3, 128, 128)) * (f.pixel_flags == 0)[None]
+    f = oracle.forward(g, cam, wl.tile)
+    dL = np.random.default_rng(4).standard_normal((3, 128, 128))
     box = scenes.AABB((-0.5, -0.5, -math.inf), (0.5, 0.5, math.inf))
     g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
-    g2d_r = oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
-                            (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity)))
-    want = oracle.project_bwd(g, cam, g2d_r, wl.tile, aabb=box)
+    g2d_r = oracle_grad2d_array(oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
+                                                (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity))))
+    p = oracle.project(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
+    env = param_envelope(g, cam, p, g2d_r, g2d_r, wl.tile, aabb=box)
     ctx = ctx_for(wl)
     wl2 = scenes.Workload(wl.name, wl.sets, wl.cameras, [box], wl.items, wl.tile)
     batch = make_batch(wl2)
     proj = lobe.project(ctx, batch)
     grads = lobe.zero_grads(batch)
-    lobe.project_bwd(ctx, batch, proj, dev(oracle_grad2d_array(g2d_r)), grads, accumulate=True)
+    lobe.project_bwd(ctx, batch, proj, dev(g2d_r), grads, accumulate=True)
     gr = {k: v.cpu().numpy() for k, v in grads[0].items()}
-    ok = (f.proj.flags == 0) & (f.proj.radius > 0)
-    for k in ("means", "log_scales", "quats", "opacity_logits"):
-        assert_grad_close(gr[k][ok], getattr(want, k)[ok], k)
-    assert_grad_close(gr["sh"][ok], want.sh[ok], "sh")
-    np.testing.assert_array_equal(gr["sd_cnt"][ok], want.sd_cnt[ok])
-    assert_grad_close(gr["sd_acc"][ok], want.sd_acc[ok], "sd_acc")
+    assert (env["sd_cnt"][0] > 0).sum() > 50
+    assert_params_in_envelope(gr, env, "project_bwd small (stage)")
 
-
-# ----------------------------------------------------------------------------- end to end
 
 @pytest.mark.parametrize("recompute", [False, True])
 def test_end_to_end_small(small, recompute):
     wl, g = small
     cam = wl.cameras[0].as_dict()
-    f = oracle.forward(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
-    ok_px = f.pixel_flags == 0
-    assert ok_px.mean() > 0.97, ok_px.mean()
+    p = oracle.project(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
+    eb = oracle.bin_ext(p, cam, wl.tile)
+    lv = oracle.render_leaves(p, eb, cam, wl.tile, margins=oracle.MARGINS_E2E)
     ctx = ctx_for(wl, recompute_T=recompute)
     batch = make_batch(wl)
     proj, bins, img = lobe.forward(ctx, batch)
     rgb = img.rgb.view(3, 128, 128).cpu().numpy()
-    assert_img_close(rgb[:, ok_px], f.image.rgb[:, ok_px], "image small (end to end)")
-    # sort order: per tile, identical lists once marginal Gaussians are removed
-    marg = (f.proj.flags & (oracle.F_GUARD | oracle.F_RADIUS | oracle.F_RECT)) != 0
-    gids = bins.ids().cpu().numpy()
-    gts = bins.tile_start.cpu().numpy()
-    for t in range(len(f.tile_start) - 1):
-        a = gids[gts[t]:gts[t + 1]]
-        b = f.ids[f.tile_start[t]:f.tile_start[t + 1]]
-        np.testing.assert_array_equal(a[~marg[a]], b[~marg[b]])
-    dL = (np.random.default_rng(5).standard_normal((3, 128, 128)) * ok_px[None]).astype(np.float32)
-    g2d_o, pg = oracle.backward(g, cam, f, dL.astype(np.float64), wl.tile)
+    adm = match_image(lv, rgb, img.T_final.view(128, 128).cpu().numpy(), None, "image small (end to end)")
+    # sort order: per tile the GPU's list is the oracle's, each uncertain member in or out
+    gx, gy = oracle.grid(cam, wl.tile)
+    check_lists_admissible(bins.ids().cpu().numpy(), bins.tile_start.cpu().numpy(), eb, range(gx * gy),
+                           name="tile lists small (end to end)")
+    dL = np.random.default_rng(5).standard_normal((3, 128, 128)).astype(np.float32).astype(np.float64)
+    lo, hi, _ = oracle.render_bwd_envelope(p, eb, cam, dL, adm, wl.tile, margins=oracle.MARGINS_E2E)
     g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dev(dL).reshape(-1))
+    got2 = g2d.cpu().numpy()
+    for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                       ("color", slice(6, 9))]:
+        assert_envelope(got2[:, cols], lo[:, cols], hi[:, cols], name + " small (end to end)")
+    env = param_envelope(g, cam, p, lo, hi, wl.tile)
     grads = lobe.project_bwd(ctx, batch, proj, g2d)
     gr = {k: v.cpu().numpy() for k, v in grads[0].items()}
-    okg = ~marg & ((f.proj.flags & oracle.F_COLOR) == 0) & (f.proj.radius > 0)
-    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-        assert_grad_close(gr[k][okg], getattr(pg, k)[okg], k)
+    assert_params_in_envelope(gr, env, "small (end to end)")
 
 
 def test_project_bwd_sums_views_like_oracle(small):
@@ -333,20 +336,16 @@ def test_project_bwd_sums_views_like_oracle(small):
     box = scenes.AABB((-0.6, -0.4, -math.inf), (0.5, 0.7, math.inf))
     wl2 = scenes.Workload(wl.name, wl.sets, [scenes.Camera(**c) for c in cams], [box], [(0, 0, 0), (0, 1, 0)],
                           wl.tile)
-    want = None
-    g2ds, flags = [], np.zeros(g["means"].shape[0], np.int32)
+    env, g2ds = None, []
     for v, cam in enumerate(cams):
-        f = oracle.forward(g, cam, wl.tile, margins=oracle.MARGINS_STAGE)
-        dL = np.random.default_rng(10 + v).standard_normal((3, 128, 128)) * (f.pixel_flags == 0)[None]
+        f = oracle.forward(g, cam, wl.tile)
+        dL = np.random.default_rng(10 + v).standard_normal((3, 128, 128))
         g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
-        g2d_r = oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
-                                (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity)))
-        pb = oracle.project_bwd(g, cam, g2d_r, wl.tile, aabb=box)
-        want = pb if want is None else oracle.ParamGrads(*(a + b for a, b in zip(
-            (want.means, want.log_scales, want.quats, want.opacity_logits, want.sh, want.sd_acc, want.sd_cnt),
-            (pb.means, pb.log_scales, pb.quats, pb.opacity_logits, pb.sh, pb.sd_acc, pb.sd_cnt))))
-        g2ds.append(oracle_grad2d_array(g2d_r))
-        flags |= f.proj.flags
+        g2d_r = oracle_grad2d_array(oracle.Grad2D(*(a.astype(np.float32).astype(np.float64) for a in
+                                                    (g2d.mean2d, g2d.conic, g2d.color, g2d.opacity))))
+        p = oracle.project(g, cam, wl.tile, margins=oracle.MARGINS_E2E)
+        env = add_envelopes(env, param_envelope(g, cam, p, g2d_r, g2d_r, wl.tile, aabb=box))
+        g2ds.append(g2d_r)
     ctx = ctx_for(wl2)
     batch = make_batch(wl2)
     proj = lobe.project(ctx, batch)
@@ -354,13 +353,9 @@ def test_project_bwd_sums_views_like_oracle(small):
     lobe.project_bwd(ctx, batch, proj, dev(np.concatenate(g2ds)), grads, accumulate=True)
     gr = {k: v.cpu().numpy() for k, v in grads[0].items()}
     rad = proj.radius.cpu().numpy().reshape(2, -1)
-    ok = (flags == 0) & (rad > 0).any(axis=0)
-    assert ok.sum() > 500 and ((rad > 0).all(axis=0) & ok).sum() > 100  # many seen by both views
-    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-        assert_grad_close(gr[k][ok], getattr(want, k)[ok], k + " (two views)")
-    np.testing.assert_array_equal(gr["sd_cnt"][ok], want.sd_cnt[ok])
-    assert want.sd_cnt[ok].max() == 2
-    assert_grad_close(gr["sd_acc"][ok], want.sd_acc[ok], "sd_acc (two views)")
+    assert (rad > 0).any(axis=0).sum() > 500 and (rad > 0).all(axis=0).sum() > 100  # many seen by both views
+    assert env["sd_cnt"][1].max() == 2
+    assert_params_in_envelope(gr, env, "(two views)")
 
 
 def test_batched_equals_plain():
@@ -425,11 +420,17 @@ def test_visibility_crop_matches_oracle():
     ctx = ctx_for(w2)
     batch = make_batch(w2)
     m = lobe.visibility_crop(ctx, batch)[0].cpu().numpy()
-    flags = np.zeros(g["means"].shape[0], np.int32)
+    # per view: visible for sure, or a marginal culling decision (either outcome admissible)
+    sure, maybe = np.zeros(len(want), bool), np.zeros(len(want), bool)
     for c in cams:
-        flags |= oracle.project(g, c, wl.tile, margins=oracle.MARGINS_E2E).flags
-    ok = (flags & (oracle.F_GUARD | oracle.F_RECT | oracle.F_RADIUS)) == 0
-    np.testing.assert_array_equal(m[ok], want[ok])
+        p = oracle.project(g, c, wl.tile, margins=oracle.MARGINS_E2E)
+        marg = oracle.marginal_visibility(p)
+        sure |= (p.radius > 0) & ~marg
+        maybe |= marg
+    np.testing.assert_array_equal(want[sure], 1)
+    np.testing.assert_array_equal(want[~sure & ~maybe], 0)
+    np.testing.assert_array_equal(m[sure], 1)
+    np.testing.assert_array_equal(m[~sure & ~maybe], 0)
     assert 0 < want.sum() < len(want)
 
 
@@ -475,13 +476,15 @@ def test_ragged_image_matches_oracle():
     cam = scenes.pinhole(100, 75, 90.0, cx=50.0, cy=37.5)
     wl = scenes.Workload("r", [g], [cam], [], [(0, 0, -1)], (16, 16))
     gd = oracle.set_dict(g)
-    f = oracle.forward(gd, cam.as_dict(), wl.tile, margins=oracle.MARGINS_E2E)
+    c = cam.as_dict()
+    p = oracle.project(gd, c, wl.tile, margins=oracle.MARGINS_E2E)
+    eb = oracle.bin_ext(p, c, wl.tile)
+    lv = oracle.render_leaves(p, eb, c, wl.tile, margins=oracle.MARGINS_E2E)
     ctx = ctx_for(wl)
     batch = make_batch(wl)
     _, _, img = lobe.forward(ctx, batch)
-    rgb = img.rgb.view(3, 75, 100).cpu().numpy()
-    ok = f.pixel_flags == 0
-    assert_img_close(rgb[:, ok], f.image.rgb[:, ok], "image ragged (end to end)")
+    match_image(lv, img.rgb.view(3, 75, 100).cpu().numpy(), img.T_final.view(75, 100).cpu().numpy(), None,
+                "image ragged (end to end)")
 
 
 @pytest.mark.parametrize("general", [False, True])
