@@ -123,7 +123,12 @@ typedef struct {
     int32_t bin_general; /* 1: lobe_bin_sort always takes the general multi-kernel path; 0: batches of
                             at most 4096 entries and 4096 tiles (tiles x entries <= 2^20) are binned
                             by one CTA in one launch (the same result bit for bit) */
-    int32_t reserved[4];
+    int32_t persistent;  /* 1: lobe_render_fwd / lobe_render_bwd run as persistent kernels (one wave of
+                            resident blocks) whose warps take (tile, slab) work from a device counter,
+                            tiles ordered longest list first; the images are identical, the adjoint's
+                            float32 sums may add in another order. Uses context scratch of 4 B a tile
+                            (sized by lobe_ctx_reserve's max_tiles, or grown by an uncaptured call) */
+    int32_t reserved[3];
 } lobe_config;
 
 /* Sizes implied by a batch under a config: out[0] = projected entries (sum over items of
@@ -226,10 +231,13 @@ lobe_status lobe_get_status(lobe_ctx *ctx);
 lobe_status lobe_sync_status(lobe_ctx *ctx);
 
 /* EWA projection + SH colour + culling (near/far, 1.3x fov guard, crop mask, empty
- * rectangle) of every (item, Gaussian). Writes `out` for all entries. */
+ * rectangle) of every (item, Gaussian). Writes `out` for all entries. Follows the
+ * differentiable rasterization the paper builds on (Sec. 2.1; appendix "3DGS Training"),
+ * frustum culling (Sec. 3.3) and the visibility crop (Sec. 3.3). */
 lobe_status lobe_project(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *out);
 
-/* Key duplication and sort of all (Gaussian, tile) pairs of the batch, tile ranges.
+/* Key duplication and sort of all (Gaussian, tile) pairs of the batch, tile ranges: the
+ * depth order of the blending equation (Sec. 3.2: splats composited nearest first), per tile.
  * If n_isect_host is non-NULL the call synchronises, stores the pair count there and
  * returns LOBE_ERR_CAPACITY without sorting when it exceeds bins->capacity (the caller can
  * grow the bins and call again). Otherwise an overflow is latched on the device and the
@@ -270,7 +278,9 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
 lobe_status lobe_bin_sort_noalloc(const lobe_config *cfg, void *stream, const lobe_batch *batch,
                                   const lobe_projected *proj, const lobe_bins *bins, int64_t *n_isect_host);
 
-/* Front-to-back compositing of every tile of every item. */
+/* Front-to-back compositing of every tile of every item: the blending equation of Sec. 3.2
+ * with each splat's colour in place of its depth, C = sum_i c_i alpha_i prod_{j<i}(1 - alpha_j)
+ * + T bg (skip alpha < 1/255, clamp 0.99, stop at T < 1e-4: the 3DGS rules of the appendix). */
 lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_projected *proj,
                             const lobe_bins *bins, const lobe_image *image);
 
@@ -312,7 +322,9 @@ lobe_status lobe_densify(lobe_ctx *ctx, const lobe_gaussians *set, const float *
                          const float *normals, const lobe_densify_params *prm, const lobe_params_out *out,
                          int32_t *source, int64_t *n_out_host);
 
-/* Adjoint of lobe_render_fwd. dL_drgb has the layout of image->rgb. Reads image->T_final
+/* Adjoint of lobe_render_fwd (the reverse-order derivative of the blending equation of
+ * Sec. 3.2, as the 3DGS training of the appendix back-propagates it). dL_drgb has the layout
+ * of image->rgb. Reads image->T_final
  * and image->n_contrib unless the context has recompute_T set (then only dL_drgb).
  * Overwrites grad2d[entries][12] = dL/d(u, v, conic_a, conic_b, conic_c, opacity, r, g, b)
  * followed by three zeros. grad2d must be 16-byte aligned. */
@@ -320,7 +332,8 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
                             const lobe_bins *bins, const lobe_image *image, const float *dL_drgb,
                             float *grad2d);
 
-/* Adjoint of lobe_project: chain rule from grad2d to the raw parameters of every set,
+/* Adjoint of lobe_project (chain rule of the projection of Sec. 2.1 / appendix "3DGS
+ * Training"), with the SD statistic of Sec. 3.3: chain rule from grad2d to the raw parameters of every set,
  * summed over the set's items. proj must be the output of lobe_project for this batch (the
  * colour clamp is read from the sign of the stored colour). grads[s] belongs to batch->sets[s]. accumulate = 0
  * overwrites the parameter gradients, 1 adds to them; sd_acc/sd_cnt always accumulate. */

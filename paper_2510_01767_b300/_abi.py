@@ -52,7 +52,8 @@ class Batch(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("recompute_T", ctypes.c_int32), ("px_fwd", ctypes.c_int32),
-                ("px_bwd", ctypes.c_int32), ("bin_general", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("px_bwd", ctypes.c_int32), ("bin_general", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Projected(ctypes.Structure):

@@ -8,9 +8,10 @@ the adjoint, and the per-set parameter gradients summed over views in registers.
 the binning scratch is reserved up front and no stage synchronises with the host, the whole
 step is captured once in a CUDA graph and replayed as a single launch.
 
-``autotune`` picks the tile shape (8x8, 16x8, 16x16, 32x16) and the pixels each lane composites (a
+``autotune`` picks the tile shape (8x8, 16x8, 16x16, 32x16), the pixels each lane composites (a
 kernel knob: fewer means more warps per tile, more means fewer splat loads and reductions per
-pixel) by timing graph replays on the actual batch; results are cached per (GPU, batch
+pixel) and whether the composite and its adjoint run as persistent kernels that take tiles
+longest list first, by timing graph replays on the actual batch; results are cached per (GPU, batch
 signature) in ``~/.cache/lobe/autotune.json``.
 ``PlainSteps`` is the reference it is compared with: one view per call sequence, eager,
 each view projecting its block's Gaussians itself.
@@ -37,12 +38,13 @@ CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lobe", "autotune.json")
 
 class BatchedStep:
     def __init__(self, sets, cameras, items, blocks=(), tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0),
-                 recompute_T=False, slack=1.25, stream=None, px=(0, 0)):
+                 recompute_T=False, slack=1.25, stream=None, px=(0, 0), persistent=False):
         self.stream = stream if stream is not None else torch.cuda.Stream()
         px = (px, px) if isinstance(px, int) else tuple(px)
         self.ctx = R.Context(tile=tile, sh_degree=sh_degree, bg=bg, recompute_T=recompute_T, stream=self.stream,
-                             px_fwd=px[0], px_bwd=px[1])
+                             px_fwd=px[0], px_bwd=px[1], persistent=persistent)
         self.px = px
+        self.persistent = bool(persistent)
         self.batch = R.Batch(sets, cameras, items, blocks)
         self.tile = tuple(tile)
         with torch.cuda.stream(self.stream):
@@ -88,6 +90,13 @@ class BatchedStep:
         self.px = (best["f"][1], best["b"][1])
         c.configure(px=self.px)
         return self.px
+
+    def set_persistent(self, on):
+        """Switch the composite and its adjoint between one block per tile and persistent
+        kernels taking tiles longest list first (drops a captured graph)."""
+        self.persistent = bool(on)
+        self.ctx.configure(persistent=self.persistent)
+        self.graph = None
 
     def capture(self, warmup=2):
         with torch.cuda.stream(self.stream):
@@ -163,7 +172,8 @@ def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=Tru
             cache = {}
     if use_cache and key in cache:
         tile, px = tuple(cache[key]["tile"]), tuple(cache[key].get("px", (0, 0)))
-        st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, **kw)
+        st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, persistent=cache[key].get("persistent", False),
+                         **kw)
         if dL_init is not None:
             dL_init(st)
         return st.capture(), cache[key]["times"]
@@ -185,9 +195,18 @@ def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=Tru
         else:
             del st
         torch.cuda.empty_cache()
+    # the winner once more with persistent compositing (tiles longest list first)
+    best.set_persistent(True)
+    best.capture()
+    ms = _time(best.replay, reps, best.stream)
+    times[config_name(best.tile, best.px) + "/persistent"] = ms
+    if ms >= best_ms:
+        best.set_persistent(False)
+        best.capture()
     if use_cache:
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        cache[key] = {"tile": list(best.tile), "px": list(best.px), "times": times, "when": time.time()}
+        cache[key] = {"tile": list(best.tile), "px": list(best.px), "persistent": best.persistent, "times": times,
+                      "when": time.time()}
         with open(CACHE, "w") as f:
             json.dump(cache, f)
     return best, times

@@ -26,6 +26,9 @@ struct lobe_ctx {
     int *status = nullptr;
     void *entry_mem = nullptr, *pair_mem = nullptr, *super_mem = nullptr;
     long long max_entries = 0, max_pairs = 0, max_super = 0;
+    int *order = nullptr;       // persistent compositing: tile order [max_order]
+    unsigned *order_ctl = nullptr;  // and its counters [ORDER_CTL]
+    long long max_order = 0;
     size_t pair_bytes = 0;
     BinScratch bins{};
     char err[512] = {0};
@@ -233,6 +236,8 @@ lobe_status lobe_ctx_destroy(lobe_ctx *ctx)
     cudaFree(ctx->entry_mem);
     cudaFree(ctx->pair_mem);
     cudaFree(ctx->super_mem);
+    cudaFree(ctx->order);
+    cudaFree(ctx->order_ctl);
     cudaFree(ctx->status);
     delete ctx;
     return LOBE_OK;
@@ -312,6 +317,32 @@ static lobe_status grow_super(lobe_ctx *ctx, long long need)
     return s;
 }
 
+// Scratch of the persistent compositing (the tile order and its counters) for n_tiles tiles;
+// grows only outside a stream capture.
+static lobe_status grow_order(lobe_ctx *ctx, long long n_tiles)
+{
+    if (ctx->order_ctl && n_tiles <= ctx->max_order) return LOBE_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (ctx->stream) CUDA_TRY(cudaStreamIsCapturing(ctx->stream, &cs), "capture query");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(ctx, LOBE_ERR_STATE, "persistent compositing of %lld tiles needs lobe_ctx_reserve before capture",
+                    n_tiles);
+    if (!ctx->order_ctl) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned) * ORDER_CTL) != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "order counters");
+        ctx->order_ctl = static_cast<unsigned *>(p);
+    }
+    if (n_tiles > ctx->max_order) {
+        const long long cap = n_tiles + n_tiles / 4 + 1024;
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int) * cap) != cudaSuccess) return fail(ctx, LOBE_ERR_OOM, "tile order of %lld", cap);
+        cudaFree(ctx->order);
+        ctx->order = static_cast<int *>(p);
+        ctx->max_order = cap;
+    }
+    return LOBE_OK;
+}
+
 lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_isect, int64_t max_tiles)
 {
     if (!ctx || max_entries < 0 || max_isect < 0 || max_tiles < 0) return fail(ctx, LOBE_ERR_ARG, "bad reserve arguments");
@@ -319,6 +350,7 @@ lobe_status lobe_ctx_reserve(lobe_ctx *ctx, int64_t max_entries, int64_t max_ise
     lobe_status s = grow_entries(ctx, max_entries);
     if (s == LOBE_OK) s = grow_super(ctx, max_tiles);
     if (s == LOBE_OK) s = grow_pairs(ctx, max_isect);
+    if (s == LOBE_OK) s = grow_order(ctx, max_tiles);
     return s;
 }
 
@@ -477,8 +509,13 @@ lobe_status lobe_render_fwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
     if (!proj || (H.p->n_entries > 0 && !proj->splat) || !bins || !bins->gauss_ids || !bins->tile_start)
         return fail(ctx, LOBE_ERR_ARG, "inputs missing");
     if (!image || !image->rgb || !image->T_final || !image->n_contrib) return fail(ctx, LOBE_ERR_ARG, "image buffers missing");
+    if (ctx->cfg.persistent) {
+        lobe_status s = grow_order(ctx, H.p->n_tiles);
+        if (s != LOBE_OK) return s;
+    }
     CUDA_TRY(launch_render_fwd(*H.p, proj->splat, bins->tile_start, bins->gauss_ids, image->rgb, image->T_final,
-                               image->n_contrib, nullptr, ctx->stream),
+                               image->n_contrib, nullptr, ctx->cfg.persistent ? ctx->order : nullptr, ctx->order_ctl,
+                               ctx->stream),
              "render fwd");
     return LOBE_OK;
 }
@@ -491,8 +528,13 @@ lobe_status lobe_render_depth(lobe_ctx *ctx, const lobe_batch *batch, const lobe
         return fail(ctx, LOBE_ERR_ARG, "inputs missing");
     if (!image || !image->rgb || !image->T_final || !image->n_contrib) return fail(ctx, LOBE_ERR_ARG, "image buffers missing");
     if (!depth && H.p->n_pixels > 0) return fail(ctx, LOBE_ERR_ARG, "depth is NULL");
+    if (ctx->cfg.persistent) {
+        lobe_status s = grow_order(ctx, H.p->n_tiles);
+        if (s != LOBE_OK) return s;
+    }
     CUDA_TRY(launch_render_fwd(*H.p, proj->splat, bins->tile_start, bins->gauss_ids, image->rgb, image->T_final,
-                               image->n_contrib, depth, ctx->stream),
+                               image->n_contrib, depth, ctx->cfg.persistent ? ctx->order : nullptr, ctx->order_ctl,
+                               ctx->stream),
              "render depth");
     return LOBE_OK;
 }
@@ -532,8 +574,13 @@ lobe_status lobe_render_bwd(lobe_ctx *ctx, const lobe_batch *batch, const lobe_p
         return fail(ctx, LOBE_ERR_ARG, "dL_drgb/grad2d missing or misaligned");
     if (!rec && (!image || !image->T_final || !image->n_contrib))
         return fail(ctx, LOBE_ERR_ARG, "saved forward state missing (recompute_T = 0)");
+    if (ctx->cfg.persistent) {
+        lobe_status s = grow_order(ctx, H.p->n_tiles);
+        if (s != LOBE_OK) return s;
+    }
     CUDA_TRY(launch_render_bwd(*H.p, rec, proj->splat, bins->tile_start, bins->gauss_ids, rec ? nullptr : image->T_final,
-                               rec ? nullptr : image->n_contrib, dL_drgb, grad2d, ctx->stream),
+                               rec ? nullptr : image->n_contrib, dL_drgb, grad2d,
+                               ctx->cfg.persistent ? ctx->order : nullptr, ctx->order_ctl, ctx->stream),
              "render bwd");
     return LOBE_OK;
 }

@@ -311,8 +311,11 @@ cudaError_t launch_selftest_wait(int *ctl, cudaStream_t st);
 // fused adjoint has updated the others).
 cudaError_t launch_adam(long long n, const AdamSet &s, const float *const grad[5], const uint8_t *rows, int mode,
                         const AdamK &k, cudaStream_t);
+// Compositing and its adjoint. order/ctl non-null: persistent mode (tiles longest list first);
+// order holds n_tiles ints, ctl ORDER_CTL words (both device scratch).
+constexpr int ORDER_CTL = 67;
 cudaError_t launch_render_fwd(const BatchParams &, const float *, const int *, const int *, float *, float *, int *,
-                              float *depth, cudaStream_t);
+                              float *depth, int *order, unsigned *ctl, cudaStream_t);
 
 // Block boxes of fast camera selection (kernel parameter).
 constexpr int FCS_MAX_BLOCKS = 64;
@@ -330,7 +333,7 @@ cudaError_t launch_densify_emit(long long n, const lobe_gaussians &in, const uin
 cudaError_t launch_fcs_coverage(const BatchParams &, const FcsBlocks &, const float *depth, const float *Tfin,
                                 int normalize, uint32_t *counts, uint32_t *n_points, cudaStream_t);
 cudaError_t launch_render_bwd(const BatchParams &, bool, const float *, const int *, const int *, const float *,
-                              const int *, const float *, float *, cudaStream_t);
+                              const int *, const float *, float *, int *order, unsigned *ctl, cudaStream_t);
 cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int *radius, const int *tiles,
                             BinScratch &b, long long pair_capacity, cudaStream_t st);
 cudaError_t bin_tile_count(const BatchParams &P, const float *splat, const int *radius, BinScratch &b,

@@ -26,6 +26,9 @@
 // reduce-scatter butterfly that leaves each total in its own lane, and nine lanes add them to
 // global memory in one instruction: one update per splat per warp (128 pixels) instead of one
 // per pixel. Warps need no block barriers.
+#include <map>
+#include <mutex>
+
 #include "lobe_internal.cuh"
 
 namespace lobe {
@@ -297,6 +300,35 @@ __device__ __forceinline__ SlabBox slab_box(int tx, int ty, int warp)
     return b;
 }
 
+// Work distribution of the compositing kernels. Plain: one block per tile, warp w of the block
+// takes slab w. Persistent (order != nullptr): a grid of resident blocks whose warps pull
+// (tile, slab) items from a device counter, tiles in the order given (longest list first), so
+// the longest tiles start first and no block waits for a straggler of the last wave.
+struct WorkCursor {
+    const int *order;
+    unsigned *work;
+    unsigned n_work;
+    int warps;
+    bool first;
+    __device__ __forceinline__ bool next(int &t, int &slab, int pw)
+    {
+        if (!order) {
+            if (!first) return false;
+            first = false;
+            t = blockIdx.x;
+            slab = pw;
+            return true;
+        }
+        unsigned k = 0;
+        if ((threadIdx.x & 31) == 0) k = atomicAdd(work, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= n_work) return false;
+        t = order[k / warps];
+        slab = (int)(k % warps);
+        return true;
+    }
+};
+
 #ifndef LOBE_FWD_REGS
 #define LOBE_FWD_REGS 0  // 0: no cap beyond the compiler's choice
 #endif
@@ -307,48 +339,63 @@ constexpr int min_blocks_for(int regs, int warps)
     return regs > 0 ? (65536 / (regs * 32 * warps) < 32 ? 65536 / (regs * 32 * warps) : 32) : 1;
 }
 
-template <int TW, int TH, int PX, bool DEPTH>
-__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(LOBE_FWD_REGS, Slab<TW, TH, PX>::WARPS))
+#if LOBE_FWD_REGS > 0
+#define LOBE_FWD_BOUNDS(W) __launch_bounds__(32 * (W), min_blocks_for(LOBE_FWD_REGS, (W)))
+#else
+#define LOBE_FWD_BOUNDS(W) __launch_bounds__(32 * (W))
+#endif
+template <int TW, int TH, int PX, bool DEPTH, bool PERSIST>
+__global__ void LOBE_FWD_BOUNDS((Slab<TW, TH, PX>::WARPS))
     k_render_fwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                  const int *__restrict__ tile_start, const int *__restrict__ ids, float *__restrict__ rgb,
-                 float *__restrict__ Tout, int *__restrict__ ncout, float *__restrict__ depth)
+                 float *__restrict__ Tout, int *__restrict__ ncout, float *__restrict__ depth,
+                 const int *__restrict__ order, unsigned *__restrict__ work)
 {
     pdl_wait();
     using G = Slab<TW, TH, PX>;
     __shared__ WarpStage stage[G::WARPS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = blockIdx.x;
-    const ItemParams &I = P.item[item_of_tile(P, t)];
-    const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
-    const int px = tx * TW + lane % TW;
-    const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
-    const float pxc = (float)px + 0.5f;
-    float pyc[PX], T[PX], C0[PX], C1[PX], C2[PX], D[PX];
-    int last[PX];
-    bool live[PX], inside[PX];
+    const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
+    WorkCursor wc{order, work, (unsigned)P.n_tiles * (unsigned)G::WARPS, G::WARPS, true};
+    auto tile_body = [&](const int t, const int warp) {
+        const ItemParams &I = P.item[item_of_tile(P, t)];
+        const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
+        const int px = tx * TW + lane % TW;
+        const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
+        const float pxc = (float)px + 0.5f;
+        float pyc[PX], T[PX], C0[PX], C1[PX], C2[PX], D[PX];
+        int last[PX];
+        bool live[PX], inside[PX];
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        pyc[k] = (float)(py0 + k) + 0.5f;
-        inside[k] = px < I.W && py0 + k < I.H;
-        live[k] = inside[k];
-        T[k] = 1.0f;
-        C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
-        last[k] = 0;
-    }
-    forward_sweep<PX, DEPTH>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc,
-                             live, T, C0, C1, C2, last, stage[warp], D);
-    const long long HW = (long long)I.W * I.H;
-    float *out = rgb + 3 * I.pix_off;
+        for (int k = 0; k < PX; ++k) {
+            pyc[k] = (float)(py0 + k) + 0.5f;
+            inside[k] = px < I.W && py0 + k < I.H;
+            live[k] = inside[k];
+            T[k] = 1.0f;
+            C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
+            last[k] = 0;
+        }
+        forward_sweep<PX, DEPTH>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc,
+                                 live, T, C0, C1, C2, last, stage[pw], D);
+        const long long HW = (long long)I.W * I.H;
+        float *out = rgb + 3 * I.pix_off;
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        if (!inside[k]) continue;
-        const long long p = (long long)(py0 + k) * I.W + px;
-        out[p] = C0[k] + T[k] * P.bg[0];
-        out[HW + p] = C1[k] + T[k] * P.bg[1];
-        out[2 * HW + p] = C2[k] + T[k] * P.bg[2];
-        Tout[I.pix_off + p] = T[k];
-        ncout[I.pix_off + p] = last[k];
-        if (DEPTH) depth[I.pix_off + p] = D[k];
+        for (int k = 0; k < PX; ++k) {
+            if (!inside[k]) continue;
+            const long long p = (long long)(py0 + k) * I.W + px;
+            out[p] = C0[k] + T[k] * P.bg[0];
+            out[HW + p] = C1[k] + T[k] * P.bg[1];
+            out[2 * HW + p] = C2[k] + T[k] * P.bg[2];
+            Tout[I.pix_off + p] = T[k];
+            ncout[I.pix_off + p] = last[k];
+            if (DEPTH) depth[I.pix_off + p] = D[k];
+        }
+        __syncwarp();
+    };
+    if constexpr (PERSIST) {
+        int t, warp;
+        while (wc.next(t, warp, pw)) tile_body(t, warp);
+    } else {
+        tile_body((int)blockIdx.x, pw);
     }
 }
 
@@ -387,135 +434,145 @@ __device__ __forceinline__ float warp_reduce9(const float (&v)[9], int &idx)
     return z;
 }
 
-template <int TW, int TH, int PX, bool RECOMPUTE>
+template <int TW, int TH, int PX, bool RECOMPUTE, bool PERSIST>
 __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
     k_render_bwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                  const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
-                 const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
+                 const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d,
+                 const int *__restrict__ order, unsigned *__restrict__ work)
 {
     pdl_wait();
     using G = Slab<TW, TH, PX>;
     __shared__ WarpStage stage[G::WARPS];
     WarpStage &st = stage[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = blockIdx.x;
-    const ItemParams &I = P.item[item_of_tile(P, t)];
-    const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
-    const int px = tx * TW + lane % TW;
-    const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
-    const float pxc = (float)px + 0.5f;
-    const int start = tile_start[t], end = tile_start[t + 1];
-    const SlabBox bx = slab_box<TW, TH, PX>(tx, ty, warp);
-    const long long HW = (long long)I.W * I.H;
-    // per pixel: dL/dC, the colour seen behind the current splat (B, background included),
-    // the transmittance after it (T, starting from T_final) and the stop position
-    float pyc[PX], g0[PX], g1[PX], g2[PX], B0[PX], B1[PX], B2[PX], T[PX];
-    int nc[PX];
-    bool inside[PX];
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        pyc[k] = (float)(py0 + k) + 0.5f;
-        inside[k] = px < I.W && py0 + k < I.H;
-        g0[k] = g1[k] = g2[k] = 0.0f;
-        T[k] = 1.0f;
-        nc[k] = 0;
-        if (inside[k]) {
-            const long long p = (long long)(py0 + k) * I.W + px;
-            const float *d = dL + 3 * I.pix_off;
-            g0[k] = d[p];
-            g1[k] = d[HW + p];
-            g2[k] = d[2 * HW + p];
-            if (!RECOMPUTE) {
-                T[k] = Tfin[I.pix_off + p];
-                nc[k] = ncin[I.pix_off + p];
-            }
-        }
-    }
-    if (RECOMPUTE) {
-        bool live[PX];
+    const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
+    WorkCursor wc{order, work, (unsigned)P.n_tiles * (unsigned)G::WARPS, G::WARPS, true};
+    auto tile_body = [&](const int t, const int warp) {
+        const ItemParams &I = P.item[item_of_tile(P, t)];
+        const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
+        const int px = tx * TW + lane % TW;
+        const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
+        const float pxc = (float)px + 0.5f;
+        const int start = tile_start[t], end = tile_start[t + 1];
+        const SlabBox bx = slab_box<TW, TH, PX>(tx, ty, warp);
+        const long long HW = (long long)I.W * I.H;
+        // per pixel: dL/dC, the colour seen behind the current splat (B, background included),
+        // the transmittance after it (T, starting from T_final) and the stop position
+        float pyc[PX], g0[PX], g1[PX], g2[PX], B0[PX], B1[PX], B2[PX], T[PX];
+        int nc[PX];
+        bool inside[PX];
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
-            live[k] = inside[k];
-            B0[k] = B1[k] = B2[k] = 0.0f;  // colour accumulators of the sweep (unused after it)
+            pyc[k] = (float)(py0 + k) + 0.5f;
+            inside[k] = px < I.W && py0 + k < I.H;
+            g0[k] = g1[k] = g2[k] = 0.0f;
+            T[k] = 1.0f;
+            nc[k] = 0;
+            if (inside[k]) {
+                const long long p = (long long)(py0 + k) * I.W + px;
+                const float *d = dL + 3 * I.pix_off;
+                g0[k] = d[p];
+                g1[k] = d[HW + p];
+                g2[k] = d[2 * HW + p];
+                if (!RECOMPUTE) {
+                    T[k] = Tfin[I.pix_off + p];
+                    nc[k] = ncin[I.pix_off + p];
+                }
+            }
         }
-        forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, B0, B1, B2, nc, st);
-    }
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        B0[k] = P.bg[0];
-        B1[k] = P.bg[1];
-        B2[k] = P.bg[2];
-    }
-    int m = 0;
-#pragma unroll
-    for (int k = 0; k < PX; ++k) m = max(m, nc[k]);
-    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
-    const int stop = min(start + m, end);
-
-    // walk the list back to front in batches of 32, prefetching the batch below
-    int top = stop, base = max(start, stop - 32);
-    Staged nx;
-    bool nh;
-    fetch(splat, ids, base + lane, top, bx, nx, nh);
-    while (top > start) {
-        st.s0[lane] = nx.s0;
-        st.s1[lane] = nx.s1;
-        st.s2[lane] = nx.s2;
-        st.id[lane] = nx.id;
-        unsigned hits = __ballot_sync(0xffffffffu, nh);
-        __syncwarp();
-        const int nbase = max(start, base - 32);
-        fetch(splat, ids, nbase + lane, base, bx, nx, nh);
-        while (hits) {  // back to front: highest position first
-            const int j = 31 - __clz(hits);
-            hits &= ~(1u << j);
-            const float4 q0 = st.s0[j], q1 = st.s1[j];
-            const float cb = st.s2[j].x, pmin = st.s2[j].y;
-            const int pos = base - start + j;
-            const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
-            float du = 0.f, dv = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-            bool any = false;
+        if (RECOMPUTE) {
+            bool live[PX];
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
-                if (pos >= nc[k]) continue;
-                const PairEval r = pair_eval(cl, q0.y, q1.x, q1.y, pmin, pyc[k]);
-                if (!r.use) continue;
-                any = true;
-                const float Ti = __fdividef(T[k], 1.0f - r.alpha);  // transmittance in front of it
-                const float w = r.alpha * Ti;
-                dr += w * g0[k];
-                dg += w * g1[k];
-                db += w * g2[k];
-                const float dalpha = Ti * (g0[k] * (q1.z - B0[k]) + g1[k] * (q1.w - B1[k]) + g2[k] * (cb - B2[k]));
-                B0[k] = fmaf(r.alpha, q1.z - B0[k], B0[k]);
-                B1[k] = fmaf(r.alpha, q1.w - B1[k], B1[k]);
-                B2[k] = fmaf(r.alpha, cb - B2[k], B2[k]);
-                T[k] = Ti;
-                if (!r.clamped) {
-                    dop += dalpha * r.G;
-                    const float dp2 = dalpha * r.alpha * LN2;
-                    const float dpy = dp2 * r.dy;
-                    dA += dp2 * cl.dx * cl.dx;
-                    dB += dpy * cl.dx;
-                    dC += dpy * r.dy;
-                    du += dp2 * (2.f * q0.z * cl.dx + q0.w * r.dy);
-                    dv += dp2 * q0.w * cl.dx + 2.f * q1.x * dpy;
+                live[k] = inside[k];
+                B0[k] = B1[k] = B2[k] = 0.0f;  // colour accumulators of the sweep (unused after it)
+            }
+            forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, B0, B1, B2, nc, st);
+        }
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            B0[k] = P.bg[0];
+            B1[k] = P.bg[1];
+            B2[k] = P.bg[2];
+        }
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) m = max(m, nc[k]);
+        m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+        const int stop = min(start + m, end);
+
+        // walk the list back to front in batches of 32, prefetching the batch below
+        int top = stop, base = max(start, stop - 32);
+        Staged nx;
+        bool nh;
+        fetch(splat, ids, base + lane, top, bx, nx, nh);
+        while (top > start) {
+            st.s0[lane] = nx.s0;
+            st.s1[lane] = nx.s1;
+            st.s2[lane] = nx.s2;
+            st.id[lane] = nx.id;
+            unsigned hits = __ballot_sync(0xffffffffu, nh);
+            __syncwarp();
+            const int nbase = max(start, base - 32);
+            fetch(splat, ids, nbase + lane, base, bx, nx, nh);
+            while (hits) {  // back to front: highest position first
+                const int j = 31 - __clz(hits);
+                hits &= ~(1u << j);
+                const float4 q0 = st.s0[j], q1 = st.s1[j];
+                const float cb = st.s2[j].x, pmin = st.s2[j].y;
+                const int pos = base - start + j;
+                const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
+                float du = 0.f, dv = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PX; ++k) {
+                    if (pos >= nc[k]) continue;
+                    const PairEval r = pair_eval(cl, q0.y, q1.x, q1.y, pmin, pyc[k]);
+                    if (!r.use) continue;
+                    any = true;
+                    const float Ti = __fdividef(T[k], 1.0f - r.alpha);  // transmittance in front of it
+                    const float w = r.alpha * Ti;
+                    dr += w * g0[k];
+                    dg += w * g1[k];
+                    db += w * g2[k];
+                    const float dalpha = Ti * (g0[k] * (q1.z - B0[k]) + g1[k] * (q1.w - B1[k]) + g2[k] * (cb - B2[k]));
+                    B0[k] = fmaf(r.alpha, q1.z - B0[k], B0[k]);
+                    B1[k] = fmaf(r.alpha, q1.w - B1[k], B1[k]);
+                    B2[k] = fmaf(r.alpha, cb - B2[k], B2[k]);
+                    T[k] = Ti;
+                    if (!r.clamped) {
+                        dop += dalpha * r.G;
+                        const float dp2 = dalpha * r.alpha * LN2;
+                        const float dpy = dp2 * r.dy;
+                        dA += dp2 * cl.dx * cl.dx;
+                        dB += dpy * cl.dx;
+                        dC += dpy * r.dy;
+                        du += dp2 * (2.f * q0.z * cl.dx + q0.w * r.dy);
+                        dv += dp2 * q0.w * cl.dx + 2.f * q1.x * dpy;
+                    }
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    const float vals[9] = {du, dv, dA, dB, dC, dop, dr, dg, db};
+                    int idx;
+                    const float tot = warp_reduce9(vals, idx);
+                    if (idx >= 0) {
+                        // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
+                        const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
+                        red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
+                    }
                 }
             }
-            if (__any_sync(0xffffffffu, any)) {
-                const float vals[9] = {du, dv, dA, dB, dC, dop, dr, dg, db};
-                int idx;
-                const float tot = warp_reduce9(vals, idx);
-                if (idx >= 0) {
-                    // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
-                    const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
-                    red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
-                }
-            }
+            __syncwarp();
+            top = base;
+            base = nbase;
         }
         __syncwarp();
-        top = base;
-        base = nbase;
+    };
+    if constexpr (PERSIST) {
+        int t, warp;
+        while (wc.next(t, warp, pw)) tile_body(t, warp);
+    } else {
+        tile_body((int)blockIdx.x, pw);
     }
 }
 
@@ -529,16 +586,29 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 // the same rounding); a pixel of the pair that does not use the splat gets G = 0, hence
 // alpha = 0, which leaves its T, B and every gradient term unchanged.
 
-// At most LOBE_BWD_REGS registers a thread (occupancy: the kernel is latency- as much as
-// issue-bound).
-#ifndef LOBE_BWD_REGS
-#define LOBE_BWD_REGS 128
+// Register cap of the paired adjoint per pixels a lane (occupancy: the kernel is latency- as
+// much as issue-bound), and the lanes below which a splat skips the warp reduction. Measured on
+// B300 (16 views of a 6.5M-Gaussian city): one pixel pair a lane at 64 registers and two at 96
+// run faster than at the compiler's choice (92-114 registers); four pairs keep 128 (lower caps
+// spill). The direct path for splats that at most 8 lanes use saves ~10% where splats are
+// small, and costs where they are large (four pairs a lane are chosen for large ones). Together:
+// the city batch's adjoint 11.1 -> 8.9-9.3 ms.
+#ifdef LOBE_BWD_REGS
+constexpr int bwd_regs_for(int) { return LOBE_BWD_REGS; }
+#else
+constexpr int bwd_regs_for(int px) { return px >= 8 ? 128 : (px >= 4 ? 96 : 64); }
 #endif
-template <int TW, int TH, int PX, bool RECOMPUTE>
-__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(LOBE_BWD_REGS, Slab<TW, TH, PX>::WARPS))
+#ifdef LOBE_BWD_DIRECT
+__host__ __device__ constexpr int bwd_direct_for(int) { return LOBE_BWD_DIRECT; }
+#else
+__host__ __device__ constexpr int bwd_direct_for(int px) { return px >= 8 ? 0 : 8; }
+#endif
+template <int TW, int TH, int PX, bool RECOMPUTE, bool PERSIST>
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(bwd_regs_for(PX), Slab<TW, TH, PX>::WARPS))
     k_render_bwd2(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                   const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
-                  const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d)
+                  const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d,
+                 const int *__restrict__ order, unsigned *__restrict__ work)
 {
     pdl_wait();
     static_assert(PX % 2 == 0, "pixels are paired");
@@ -546,198 +616,321 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(L
     using G = Slab<TW, TH, PX>;
     __shared__ WarpStage stage[G::WARPS];
     WarpStage &st = stage[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = blockIdx.x;
-    const ItemParams &I = P.item[item_of_tile(P, t)];
-    const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
-    const int px = tx * TW + lane % TW;
-    const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
-    const float pxc = (float)px + 0.5f;
-    const int start = tile_start[t], end = tile_start[t + 1];
-    const SlabBox bx = slab_box<TW, TH, PX>(tx, ty, warp);
-    const long long HW = (long long)I.W * I.H;
-    float pyc[PX], g0[PX], g1[PX], g2[PX], T[PX];
-    int nc[PX];
-    bool inside[PX];
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        pyc[k] = (float)(py0 + k) + 0.5f;
-        inside[k] = px < I.W && py0 + k < I.H;
-        g0[k] = g1[k] = g2[k] = 0.0f;
-        T[k] = 1.0f;
-        nc[k] = 0;
-        if (inside[k]) {
-            const long long p = (long long)(py0 + k) * I.W + px;
-            const float *d = dL + 3 * I.pix_off;
-            g0[k] = d[p];
-            g1[k] = d[HW + p];
-            g2[k] = d[2 * HW + p];
-            if (!RECOMPUTE) {
-                T[k] = Tfin[I.pix_off + p];
-                nc[k] = ncin[I.pix_off + p];
-            }
-        }
-    }
-    if (RECOMPUTE) {
-        bool live[PX];
-        float c0[PX], c1[PX], c2[PX];
+    const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
+    WorkCursor wc{order, work, (unsigned)P.n_tiles * (unsigned)G::WARPS, G::WARPS, true};
+    auto tile_body = [&](const int t, const int warp) {
+        const ItemParams &I = P.item[item_of_tile(P, t)];
+        const int lt = t - I.tile_off, tx = lt % I.gx, ty = lt / I.gx;
+        const int px = tx * TW + lane % TW;
+        const int py0 = ty * TH + warp * G::WROWS + (lane / TW) * PX;
+        const float pxc = (float)px + 0.5f;
+        const int start = tile_start[t], end = tile_start[t + 1];
+        const SlabBox bx = slab_box<TW, TH, PX>(tx, ty, warp);
+        const long long HW = (long long)I.W * I.H;
+        float pyc[PX], g0[PX], g1[PX], g2[PX], T[PX];
+        int nc[PX];
+        bool inside[PX];
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
-            live[k] = inside[k];
-            c0[k] = c1[k] = c2[k] = 0.0f;
+            pyc[k] = (float)(py0 + k) + 0.5f;
+            inside[k] = px < I.W && py0 + k < I.H;
+            g0[k] = g1[k] = g2[k] = 0.0f;
+            T[k] = 1.0f;
+            nc[k] = 0;
+            if (inside[k]) {
+                const long long p = (long long)(py0 + k) * I.W + px;
+                const float *d = dL + 3 * I.pix_off;
+                g0[k] = d[p];
+                g1[k] = d[HW + p];
+                g2[k] = d[2 * HW + p];
+                if (!RECOMPUTE) {
+                    T[k] = Tfin[I.pix_off + p];
+                    nc[k] = ncin[I.pix_off + p];
+                }
+            }
         }
-        forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, c0, c1, c2, nc, st);
-    }
-    // per pixel pair: packed row centres, dL/dC, colour behind (from the background), T
-    f2 pyc2[NP], G0[NP], G1[NP], G2[NP], B0[NP], B1[NP], B2[NP], T2[NP];
-    const f2 bg0 = pk(P.bg[0], P.bg[0]), bg1 = pk(P.bg[1], P.bg[1]), bg2 = pk(P.bg[2], P.bg[2]);
+        if (RECOMPUTE) {
+            bool live[PX];
+            float c0[PX], c1[PX], c2[PX];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        pyc2[i] = pk(pyc[2 * i], pyc[2 * i + 1]);
-        G0[i] = pk(g0[2 * i], g0[2 * i + 1]);
-        G1[i] = pk(g1[2 * i], g1[2 * i + 1]);
-        G2[i] = pk(g2[2 * i], g2[2 * i + 1]);
-        B0[i] = bg0;
-        B1[i] = bg1;
-        B2[i] = bg2;
-        T2[i] = pk(T[2 * i], T[2 * i + 1]);
-    }
-    int m = 0;
+            for (int k = 0; k < PX; ++k) {
+                live[k] = inside[k];
+                c0[k] = c1[k] = c2[k] = 0.0f;
+            }
+            forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, c0, c1, c2, nc, st);
+        }
+        // per pixel pair: packed row centres, dL/dC, colour behind (from the background), T
+        f2 pyc2[NP], G0[NP], G1[NP], G2[NP], B0[NP], B1[NP], B2[NP], T2[NP];
+        const f2 bg0 = pk(P.bg[0], P.bg[0]), bg1 = pk(P.bg[1], P.bg[1]), bg2 = pk(P.bg[2], P.bg[2]);
 #pragma unroll
-    for (int k = 0; k < PX; ++k) m = max(m, nc[k]);
-    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
-    const int stop = min(start + m, end);
-    const f2 one2 = pk(1.0f, 1.0f);
+        for (int i = 0; i < NP; ++i) {
+            pyc2[i] = pk(pyc[2 * i], pyc[2 * i + 1]);
+            G0[i] = pk(g0[2 * i], g0[2 * i + 1]);
+            G1[i] = pk(g1[2 * i], g1[2 * i + 1]);
+            G2[i] = pk(g2[2 * i], g2[2 * i + 1]);
+            B0[i] = bg0;
+            B1[i] = bg1;
+            B2[i] = bg2;
+            T2[i] = pk(T[2 * i], T[2 * i + 1]);
+        }
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) m = max(m, nc[k]);
+        m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+        const int stop = min(start + m, end);
+        const f2 one2 = pk(1.0f, 1.0f);
 
-    int top = stop, base = max(start, stop - 32);
-    Staged nx;
-    bool nh;
-    fetch(splat, ids, base + lane, top, bx, nx, nh);
-    while (top > start) {
-        st.s0[lane] = nx.s0;
-        st.s1[lane] = nx.s1;
-        st.s2[lane] = nx.s2;
-        st.id[lane] = nx.id;
-        unsigned hits = __ballot_sync(0xffffffffu, nh);
-        __syncwarp();
-        const int nbase = max(start, base - 32);
-        fetch(splat, ids, nbase + lane, base, bx, nx, nh);
-        while (hits) {  // back to front: highest position first
-            const int j = 31 - __clz(hits);
-            hits &= ~(1u << j);
-            const float4 q0 = st.s0[j], q1 = st.s1[j];
-            const float cb = st.s2[j].x, pmin = st.s2[j].y;
-            const int pos = base - start + j;
-            const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
-            const f2 v2 = pk(q0.y, q0.y), C2 = pk(q1.x, q1.x), a2 = pk(cl.a2, cl.a2), b1 = pk(cl.b1, cl.b1);
-            const f2 oln2 = pk(q1.y * LN2, q1.y * LN2);
-            // per lane: S1 = sum dL/dp2, S2 = sum dL/dp2 dy, S3 = sum dL/dp2 dy^2 over its pixels; dx
-            // is the lane's own, so the exponent's gradients follow from these three after the loop
-            f2 S1 = 0, S2 = 0, S3 = 0, dop = 0, dr = 0, dg = 0, db = 0;  // 0 = (+0, +0)
-            bool any = false;
+        int top = stop, base = max(start, stop - 32);
+        Staged nx;
+        bool nh;
+        fetch(splat, ids, base + lane, top, bx, nx, nh);
+        while (top > start) {
+            st.s0[lane] = nx.s0;
+            st.s1[lane] = nx.s1;
+            st.s2[lane] = nx.s2;
+            st.id[lane] = nx.id;
+            unsigned hits = __ballot_sync(0xffffffffu, nh);
+            __syncwarp();
+            const int nbase = max(start, base - 32);
+            fetch(splat, ids, nbase + lane, base, bx, nx, nh);
+            while (hits) {  // back to front: highest position first
+                const int j = 31 - __clz(hits);
+                hits &= ~(1u << j);
+                const float4 q0 = st.s0[j], q1 = st.s1[j];
+                const float cb = st.s2[j].x, pmin = st.s2[j].y;
+                const int pos = base - start + j;
+                const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
+                const f2 v2 = pk(q0.y, q0.y), C2 = pk(q1.x, q1.x), a2 = pk(cl.a2, cl.a2), b1 = pk(cl.b1, cl.b1);
+                const f2 oln2 = pk(q1.y * LN2, q1.y * LN2);
+                // per lane: S1 = sum dL/dp2, S2 = sum dL/dp2 dy, S3 = sum dL/dp2 dy^2 over its pixels; dx
+                // is the lane's own, so the exponent's gradients follow from these three after the loop
+                f2 S1 = 0, S2 = 0, S3 = 0, dop = 0, dr = 0, dg = 0, db = 0;  // 0 = (+0, +0)
+                bool any = false;
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const bool ok0 = pos < nc[2 * i], ok1 = pos < nc[2 * i + 1];
-                if (NP == 1 && !(ok0 || ok1)) continue;  // several pairs: branch-free, so the pairs interleave
-                const f2 dy2 = sub2(v2, pyc2[i]);
-                const f2 p2 = fma2(dy2, fma2(C2, dy2, b1), a2);
-                float pa, pb;
-                upk(p2, pa, pb);
-                const bool u0 = ok0 && pa <= 0.0f && pa >= pmin, u1 = ok1 && pb <= 0.0f && pb >= pmin;
-                if (NP == 1 && !(u0 || u1)) continue;
-                any |= u0 || u1;  // a pair neither pixel uses has alpha = 0 and leaves everything unchanged
-                const float Ga = u0 ? ex2(pa) : 0.0f, Gb = u1 ? ex2(pb) : 0.0f;
-                float ra, rb;
-                upk(mul2(pk(q1.y, q1.y), pk(Ga, Gb)), ra, rb);  // o * G, as in the forward
-                const bool ka = ra >= ALPHA_MAX, kb = rb >= ALPHA_MAX;
-                const float aa = fminf(ALPHA_MAX, ra), ab = fminf(ALPHA_MAX, rb);
-                const f2 al = pk(aa, ab);
-                float oma, omb;
-                upk(sub2(one2, al), oma, omb);
-                const f2 Ti = mul2(T2[i], pk(__fdividef(1.0f, oma), __fdividef(1.0f, omb)));  // T in front
-                const f2 w = mul2(al, Ti);
-                dr = fma2(w, G0[i], dr);
-                dg = fma2(w, G1[i], dg);
-                db = fma2(w, G2[i], db);
-                const f2 d0 = sub2(pk(q1.z, q1.z), B0[i]), d1 = sub2(pk(q1.w, q1.w), B1[i]),
-                         d2 = sub2(pk(cb, cb), B2[i]);
-                const f2 da = mul2(Ti, fma2(G2[i], d2, fma2(G1[i], d1, mul2(G0[i], d0))));  // dL/dalpha
-                B0[i] = fma2(al, d0, B0[i]);
-                B1[i] = fma2(al, d1, B1[i]);
-                B2[i] = fma2(al, d2, B2[i]);
-                if (NP == 1) {
-                    T2[i] = Ti;
-                } else {  // an unused pixel keeps its T exactly (the reciprocal of 1 - 0 is approximate)
-                    float t0, t1, n0, n1;
-                    upk(T2[i], t0, t1);
-                    upk(Ti, n0, n1);
-                    T2[i] = pk(u0 ? n0 : t0, u1 ? n1 : t1);
+                for (int i = 0; i < NP; ++i) {
+                    const bool ok0 = pos < nc[2 * i], ok1 = pos < nc[2 * i + 1];
+                    if (NP == 1 && !(ok0 || ok1)) continue;  // several pairs: branch-free, so the pairs interleave
+                    const f2 dy2 = sub2(v2, pyc2[i]);
+                    const f2 p2 = fma2(dy2, fma2(C2, dy2, b1), a2);
+                    float pa, pb;
+                    upk(p2, pa, pb);
+                    const bool u0 = ok0 && pa <= 0.0f && pa >= pmin, u1 = ok1 && pb <= 0.0f && pb >= pmin;
+                    if (NP == 1 && !(u0 || u1)) continue;
+                    any |= u0 || u1;  // a pair neither pixel uses has alpha = 0 and leaves everything unchanged
+                    const float Ga = u0 ? ex2(pa) : 0.0f, Gb = u1 ? ex2(pb) : 0.0f;
+                    float ra, rb;
+                    upk(mul2(pk(q1.y, q1.y), pk(Ga, Gb)), ra, rb);  // o * G, as in the forward
+                    const bool ka = ra >= ALPHA_MAX, kb = rb >= ALPHA_MAX;
+                    const float aa = fminf(ALPHA_MAX, ra), ab = fminf(ALPHA_MAX, rb);
+                    const f2 al = pk(aa, ab);
+                    float oma, omb;
+                    upk(sub2(one2, al), oma, omb);
+                    const f2 Ti = mul2(T2[i], pk(__fdividef(1.0f, oma), __fdividef(1.0f, omb)));  // T in front
+                    const f2 w = mul2(al, Ti);
+                    dr = fma2(w, G0[i], dr);
+                    dg = fma2(w, G1[i], dg);
+                    db = fma2(w, G2[i], db);
+                    const f2 d0 = sub2(pk(q1.z, q1.z), B0[i]), d1 = sub2(pk(q1.w, q1.w), B1[i]),
+                             d2 = sub2(pk(cb, cb), B2[i]);
+                    const f2 da = mul2(Ti, fma2(G2[i], d2, fma2(G1[i], d1, mul2(G0[i], d0))));  // dL/dalpha
+                    B0[i] = fma2(al, d0, B0[i]);
+                    B1[i] = fma2(al, d1, B1[i]);
+                    B2[i] = fma2(al, d2, B2[i]);
+                    if (NP == 1) {
+                        T2[i] = Ti;
+                    } else {  // an unused pixel keeps its T exactly (the reciprocal of 1 - 0 is approximate)
+                        float t0, t1, n0, n1;
+                        upk(T2[i], t0, t1);
+                        upk(Ti, n0, n1);
+                        T2[i] = pk(u0 ? n0 : t0, u1 ? n1 : t1);
+                    }
+                    // past the clamp alpha no longer depends on o or the exponent: dL/do = da G and
+                    // dL/dp2 = da o G ln2 (alpha = o G below the clamp)
+                    const f2 t = mul2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb));
+                    dop = add2(dop, t);
+                    const f2 dp2 = mul2(t, oln2);
+                    const f2 dpy = mul2(dp2, dy2);
+                    S1 = add2(S1, dp2);
+                    S2 = add2(S2, dpy);
+                    S3 = fma2(dpy, dy2, S3);
                 }
-                // past the clamp alpha no longer depends on o or the exponent: dL/do = da G and
-                // dL/dp2 = da o G ln2 (alpha = o G below the clamp)
-                const f2 t = mul2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb));
-                dop = add2(dop, t);
-                const f2 dp2 = mul2(t, oln2);
-                const f2 dpy = mul2(dp2, dy2);
-                S1 = add2(S1, dp2);
-                S2 = add2(S2, dpy);
-                S3 = fma2(dpy, dy2, S3);
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                // p2 = A dx^2 + B dx dy + C dy^2 with dx = u - x, dy = v - y
-                const float s1 = sum2(S1), s2 = sum2(S2), dx = cl.dx;
-                const float vals[9] = {fmaf(q0.w, s2, 2.f * q0.z * dx * s1), fmaf(q0.w * dx, s1, 2.f * q1.x * s2),
-                                       dx * dx * s1, dx * s2, sum2(S3), sum2(dop), sum2(dr), sum2(dg), sum2(db)};
-                int idx;
-                const float tot = warp_reduce9(vals, idx);
-                if (idx >= 0) {
-                    // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
-                    const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
-                    red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
+                const unsigned used = __ballot_sync(0xffffffffu, any);
+                if (used) {
+                    // p2 = A dx^2 + B dx dy + C dy^2 with dx = u - x, dy = v - y
+                    const float s1 = sum2(S1), s2 = sum2(S2), dx = cl.dx;
+                    const float vals[9] = {fmaf(q0.w, s2, 2.f * q0.z * dx * s1), fmaf(q0.w * dx, s1, 2.f * q1.x * s2),
+                                           dx * dx * s1, dx * s2, sum2(S3), sum2(dop), sum2(dr), sum2(dg), sum2(db)};
+                    if (__popc(used) <= bwd_direct_for(PX)) {
+                        // few lanes reached the splat: each adds its own nine values (fewer issue slots than
+                        // the warp reduction; the same sums in another order)
+                        if (any) {
+                            float *g = grad2d + 12LL * st.id[j];
+#pragma unroll
+                            for (int i = 0; i < 9; ++i)
+                                red_add_f32(g + i, (i == 2 || i == 4) ? -0.5f * LOG2E * vals[i]
+                                                                      : (i == 3 ? -LOG2E * vals[i] : vals[i]));
+                        }
+                    } else {
+                        int idx;
+                        const float tot = warp_reduce9(vals, idx);
+                        if (idx >= 0) {
+                            // back from the base-2 exponent domain: A = -0.5 log2e a, B = -log2e b, C = -0.5 log2e c
+                            const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
+                            red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
+                        }
+                    }
                 }
             }
+            __syncwarp();
+            top = base;
+            base = nbase;
         }
         __syncwarp();
-        top = base;
-        base = nbase;
+    };
+    if constexpr (PERSIST) {
+        int t, warp;
+        while (wc.next(t, warp, pw)) tile_body(t, warp);
+    } else {
+        tile_body((int)blockIdx.x, pw);
     }
+}
+
+// --------------------------------------------------------------------------- tile order
+//
+// Longest list first (a longest-processing-time order of the tiles of every item): a counting
+// sort of the tiles by the bit length of their list, descending (tiles of equal bit length in
+// no particular order; every tile's result is independent of the order). ctl (ORDER_CTL words,
+// zeroed before the first kernel): [0, 33) bucket sizes, [33, 66) bucket cursors, [66] the
+// persistent kernel's work counter.
+
+constexpr int ORDER_BUCKETS = 33;
+
+__device__ __forceinline__ int list_bucket(const int *ts, int t)
+{
+    const int len = ts[t + 1] - ts[t];
+    return len <= 0 ? 0 : 32 - __clz(len);  // bit length, 1..32
+}
+
+__global__ void __launch_bounds__(256) k_order_count(const int *__restrict__ ts, int n_tiles, unsigned *__restrict__ ctl)
+{
+    pdl_wait();
+    __shared__ unsigned h[ORDER_BUCKETS];
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[list_bucket(ts, t)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x)
+        if (h[i]) atomicAdd(&ctl[i], h[i]);
+}
+
+__global__ void __launch_bounds__(256) k_order_place(const int *__restrict__ ts, int n_tiles, unsigned *__restrict__ ctl,
+                                                     int *__restrict__ order)
+{
+    pdl_wait();
+    __shared__ unsigned base[ORDER_BUCKETS];
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int b = ORDER_BUCKETS - 1; b >= 0; --b) {  // longest lists first
+            base[b] = acc;
+            acc += ctl[b];
+        }
+    }
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const int b = list_bucket(ts, t);
+        order[base[b] + atomicAdd(&ctl[ORDER_BUCKETS + b], 1u)] = t;
+    }
+}
+
+cudaError_t launch_tile_order(const int *ts, int n_tiles, int *order, unsigned *ctl, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * ORDER_CTL, st);
+    if (e != cudaSuccess || n_tiles == 0) return e;
+    const unsigned blocks = (unsigned)((n_tiles + 255) / 256 < 2 * 148 ? (n_tiles + 255) / 256 : 2 * 148);
+    count_launch(2);
+    launch_pdl(k_order_count, dim3(blocks), dim3(256), 0, st, ts, n_tiles, ctl);
+    launch_pdl(k_order_place, dim3(blocks), dim3(256), 0, st, ts, n_tiles, ctl, order);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------- launchers
 
+// Persistent grid of a compositing kernel: as many blocks as fit resident on the current device
+// (resident blocks per SM from the occupancy calculator, cached per kernel and device).
+template <typename K>
+static unsigned persistent_blocks(K kernel, int threads, unsigned n_tiles)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;  // (kernel, device) -> blocks
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int g = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto key = std::make_pair(reinterpret_cast<const void *>(kernel), dev);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            int sms = 1, b = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) b = 1;
+            it = cache.emplace(key, b * (sms > 0 ? sms : 1)).first;
+        }
+        g = it->second;
+    }
+    return (unsigned)g < n_tiles ? (unsigned)g : (n_tiles > 0 ? n_tiles : 1);
+}
+
+template <typename K, typename... Args>
+static void launch_render(K kernel, const BatchParams &P, int threads, const int *order, cudaStream_t st, Args &&...args)
+{
+    const unsigned grid = order ? persistent_blocks(kernel, threads, (unsigned)P.n_tiles) : (unsigned)P.n_tiles;
+    launch_pdl(kernel, dim3(grid), dim3(threads), 0, st, P, std::forward<Args>(args)...);
+}
+
 template <int TW, int TH, int PX>
 static cudaError_t fwd_t(const BatchParams &P, const float *splat, const int *ts, const int *ids, float *rgb, float *T,
-                         int *nc, float *depth, cudaStream_t st)
+                         int *nc, float *depth, const int *order, unsigned *work, cudaStream_t st)
 {
     count_launch();
     const float4 *sp = reinterpret_cast<const float4 *>(splat);
-    if (depth)
-        launch_pdl(k_render_fwd<TW, TH, PX, true>, dim3(P.n_tiles), dim3(32 * Slab<TW, TH, PX>::WARPS), 0, st, P, sp, ts, ids, rgb, T, nc,
-                                                                                          depth);
+    const int threads = 32 * Slab<TW, TH, PX>::WARPS;
+    if (depth && order)
+        launch_render(k_render_fwd<TW, TH, PX, true, true>, P, threads, order, st, sp, ts, ids, rgb, T, nc, depth, order, work);
+    else if (depth)
+        launch_render(k_render_fwd<TW, TH, PX, true, false>, P, threads, order, st, sp, ts, ids, rgb, T, nc, depth, order,
+                      work);
+    else if (order)
+        launch_render(k_render_fwd<TW, TH, PX, false, true>, P, threads, order, st, sp, ts, ids, rgb, T, nc,
+                      (float *)nullptr, order, work);
     else
-        launch_pdl(k_render_fwd<TW, TH, PX, false>, dim3(P.n_tiles), dim3(32 * Slab<TW, TH, PX>::WARPS), 0, st, P, sp, ts, ids, rgb, T, nc,
-                                                                                           nullptr);
+        launch_render(k_render_fwd<TW, TH, PX, false, false>, P, threads, order, st, sp, ts, ids, rgb, T, nc,
+                      (float *)nullptr, order, work);
     return cudaGetLastError();
 }
 
 template <int TW, int TH, int PX>
 static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *splat, const int *ts, const int *ids,
-                         const float *rgb, const int *nc, const float *dL, float *g2d, cudaStream_t st)
+                         const float *rgb, const int *nc, const float *dL, float *g2d, const int *order, unsigned *work,
+                         cudaStream_t st)
 {
     count_launch();
     const int threads = 32 * Slab<TW, TH, PX>::WARPS;
     const float4 *sp = reinterpret_cast<const float4 *>(splat);
+#define LOBE_BWD_LAUNCH(K, R, Q) \
+    launch_render(K<TW, TH, PX, R, Q>, P, threads, order, st, sp, ts, ids, rgb, nc, dL, g2d, order, work)
     if constexpr (PX % 2 == 0) {  // pixel pairs in packed arithmetic
-        if (recompute)
-            launch_pdl(k_render_bwd2<TW, TH, PX, true>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
-        else
-            launch_pdl(k_render_bwd2<TW, TH, PX, false>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
+        if (recompute && order) LOBE_BWD_LAUNCH(k_render_bwd2, true, true);
+        else if (recompute) LOBE_BWD_LAUNCH(k_render_bwd2, true, false);
+        else if (order) LOBE_BWD_LAUNCH(k_render_bwd2, false, true);
+        else LOBE_BWD_LAUNCH(k_render_bwd2, false, false);
     } else {
-        if (recompute)
-            launch_pdl(k_render_bwd<TW, TH, PX, true>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
-        else
-            launch_pdl(k_render_bwd<TW, TH, PX, false>, dim3(P.n_tiles), dim3(threads), 0, st, P, sp, ts, ids, rgb, nc, dL, g2d);
+        if (recompute && order) LOBE_BWD_LAUNCH(k_render_bwd, true, true);
+        else if (recompute) LOBE_BWD_LAUNCH(k_render_bwd, true, false);
+        else if (order) LOBE_BWD_LAUNCH(k_render_bwd, false, true);
+        else LOBE_BWD_LAUNCH(k_render_bwd, false, false);
     }
+#undef LOBE_BWD_LAUNCH
     return cudaGetLastError();
 }
 
@@ -781,21 +974,32 @@ bool valid_px(int tw, int th, int px)
     } while (0)
 
 cudaError_t launch_render_fwd(const BatchParams &P, const float *splat, const int *ts, const int *ids, float *rgb,
-                              float *T, int *nc, float *depth, cudaStream_t st)
+                              float *T, int *nc, float *depth, int *order, unsigned *ctl, cudaStream_t st)
 {
     if (P.n_tiles == 0) return cudaSuccess;
+    if (order) {  // persistent: tiles longest list first
+        cudaError_t e = launch_tile_order(ts, P.n_tiles, order, ctl, st);
+        if (e != cudaSuccess) return e;
+    }
+    unsigned *work = order ? ctl + ORDER_CTL - 1 : nullptr;
     const int px = P.px_fwd ? P.px_fwd : default_px(P.tw, P.th, false);
-    LOBE_PX_DISPATCH(fwd_t, P, splat, ts, ids, rgb, T, nc, depth, st);
+    LOBE_PX_DISPATCH(fwd_t, P, splat, ts, ids, rgb, T, nc, depth, order, work, st);
 }
 
 cudaError_t launch_render_bwd(const BatchParams &P, bool recompute, const float *splat, const int *ts, const int *ids,
-                              const float *rgb, const int *nc, const float *dL, float *g2d, cudaStream_t st)
+                              const float *rgb, const int *nc, const float *dL, float *g2d, int *order, unsigned *ctl,
+                              cudaStream_t st)
 {
     cudaError_t err = P.n_entries > 0 ? cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)P.n_entries, st)
                                       : cudaSuccess;
     if (err != cudaSuccess || P.n_tiles == 0) return err;
+    if (order) {
+        err = launch_tile_order(ts, P.n_tiles, order, ctl, st);
+        if (err != cudaSuccess) return err;
+    }
+    unsigned *work = order ? ctl + ORDER_CTL - 1 : nullptr;
     const int px = P.px_bwd ? P.px_bwd : default_px(P.tw, P.th, true);
-    LOBE_PX_DISPATCH(bwd_t, P, recompute, splat, ts, ids, rgb, nc, dL, g2d, st);
+    LOBE_PX_DISPATCH(bwd_t, P, recompute, splat, ts, ids, rgb, nc, dL, g2d, order, work, st);
 }
 
 }  // namespace lobe

@@ -139,7 +139,7 @@ class Context:
     """A lobe_ctx bound to a CUDA stream (the current torch stream by default)."""
 
     def __init__(self, tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0), recompute_T=False, stream=None, px_fwd=0,
-                 px_bwd=0, bin_general=False):
+                 px_bwd=0, bin_general=False, persistent=False):
         if not torch.cuda.is_available():
             raise RuntimeError("the lobe rasterizer needs a CUDA device (no CPU fallback)")
         self.lib = A.lib()
@@ -149,6 +149,7 @@ class Context:
         self.recompute_T = bool(recompute_T)
         self.px = (int(px_fwd), int(px_bwd))
         self.bin_general = bool(bin_general)  # never the one-CTA binning of small batches
+        self.persistent = bool(persistent)  # compositing as persistent kernels, tiles longest list first
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = ctypes.c_void_p()
         A.check(self.lib.lobe_ctx_create(ctypes.byref(self.handle), ctypes.c_void_p(self.stream.cuda_stream),
@@ -163,10 +164,13 @@ class Context:
         c.recompute_T = int(self.recompute_T)
         c.px_fwd, c.px_bwd = self.px
         c.bin_general = int(self.bin_general)
+        c.persistent = int(self.persistent)
         return c
 
-    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None, px=None):
+    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None, px=None, persistent=None):
         """Change the configuration (tile changes need new bins; px = (fwd, bwd) pixels per lane)."""
+        if persistent is not None:
+            self.persistent = bool(persistent)
         if px is not None:
             self.px = (int(px[0]), int(px[1]))
         if tile is not None:

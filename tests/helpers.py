@@ -207,6 +207,17 @@ def assert_envelope(gpu, lo, hi, name, abs_sum=None, rtol=GRAD_RTOL):
     return e
 
 
+# End to end, the GPU composites its own float32 splats, whose per-pixel terms differ from the
+# oracle's FP64 ones by the float32 projection's error, not only by float32 sums. Where a
+# per-splat gradient is a sum of terms that cancel, that difference is a fraction of the sum of
+# the terms' magnitudes, not of the result: the end-to-end envelope is widened by E2E_TERM_REL
+# times that sum. E2E_TERM_REL is the relative float32 error of an end-to-end alpha that the
+# branch margins already assume (MARGINS_E2E); the largest seen on the full-size batched views
+# was 4e-4 of the sum. The stage tests, on identical float32 splats, keep the tight
+# float32-summation floor.
+E2E_TERM_REL = float(oracle.MARGINS_E2E[0])
+
+
 def split2d(a):
     """[n,12] grad2d layout -> oracle.Grad2D."""
     a = np.asarray(a, np.float64)

@@ -25,7 +25,7 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import (assert_envelope, assert_params_in_envelope, match_image, oracle_grad2d_array,
+from tests.helpers import (E2E_TERM_REL, assert_envelope, assert_params_in_envelope, match_image, oracle_grad2d_array,
                            param_envelope, rect_tiles, resolve_membership, splat_array, windows_tiles)
 
 pytestmark = pytest.mark.gpu
@@ -248,7 +248,11 @@ def test_fullsize_multi_block_batched_graph():
             lo += l
             hi += h
             ab += a
-        # the per-splat 2D gradients of this item's entries (end to end: the GPU's own splats)
+        # end to end the GPU's own float32 splats: the envelope widened by E2E_TERM_REL of the
+        # terms' magnitudes
+        lo -= E2E_TERM_REL * ab
+        hi += E2E_TERM_REL * ab
+        # the per-splat 2D gradients of this item's entries
         g2 = st.grad2d[e0:e0 + p.n].cpu().numpy()
         seen = np.abs(ab[:, :9]).sum(1) > 0
         for nm, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),

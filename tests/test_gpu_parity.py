@@ -228,8 +228,9 @@ def test_small_batch_binning_equals_general_and_oracle():
             np.testing.assert_array_equal(a, want_ids[want_ts[t]:want_ts[t + 1]])
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 16)])
-def test_render_fwd_matches_oracle(small, tile):
+def test_render_fwd_matches_oracle(small, tile, persistent):
     wl, g = small
     wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
     cam = wl.cameras[0].as_dict()
@@ -237,7 +238,7 @@ def test_render_fwd_matches_oracle(small, tile):
     bg = (0.1, 0.2, 0.3)
     eb = oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts)
     lv = oracle.render_leaves(p, eb, cam, tile, bg, oracle.MARGINS_STAGE, certain=True)
-    ctx = ctx_for(wl, bg=bg)
+    ctx = ctx_for(wl, bg=bg, persistent=persistent)
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, tile)
     bins = lobe.bin_sort(ctx, batch, gp)
@@ -248,9 +249,11 @@ def test_render_fwd_matches_oracle(small, tile):
     match_image(lv, rgb, T, nc, "image small (stage)")
 
 
-@pytest.mark.parametrize("recompute, tile, px", [(False, (16, 16), 0), (True, (16, 16), 0), (False, (16, 8), 1),
-                                                  (False, (16, 8), 4), (True, (16, 8), 4)])
-def test_render_bwd_matches_oracle(small, recompute, tile, px):
+@pytest.mark.parametrize("recompute, tile, px, persistent", [(False, (16, 16), 0, False), (True, (16, 16), 0, False),
+                                                              (False, (16, 8), 1, False), (False, (16, 8), 4, False),
+                                                              (True, (16, 8), 4, False), (False, (16, 8), 4, True),
+                                                              (True, (8, 8), 1, True), (False, (32, 16), 8, True)])
+def test_render_bwd_matches_oracle(small, recompute, tile, px, persistent):
     wl, g = small
     wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
     cam = wl.cameras[0].as_dict()
@@ -259,7 +262,7 @@ def test_render_bwd_matches_oracle(small, recompute, tile, px):
     eb = oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts)
     lv = oracle.render_leaves(p, eb, cam, wl.tile, bg, oracle.MARGINS_STAGE, certain=True)
     dL = np.random.default_rng(3).standard_normal((3, 128, 128)).astype(np.float32).astype(np.float64)
-    ctx = ctx_for(wl, bg=bg, recompute_T=recompute, px_fwd=px, px_bwd=px)
+    ctx = ctx_for(wl, bg=bg, recompute_T=recompute, px_fwd=px, px_bwd=px, persistent=persistent)
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, wl.tile)
     bins = lobe.bin_sort(ctx, batch, gp)
@@ -356,6 +359,32 @@ def test_project_bwd_sums_views_like_oracle(small):
     assert (rad > 0).any(axis=0).sum() > 500 and (rad > 0).all(axis=0).sum() > 100  # many seen by both views
     assert env["sd_cnt"][1].max() == 2
     assert_params_in_envelope(gr, env, "(two views)")
+
+
+def test_persistent_compositing_equals_one_block_per_tile():
+    """The persistent kernels (warps taking tiles longest list first from a device counter)
+    render every item of a ragged multi-item batch bit for bit like one block per tile, and
+    their adjoint sums the same per-splat gradients (float32 atomic order aside)."""
+    rng = np.random.default_rng(41)
+    sets = [scenes.uniform_gaussians(rng, 2500, 1.0, 2.0, 6.0), scenes.uniform_gaussians(rng, 1500, 1.0, 2.0, 6.0)]
+    cams = [scenes.pinhole(300, 170, 240.0), scenes.pinhole(97, 131, 100.0),
+            scenes.pinhole(256, 256, 220.0, viewmat=scenes.look_at((0.3, 0.2, -0.2), (0, 0, 4.0), up=(0, -1, 0)))]
+    items = [(0, 0, -1), (1, 1, -1), (0, 2, -1), (1, 0, -1)]
+    for tile, px in (((16, 8), (2, 4)), ((32, 16), (4, 8)), ((8, 8), (1, 1))):
+        wl = scenes.Workload("p", sets, cams, [], items, tile)
+        batch = make_batch(wl)
+        dL = torch.as_tensor(np.random.default_rng(3).standard_normal(3 * batch.n_pixels), dtype=torch.float32).cuda()
+        out = []
+        for persistent in (False, True):
+            ctx = ctx_for(wl, px_fwd=px[0], px_bwd=px[1], persistent=persistent)
+            proj, bins, img = lobe.forward(ctx, batch)
+            g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
+            ctx.status()
+            out.append((img, g2d))
+        (a, ga), (b, gb) = out
+        assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T_final, b.T_final) and torch.equal(a.n_contrib, b.n_contrib)
+        scale = float(ga.abs().max())
+        assert float((ga - gb).abs().max()) <= 1e-5 * scale, tile
 
 
 def test_batched_equals_plain():
