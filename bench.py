@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--workload", default="multi", choices=WORKLOADS)
     ap.add_argument("--tile", default="auto", help="WxH, or auto: tile shape and pixels per lane by the autotuner")
     ap.add_argument("--px", default="0,0", help="with --tile WxH: pixels per lane of the composite and its adjoint")
+    ap.add_argument("--persistent", action="store_true", help="with --tile WxH: persistent compositing kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the medium view, batched-vs-plain, fast camera "
                                                               "selection, densification, Adam and training measurements")
@@ -348,7 +349,8 @@ def make_step(lobe, wl, args, rank, sets=None, tile=None, px=None):
         st, tuning = autotune(sets, cams, wl.items, wl.blocks, reps=3, use_cache=False, dL_init=fill,
                               recompute_T=args.recompute)
     else:
-        st = BatchedStep(sets, cams, wl.items, wl.blocks, tile=tile, px=px, recompute_T=args.recompute)
+        st = BatchedStep(sets, cams, wl.items, wl.blocks, tile=tile, px=px, recompute_T=args.recompute,
+                         persistent=args.persistent)
     # dL/dC of the training loss
     tsets = [lobe.GaussianSet.from_numpy(scenes.perturbed_copy(s, seed=2 + rank)) for s in wl.sets]
     if wl.name.startswith("city"):
@@ -953,7 +955,7 @@ def main():
         sampler.close()
     if world == 1 and not args.no_extras:
         extras["batched_vs_plain"] = batched_vs_plain(lobe, torch, wl, sets, st, float(np.median(step_ms)))
-    graph_tile, graph_px = st.tile, st.px
+    graph_tile, graph_px, graph_persistent = st.tile, st.px, st.persistent
     del st
     torch.cuda.empty_cache()
     if world == 1 and not args.no_extras and args.workload != "medium":
@@ -977,6 +979,7 @@ def main():
                        "views": len(wl.items), "pixels": st_pixels(wl),
                        "tile": list(graph_tile), "px_per_lane": {"fwd": graph_px[0] or "default",
                                                                   "bwd": graph_px[1] or "default"},
+                       "persistent_compositing": graph_persistent,
                        "tuning_ms": ({k: round(v, 4) for k, v in tuning.items()} if tuning else None),
                        "sh_degree": 3, **counts,
                        "step": "one CUDA graph replay: projection (each set once for all its views), binning of "

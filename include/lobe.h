@@ -410,6 +410,35 @@ lobe_status lobe_project_bwd_adam(lobe_ctx *ctx, const lobe_batch *batch, const 
  * masks[s] are device pointers (uint8 [n]); they are OR-ed into, not cleared. */
 lobe_status lobe_visibility_crop(lobe_ctx *ctx, const lobe_batch *batch, uint8_t *const *masks);
 
+/* Load-balanced KD-tree partition with cutline refinement (Alg. 1, Sec. 3.1). Host code, no
+ * device work of its own. The tree grows best first on the workload L(B) = |C(B)|, the number
+ * of cameras assigned to a box (largest first; the earliest created among equals); a node is
+ * cut along the longer of the x / y extents of the coarse centres inside it (centers: HOST
+ * [n][3], doubles), at the q-quantile of those centres' coordinates (linear interpolation
+ * between order statistics at (n - 1) q), q starting at 0.5 and, for `steps` rounds, moved by
+ * bisection toward the lighter child within [q_lo, q_hi]; the children of the last evaluated cut
+ * are kept. A child's cameras are its parent's whose visibility ratio V (Sec. 3.2) for the
+ * child box reaches tau. Boxes are half-open, lo <= p < hi, and may be infinite.
+ * `ratios(user, boxes, n_boxes, V)` must write V[c * n_boxes + b] for every camera c < n_cams
+ * and return 0 (nonzero aborts with LOBE_ERR_ARG); on the GPU it is one lobe_fcs_coverage pass
+ * over the cameras' depth maps. Outputs (host): leaves[n_blocks] in creation order and
+ * leaf_cams[n_blocks][n_cams] (1 = camera assigned). The paper's values: tau = 0.1, q in [0.1,
+ * 0.9], 3 rounds. */
+typedef struct {
+    double lo[3];
+    double hi[3];
+} lobe_box_d;
+typedef int32_t (*lobe_ratio_fn)(void *user, const lobe_box_d *boxes, int32_t n_boxes, double *V);
+typedef struct {
+    int32_t n_blocks;  /* leaves to grow, >= 1 */
+    double tau;        /* camera assignment threshold on V [0.1] */
+    double q_lo, q_hi; /* bounds of the cut percentile [0.1, 0.9] */
+    int32_t steps;     /* refinement rounds, >= 1 [3] */
+} lobe_kd_params;
+lobe_status lobe_kd_partition(const double *centers, int64_t n, const lobe_box_d *root, int32_t n_cams,
+                              lobe_ratio_fn ratios, void *user, const lobe_kd_params *prm, lobe_box_d *leaves,
+                              uint8_t *leaf_cams);
+
 /* Throughput probe of one instruction kind (a measurement helper, not part of the method):
  * `blocks` blocks of 256 threads, each thread running eight independent chains of `iters`
  * steps of kind 0 = scalar fma.rn.f32 (2 FLOP), 1 = packed fma.rn.f32x2 (4 FLOP), 2 =

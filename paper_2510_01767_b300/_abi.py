@@ -49,6 +49,19 @@ class Batch(ctypes.Structure):
                 ("items", ctypes.POINTER(Item)), ("n_items", ctypes.c_int32)]
 
 
+class BoxD(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class KdParams(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("tau", ctypes.c_double), ("q_lo", ctypes.c_double),
+                ("q_hi", ctypes.c_double), ("steps", ctypes.c_int32)]
+
+
+RATIO_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(BoxD), ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_double))
+
+
 class Config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("recompute_T", ctypes.c_int32), ("px_fwd", ctypes.c_int32),
@@ -103,6 +116,8 @@ SIGNATURES = {
     "lobe_abi_version": (ctypes.c_int32, []),
     "lobe_peak_probe": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp]),
     "lobe_sync_status": (ctypes.c_int, [vp]),
+    "lobe_kd_partition": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(BoxD), ctypes.c_int32, RATIO_FN, vp,
+                                         ctypes.POINTER(KdParams), ctypes.POINTER(BoxD), vp]),
     "lobe_fcs_select": (ctypes.c_int, [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp]),
     "lobe_kernel_launches": (ctypes.c_int64, []),
     "lobe_batch_sizes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Batch), ctypes.POINTER(ctypes.c_int64)]),

@@ -2,25 +2,25 @@
 fast camera selection on the GPU (Sec. 3.2).
 
 The camera sets of candidate boxes come from ``lobe_fcs_coverage`` over the depth maps of all
-cameras, rendered once from the coarse model (``camera_depths``); every cut the refinement
+cameras, rendered once from the coarse model (``CameraDepths``); every cut the refinement
 tries costs one pass over those maps. The tree logic itself (best-first growth on the
 workload L(B) = |C(B)|, axis choice, percentile cuts, bisection toward the lighter child) is
-host-side bookkeeping.
+host code in the library, ``lobe_kd_partition``; this module marshals its arguments.
 
 Readings (the paper leaves them open): boxes are half-open (lo <= p < hi) as for selective
 densification; the split axis is the longer of the x / y extents of the coarse centres inside
-the node; the cut at percentile q is numpy's linear-interpolated quantile of those centres'
-coordinates; after the bisection the children of the last evaluated cut are kept; among
+the node; the cut at percentile q interpolates linearly between the order statistics of those
+centres' coordinates at (n - 1) q; after the bisection the children of the last evaluated cut are kept; among
 leaves of equal workload the earliest created is split first.
 """
 from __future__ import annotations
 
-import heapq
-import math
+import ctypes
 
 import numpy as np
 import torch
 
+from . import _abi as A
 from . import raster as R
 
 
@@ -54,8 +54,8 @@ class CameraDepths:
     def ratios(self, boxes):
         """V[camera, box] = points inside the box / the camera's points (0 without points)."""
         counts, npts = R.fcs_coverage(self.ctx, self.batch, self.image, self.depth, boxes, self.normalize)
-        c, n = counts.cpu().numpy().astype(np.float64), npts.cpu().numpy().astype(np.float64)
-        return np.where(n[:, None] > 0, c / np.maximum(n, 1)[:, None], 0.0)
+        V, _ = R.fcs_select(counts, npts, tau=0.0)
+        return V.numpy()
 
 
 class Box:
@@ -63,44 +63,38 @@ class Box:
         self.lo, self.hi = tuple(float(x) for x in lo), tuple(float(x) for x in hi)
 
 
-def kd_partition(centers, root, n_blocks: int, depths: CameraDepths, tau=0.1, q_lo=0.1, q_hi=0.9, steps=3):
-    """Returns the leaves [(lo, hi, camera indices)] in creation order (see the module)."""
-    centers = np.asarray(centers, np.float64)
-    lo0 = np.array(root.lo, np.float64)
-    hi0 = np.array(root.hi, np.float64)
+def kd_partition(centers, root, n_blocks: int, depths, tau=0.1, q_lo=0.1, q_hi=0.9, steps=3):
+    """Returns the leaves [(lo, hi, camera indices)] in creation order (see the module); the
+    tree runs in the library (``lobe_kd_partition``), calling back here only for the ratios
+    (``depths.ratios(boxes)``, a [cameras, boxes] array)."""
+    c = np.ascontiguousarray(np.asarray(centers, np.float64).reshape(-1, 3))
+    n_cams = len(depths.cameras)
+    root_box = A.BoxD()
+    root_box.lo[:] = [float(x) for x in root.lo]
+    root_box.hi[:] = [float(x) for x in root.hi]
+    failure = []
 
-    def cams_of(boxes, parent):
-        V = depths.ratios([Box(lo, hi) for lo, hi in boxes])
-        return [[c for c in parent if V[c, b] >= tau] for b in range(len(boxes))]
+    def ratios(_user, boxes, nb, out):
+        try:
+            bx = [Box(tuple(boxes[b].lo), tuple(boxes[b].hi)) for b in range(nb)]
+            V = np.ascontiguousarray(depths.ratios(bx), np.float64).reshape(n_cams, nb)
+            ctypes.memmove(out, V.ctypes.data, V.nbytes)
+            return 0
+        except Exception as e:  # reported after the call returns
+            failure.append(e)
+            return 1
 
-    root_cams = cams_of([(lo0, hi0)], list(range(len(depths.cameras))))[0]
-    heap = [(-len(root_cams), 0, lo0, hi0, root_cams)]
-    serial = 1
-    while len(heap) < n_blocks:
-        _, _, lo, hi, cams = heapq.heappop(heap)
-        m = np.all((centers >= lo) & (centers < hi), axis=1)
-        pts = centers[m]
-        ext = [float(pts[:, d].max() - pts[:, d].min()) if len(pts) else 0.0 for d in (0, 1)]
-        a = 0 if ext[0] >= ext[1] else 1
-        coords = np.sort(pts[:, a])
-        qlo, qhi, q = q_lo, q_hi, 0.5
-        for _ in range(steps):
-            cut = float(np.quantile(coords, q)) if len(coords) else 0.5 * (lo[a] + hi[a])
-            hl, lr = hi.copy(), lo.copy()
-            hl[a] = cut
-            lr[a] = cut
-            cl, cr = cams_of([(lo, hl), (lr, hi)], cams)
-            if len(cl) > len(cr):
-                qhi, q = q, 0.5 * (qlo + q)
-            elif len(cr) > len(cl):
-                qlo, q = q, 0.5 * (qhi + q)
-            else:
-                break
-        heapq.heappush(heap, (-len(cl), serial, lo, hl, cl))
-        heapq.heappush(heap, (-len(cr), serial + 1, lr, hi, cr))
-        serial += 2
-    leaves = sorted(heap, key=lambda e: e[1])
-    return [(lo, hi, cams) for _, _, lo, hi, cams in leaves]
+    cb = A.RATIO_FN(ratios)
+    prm = A.KdParams(int(n_blocks), float(tau), float(q_lo), float(q_hi), int(steps))
+    leaves = (A.BoxD * int(n_blocks))()
+    cams = np.zeros((int(n_blocks), max(n_cams, 1)), np.uint8)
+    code = A.lib().lobe_kd_partition(c.ctypes.data, c.shape[0], ctypes.byref(root_box), n_cams, cb, None,
+                                     ctypes.byref(prm), leaves, cams.ctypes.data)
+    if failure:
+        raise failure[0]
+    A.check(code)
+    return [(np.array(leaves[b].lo), np.array(leaves[b].hi), [int(k) for k in np.nonzero(cams[b, :n_cams])[0]])
+            for b in range(int(n_blocks))]
 
 
 def workloads(leaves):
