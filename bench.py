@@ -932,6 +932,7 @@ def main():
 
     work, counts = stage_algorithmic_work(torch, st, reference_pairs(lobe, torch, st))
     stages, dom = stage_table(stage_ms, work, hbm_peak, fp32_peak)
+    st_tile, st_px, st_persistent = st.tile, st.px, st.persistent
     tb = traffic_of("bin_sort", wl.name)
     if tb:
         stages["bin_sort"]["dram_bytes_per_call"] = tb["bytes_per_launch"]
@@ -941,6 +942,9 @@ def main():
     stages["bin_sort"]["work_note"] = ("achieved/frac count 44 B per intersection: the duplication + pair sort + "
                                        "ranges of the 3DGS design, a work-equivalent this binning does not run")
     tr = traffic_of(dom, wl.name)
+    if tr and "tile" in tr and (list(tr["tile"]) != list(st_tile) or list(tr["px"]) != list(st_px) or
+                                bool(tr["persistent"]) != bool(st_persistent)):
+        tr = None  # captured with another kernel configuration than the one timed
     roof = {"stage": dom, "bound": stages[dom]["bound"], "achieved": stages[dom]["achieved"],
             "peak": stages[dom]["peak"], "unit": stages[dom]["unit"], "frac": stages[dom]["frac"],
             "traffic": tr.get("bytes_per_launch") if tr else None,

@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(256) k_order_place(const int *__restrict__ ts,
                                                      int *__restrict__ order)
 {
     pdl_wait();
-    __shared__ unsigned base[ORDER_BUCKETS];
+    __shared__ unsigned base[ORDER_BUCKETS], cnt[ORDER_BUCKETS], off[ORDER_BUCKETS];
     if (threadIdx.x == 0) {
         unsigned acc = 0;
         for (int b = ORDER_BUCKETS - 1; b >= 0; --b) {  // longest lists first
@@ -836,10 +836,23 @@ __global__ void __launch_bounds__(256) k_order_place(const int *__restrict__ ts,
             acc += ctl[b];
         }
     }
-    __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
-        const int b = list_bucket(ts, t);
-        order[base[b] + atomicAdd(&ctl[ORDER_BUCKETS + b], 1u)] = t;
+    for (int t0 = blockIdx.x * blockDim.x; t0 < n_tiles; t0 += gridDim.x * blockDim.x) {
+        for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        const int t = t0 + (int)threadIdx.x;
+        int b = -1;
+        unsigned rank = 0;
+        if (t < n_tiles) {
+            b = list_bucket(ts, t);
+            rank = atomicAdd(&cnt[b], 1u);  // rank within the block's share of the bucket
+        }
+        __syncthreads();
+        // one global reservation per (block round, bucket) instead of one per tile
+        for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x)
+            off[i] = cnt[i] ? atomicAdd(&ctl[ORDER_BUCKETS + i], cnt[i]) : 0u;
+        __syncthreads();
+        if (b >= 0) order[base[b] + off[b] + rank] = t;
+        __syncthreads();
     }
 }
 
