@@ -76,7 +76,8 @@ typedef struct {
 } lobe_gaussians;
 
 /* Pinhole camera (host struct). viewmat is the row-major 4x4 world->camera rigid transform
- * in OpenCV axes (x right, y down, +z forward); pixel (i,j) has centre (i+0.5, j+0.5). */
+ * in OpenCV axes (x right, y down, +z forward); pixel (i,j) has centre (i+0.5, j+0.5).
+ * An image may span at most 65535 tiles in each direction (LOBE_ERR_ARG beyond). */
 typedef struct {
     float viewmat[16];
     float fx, fy, cx, cy;

@@ -19,6 +19,8 @@
 //
 // A tile's list is its super-tile's list filtered by "tile in the splat's tile rectangle",
 // which preserves (depth, entry) order, so the output equals the global pair sort bit for bit.
+#include <type_traits>
+
 #include "sort_prims.cuh"
 
 namespace lobe {
@@ -29,34 +31,42 @@ constexpr int KEY_SHIFT = 16; // super-tile id above, packed local rectangle bel
 constexpr long long MAX_SUPER = 1LL << 16;
 constexpr long long MAX_SCAN_TILES = 1LL << 22;  // tiles per call (the tile scan's length)
 
-__device__ __forceinline__ void splat_rect(const BatchParams &P, const ItemParams &I, const float *splat,
-                                           const int *radius, uint32_t e, int &x0, int &y0, int &x1, int &y1)
-{
-    const float2 uv = *reinterpret_cast<const float2 *>(splat + 12LL * e);
-    tile_rect(uv.x, uv.y, radius[e], P.tw, P.th, I.gx, I.gy, x0, y0, x1, y1);
-}
-
 // Per depth-ordered visible splat k: its super-rectangle area (area[k]) and what the pair
 // expansion needs, in three words: info0 = super-tile id of the rectangle's origin | super
 // grid width << 16, info1 = (x0, x1) and info2 = (y0, y1) of its tile rectangle relative to
-// that origin (16 bits each).
+// that origin (16 bits each). The rectangle comes from rect[e], stored by the compaction.
 __global__ void __launch_bounds__(256) k_super_area(const __grid_constant__ BatchParams P, const uint32_t *V_dev,
-                                                    const uint32_t *__restrict__ order, const float *__restrict__ splat,
-                                                    const int *__restrict__ radius, uint32_t *__restrict__ area,
-                                                    uint32_t *__restrict__ info0, uint32_t *__restrict__ info1,
-                                                    uint32_t *__restrict__ info2)
+                                                    const uint32_t *__restrict__ order, const uint2 *__restrict__ rect,
+                                                    uint32_t *__restrict__ area, uint32_t *__restrict__ info0,
+                                                    uint32_t *__restrict__ info1, uint32_t *__restrict__ info2)
 {
+    // the items' entry offsets and super-tile grids, in shared memory: the splats of a warp
+    // belong to different items, and a search over the kernel parameters would serialise
+    static_assert(LOBE_MAX_ITEMS <= 256, "one thread of the block per item");
+    __shared__ int s_eoff[LOBE_MAX_ITEMS], s_soff[LOBE_MAX_ITEMS], s_sgx[LOBE_MAX_ITEMS];
     pdl_wait();
+    const int n_items = P.n_items;
+    if (threadIdx.x < n_items) {
+        const ItemParams &I = P.item[threadIdx.x];
+        s_eoff[threadIdx.x] = (int)I.entry_off;
+        s_soff[threadIdx.x] = I.super_off;
+        s_sgx[threadIdx.x] = I.sgx;
+    }
+    __syncthreads();
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= *V_dev) return;
     const uint32_t e = order[k];
-    const ItemParams &I = P.item[item_of_entry(P, e)];
-    int x0, y0, x1, y1;
-    splat_rect(P, I, splat, radius, e, x0, y0, x1, y1);
-    const int S = P.S;
+    const uint2 r = rect[e];
+    int lo = 0, hi = n_items - 1;  // item of entry e: the last whose entries start at or before e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint32_t)s_eoff[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int x0 = (int)(r.x & 0xffffu), y0 = (int)(r.x >> 16), x1 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
+    const int S = P.S, sgx = s_sgx[lo];
     const int sx0 = x0 / S, sy0 = y0 / S;
     area[k] = (uint32_t)(((x1 + S - 1) / S - sx0) * ((y1 + S - 1) / S - sy0));
-    info0[k] = (uint32_t)(I.super_off + sy0 * I.sgx + sx0) | ((uint32_t)I.sgx << 16);
+    info0[k] = (uint32_t)(s_soff[lo] + sy0 * sgx + sx0) | ((uint32_t)sgx << 16);
     info1[k] = (uint32_t)(x0 - sx0 * S) | ((uint32_t)(x1 - sx0 * S) << 16);
     info2[k] = (uint32_t)(y0 - sy0 * S) | ((uint32_t)(y1 - sy0 * S) << 16);
 }
@@ -197,10 +207,36 @@ __global__ void __launch_bounds__(256) k_chunk_map(const uint32_t *__restrict__ 
     }
 }
 
-__device__ __forceinline__ bool covers(uint32_t key, int tx, int ty)
+// Local tiles of the super-tile that a super pair's key covers, as a bit mask (bit ty * S + tx):
+// the row's bits [x0, x1) repeated on rows [y0, y1). The row spreads as a multiplication by a
+// word with bit S * y set for every covered row, so no carries cross rows (the row is S bits
+// wide). An empty rectangle (the key 0 of a missing pair) gives 0.
+template <int S>
+struct CoverMask {
+    using T = typename std::conditional<S == 8, unsigned long long, uint32_t>::type;
+    static constexpr T ROWS = S == 8 ? (T)0x0101010101010101ull : (T)0x1111u;  // bit S * y for y < S
+    __device__ static __forceinline__ T of(uint32_t key)
+    {
+        const uint32_t x0 = key & 15u, x1 = (key >> 4) & 15u, y0 = (key >> 8) & 15u, y1 = (key >> 12) & 15u;
+        const uint32_t row = ((1u << x1) - 1u) & ~((1u << x0) - 1u);
+        const T below1 = y1 >= (uint32_t)S ? ROWS : (T)(ROWS & (((T)1 << (S * y1)) - 1));
+        const T below0 = y0 >= (uint32_t)S ? ROWS : (T)(ROWS & (((T)1 << (S * y0)) - 1));
+        return (T)row * (below1 & ~below0);
+    }
+};
+
+// Per local tile, how many of the warp's 32 keys cover it, four tiles a word: byte j of
+// word q counts tile 4q + j (at most 32, so the bytes never carry). Each lane spreads four
+// mask bits into the low bits of four bytes (the multiplication places bit j at bit 8j, the
+// mask drops the other copies) and one integer warp reduction adds the words of all lanes.
+template <int S>
+__device__ __forceinline__ void warp_tile_counts(typename CoverMask<S>::T mask, uint32_t (&c)[S * S / 4])
 {
-    return tx >= (int)(key & 15u) && tx < (int)((key >> 4) & 15u) && ty >= (int)((key >> 8) & 15u) &&
-           ty < (int)((key >> 12) & 15u);
+#pragma unroll
+    for (int q = 0; q < S * S / 4; ++q) {
+        const uint32_t nib = (uint32_t)(mask >> (4 * q)) & 15u;
+        c[q] = __reduce_add_sync(0xffffffffu, (nib * 0x00204081u) & 0x01010101u);
+    }
 }
 
 // Pass 1: cnt[w * S*S + t] = splats of chunk w covering local tile t.
@@ -212,26 +248,26 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_count(const uint32_t *__r
 {
     pdl_wait();
     constexpr int NT = S * S;
-    __shared__ uint32_t wc[BIN_THREADS / 32][NT];
+    __shared__ uint32_t wc[BIN_THREADS / 32][NT / 4];  // packed per-warp counts
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n_work = chunk_base[n_super];
     uint32_t w = blockIdx.x;
     uint4 wk = w < n_work ? work[w] : make_uint4(0u, 0u, 0u, 0u);
     while (w < n_work) {
         const uint32_t i = wk.y + threadIdx.x;
-        const uint32_t key = i < wk.z ? keys[i] : 0u;  // 0 = empty rectangle
+        const auto mask = CoverMask<S>::of(i < wk.z ? keys[i] : 0u);  // 0 = empty rectangle
         const uint32_t wn = w + gridDim.x;
         const uint4 wkn = wn < n_work ? work[wn] : make_uint4(0u, 0u, 0u, 0u);  // next item, in flight
+        uint32_t c4[NT / 4];
+        warp_tile_counts<S>(mask, c4);
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
-            if (lane == (t & 31)) wc[warp][t] = __popc(m);
-        }
+        for (int q = 0; q < NT / 4; ++q)
+            if (lane == q) wc[warp][q] = c4[q];
         __syncthreads();
         if (threadIdx.x < NT) {
             uint32_t c = 0;
 #pragma unroll
-            for (int q = 0; q < BIN_THREADS / 32; ++q) c += wc[q][threadIdx.x];
+            for (int q = 0; q < BIN_THREADS / 32; ++q) c += (wc[q][threadIdx.x >> 2] >> (8 * (threadIdx.x & 3))) & 255u;
             cnt[(size_t)w * NT + threadIdx.x] = c;
         }
         __syncthreads();
@@ -278,7 +314,10 @@ __global__ void __launch_bounds__(256) k_chunk_prefix(const __grid_constant__ Ba
     }
 }
 
-// Pass 3: each chunk's splats, in list order, to their tiles' ranges.
+// Pass 3: each chunk's splats, in list order, to their tiles' ranges. Per tile, warp w's
+// splats start at (tile's range start) + (chunk's offset in the tile) + (splats of warps < w):
+// that sum is formed once per (warp, tile) in shared memory; a splat's rank among its warp's
+// splats of the tile is the count of lower lanes in the tile's ballot.
 template <int S>
 __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constant__ BatchParams P,
                                                             const uint32_t *__restrict__ keys,
@@ -292,7 +331,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
     pdl_wait();
     constexpr int NT = S * S;
     __shared__ uint32_t wc[BIN_THREADS / 32][NT];
-    __shared__ uint32_t base[NT];
+    __shared__ uint32_t wcp[BIN_THREADS / 32][NT / 4];  // packed per-warp counts
     if (*n_use == 0) return;  // no pairs, or more than the bins hold
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
@@ -304,7 +343,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
         // this chunk's splats, its tiles' bases and the next work item, loaded together
         const int s = (int)wk.x;
         const uint32_t i = wk.y + threadIdx.x;
-        const uint32_t key = i < wk.z ? keys[i] : 0u;
+        const auto mask = CoverMask<S>::of(i < wk.z ? keys[i] : 0u);
         const int id = i < wk.z ? (int)vals[i] : 0;
         uint32_t tbase = 0;
         if (threadIdx.x < NT) {
@@ -316,28 +355,26 @@ __global__ void __launch_bounds__(BIN_THREADS) k_chunk_emit(const __grid_constan
         }
         const uint32_t wn = w + gridDim.x;
         const uint4 wkn = wn < n_work ? work[wn] : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t c4[NT / 4];
+        warp_tile_counts<S>(mask, c4);
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const unsigned m = __ballot_sync(0xffffffffu, covers(key, t % S, t / S));
-            if (lane == (t & 31)) wc[warp][t] = __popc(m);
-        }
+        for (int q = 0; q < NT / 4; ++q)
+            if (lane == q) wcp[warp][q] = c4[q];
         __syncthreads();
         if (threadIdx.x < NT) {
-            uint32_t r = 0;
+            uint32_t r = tbase;
 #pragma unroll
             for (int q = 0; q < BIN_THREADS / 32; ++q) {
-                const uint32_t c = wc[q][threadIdx.x];
                 wc[q][threadIdx.x] = r;
-                r += c;
+                r += (wcp[q][threadIdx.x >> 2] >> (8 * (threadIdx.x & 3))) & 255u;
             }
-            base[threadIdx.x] = tbase;
         }
         __syncthreads();
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const bool cov = covers(key, t % S, t / S);
+            const bool cov = (mask >> t) & 1u;
             const unsigned m = __ballot_sync(0xffffffffu, cov);
-            if (cov) gauss_ids[base[t] + wc[warp][t] + __popc(m & lt)] = id;
+            if (cov) gauss_ids[wc[warp][t] + __popc(m & lt)] = id;
         }
         __syncthreads();
         w = wn;
@@ -373,19 +410,18 @@ cudaError_t bin_super_count(const BatchParams &P, const float *splat, const int 
 {
     const long long n = P.n_entries;
     uint32_t *V = b.scalars, *n_sp = b.scalars + 1, *sp_total = b.scalars + 4;
-    scan(LoadVisible{tiles}, nullptr, n, b.vis_pos, V, nullptr, nullptr, -1, lb_of(b, ST_SCAN_VISIBLE), st, true,
-         b.os_hist, 4 * 256);
-    if (n > 0) {
+    {
+        const long long nt = (n + CH_SPAN - 1) / CH_SPAN;
         count_launch();
-        launch_pdl(k_compact_hist, dim3((unsigned)((n + CH_SPAN - 1) / CH_SPAN)), dim3(CH_THREADS), 0, st, n, tiles, splat,
-                   b.vis_pos, b.dkA, b.dvA, b.os_hist);
+        launch_pdl(k_compact, dim3((unsigned)(nt < 1 ? 1 : nt)), dim3(CH_THREADS), 0, st, P, tiles, splat, radius, b.dkA,
+                   b.dvA, b.rect, b.os_hist, V, lb_of(b, ST_SCAN_VISIBLE));
     }
     onesweep_sort32(V, n, b.dkA, b.dvA, b.dkB, b.dvB, b.dkA, b.vis_pos, b.os_hist, b.os_slots, lb_of(b, ST_DEPTH_PASS),
                     st);
     if (n > 0) {
         count_launch();
-        launch_pdl(k_super_area, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, P, V, b.vis_pos, splat, radius, b.offs, b.dkA,
-                                                                  b.dvA, b.dkB);  // free after the depth sort
+        launch_pdl(k_super_area, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, P, V, b.vis_pos, b.rect, b.offs, b.dkA,
+                   b.dvA, b.dkB);  // free after the depth sort
     }
     scan(LoadPlain{b.offs}, V, n, b.offs, sp_total, nullptr, n_sp, pair_capacity, lb_of(b, ST_SCAN_OFFS), st);
     return cudaGetLastError();
@@ -466,22 +502,37 @@ cudaError_t bin_sort_emit(const BatchParams &P, const float *splat, const int *r
 
 // ------------------------------------------------------------------ scratch layout
 //
-// entry part: 6 arrays of max_entries words, radix digit counts, scalars, the scans' look-back
-//             words (one per 4096 elements of the longest scan), the depth keys' four digit
-//             histograms, the depth sort's look-back words (256 per 2048 entries)
+// entry part: 6 arrays of max_entries words, the radix digit counts (sized for the larger of
+//             the counts and 2 words per entry: the same words hold the tile rectangles from
+//             the compaction to the pass over the depth-ordered splats, before the super-tile
+//             sort counts), scalars, the look-back words of the scans and the compaction (one
+//             per tile of the longest of them), the depth keys' four digit histograms, the depth sort's look-back
+//             words (256 per OS_TILE entries)
 // pair part:  4 arrays of max_pairs words (super-tile pairs, ping-pong), the chunk work table
 //             (16 B per chunk), per-chunk tile counts
 // super part: super-tile list starts and chunk bases (max_super + 1 words each)
 // Look-back slots must be zero (or hold words of earlier calls) before first use.
 
 static size_t words_rounded(size_t words) { return ((words * 4 + 255) / 256) * 256; }
+// look-back words of the scans and of the compaction (one per tile of the longest of them)
+static long long lookback_slots(long long max_entries)
+{
+    const long long a = scan_slots(max_scan_length(max_entries));
+    const long long c = ((max_entries > 0 ? max_entries : 1) + CH_SPAN - 1) / CH_SPAN;
+    return a > c ? a : c;
+}
+static size_t count_words(size_t e)
+{
+    const size_t c = (size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS;
+    return c > 2 * e ? c : 2 * e;
+}
 static size_t slots_rounded(long long slots) { return (((size_t)slots * 8 + 255) / 256) * 256; }
 
 size_t entry_scratch_bytes(long long max_entries)
 {
     size_t e = (size_t)(max_entries > 0 ? max_entries : 1);
-    return 6 * words_rounded(e) + words_rounded((size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS) + words_rounded(16) +
-           slots_rounded(scan_slots(max_scan_length(max_entries))) + words_rounded(4 * 256) +
+    return 6 * words_rounded(e) + words_rounded(count_words(e)) + words_rounded(16) +
+           slots_rounded(lookback_slots(max_entries)) + words_rounded(4 * 256) +
            slots_rounded(onesweep_slots(max_entries));
 }
 
@@ -525,9 +576,10 @@ void entry_scratch_carve(void *mem, long long max_entries, int *ctl, BinScratch 
     Carver c{static_cast<char *>(mem)};
     b.vis_pos = c.take(e); b.dkA = c.take(e); b.dvA = c.take(e); b.dkB = c.take(e); b.dvB = c.take(e);
     b.offs = c.take(e);
-    b.counts = c.take((size_t)RS_MAX_DIGITS * RS_MAX_BLOCKS);
+    b.counts = c.take(count_words(e));
+    b.rect = reinterpret_cast<uint2 *>(b.counts);
     b.scalars = c.take(16);
-    b.scan_slots = c.take_slots(scan_slots(max_scan_length(max_entries)));
+    b.scan_slots = c.take_slots(lookback_slots(max_entries));
     b.os_hist = c.take(4 * 256);
     b.os_slots = c.take_slots(onesweep_slots(max_entries));
     b.ctl = ctl;

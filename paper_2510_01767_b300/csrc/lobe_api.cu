@@ -154,6 +154,8 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
         I.H = c.height;
         I.gx = (c.width + cfg.tile_w - 1) / cfg.tile_w;
         I.gy = (c.height + cfg.tile_h - 1) / cfg.tile_h;
+        if (I.gx > 65535 || I.gy > 65535)  // tile rectangles are packed in 16-bit fields
+            return fail(ctx, LOBE_ERR_ARG, "camera %d: more than 65535 tiles in a row or column", it.camera);
         I.tile_off = (int)toff;
         I.sgx = (I.gx + P.S - 1) / P.S;
         I.sgy = (I.gy + P.S - 1) / P.S;

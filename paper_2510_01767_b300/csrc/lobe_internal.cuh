@@ -246,6 +246,7 @@ struct AdamBatch {
 struct BinScratch {
     uint32_t *vis_pos, *dkA, *dvA, *dkB, *dvB, *offs;  // [max_entries]
     uint32_t *counts;   // radix digit counts per block [256][blocks], scanned in place
+    uint2 *rect;        // [max_entries] tile rectangles of the visible entries (aliases counts)
     uint32_t *scalars;  // [0] visible splats, [1] usable super pairs, [2] usable pairs, [4] super pairs
     unsigned long long *scan_slots;                    // decoupled look-back words of the scans
     uint32_t *os_hist;                                 // [4][256] digit histograms of the depth keys

@@ -28,7 +28,7 @@ enum : uint32_t { LB_AGG = 1u, LB_INC = 2u };
 constexpr int CTL_WORDS = 2 + LB_STAGES;
 
 enum : int {  // look-back stages (each scan has its own ticket counter and tag)
-    ST_SCAN_VISIBLE = 0,
+    ST_SCAN_VISIBLE = 0,  // compaction of the visible entries (opens a binning call)
     ST_DEPTH_PASS = 1,  // .. 4: the depth sort's onesweep passes
     ST_SCAN_OFFS = 5,
     ST_SUPER_PASS = 6,  // .. 7: digit-count scans of the super-tile sort
@@ -153,24 +153,23 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t &e
 }
 
 constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 16;                       // per lane, warp-striped
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 4096 elements per tile
+#ifndef LOBE_SCAN_ITEMS
+#define LOBE_SCAN_ITEMS 16
+#endif
+constexpr int SCAN_ITEMS = LOBE_SCAN_ITEMS;          // per lane, warp-striped
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // elements per tile
 
 // ------------------------------------------------------------------ single-pass exclusive scan
 //
 // out[i] = sum_{j<i} in(j) for i < n, n read from device memory when n_dev is given (the launch
 // shape then depends only on an upper bound, so the call is graph-capturable). Each block scans
-// one 4096-element tile (warp-striped, coalesced) and gets the tile's offset by look-back. The
+// one SCAN_TILE-element tile (warp-striped, coalesced) and gets the tile's offset by look-back. The
 // block of the last tile writes the grand total to total32/total64 (nullable) and the count the
 // next stage may use to n_use: the total, or 0 with a latched capacity error when it exceeds
 // `capacity` (< 0: unlimited). In-place use (out == the loaded array) is safe: each element is
 // read and later written by the same thread. The block with ticket 0 zeroes zero_words words at
 // zero_buf (accumulators of later kernels).
 
-struct LoadVisible {  // 1 where a projected entry touches at least one tile
-    const int *tiles;
-    __device__ uint32_t operator()(long long i) const { return tiles[i] > 0 ? 1u : 0u; }
-};
 struct LoadPlain {
     const uint32_t *src;
     __device__ uint32_t operator()(long long i) const { return src[i]; }
@@ -202,7 +201,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(L load, const uint32_t *n
     const long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tile >= (ntiles > 0 ? ntiles : 1)) return;
     const uint32_t tag = lb_tag(s_gen, lb.stage);
-    // warp w owns elements [t0 + w * 512, t0 + (w + 1) * 512), lane-striped per round
+    // warp w owns elements [t0 + w * 32 * SCAN_ITEMS, t0 + (w + 1) * 32 * SCAN_ITEMS), lane-striped
     const long long w0 = (long long)tile * SCAN_TILE + (long long)warp * (32 * SCAN_ITEMS);
     uint32_t x[SCAN_ITEMS];
 #pragma unroll
