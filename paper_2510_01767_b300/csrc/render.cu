@@ -704,7 +704,9 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                 const f2 oln2 = pk(q1.y * LN2, q1.y * LN2);
                 // per lane: S1 = sum dL/dp2, S2 = sum dL/dp2 dy, S3 = sum dL/dp2 dy^2 over its pixels; dx
                 // is the lane's own, so the exponent's gradients follow from these three after the loop
-                f2 S1 = 0, S2 = 0, S3 = 0, dop = 0, dr = 0, dg = 0, db = 0;  // 0 = (+0, +0)
+                // with several pairs the first pair's terms initialise the sums (no zeroing, no add)
+                f2 S1, S2, S3, dop, dr, dg, db;
+                if constexpr (NP == 1) S1 = S2 = S3 = dop = dr = dg = db = 0;  // 0 = (+0, +0)
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
@@ -727,9 +729,10 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                     upk(sub2(one2, al), oma, omb);
                     const f2 Ti = mul2(T2[i], pk(__fdividef(1.0f, oma), __fdividef(1.0f, omb)));  // T in front
                     const f2 w = mul2(al, Ti);
-                    dr = fma2(w, G0[i], dr);
-                    dg = fma2(w, G1[i], dg);
-                    db = fma2(w, G2[i], db);
+                    const bool first = NP > 1 && i == 0;  // resolved at compile time (unrolled)
+                    dr = first ? mul2(w, G0[i]) : fma2(w, G0[i], dr);
+                    dg = first ? mul2(w, G1[i]) : fma2(w, G1[i], dg);
+                    db = first ? mul2(w, G2[i]) : fma2(w, G2[i], db);
                     const f2 d0 = sub2(pk(q1.z, q1.z), B0[i]), d1 = sub2(pk(q1.w, q1.w), B1[i]),
                              d2 = sub2(pk(cb, cb), B2[i]);
                     const f2 da = mul2(Ti, fma2(G2[i], d2, fma2(G1[i], d1, mul2(G0[i], d0))));  // dL/dalpha
@@ -747,12 +750,12 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                     // past the clamp alpha no longer depends on o or the exponent: dL/do = da G and
                     // dL/dp2 = da o G ln2 (alpha = o G below the clamp)
                     const f2 t = mul2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb));
-                    dop = add2(dop, t);
+                    dop = first ? t : add2(dop, t);
                     const f2 dp2 = mul2(t, oln2);
                     const f2 dpy = mul2(dp2, dy2);
-                    S1 = add2(S1, dp2);
-                    S2 = add2(S2, dpy);
-                    S3 = fma2(dpy, dy2, S3);
+                    S1 = first ? dp2 : add2(S1, dp2);
+                    S2 = first ? dpy : add2(S2, dpy);
+                    S3 = first ? mul2(dpy, dy2) : fma2(dpy, dy2, S3);
                 }
                 const unsigned used = __ballot_sync(0xffffffffu, any);
                 if (used) {
