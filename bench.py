@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--tile", default="auto", help="WxH, or auto: tile shape and pixels per lane by the autotuner")
     ap.add_argument("--px", default="0,0", help="with --tile WxH: pixels per lane of the composite and its adjoint")
     ap.add_argument("--persistent", action="store_true", help="with --tile WxH: persistent compositing kernels")
+    ap.add_argument("--batch", default="32,32", help="with --tile WxH: splats a warp stages per round in the "
+                                                      "composite and its adjoint (32 or 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the medium view, batched-vs-plain, fast camera "
                                                               "selection, densification, Adam and training measurements")
@@ -350,7 +352,7 @@ def make_step(lobe, wl, args, rank, sets=None, tile=None, px=None):
                               recompute_T=args.recompute)
     else:
         st = BatchedStep(sets, cams, wl.items, wl.blocks, tile=tile, px=px, recompute_T=args.recompute,
-                         persistent=args.persistent)
+                         persistent=args.persistent, batch=tuple(int(x) for x in args.batch.split(",")))
     # dL/dC of the training loss
     tsets = [lobe.GaussianSet.from_numpy(scenes.perturbed_copy(s, seed=2 + rank)) for s in wl.sets]
     if wl.name.startswith("city"):
@@ -806,13 +808,15 @@ def training_benchmark(steps=200, warm=20):
 
 def batched_vs_plain(lobe, torch, wl, sets, st, batched_ms, reps=5):
     """The batched graph step (already timed) against the plain path on the same batch: one
-    view per call sequence, eager, same tile shape and pixels per lane; and against the
+    view per call sequence, eager, same tile shape, pixels per lane, persistent choice and
+    staging batch; and against the
     autograd.Function called view by view (host-timed: each forward synchronises once to size
     its bins)."""
     from paper_2510_01767_b300.batched import PlainSteps, _time
     cams = [c.as_dict() for c in wl.cameras]
     gen = torch.Generator(device="cuda").manual_seed(7)
-    plain = PlainSteps(sets, cams, wl.items, wl.blocks, tile=st.tile, px=st.px)
+    plain = PlainSteps(sets, cams, wl.items, wl.blocks, tile=st.tile, px=st.px, persistent=st.persistent,
+                       batch=st.batch_size)
     for p in plain.steps:
         p.dL.copy_(torch.randn(p.dL.shape, generator=gen, device="cuda"))
     plain_ms = _time(plain.run, reps, torch.cuda.current_stream())
@@ -837,8 +841,8 @@ def batched_vs_plain(lobe, torch, wl, sets, st, batched_ms, reps=5):
     del params, rasters, dls
     torch.cuda.empty_cache()
     pixels = st.batch.n_pixels
-    return {"workload": wl.name, "tile": list(st.tile), "px_per_lane": list(st.px),
-            "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
+    return {"workload": wl.name, "tile": list(st.tile), "px_per_lane": list(st.px), "persistent": st.persistent,
+            "staging_batch": list(st.batch_size), "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
             "batched_mpix_s": round(pixels / batched_ms / 1e3, 1), "plain_mpix_s": round(pixels / plain_ms / 1e3, 1),
             "ratio": round(plain_ms / batched_ms, 3),
             "autograd_per_view_ms": round(autograd_ms, 3), "ratio_vs_autograd_per_view": round(autograd_ms / batched_ms, 3),
@@ -959,7 +963,7 @@ def main():
         sampler.close()
     if world == 1 and not args.no_extras:
         extras["batched_vs_plain"] = batched_vs_plain(lobe, torch, wl, sets, st, float(np.median(step_ms)))
-    graph_tile, graph_px, graph_persistent = st.tile, st.px, st.persistent
+    graph_tile, graph_px, graph_persistent, graph_batch = st.tile, st.px, st.persistent, st.batch_size
     del st
     torch.cuda.empty_cache()
     if world == 1 and not args.no_extras and args.workload != "medium":
@@ -984,6 +988,7 @@ def main():
                        "tile": list(graph_tile), "px_per_lane": {"fwd": graph_px[0] or "default",
                                                                   "bwd": graph_px[1] or "default"},
                        "persistent_compositing": graph_persistent,
+                       "staging_batch": {"fwd": graph_batch[0] or 32, "bwd": graph_batch[1] or 32},
                        "tuning_ms": ({k: round(v, 4) for k, v in tuning.items()} if tuning else None),
                        "sh_degree": 3, **counts,
                        "step": "one CUDA graph replay: projection (each set once for all its views), binning of "

@@ -129,7 +129,12 @@ typedef struct {
                             tiles ordered longest list first; the images are identical, the adjoint's
                             float32 sums may add in another order. Uses context scratch of 4 B a tile
                             (sized by lobe_ctx_reserve's max_tiles, or grown by an uncaptured call) */
-    int32_t reserved[3];
+    int32_t batch_fwd;   /* splats each warp stages from its tile's list per round in render_fwd: 0 or 32
+                            (default), or 64 (two per lane: twice the prefetch depth, half the rounds;
+                            needs two or more pixels a lane; lobe_render_depth always stages 32).
+                            The results do not depend on it */
+    int32_t batch_bwd;   /* the same for render_bwd: 0, 32 or 64 (64 needs an even pixels-per-lane count) */
+    int32_t reserved;
 } lobe_config;
 
 /* Sizes implied by a batch under a config: out[0] = projected entries (sum over items of

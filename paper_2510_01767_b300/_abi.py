@@ -66,7 +66,7 @@ class Config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("recompute_T", ctypes.c_int32), ("px_fwd", ctypes.c_int32),
                 ("px_bwd", ctypes.c_int32), ("bin_general", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("batch_fwd", ctypes.c_int32), ("batch_bwd", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Projected(ctypes.Structure):

@@ -10,9 +10,10 @@ step is captured once in a CUDA graph and replayed as a single launch.
 
 ``autotune`` picks the tile shape (8x8, 16x8, 16x16, 32x16), the pixels each lane composites (a
 kernel knob: fewer means more warps per tile, more means fewer splat loads and reductions per
-pixel) and whether the composite and its adjoint run as persistent kernels that take tiles
-longest list first, by timing graph replays on the actual batch; results are cached per (GPU, batch
-signature) in ``~/.cache/lobe/autotune.json``.
+pixel), whether the composite and its adjoint run as persistent kernels that take tiles
+longest list first, and the per-tile staging batch (32 or 64 splats of the tile's list fetched by
+a warp per round), by timing graph replays on the actual batch; results are cached per (GPU,
+batch signature) in ``~/.cache/lobe/autotune.json``.
 ``PlainSteps`` is the reference it is compared with: one view per call sequence, eager,
 each view projecting its block's Gaussians itself.
 """
@@ -29,21 +30,26 @@ from . import raster as R
 
 TILES = ((8, 8), (16, 8), (16, 16), (32, 16))
 PX_OPTIONS = {(8, 8): (1, 2), (16, 8): (1, 2, 4), (16, 16): (2, 4, 8), (32, 16): (2, 4, 8)}  # pixels per lane per tile shape
+BATCH_OPTIONS = (32, 64)  # splats a warp stages from its tile's list per round
 
 
-def config_name(tile, px=(0, 0)):
-    return f"{tile[0]}x{tile[1]}" + (f"/f{px[0]}b{px[1]}" if px and px[0] else "")
+def config_name(tile, px=(0, 0), batch=(0, 0)):
+    nb = tuple(n or 32 for n in batch) if batch else (32, 32)
+    return (f"{tile[0]}x{tile[1]}" + (f"/f{px[0]}b{px[1]}" if px and px[0] else "") +
+            (f"/s{nb[0]}.{nb[1]}" if nb != (32, 32) else ""))
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lobe", "autotune.json")
 
 
 class BatchedStep:
     def __init__(self, sets, cameras, items, blocks=(), tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0),
-                 recompute_T=False, slack=1.25, stream=None, px=(0, 0), persistent=False):
+                 recompute_T=False, slack=1.25, stream=None, px=(0, 0), persistent=False, batch=(0, 0)):
         self.stream = stream if stream is not None else torch.cuda.Stream()
         px = (px, px) if isinstance(px, int) else tuple(px)
+        batch = (batch, batch) if isinstance(batch, int) else tuple(batch)
         self.ctx = R.Context(tile=tile, sh_degree=sh_degree, bg=bg, recompute_T=recompute_T, stream=self.stream,
-                             px_fwd=px[0], px_bwd=px[1], persistent=persistent)
+                             px_fwd=px[0], px_bwd=px[1], persistent=persistent, batch=batch)
         self.px = px
+        self.batch_size = batch
         self.persistent = bool(persistent)
         self.batch = R.Batch(sets, cameras, items, blocks)
         self.tile = tuple(tile)
@@ -90,6 +96,44 @@ class BatchedStep:
         self.px = (best["f"][1], best["b"][1])
         c.configure(px=self.px)
         return self.px
+
+    def tune_batch(self, options=BATCH_OPTIONS, reps=3):
+        """Times the composite and its adjoint at each staging batch (splats a warp fetches from
+        its tile's list per round) and keeps the fastest for each; a size the library rejects for
+        this configuration (64 needs two or more pixels a lane, an even count in the adjoint) is
+        skipped. Returns (fwd, bwd)."""
+        c, b = self.ctx, self.batch
+        best = {"f": (float("inf"), 32), "b": (float("inf"), 32)}
+
+        def settable(batch):
+            old = c.batch
+            try:
+                c.configure(batch=batch)
+                return True
+            except R.A.LobeError:
+                c.batch = old
+                return False
+
+        with torch.cuda.stream(self.stream):
+            self.run()
+            for n in options:
+                if settable((n, 32)):
+                    fwd = _time(lambda: R.render_fwd(c, b, self.proj, self.bins, self.image), reps, self.stream)
+                    if fwd < best["f"][0]:
+                        best["f"] = (fwd, n)
+                if settable((32, n)):
+                    bwd = _time(lambda: R.render_bwd(c, b, self.proj, self.bins, self.image, self.dL, self.grad2d),
+                                reps, self.stream)
+                    if bwd < best["b"][0]:
+                        best["b"] = (bwd, n)
+        self.set_batch((best["f"][1], best["b"][1]))
+        return self.batch_size
+
+    def set_batch(self, batch):
+        """Set the staging batch (fwd, bwd) of the composite and its adjoint (drops a captured graph)."""
+        self.batch_size = tuple(batch)
+        self.ctx.configure(batch=self.batch_size)
+        self.graph = None
 
     def set_persistent(self, on):
         """Switch the composite and its adjoint between one block per tile and persistent
@@ -173,7 +217,7 @@ def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=Tru
     if use_cache and key in cache:
         tile, px = tuple(cache[key]["tile"]), tuple(cache[key].get("px", (0, 0)))
         st = BatchedStep(sets, cameras, items, blocks, tile=tile, px=px, persistent=cache[key].get("persistent", False),
-                         **kw)
+                         batch=tuple(cache[key].get("batch", (0, 0))), **kw)
         if dL_init is not None:
             dL_init(st)
         return st.capture(), cache[key]["times"]
@@ -203,10 +247,25 @@ def autotune(sets, cameras, items, blocks=(), tiles=TILES, reps=5, use_cache=Tru
     if ms >= best_ms:
         best.set_persistent(False)
         best.capture()
+    else:
+        best_ms = ms
+    # then the staging batch of the composite and of its adjoint, kept if the whole step is faster
+    if tune_px:
+        nb = best.tune_batch(reps=max(2, reps // 2))
+        if nb != (32, 32):
+            best.capture()
+            ms = _time(best.replay, reps, best.stream)
+            times[config_name(best.tile, best.px, nb) + ("/persistent" if best.persistent else "")] = ms
+            if ms >= best_ms:
+                best.set_batch((32, 32))
+                best.capture()
+        else:
+            best.set_batch((32, 32))
+            best.capture()
     if use_cache:
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        cache[key] = {"tile": list(best.tile), "px": list(best.px), "persistent": best.persistent, "times": times,
-                      "when": time.time()}
+        cache[key] = {"tile": list(best.tile), "px": list(best.px), "persistent": best.persistent,
+                      "batch": list(best.batch_size), "times": times, "when": time.time()}
         with open(CACHE, "w") as f:
             json.dump(cache, f)
     return best, times

@@ -70,6 +70,13 @@ static lobe_status check_config(lobe_ctx *ctx, const lobe_config *cfg)
     if (!valid_px(cfg->tile_w, cfg->tile_h, cfg->px_fwd) || !valid_px(cfg->tile_w, cfg->tile_h, cfg->px_bwd))
         return fail(ctx, LOBE_ERR_ARG, "pixels per lane %d/%d not supported with %dx%d tiles", cfg->px_fwd, cfg->px_bwd,
                     cfg->tile_w, cfg->tile_h);
+    const int pf = cfg->px_fwd ? cfg->px_fwd : default_px(cfg->tile_w, cfg->tile_h, false);
+    const int pb = cfg->px_bwd ? cfg->px_bwd : default_px(cfg->tile_w, cfg->tile_h, true);
+    const auto batch_ok = [](int b) { return b == 0 || b == 32 || b == 64; };
+    if (!batch_ok(cfg->batch_fwd) || !batch_ok(cfg->batch_bwd) || (cfg->batch_fwd == 64 && pf < 2) ||
+        (cfg->batch_bwd == 64 && pb % 2 != 0))
+        return fail(ctx, LOBE_ERR_ARG, "staging batch %d/%d not supported with %d/%d pixels a lane", cfg->batch_fwd,
+                    cfg->batch_bwd, pf, pb);
     return LOBE_OK;
 }
 
@@ -91,6 +98,8 @@ static lobe_status build_params(lobe_ctx *ctx, const lobe_config &cfg, const lob
     P.th = cfg.tile_h;
     P.px_fwd = cfg.px_fwd;
     P.px_bwd = cfg.px_bwd;
+    P.nb_fwd = cfg.batch_fwd == 64 ? 2 : 1;
+    P.nb_bwd = cfg.batch_bwd == 64 ? 2 : 1;
     P.sh_degree = cfg.sh_degree;
     for (int c = 0; c < 3; ++c) P.bg[c] = cfg.bg[c];
     long long goff = 0;

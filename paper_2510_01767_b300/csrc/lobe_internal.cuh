@@ -61,6 +61,7 @@ struct BatchParams {
     long long n_pixels;
     int tw, th;
     int px_fwd, px_bwd;   // pixels per lane of the render kernels (0 = default)
+    int nb_fwd, nb_bwd;   // 32-splat staging rounds a warp fetches at once in the render kernels (1 or 2)
     int sh_degree;
     float bg[3];
 };

@@ -177,66 +177,134 @@ __device__ __forceinline__ bool project_cam(const BatchParams &P, const ItemPara
 }
 
 // --------------------------------------------------------------------------- forward
+//
+// Memory layout of the forward (B300): a warp takes 32 consecutive Gaussians. Their SH rows
+// (192 contiguous bytes each, 6 KB for the warp) are copied once into shared memory by
+// coalesced 16-byte asynchronous copies (cp.async: no registers, all in flight while the
+// geometry is loaded and projected), into rows of 13 float4 so that the per-thread reads of
+// every view fall in distinct banks. Each view's 48-byte splat records go out the same way:
+// staged per warp, then written as contiguous 16-byte stores. A warp whose Gaussians span two
+// sets (at most one warp per set boundary) copies and stores per thread instead.
 
-__global__ void __launch_bounds__(256, 4) k_project_fwd(const __grid_constant__ BatchParams P, float4 *__restrict__ splat,
-                                                     int *__restrict__ radius, int *__restrict__ tiles)
+constexpr int PF_THREADS = 128;
+constexpr int PF_WARPS = PF_THREADS / 32;
+constexpr int PF_ROW = 13;  // float4 per staged SH row: 12 used, 1 pad (208-byte rows: conflict-free 16-byte reads)
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(PF_THREADS, 7) k_project_fwd(const __grid_constant__ BatchParams P,
+                                                              float4 *__restrict__ splat, int *__restrict__ radius,
+                                                              int *__restrict__ tiles)
 {
     pdl_wait();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P.n_gauss) return;
-    const int s = set_of_gauss(P, t);
+    __shared__ float4 s_sh[PF_WARPS][32 * PF_ROW];
+    __shared__ float4 s_out[PF_WARPS][32 * 3];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const long long t = (long long)blockIdx.x * PF_THREADS + threadIdx.x;
+    if (t - lane >= P.n_gauss) return;  // the whole warp is past the end
+    const bool valid = t < P.n_gauss;
+    const int s = valid ? set_of_gauss(P, t) : P.n_sets - 1;
     const SetParams &S = P.set[s];
     const long long g = t - S.gauss_off;
-    const bool cropped = S.crop != nullptr && S.crop[g] == 0;
-    World w;
-    const float4 *shg = reinterpret_cast<const float4 *>(S.sh + 48 * g);
-    if (!cropped) {
-        // the SH coefficients toward L2 while the geometry is loaded and projected: their loads
-        // below then wait on L2 rather than on DRAM (a culled Gaussian's lines are wasted reads)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(shg));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(shg + 6));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(shg + 11));
-        load_world(S, g, w);
-    }
+    const bool cropped = !valid || (S.crop != nullptr && S.crop[g] == 0);
+    const unsigned need = __ballot_sync(0xffffffffu, !cropped);
+    // one set for the whole warp (lanes past the end count as the last set): contiguous rows
+    const bool one_set = __all_sync(0xffffffffu, s == __shfl_sync(0xffffffffu, s, 0));
     const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
+    const int per = (3 * nb + 3) / 4;  // float4 chunks holding the used coefficients
+    float4 *row = &s_sh[wp][lane * PF_ROW];
+    if (one_set) {
+        // chunk f = lane + 32 r of the warp's 32 x 12: Gaussian f / 12, chunk f % 12
+        const float4 *base = reinterpret_cast<const float4 *>(S.sh) + 12 * (g - lane);
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int f = lane + 32 * r, i = f / 12, c = f - 12 * i;
+            if (c < per && ((need >> i) & 1u)) cp_async16(&s_sh[wp][i * PF_ROW + c], base + f);
+        }
+    } else if (!cropped) {
+        const float4 *shg = reinterpret_cast<const float4 *>(S.sh + 48 * g);
+        for (int c = 0; c < per; ++c) cp_async16(row + c, shg + c);
+    }
+    World w;
+    if (!cropped) load_world(S, g, w);
+    cp_async_wait_all();
+    __syncwarp();
     float opacity = 0.0f;
     bool first = true;
-    for (int k = 0; k < S.item_count; ++k) {
-        const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
-        const long long e = I.entry_off + g;
-        Cam2D c;
-        if (cropped || !project_cam(P, I, w, c)) {
-            radius[e] = 0;
-            tiles[e] = 0;
-            continue;
-        }
-        if (first) {
-            opacity = 1.0f / (1.0f + __expf(-S.logits[g]));
-            first = false;
-        }
-        float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
-        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-        float Pp[16];
-        sh_poly(P.sh_degree, dx * il, dy * il, dz * il, Pp);
-        // colour: the coefficients stream from memory per view (cache hits after the first view)
-        float col[3] = {0.f, 0.f, 0.f};
+    // every lane walks the longest item list of the warp's sets (one set: the same list)
+    const int n_it = valid ? S.item_count : 0;
+    const int n_loop = one_set ? S.item_count : __reduce_max_sync(0xffffffffu, (unsigned)n_it);
+    for (int k = 0; k < n_loop; ++k) {
+        const bool has = k < n_it;
+        bool vis = false;
+        long long e = 0;
+        float4 o0, o1, o2;
+        if (has) {
+            const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
+            e = I.entry_off + g;
+            Cam2D c;
+            vis = !cropped && project_cam(P, I, w, c);
+            if (vis) {
+                if (first) {
+                    opacity = 1.0f / (1.0f + __expf(-S.logits[g]));
+                    first = false;
+                }
+                float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
+                float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+                float Pp[16];
+                sh_poly(P.sh_degree, dx * il, dy * il, dz * il, Pp);
+                float col[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            if (4 * i >= 3 * nb) break;
-            const float4 q = shg[i];
-            const float qv[4] = {q.x, q.y, q.z, q.w};
+                for (int i = 0; i < 12; ++i) {
+                    if (4 * i >= 3 * nb) break;
+                    const float4 q = row[i];
+                    const float qv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int idx = 4 * i + m, b = idx / 3;
-                if (b < nb) col[idx % 3] += kSH[b] * Pp[b] * qv[m];
+                    for (int m = 0; m < 4; ++m) {
+                        const int idx = 4 * i + m, b = idx / 3;
+                        if (b < nb) col[idx % 3] += kSH[b] * Pp[b] * qv[m];
+                    }
+                }
+                o0 = make_float4(c.u, c.v, c.ca, c.cb);
+                o1 = make_float4(c.cc, opacity, clamp_color(col[0] + 0.5f), clamp_color(col[1] + 0.5f));
+                o2 = make_float4(clamp_color(col[2] + 0.5f), c.z, 0.f, 0.f);
             }
+            radius[e] = vis ? c.radius : 0;
+            tiles[e] = vis ? (c.x1 - c.x0) * (c.y1 - c.y0) : 0;
         }
-        float4 *o = splat + 3 * e;
-        o[0] = make_float4(c.u, c.v, c.ca, c.cb);
-        o[1] = make_float4(c.cc, opacity, clamp_color(col[0] + 0.5f), clamp_color(col[1] + 0.5f));
-        o[2] = make_float4(clamp_color(col[2] + 0.5f), c.z, 0.f, 0.f);
-        radius[e] = c.radius;
-        tiles[e] = (c.x1 - c.x0) * (c.y1 - c.y0);
+        if (one_set) {
+            // the warp's 32 consecutive entries of this item (lane 0 is always in range): records
+            // staged, then contiguous 16-byte stores of the visible ones
+            const unsigned vm = __ballot_sync(0xffffffffu, vis);
+            const long long e0 = __shfl_sync(0xffffffffu, e - lane, 0);
+            if (vm == 0u) continue;
+            if (vis) {
+                s_out[wp][3 * lane] = o0;
+                s_out[wp][3 * lane + 1] = o1;
+                s_out[wp][3 * lane + 2] = o2;
+            }
+            __syncwarp();
+            float4 *dst = splat + 3 * e0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int f = lane + 32 * r;
+                if ((vm >> (f / 3)) & 1u) dst[f] = s_out[wp][f];
+            }
+            __syncwarp();
+        } else if (vis) {
+            float4 *o = splat + 3 * e;
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+        }
     }
 }
 
@@ -398,6 +466,7 @@ __device__ __forceinline__ void project_bwd_body(const BatchParams &P, const flo
     const SetParams &S = P.set[s];
     const long long g = t - S.gauss_off;
     World w;
+    unsigned seen = 0;  // bit k: item k of the set (k < 32) sees the Gaussian
     if (any) {
         load_world(S, g, w);  // in flight while the block stages its SH coefficients
         s_src[threadIdx.x] = S.sh + 48 * g;
@@ -409,12 +478,24 @@ __device__ __forceinline__ void project_bwd_body(const BatchParams &P, const flo
         } else {
             s_dst[threadIdx.x] = S.g_sh + 48 * g;
         }
-        // the first item's per-entry inputs, toward L2 meanwhile
-        const long long e0 = P.item[P.set_items[S.item_begin]].entry_off + g;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e0));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e0 + 2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(splat + 3 * e0 + 1));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(radius + e0));
+        // which of the first 32 items see it (their radii read together, one round trip per
+        // four), then every seen entry's inputs toward L2, so that the per-item loop below waits
+        // on L2 rather than on DRAM (culled entries' lines are not fetched)
+        const int nk = S.item_count < 32 ? S.item_count : 32;
+        for (int k0 = 0; k0 < nk; k0 += 4) {
+            int r4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                r4[j] = k0 + j < nk ? radius[P.item[P.set_items[S.item_begin + k0 + j]].entry_off + g] : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) seen |= (r4[j] > 0 ? 1u : 0u) << (k0 + j);
+        }
+        for (unsigned m = seen; m; m &= m - 1) {
+            const long long e = P.item[P.set_items[S.item_begin + __ffs(m) - 1]].entry_off + g;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(grad2d + 3 * e + 2));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(splat + 3 * e + 1));
+        }
         if constexpr (ADAM) {
             // this Gaussian's Adam state, toward L2 while the adjoint computes: the SH moments
             // (192 bytes each, at most three 128-byte lines) and the other arrays' entries
@@ -474,7 +555,7 @@ __device__ __forceinline__ void project_bwd_body(const BatchParams &P, const flo
         for (int k = 0; k < S.item_count; ++k) {
             const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
             const long long e = I.entry_off + g;
-            if (radius[e] <= 0) continue;
+            if (k < 32 ? !((seen >> k) & 1u) : radius[e] <= 0) continue;
             Cam2D c;
             project_cam(P, I, w, c);  // recompute the forward intermediates (visible by radius > 0)
             const float4 g0 = grad2d[3 * e + 0], g1 = grad2d[3 * e + 1], g2 = grad2d[3 * e + 2];
@@ -731,9 +812,10 @@ __global__ void __launch_bounds__(PB_THREADS, 8)
 cudaError_t launch_project_fwd(const BatchParams &P, float *splat, int *radius, int *tiles, cudaStream_t st)
 {
     if (P.n_gauss == 0) return cudaSuccess;
-    unsigned blocks = (unsigned)((P.n_gauss + 255) / 256);
+    unsigned blocks = (unsigned)((P.n_gauss + PF_THREADS - 1) / PF_THREADS);
     count_launch();
-    launch_pdl(k_project_fwd, dim3(blocks), dim3(256), 0, st, P, reinterpret_cast<float4 *>(splat), radius, tiles);
+    launch_pdl(k_project_fwd, dim3(blocks), dim3(PF_THREADS), 0, st, P, reinterpret_cast<float4 *>(splat), radius,
+               tiles);
     return cudaGetLastError();
 }
 

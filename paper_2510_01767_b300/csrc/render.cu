@@ -186,42 +186,54 @@ __device__ __forceinline__ float sum2(f2 v)
     return a + b;
 }
 
-struct WarpStage {
-    float4 s0[32];
-    float4 s1[32];
-    float2 s2[32];
-    int id[32];
-    float dep[32];
+// A warp's staged batch: 32 NB splats of its tile's list (NB = 1 or 2: each lane fetches NB
+// splats a round; 2 doubles the prefetch depth and halves the rounds of long sparse lists).
+template <int NB = 1>
+struct WarpStageN {
+    float4 s0[32 * NB];
+    float4 s1[32 * NB];
+    float2 s2[32 * NB];
+    int id[32 * NB];
+    float dep[32 * NB];
 };
+using WarpStage = WarpStageN<1>;
 
 // Front-to-back walk of [start, end) for a lane's PX pixels (forward, and the first sweep
 // of the recompute adjoint). live[k] must be false for pixels outside the image. With DEPTH,
 // D[k] also accumulates sum_i d_i alpha_i T_i (the depth compositing of fast camera selection,
 // Sec. 3.2: the blending equation with each splat's camera-space depth in place of colour).
-template <int PX, bool DEPTH = false>
+template <int PX, bool DEPTH = false, int NB = 1>
 __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, const int *__restrict__ ids, int start,
                                               int end, const SlabBox &bx, float pxc, const float (&pyc)[PX],
                                               bool (&live)[PX], float (&T)[PX], float (&C0)[PX], float (&C1)[PX],
-                                              float (&C2)[PX], int (&last)[PX], WarpStage &st, float *D = nullptr)
+                                              float (&C2)[PX], int (&last)[PX], WarpStageN<NB> &st, float *D = nullptr)
 {
     const int lane = threadIdx.x & 31;
-    Staged nx;
-    bool nh;
-    fetch(splat, ids, start + lane, end, bx, nx, nh);
-    for (int base = start; base < end; base += 32) {
+    Staged nx[NB];
+    bool nh[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) fetch(splat, ids, start + 32 * b + lane, end, bx, nx[b], nh[b]);
+    for (int base = start; base < end; base += 32 * NB) {
         bool any = false;
 #pragma unroll
         for (int k = 0; k < PX; ++k) any |= live[k];
         if (!__any_sync(0xffffffffu, any)) break;
-        st.s0[lane] = nx.s0;
-        st.s1[lane] = nx.s1;
-        st.s2[lane] = nx.s2;
-        if (DEPTH) st.dep[lane] = nx.dep;
-        unsigned hits = __ballot_sync(0xffffffffu, nh);  // splats of the batch that can reach the slab
+        unsigned hitb[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            st.s0[32 * b + lane] = nx[b].s0;
+            st.s1[32 * b + lane] = nx[b].s1;
+            st.s2[32 * b + lane] = nx[b].s2;
+            if (DEPTH) st.dep[32 * b + lane] = nx[b].dep;
+            hitb[b] = __ballot_sync(0xffffffffu, nh[b]);  // splats of the batch that can reach the slab
+        }
         __syncwarp();
-        fetch(splat, ids, base + 32 + lane, end, bx, nx, nh);
-        while (hits) {
-            const int j = __ffs(hits) - 1;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) fetch(splat, ids, base + 32 * (NB + b) + lane, end, bx, nx[b], nh[b]);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+        for (unsigned hits = hitb[b]; hits;) {
+            const int j = 32 * b + __ffs(hits) - 1;  // stage slot = list position - base
             hits &= hits - 1;
             const float4 q0 = st.s0[j], q1 = st.s1[j];
             const float cb = st.s2[j].x, pmin = st.s2[j].y;
@@ -263,6 +275,33 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
                     if (DEPTH) D[k] += dj * w;
                     T[k] = Tn;
                     last[k] = base - start + j + 1;
+                } else if constexpr (PX % 2 == 0) {
+                    // several pixels a lane, in pairs: branch-free, so the pixels' chains
+                    // interleave, with the transmittance, the weights and the sums in packed
+                    // f32x2 arithmetic (each half rounded as the scalar step). A pixel that
+                    // skips or stops gets weight 0 and keeps T and last exactly
+                    if (k % 2) continue;
+                    const float pa = pv[k], pb = pv[k + 1];
+                    const bool ua = live[k] && pa <= 0.0f && pa >= pmin, ub = live[k + 1] && pb <= 0.0f && pb >= pmin;
+                    float ra, rb;
+                    upk(mul2(pk(q1.y, q1.y), pk(ua ? ex2(pa) : 0.0f, ub ? ex2(pb) : 0.0f)), ra, rb);
+                    const float aa = fminf(ALPHA_MAX, ra), ab = fminf(ALPHA_MAX, rb);
+                    const f2 T2 = pk(T[k], T[k + 1]);
+                    float ta, tb;
+                    upk(mul2(T2, sub2(pk(1.0f, 1.0f), pk(aa, ab))), ta, tb);  // next_T of both pixels
+                    const bool sa = ua && ta < T_MIN, sb = ub && tb < T_MIN;
+                    const bool wa = ua && !sa, wb = ub && !sb;
+                    live[k] = live[k] && !sa;
+                    live[k + 1] = live[k + 1] && !sb;
+                    const f2 w2 = mul2(pk(wa ? aa : 0.0f, wb ? ab : 0.0f), T2);
+                    upk(fma2(pk(q1.z, q1.z), w2, pk(C0[k], C0[k + 1])), C0[k], C0[k + 1]);
+                    upk(fma2(pk(q1.w, q1.w), w2, pk(C1[k], C1[k + 1])), C1[k], C1[k + 1]);
+                    upk(fma2(pk(cb, cb), w2, pk(C2[k], C2[k + 1])), C2[k], C2[k + 1]);
+                    if (DEPTH) upk(fma2(pk(dj, dj), w2, pk(D[k], D[k + 1])), D[k], D[k + 1]);
+                    T[k] = wa ? ta : T[k];
+                    T[k + 1] = wb ? tb : T[k + 1];
+                    last[k] = wa ? base - start + j + 1 : last[k];
+                    last[k + 1] = wb ? base - start + j + 1 : last[k + 1];
                 } else {
                     // several pixels a lane: branch-free, so the pixels' chains interleave; a
                     // pixel that skips or stops gets weight 0 and keeps T and last exactly
@@ -344,7 +383,7 @@ constexpr int min_blocks_for(int regs, int warps)
 #else
 #define LOBE_FWD_BOUNDS(W) __launch_bounds__(32 * (W))
 #endif
-template <int TW, int TH, int PX, bool DEPTH, bool PERSIST>
+template <int TW, int TH, int PX, bool DEPTH, bool PERSIST, int NB = 1>
 __global__ void LOBE_FWD_BOUNDS((Slab<TW, TH, PX>::WARPS))
     k_render_fwd(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                  const int *__restrict__ tile_start, const int *__restrict__ ids, float *__restrict__ rgb,
@@ -353,7 +392,7 @@ __global__ void LOBE_FWD_BOUNDS((Slab<TW, TH, PX>::WARPS))
 {
     pdl_wait();
     using G = Slab<TW, TH, PX>;
-    __shared__ WarpStage stage[G::WARPS];
+    __shared__ WarpStageN<NB> stage[G::WARPS];
     const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
     WorkCursor wc{order, work, (unsigned)P.n_tiles * (unsigned)G::WARPS, G::WARPS, true};
     auto tile_body = [&](const int t, const int warp) {
@@ -374,7 +413,7 @@ __global__ void LOBE_FWD_BOUNDS((Slab<TW, TH, PX>::WARPS))
             C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
             last[k] = 0;
         }
-        forward_sweep<PX, DEPTH>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc,
+        forward_sweep<PX, DEPTH, NB>(splat, ids, tile_start[t], tile_start[t + 1], slab_box<TW, TH, PX>(tx, ty, warp), pxc, pyc,
                                  live, T, C0, C1, C2, last, stage[pw], D);
         const long long HW = (long long)I.W * I.H;
         float *out = rgb + 3 * I.pix_off;
@@ -594,17 +633,32 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 // small, and costs where they are large (four pairs a lane are chosen for large ones). Together:
 // the city batch's adjoint 11.1 -> 8.9-9.3 ms.
 #ifdef LOBE_BWD_REGS
-constexpr int bwd_regs_for(int) { return LOBE_BWD_REGS; }
+constexpr int bwd_regs_for(int, int = 1) { return LOBE_BWD_REGS; }
 #else
-constexpr int bwd_regs_for(int px) { return px >= 8 ? 128 : (px >= 4 ? 96 : 64); }
+// 64-splat staging rounds keep a second prefetched splat per lane: 16 more registers
+constexpr int bwd_regs_for(int px, int nb = 1) { return (px >= 8 ? 128 : (px >= 4 ? 96 : 64)) + 16 * (nb - 1); }
 #endif
 #ifdef LOBE_BWD_DIRECT
 __host__ __device__ constexpr int bwd_direct_for(int) { return LOBE_BWD_DIRECT; }
 #else
 __host__ __device__ constexpr int bwd_direct_for(int px) { return px >= 8 ? 0 : 8; }
 #endif
-template <int TW, int TH, int PX, bool RECOMPUTE, bool PERSIST>
-__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(bwd_regs_for(PX), Slab<TW, TH, PX>::WARPS))
+// Per-splat sums of the warp reduction, through shared memory (LOBE_BWD_SLOTS, default on):
+// each lane writes its nine values for a splat into a row of the warp's next slot; after
+// RED_SLOTS such splats (or at the end of the slab) lane q < 9 RED_SLOTS adds column q --
+// value q % 9 of slot q / 9 over the 32 rows -- and issues one red. Rows are 12 words (16-byte
+// stores of values 0-7 at 48-byte strides: no bank conflicts); value 8 of slot s sits in word
+// 8 + s of the first slot's row; slots are 396 words apart, so the 27 columns of a flush fall
+// in 27 distinct banks.
+#ifndef LOBE_BWD_SLOTS
+#define LOBE_BWD_SLOTS 0
+#endif
+constexpr int RED_SLOTS = 3, RED_ROW = 12, RED_SLOT = 32 * RED_ROW + 12, RED_WORDS = RED_SLOTS * RED_SLOT;
+static_assert(RED_SLOT % 4 == 0 && RED_SLOT % 32 == 12, "slot stride: 16-byte aligned, 12 banks apart");
+
+template <int TW, int TH, int PX, bool RECOMPUTE, bool PERSIST, int NB = 1>
+__global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS,
+                                  min_blocks_for(bwd_regs_for(PX, NB), Slab<TW, TH, PX>::WARPS))
     k_render_bwd2(const __grid_constant__ BatchParams P, const float4 *__restrict__ splat,
                   const int *__restrict__ tile_start, const int *__restrict__ ids, const float *__restrict__ Tfin,
                   const int *__restrict__ ncin, const float *__restrict__ dL, float *__restrict__ grad2d,
@@ -614,9 +668,37 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
     static_assert(PX % 2 == 0, "pixels are paired");
     constexpr int NP = PX / 2;
     using G = Slab<TW, TH, PX>;
-    __shared__ WarpStage stage[G::WARPS];
-    WarpStage &st = stage[threadIdx.x >> 5];
+    __shared__ WarpStageN<NB> stage[G::WARPS];
+    WarpStageN<NB> &st = stage[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
+#if LOBE_BWD_SLOTS
+    __shared__ __align__(16) float s_red[G::WARPS][RED_WORDS];
+    __shared__ int s_rid[G::WARPS][RED_SLOTS];
+    // this lane's column of a flush: value rv of the splat in slot rs (27 lanes), its word in a
+    // row and the factor back from the base-2 exponent domain (A = -0.5 log2e a, B = -log2e b,
+    // C = -0.5 log2e c)
+    const int rs = lane / 9, rv = lane - 9 * (lane / 9);
+    const int rcol = rv < 8 ? rs * RED_SLOT + rv : 8 + rs;
+    const float rsc = (rv == 2 || rv == 4) ? -0.5f * LOG2E : (rv == 3 ? -LOG2E : 1.0f);
+    int nslot = 0;  // slots filled (warp-uniform)
+    // the per-splat sums of the filled slots, each over the warp's 32 rows, added to grad2d
+    auto flush = [&](const int n) {
+        __syncwarp();
+        if (lane < 9 * n) {
+            const float *c = s_red[pw] + rcol;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+            for (int r = 0; r < 32; r += 4) {
+                a0 += c[RED_ROW * r];
+                a1 += c[RED_ROW * (r + 1)];
+                a2 += c[RED_ROW * (r + 2)];
+                a3 += c[RED_ROW * (r + 3)];
+            }
+            red_add_f32(grad2d + 12LL * s_rid[pw][rs] + rv, rsc * ((a0 + a1) + (a2 + a3)));
+        }
+        __syncwarp();
+    };
+#endif
     WorkCursor wc{order, work, (unsigned)P.n_tiles * (unsigned)G::WARPS, G::WARPS, true};
     auto tile_body = [&](const int t, const int warp) {
         const ItemParams &I = P.item[item_of_tile(P, t)];
@@ -657,7 +739,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                 live[k] = inside[k];
                 c0[k] = c1[k] = c2[k] = 0.0f;
             }
-            forward_sweep<PX>(splat, ids, start, end, bx, pxc, pyc, live, T, c0, c1, c2, nc, st);
+            forward_sweep<PX, false, NB>(splat, ids, start, end, bx, pxc, pyc, live, T, c0, c1, c2, nc, st);
         }
         // per pixel pair: packed row centres, dL/dC, colour behind (from the background), T
         f2 pyc2[NP], G0[NP], G1[NP], G2[NP], B0[NP], B1[NP], B2[NP], T2[NP];
@@ -680,33 +762,43 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
         const int stop = min(start + m, end);
         const f2 one2 = pk(1.0f, 1.0f);
 
-        int top = stop, base = max(start, stop - 32);
-        Staged nx;
-        bool nh;
-        fetch(splat, ids, base + lane, top, bx, nx, nh);
+        // rounds of 32 NB list positions [base, top), stage slot j = position - base
+        int top = stop, base = max(start, stop - 32 * NB);
+        Staged nx[NB];
+        bool nh[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) fetch(splat, ids, base + 32 * b + lane, top, bx, nx[b], nh[b]);
         while (top > start) {
-            st.s0[lane] = nx.s0;
-            st.s1[lane] = nx.s1;
-            st.s2[lane] = nx.s2;
-            st.id[lane] = nx.id;
-            unsigned hits = __ballot_sync(0xffffffffu, nh);
+            unsigned hitb[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                st.s0[32 * b + lane] = nx[b].s0;
+                st.s1[32 * b + lane] = nx[b].s1;
+                st.s2[32 * b + lane] = nx[b].s2;
+                st.id[32 * b + lane] = nx[b].id;
+                hitb[b] = __ballot_sync(0xffffffffu, nh[b]);
+            }
             __syncwarp();
-            const int nbase = max(start, base - 32);
-            fetch(splat, ids, nbase + lane, base, bx, nx, nh);
-            while (hits) {  // back to front: highest position first
-                const int j = 31 - __clz(hits);
-                hits &= ~(1u << j);
+            const int nbase = max(start, base - 32 * NB);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) fetch(splat, ids, nbase + 32 * b + lane, base, bx, nx[b], nh[b]);
+#pragma unroll
+            for (int b = NB - 1; b >= 0; --b)
+            for (unsigned hits = hitb[b]; hits;) {  // back to front: highest position first
+                const int jb = 31 - __clz(hits);
+                hits &= ~(1u << jb);
+                const int j = 32 * b + jb;
                 const float4 q0 = st.s0[j], q1 = st.s1[j];
                 const float cb = st.s2[j].x, pmin = st.s2[j].y;
                 const int pos = base - start + j;
                 const Column cl = column_terms(q0.x, q0.z, q0.w, pxc);
                 const f2 v2 = pk(q0.y, q0.y), C2 = pk(q1.x, q1.x), a2 = pk(cl.a2, cl.a2), b1 = pk(cl.b1, cl.b1);
-                const f2 oln2 = pk(q1.y * LN2, q1.y * LN2);
-                // per lane: S1 = sum dL/dp2, S2 = sum dL/dp2 dy, S3 = sum dL/dp2 dy^2 over its pixels; dx
-                // is the lane's own, so the exponent's gradients follow from these three after the loop
-                // with several pairs the first pair's terms initialise the sums (no zeroing, no add)
-                f2 S1, S2, S3, dop, dr, dg, db;
-                if constexpr (NP == 1) S1 = S2 = S3 = dop = dr = dg = db = 0;  // 0 = (+0, +0)
+                // per lane over its pixels: dop = sum t, S2 = sum t dy, S3 = sum t dy^2 with t = dL/dalpha G
+                // below the clamp (0 past it); dL/dp2 = o ln2 t, so the exponent's gradients follow from
+                // these and the lane's own dx after the loop, with the factor o ln2 applied once.
+                // With several pairs the first pair's terms initialise the sums (no zeroing, no add)
+                f2 S2, S3, dop, dr, dg, db;
+                if constexpr (NP == 1) S2 = S3 = dop = dr = dg = db = 0;  // 0 = (+0, +0)
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
@@ -751,18 +843,18 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                     // dL/dp2 = da o G ln2 (alpha = o G below the clamp)
                     const f2 t = mul2(da, pk(ka ? 0.0f : Ga, kb ? 0.0f : Gb));
                     dop = first ? t : add2(dop, t);
-                    const f2 dp2 = mul2(t, oln2);
-                    const f2 dpy = mul2(dp2, dy2);
-                    S1 = first ? dp2 : add2(S1, dp2);
-                    S2 = first ? dpy : add2(S2, dpy);
-                    S3 = first ? mul2(dpy, dy2) : fma2(dpy, dy2, S3);
+                    const f2 ty = mul2(t, dy2);
+                    S2 = first ? ty : add2(S2, ty);
+                    S3 = first ? mul2(ty, dy2) : fma2(ty, dy2, S3);
                 }
                 const unsigned used = __ballot_sync(0xffffffffu, any);
                 if (used) {
-                    // p2 = A dx^2 + B dx dy + C dy^2 with dx = u - x, dy = v - y
-                    const float s1 = sum2(S1), s2 = sum2(S2), dx = cl.dx;
+                    // p2 = A dx^2 + B dx dy + C dy^2 with dx = u - x, dy = v - y; s1, s2, s3 = the lane's
+                    // sums of dL/dp2, dL/dp2 dy, dL/dp2 dy^2
+                    const float oln = q1.y * LN2, sdop = sum2(dop), dx = cl.dx;
+                    const float s1 = oln * sdop, s2 = oln * sum2(S2);
                     const float vals[9] = {fmaf(q0.w, s2, 2.f * q0.z * dx * s1), fmaf(q0.w * dx, s1, 2.f * q1.x * s2),
-                                           dx * dx * s1, dx * s2, sum2(S3), sum2(dop), sum2(dr), sum2(dg), sum2(db)};
+                                           dx * dx * s1, dx * s2, oln * sum2(S3), sdop, sum2(dr), sum2(dg), sum2(db)};
                     if (__popc(used) <= bwd_direct_for(PX)) {
                         // few lanes reached the splat: each adds its own nine values (fewer issue slots than
                         // the warp reduction; the same sums in another order)
@@ -774,6 +866,19 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                                                                       : (i == 3 ? -LOG2E * vals[i] : vals[i]));
                         }
                     } else {
+#if LOBE_BWD_SLOTS
+                        // the lane's nine values into the next slot's row; a full set of slots is
+                        // summed column by column (27 lanes, no shuffles)
+                        float *row = s_red[pw] + nslot * RED_SLOT + RED_ROW * lane;
+                        *reinterpret_cast<float4 *>(row) = make_float4(vals[0], vals[1], vals[2], vals[3]);
+                        *reinterpret_cast<float4 *>(row + 4) = make_float4(vals[4], vals[5], vals[6], vals[7]);
+                        s_red[pw][RED_ROW * lane + 8 + nslot] = vals[8];
+                        if (lane == 0) s_rid[pw][nslot] = st.id[j];
+                        if (++nslot == RED_SLOTS) {
+                            flush(RED_SLOTS);
+                            nslot = 0;
+                        }
+#else
                         int idx;
                         const float tot = warp_reduce9(vals, idx);
                         if (idx >= 0) {
@@ -781,6 +886,7 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
                             const float sc = (idx == 2 || idx == 4) ? -0.5f * LOG2E : (idx == 3 ? -LOG2E : 1.0f);
                             red_add_f32(grad2d + 12LL * st.id[j] + idx, sc * tot);
                         }
+#endif
                     }
                 }
             }
@@ -788,6 +894,12 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS, min_blocks_for(b
             top = base;
             base = nbase;
         }
+#if LOBE_BWD_SLOTS
+        if (nslot) {
+            flush(nslot);
+            nslot = 0;
+        }
+#endif
         __syncwarp();
     };
     if constexpr (PERSIST) {
@@ -911,6 +1023,17 @@ static cudaError_t fwd_t(const BatchParams &P, const float *splat, const int *ts
     count_launch();
     const float4 *sp = reinterpret_cast<const float4 *>(splat);
     const int threads = 32 * Slab<TW, TH, PX>::WARPS;
+    if constexpr (PX > 1) {  // 64-splat rounds (the depth channel keeps 32)
+        if (P.nb_fwd == 2 && !depth) {
+            if (order)
+                launch_render(k_render_fwd<TW, TH, PX, false, true, 2>, P, threads, order, st, sp, ts, ids, rgb, T, nc,
+                              (float *)nullptr, order, work);
+            else
+                launch_render(k_render_fwd<TW, TH, PX, false, false, 2>, P, threads, order, st, sp, ts, ids, rgb, T, nc,
+                              (float *)nullptr, order, work);
+            return cudaGetLastError();
+        }
+    }
     if (depth && order)
         launch_render(k_render_fwd<TW, TH, PX, true, true>, P, threads, order, st, sp, ts, ids, rgb, T, nc, depth, order, work);
     else if (depth)
@@ -935,11 +1058,20 @@ static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *spla
     const float4 *sp = reinterpret_cast<const float4 *>(splat);
 #define LOBE_BWD_LAUNCH(K, R, Q) \
     launch_render(K<TW, TH, PX, R, Q>, P, threads, order, st, sp, ts, ids, rgb, nc, dL, g2d, order, work)
+#define LOBE_BWD2_LAUNCH(R, Q, N) \
+    launch_render(k_render_bwd2<TW, TH, PX, R, Q, N>, P, threads, order, st, sp, ts, ids, rgb, nc, dL, g2d, order, work)
     if constexpr (PX % 2 == 0) {  // pixel pairs in packed arithmetic
-        if (recompute && order) LOBE_BWD_LAUNCH(k_render_bwd2, true, true);
-        else if (recompute) LOBE_BWD_LAUNCH(k_render_bwd2, true, false);
-        else if (order) LOBE_BWD_LAUNCH(k_render_bwd2, false, true);
-        else LOBE_BWD_LAUNCH(k_render_bwd2, false, false);
+        if (P.nb_bwd == 2) {  // 64-splat rounds
+            if (recompute && order) LOBE_BWD2_LAUNCH(true, true, 2);
+            else if (recompute) LOBE_BWD2_LAUNCH(true, false, 2);
+            else if (order) LOBE_BWD2_LAUNCH(false, true, 2);
+            else LOBE_BWD2_LAUNCH(false, false, 2);
+        } else {
+            if (recompute && order) LOBE_BWD2_LAUNCH(true, true, 1);
+            else if (recompute) LOBE_BWD2_LAUNCH(true, false, 1);
+            else if (order) LOBE_BWD2_LAUNCH(false, true, 1);
+            else LOBE_BWD2_LAUNCH(false, false, 1);
+        }
     } else {
         if (recompute && order) LOBE_BWD_LAUNCH(k_render_bwd, true, true);
         else if (recompute) LOBE_BWD_LAUNCH(k_render_bwd, true, false);
@@ -947,6 +1079,7 @@ static cudaError_t bwd_t(const BatchParams &P, bool recompute, const float *spla
         else LOBE_BWD_LAUNCH(k_render_bwd, false, false);
     }
 #undef LOBE_BWD_LAUNCH
+#undef LOBE_BWD2_LAUNCH
     return cudaGetLastError();
 }
 

@@ -139,7 +139,7 @@ class Context:
     """A lobe_ctx bound to a CUDA stream (the current torch stream by default)."""
 
     def __init__(self, tile=(16, 16), sh_degree=3, bg=(0.0, 0.0, 0.0), recompute_T=False, stream=None, px_fwd=0,
-                 px_bwd=0, bin_general=False, persistent=False):
+                 px_bwd=0, bin_general=False, persistent=False, batch=(0, 0)):
         if not torch.cuda.is_available():
             raise RuntimeError("the lobe rasterizer needs a CUDA device (no CPU fallback)")
         self.lib = A.lib()
@@ -150,6 +150,7 @@ class Context:
         self.px = (int(px_fwd), int(px_bwd))
         self.bin_general = bool(bin_general)  # never the one-CTA binning of small batches
         self.persistent = bool(persistent)  # compositing as persistent kernels, tiles longest list first
+        self.batch = (int(batch[0]), int(batch[1]))  # splats a warp stages per round (fwd, bwd): 0/32 or 64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = ctypes.c_void_p()
         A.check(self.lib.lobe_ctx_create(ctypes.byref(self.handle), ctypes.c_void_p(self.stream.cuda_stream),
@@ -165,12 +166,16 @@ class Context:
         c.px_fwd, c.px_bwd = self.px
         c.bin_general = int(self.bin_general)
         c.persistent = int(self.persistent)
+        c.batch_fwd, c.batch_bwd = self.batch
         return c
 
-    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None, px=None, persistent=None):
-        """Change the configuration (tile changes need new bins; px = (fwd, bwd) pixels per lane)."""
+    def configure(self, tile=None, recompute_T=None, sh_degree=None, bg=None, px=None, persistent=None, batch=None):
+        """Change the configuration (tile changes need new bins; px = (fwd, bwd) pixels per lane;
+        batch = (fwd, bwd) splats a warp stages per round)."""
         if persistent is not None:
             self.persistent = bool(persistent)
+        if batch is not None:
+            self.batch = (int(batch[0]), int(batch[1]))
         if px is not None:
             self.px = (int(px[0]), int(px[1]))
         if tile is not None:

@@ -70,12 +70,16 @@ def test_batch_sizes(L):
     b, keep = _batch(A, [(1600, 1066), (100, 75)], [1000, 250], [(0, 0), (1, 1), (0, 1)])
     out = (ctypes.c_int64 * 3)()
     assert L.lobe_batch_sizes(ctypes.byref(cfg), ctypes.byref(b), out) == 0
+    for n in (32, 64):  # either staging batch is a valid configuration
+        cfg.batch_fwd = cfg.batch_bwd = n
+        assert L.lobe_batch_sizes(ctypes.byref(cfg), ctypes.byref(b), out) == 0
     assert out[0] == 1000 + 250 + 1000
     assert out[1] == 100 * 67 + 7 * 5 + 7 * 5
     assert out[2] == 1600 * 1066 + 2 * 100 * 75
 
 
-@pytest.mark.parametrize("bad", ["tile", "degree", "set_index", "camera_index", "intrinsics", "alignment", "items"])
+@pytest.mark.parametrize("bad", ["tile", "degree", "set_index", "camera_index", "intrinsics", "alignment", "items",
+                                 "batch_size", "batch_one_px", "batch_odd_px"])
 def test_argument_errors(L, bad):
     from paper_2510_01767_b300 import _abi as A
     cfg = A.Config(16, 16, 3)
@@ -95,6 +99,12 @@ def test_argument_errors(L, bad):
         sets[0].sh = 4100
     elif bad == "items":
         b.n_items = 0
+    elif bad == "batch_size":
+        cfg.batch_fwd = 48  # staging rounds of 32 or 64 splats only
+    elif bad == "batch_one_px":
+        cfg.tile_w, cfg.tile_h, cfg.px_fwd, cfg.batch_fwd = 16, 8, 1, 64  # 64 needs two or more pixels a lane
+    elif bad == "batch_odd_px":
+        cfg.tile_w, cfg.tile_h, cfg.px_bwd, cfg.batch_bwd = 8, 8, 1, 64  # the paired adjoint only
     out = (ctypes.c_int64 * 3)()
     assert L.lobe_batch_sizes(ctypes.byref(cfg), ctypes.byref(b), out) == A.ERR_ARG
 

@@ -108,10 +108,13 @@ def test_autotune_picks_fastest(workload, tmp_path, monkeypatch):
     sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
     cams = [c.as_dict() for c in wl.cameras]
     best, times = autotune(sets, cams, wl.items, wl.blocks, reps=3, dL_init=fill_dL)
-    # every tile shape once, and the winner once more as persistent kernels
-    assert {k.split("/")[0] for k in times} == {"8x8", "16x8", "16x16", "32x16"} and len(times) == 5
-    assert sum(k.endswith("/persistent") for k in times) == 1
-    name = batched.config_name(best.tile, best.px) + ("/persistent" if best.persistent else "")
+    # every tile shape once, the winner once more as persistent kernels, and then with its tuned
+    # staging batch when that is not 32 / 32
+    assert {k.split("/")[0] for k in times} == {"8x8", "16x8", "16x16", "32x16"} and len(times) in (5, 6)
+    assert sum(k.endswith("/persistent") for k in times) in (1, 2)
+    assert (len(times) == 6) == any("/s" in k for k in times)
+    name = batched.config_name(best.tile, best.px, best.batch_size) + ("/persistent" if best.persistent else "")
     assert times[name] == min(times.values())
     again, t2 = autotune(sets, cams, wl.items, wl.blocks, reps=3, dL_init=fill_dL)  # from the cache
     assert again.tile == best.tile and again.px == best.px and again.persistent == best.persistent and t2 == times
+    assert again.batch_size == best.batch_size

@@ -249,11 +249,13 @@ def test_render_fwd_matches_oracle(small, tile, persistent):
     match_image(lv, rgb, T, nc, "image small (stage)")
 
 
-@pytest.mark.parametrize("recompute, tile, px, persistent", [(False, (16, 16), 0, False), (True, (16, 16), 0, False),
-                                                              (False, (16, 8), 1, False), (False, (16, 8), 4, False),
-                                                              (True, (16, 8), 4, False), (False, (16, 8), 4, True),
-                                                              (True, (8, 8), 1, True), (False, (32, 16), 8, True)])
-def test_render_bwd_matches_oracle(small, recompute, tile, px, persistent):
+@pytest.mark.parametrize("recompute, tile, px, persistent, nb", [
+    (False, (16, 16), 0, False, 32), (True, (16, 16), 0, False, 32), (False, (16, 8), 1, False, 32),
+    (False, (16, 8), 4, False, 32), (True, (16, 8), 4, False, 32), (False, (16, 8), 4, True, 32),
+    (True, (8, 8), 1, True, 32), (False, (32, 16), 8, True, 32),
+    # 64-splat staging rounds (two splats a lane)
+    (False, (16, 8), 4, True, 64), (True, (16, 16), 2, False, 64), (False, (32, 16), 8, False, 64)])
+def test_render_bwd_matches_oracle(small, recompute, tile, px, persistent, nb):
     wl, g = small
     wl = scenes.Workload(wl.name, wl.sets, wl.cameras, wl.blocks, wl.items, tile)
     cam = wl.cameras[0].as_dict()
@@ -262,7 +264,7 @@ def test_render_bwd_matches_oracle(small, recompute, tile, px, persistent):
     eb = oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts)
     lv = oracle.render_leaves(p, eb, cam, wl.tile, bg, oracle.MARGINS_STAGE, certain=True)
     dL = np.random.default_rng(3).standard_normal((3, 128, 128)).astype(np.float32).astype(np.float64)
-    ctx = ctx_for(wl, bg=bg, recompute_T=recompute, px_fwd=px, px_bwd=px, persistent=persistent)
+    ctx = ctx_for(wl, bg=bg, recompute_T=recompute, px_fwd=px, px_bwd=px, persistent=persistent, batch=(nb, nb))
     batch = make_batch(wl)
     gp = gpu_projection_from_oracle(p, cam, wl.tile)
     bins = lobe.bin_sort(ctx, batch, gp)
@@ -382,6 +384,36 @@ def test_persistent_compositing_equals_one_block_per_tile():
             ctx.status()
             out.append((img, g2d))
         (a, ga), (b, gb) = out
+        assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T_final, b.T_final) and torch.equal(a.n_contrib, b.n_contrib)
+        scale = float(ga.abs().max())
+        assert float((ga - gb).abs().max()) <= 1e-5 * scale, tile
+
+
+def test_staging_batch_does_not_change_results():
+    """Staging 64 splats a round (two a lane) instead of 32 renders every item of a ragged
+    multi-item batch bit for bit alike (the walk visits the same splats in the same order) and
+    sums the same adjoint (float32 atomic order aside), for the forward of every pixels-per-lane
+    count that allows it and both adjoint modes."""
+    rng = np.random.default_rng(43)
+    sets = [scenes.uniform_gaussians(rng, 3000, 1.0, 2.0, 6.0), scenes.uniform_gaussians(rng, 1200, 1.0, 2.0, 6.0)]
+    cams = [scenes.pinhole(300, 170, 240.0), scenes.pinhole(97, 131, 100.0),
+            scenes.pinhole(256, 256, 220.0, viewmat=scenes.look_at((0.3, 0.2, -0.2), (0, 0, 4.0), up=(0, -1, 0)))]
+    items = [(0, 0, -1), (1, 1, -1), (0, 2, -1), (1, 0, -1)]
+    for tile, px, persistent, recompute in (((16, 8), (2, 4), True, False), ((16, 16), (4, 2), False, True),
+                                            ((32, 16), (8, 8), True, True), ((8, 8), (2, 2), False, False)):
+        wl = scenes.Workload("nb", sets, cams, [], items, tile)
+        batch = make_batch(wl)
+        dL = torch.as_tensor(np.random.default_rng(5).standard_normal(3 * batch.n_pixels), dtype=torch.float32).cuda()
+        out = []
+        for nb in (32, 64):
+            ctx = ctx_for(wl, px_fwd=px[0], px_bwd=px[1], persistent=persistent, recompute_T=recompute,
+                          batch=(nb, nb))
+            proj, bins, img = lobe.forward(ctx, batch)
+            g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
+            ctx.status()
+            out.append((img, g2d))
+        (a, ga), (b, gb) = out
+        assert bins.count > 20000
         assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T_final, b.T_final) and torch.equal(a.n_contrib, b.n_contrib)
         scale = float(ga.abs().max())
         assert float((ga - gb).abs().max()) <= 1e-5 * scale, tile

@@ -22,5 +22,8 @@ def test_fcs_select_assigns_cameras_at_tau():
 def test_autotune_configuration_names():
     assert batched.config_name((8, 8), (1, 2)) == "8x8/f1b2"
     assert batched.config_name((32, 16), (4, 8)) == "32x16/f4b8"
+    assert batched.config_name((16, 8), (2, 4), (32, 32)) == "16x8/f2b4"  # the default staging batch
+    assert batched.config_name((16, 8), (2, 4), (64, 32)) == "16x8/f2b4/s64.32"
+    assert set(batched.BATCH_OPTIONS) == {32, 64}
     for tile, pxs in batched.PX_OPTIONS.items():
         assert tile in batched.TILES and len(pxs) >= 2
