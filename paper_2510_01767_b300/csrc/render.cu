@@ -651,7 +651,7 @@ __host__ __device__ constexpr int bwd_direct_for(int px) { return px >= 8 ? 0 : 
 // 8 + s of the first slot's row; slots are 396 words apart, so the 27 columns of a flush fall
 // in 27 distinct banks.
 #ifndef LOBE_BWD_SLOTS
-#define LOBE_BWD_SLOTS 0
+#define LOBE_BWD_SLOTS 1
 #endif
 constexpr int RED_SLOTS = 3, RED_ROW = 12, RED_SLOT = 32 * RED_ROW + 12, RED_WORDS = RED_SLOTS * RED_SLOT;
 static_assert(RED_SLOT % 4 == 0 && RED_SLOT % 32 == 12, "slot stride: 16-byte aligned, 12 banks apart");
