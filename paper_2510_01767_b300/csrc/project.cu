@@ -114,6 +114,28 @@ __device__ __forceinline__ void load_world(const SetParams &S, long long g, Worl
 __device__ __forceinline__ float clamp_color(float raw) { return raw < 0.f ? -0.0f : raw; }
 __device__ __forceinline__ bool color_clamped(float stored) { return (__float_as_uint(stored) >> 31) != 0; }
 
+// View direction n = normalize(mu - campos) and the SH basis polynomials at n (the forward and
+// the adjoint call this one function).
+__device__ __forceinline__ float view_basis(const World &w, const float campos[3], int deg, float n[3], float Pp[16])
+{
+    const float dx = w.mx - campos[0], dy = w.my - campos[1], dz = w.mz - campos[2];
+    const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(dz, dz))));
+    n[0] = __fmul_rn(dx, il);
+    n[1] = __fmul_rn(dy, il);
+    n[2] = __fmul_rn(dz, il);
+    sh_poly(deg, n[0], n[1], n[2], Pp);
+    return il;
+}
+
+// One term of the raw colour sum_b k_b P_b sh_b,ch (channel by channel in ascending band order).
+__device__ __forceinline__ float sh_term(int b, const float Pp[16], float coef, float acc)
+{
+    return fmaf(__fmul_rn(kSH[b], Pp[b]), coef, acc);
+}
+
+// Opacity of a logit.
+__device__ __forceinline__ float opacity_of(float logit) { return 1.0f / (1.0f + __expf(-logit)); }
+
 // Camera-dependent part of the projection. Returns false when culled.
 struct Cam2D {
     float x, y, z;      // camera-space mean (z rounded from the double evaluation)
@@ -181,14 +203,19 @@ __device__ __forceinline__ bool project_cam(const BatchParams &P, const ItemPara
 // Memory layout of the forward (B300): a warp takes 32 consecutive Gaussians. Their SH rows
 // (192 contiguous bytes each, 6 KB for the warp) are copied once into shared memory by
 // coalesced 16-byte asynchronous copies (cp.async: no registers, all in flight while the
-// geometry is loaded and projected), into rows of 13 float4 so that the per-thread reads of
-// every view fall in distinct banks. Each view's 48-byte splat records go out the same way:
-// staged per warp, then written as contiguous 16-byte stores. A warp whose Gaussians span two
-// sets (at most one warp per set boundary) copies and stores per thread instead.
+// geometry is loaded and projected), swizzled so that the per-thread reads of every view fall
+// in distinct banks; the per-view colour then costs shared-memory reads instead of 12 strided
+// 16-byte global loads a view. A warp whose Gaussians span two sets (at most one warp per set
+// boundary) copies per thread instead. Staging the 48-byte splat records for contiguous stores
+// as well was measured slower (it limits the SM to 7 blocks).
 
 constexpr int PF_THREADS = 128;
 constexpr int PF_WARPS = PF_THREADS / 32;
-constexpr int PF_ROW = 13;  // float4 per staged SH row: 12 used, 1 pad (208-byte rows: conflict-free 16-byte reads)
+// SH rows: 12 float4 each, chunk c of Gaussian i at c ^ ((i >> 1) & 3), so that each quarter
+// warp's 16-byte reads of one chunk index (threads i .. i + 7) fall in 8 distinct 16-byte bank
+// groups without padding; 24 KB a block, 8 blocks (32 warps) an SM at 64 registers.
+constexpr int PF_ROW = 12;
+__device__ __forceinline__ int pf_slot(int i, int c) { return i * PF_ROW + (c ^ ((i >> 1) & 3)); }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -200,13 +227,12 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(PF_THREADS, 7) k_project_fwd(const __grid_constant__ BatchParams P,
+__global__ void __launch_bounds__(PF_THREADS, 8) k_project_fwd(const __grid_constant__ BatchParams P,
                                                               float4 *__restrict__ splat, int *__restrict__ radius,
                                                               int *__restrict__ tiles)
 {
     pdl_wait();
     __shared__ float4 s_sh[PF_WARPS][32 * PF_ROW];
-    __shared__ float4 s_out[PF_WARPS][32 * 3];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const long long t = (long long)blockIdx.x * PF_THREADS + threadIdx.x;
     if (t - lane >= P.n_gauss) return;  // the whole warp is past the end
@@ -220,91 +246,59 @@ __global__ void __launch_bounds__(PF_THREADS, 7) k_project_fwd(const __grid_cons
     const bool one_set = __all_sync(0xffffffffu, s == __shfl_sync(0xffffffffu, s, 0));
     const int nb = (P.sh_degree + 1) * (P.sh_degree + 1);
     const int per = (3 * nb + 3) / 4;  // float4 chunks holding the used coefficients
-    float4 *row = &s_sh[wp][lane * PF_ROW];
+    float4 *row = &s_sh[wp][0];  // this lane's chunks at pf_slot(lane, c)
     if (one_set) {
         // chunk f = lane + 32 r of the warp's 32 x 12: Gaussian f / 12, chunk f % 12
         const float4 *base = reinterpret_cast<const float4 *>(S.sh) + 12 * (g - lane);
 #pragma unroll
         for (int r = 0; r < 12; ++r) {
             const int f = lane + 32 * r, i = f / 12, c = f - 12 * i;
-            if (c < per && ((need >> i) & 1u)) cp_async16(&s_sh[wp][i * PF_ROW + c], base + f);
+            if (c < per && ((need >> i) & 1u)) cp_async16(&s_sh[wp][pf_slot(i, c)], base + f);
         }
     } else if (!cropped) {
         const float4 *shg = reinterpret_cast<const float4 *>(S.sh + 48 * g);
-        for (int c = 0; c < per; ++c) cp_async16(row + c, shg + c);
+        for (int c = 0; c < per; ++c) cp_async16(row + pf_slot(lane, c), shg + c);
     }
     World w;
     if (!cropped) load_world(S, g, w);
     cp_async_wait_all();
     __syncwarp();
+    if (!valid) return;
     float opacity = 0.0f;
     bool first = true;
-    // every lane walks the longest item list of the warp's sets (one set: the same list)
-    const int n_it = valid ? S.item_count : 0;
-    const int n_loop = one_set ? S.item_count : __reduce_max_sync(0xffffffffu, (unsigned)n_it);
-    for (int k = 0; k < n_loop; ++k) {
-        const bool has = k < n_it;
-        bool vis = false;
-        long long e = 0;
-        float4 o0, o1, o2;
-        if (has) {
-            const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
-            e = I.entry_off + g;
-            Cam2D c;
-            vis = !cropped && project_cam(P, I, w, c);
-            if (vis) {
-                if (first) {
-                    opacity = 1.0f / (1.0f + __expf(-S.logits[g]));
-                    first = false;
-                }
-                float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
-                float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-                float Pp[16];
-                sh_poly(P.sh_degree, dx * il, dy * il, dz * il, Pp);
-                float col[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < 12; ++i) {
-                    if (4 * i >= 3 * nb) break;
-                    const float4 q = row[i];
-                    const float qv[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int idx = 4 * i + m, b = idx / 3;
-                        if (b < nb) col[idx % 3] += kSH[b] * Pp[b] * qv[m];
-                    }
-                }
-                o0 = make_float4(c.u, c.v, c.ca, c.cb);
-                o1 = make_float4(c.cc, opacity, clamp_color(col[0] + 0.5f), clamp_color(col[1] + 0.5f));
-                o2 = make_float4(clamp_color(col[2] + 0.5f), c.z, 0.f, 0.f);
-            }
-            radius[e] = vis ? c.radius : 0;
-            tiles[e] = vis ? (c.x1 - c.x0) * (c.y1 - c.y0) : 0;
+    for (int k = 0; k < S.item_count; ++k) {
+        const ItemParams &I = P.item[P.set_items[S.item_begin + k]];
+        const long long e = I.entry_off + g;
+        Cam2D c;
+        if (cropped || !project_cam(P, I, w, c)) {
+            radius[e] = 0;
+            tiles[e] = 0;
+            continue;
         }
-        if (one_set) {
-            // the warp's 32 consecutive entries of this item (lane 0 is always in range): records
-            // staged, then contiguous 16-byte stores of the visible ones
-            const unsigned vm = __ballot_sync(0xffffffffu, vis);
-            const long long e0 = __shfl_sync(0xffffffffu, e - lane, 0);
-            if (vm == 0u) continue;
-            if (vis) {
-                s_out[wp][3 * lane] = o0;
-                s_out[wp][3 * lane + 1] = o1;
-                s_out[wp][3 * lane + 2] = o2;
-            }
-            __syncwarp();
-            float4 *dst = splat + 3 * e0;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const int f = lane + 32 * r;
-                if ((vm >> (f / 3)) & 1u) dst[f] = s_out[wp][f];
-            }
-            __syncwarp();
-        } else if (vis) {
-            float4 *o = splat + 3 * e;
-            o[0] = o0;
-            o[1] = o1;
-            o[2] = o2;
+        if (first) {
+            opacity = opacity_of(S.logits[g]);
+            first = false;
         }
+        float n[3], Pp[16];
+        view_basis(w, I.campos, P.sh_degree, n, Pp);
+        float col[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            if (4 * i >= 3 * nb) break;
+            const float4 q = row[pf_slot(lane, i)];
+            const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int idx = 4 * i + m, b = idx / 3;
+                if (b < nb) col[idx % 3] = sh_term(b, Pp, qv[m], col[idx % 3]);
+            }
+        }
+        float4 *o = splat + 3 * e;
+        o[0] = make_float4(c.u, c.v, c.ca, c.cb);
+        o[1] = make_float4(c.cc, opacity, clamp_color(col[0] + 0.5f), clamp_color(col[1] + 0.5f));
+        o[2] = make_float4(clamp_color(col[2] + 0.5f), c.z, 0.f, 0.f);
+        radius[e] = c.radius;
+        tiles[e] = (c.x1 - c.x0) * (c.y1 - c.y0);
     }
 }
 
@@ -565,14 +559,14 @@ __device__ __forceinline__ void project_bwd_body(const BatchParams &P, const flo
             glogit += dop * o * (1.f - o);
             // ---- colour / SH. The forward's clamp decisions (sign bits of the stored colour)
             // mask the colour gradient: md_ch = dL/dcolour_ch where the channel was not clamped.
+            // (Recomputing the opacity and the raw colours from the staged coefficients instead
+            // of reading these 32 bytes a view was measured slower: 1.79 -> 1.89 ms.)
             const float md[3] = {color_clamped(sp1.z) ? 0.f : g1.z, color_clamped(sp1.w) ? 0.f : g1.w,
                                  color_clamped(splat[3 * e + 2].x) ? 0.f : g2.x};
+            float nv[3], Pp[16];
+            const float il = view_basis(w, I.campos, P.sh_degree, nv, Pp);
+            const float nx = nv[0], ny = nv[1], nz = nv[2];
             // dL/dsh_b,ch = k_b P_b md_ch; the view direction n gets sum_b k_b grad P_b (sum_ch md_ch sh_b,ch)
-            float dx = w.mx - I.campos[0], dy = w.my - I.campos[1], dz = w.mz - I.campos[2];
-            float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-            float nx = dx * il, ny = dy * il, nz = dz * il;
-            float Pp[16];
-            sh_poly(P.sh_degree, nx, ny, nz, Pp);
             float dn[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int b = 0; b < 16; ++b) {
@@ -770,23 +764,23 @@ __device__ __forceinline__ void project_bwd_body(const BatchParams &P, const flo
                 }
             }
         }
-        return;
-    }
-    // ---- SH gradients of the block's Gaussians: 12 float4 per Gaussian, consecutive threads
-    // take consecutive chunks of one Gaussian's 192 bytes
+    } else {
+        // ---- SH gradients of the block's Gaussians: 12 float4 per Gaussian, consecutive threads
+        // take consecutive chunks of one Gaussian's 192 bytes
 #pragma unroll
-    for (int r = 0; r < 12; ++r) {
-        const int j = threadIdx.x + r * PB_THREADS;  // float4 slot: Gaussian j / 12, chunk j % 12
-        if (j >= nblk * 12) break;
-        const int gi = j / 12, c = j - gi * 12;
-        float4 *dst = reinterpret_cast<float4 *>(s_dst[gi]) + c;
-        const float *v = s_gsh + gi * PB_ROW + 4 * c;
-        float4 a = make_float4(v[0], v[1], v[2], v[3]);
-        if (accumulate) {
-            const float4 b = *dst;
-            a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+        for (int r = 0; r < 12; ++r) {
+            const int j = threadIdx.x + r * PB_THREADS;  // float4 slot: Gaussian j / 12, chunk j % 12
+            if (j >= nblk * 12) break;
+            const int gi = j / 12, c = j - gi * 12;
+            float4 *dst = reinterpret_cast<float4 *>(s_dst[gi]) + c;
+            const float *v = s_gsh + gi * PB_ROW + 4 * c;
+            float4 a = make_float4(v[0], v[1], v[2], v[3]);
+            if (accumulate) {
+                const float4 b = *dst;
+                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+            }
+            *dst = a;
         }
-        *dst = a;
     }
 }
 
