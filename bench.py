@@ -16,6 +16,7 @@ collective on the data path.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -464,9 +465,26 @@ def stage_table(stage_ms, work, hbm_peak, fp32_peak):
     return stages, names[int(np.argmax(mean_ms))]
 
 
+def source_digest(paths):
+    """sha1 (16 hex digits) of the given package source files, in order: the traffic files
+    record it for the kernels they were captured from."""
+    h = hashlib.sha1()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_of(name, workload):
+    """DRAM bytes per launch from profiles/traffic_<stage>_<workload>.json, or None when absent
+    or when the kernel sources changed since the capture (the file's source digest)."""
     tf = os.path.join(ROOT, "profiles", f"traffic_{name}_{workload}.json")
-    return json.load(open(tf)) if os.path.exists(tf) else None
+    if not os.path.exists(tf):
+        return None
+    t = json.load(open(tf))
+    if "sources" in t and source_digest(t["sources"]) != t.get("source_sha1"):
+        return None
+    return t
 
 
 def e2e_pipelined(torch, st, K, params, world):
@@ -806,7 +824,36 @@ def training_benchmark(steps=200, warm=20):
 
 # --------------------------------------------------------------------------- batched vs plain
 
-def batched_vs_plain(lobe, torch, wl, sets, st, batched_ms, reps=5):
+def plain_stage_ms(torch, plain, reps):
+    """Where the plain path's time goes: each stage run for every view in turn (every view's
+    buffers are its own, so the stages can be grouped), CUDA events between the groups; mean
+    ms a step per stage, summed over the views."""
+    import paper_2510_01767_b300 as lobe
+    stream = torch.cuda.current_stream()
+    names = ["project", "bin_sort", "render_fwd", "render_bwd", "project_bwd"]
+
+    def stage(i, p):
+        c, b = p.ctx, p.batch
+        return [lambda: lobe.project(c, b, p.proj), lambda: lobe.bin_sort(c, b, p.proj, p.bins, sync=False),
+                lambda: lobe.render_fwd(c, b, p.proj, p.bins, p.image),
+                lambda: lobe.render_bwd(c, b, p.proj, p.bins, p.image, p.dL, p.grad2d),
+                lambda: lobe.project_bwd(c, b, p.proj, p.grad2d, p.grads, accumulate=False)][i]()
+
+    tot = np.zeros(5)
+    for r in range(reps + 1):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        evs[0].record(stream)
+        for i in range(5):
+            for p in plain.steps:
+                stage(i, p)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if r > 0:  # the first round warms up
+            tot += [evs[i].elapsed_time(evs[i + 1]) for i in range(5)]
+    return {n: round(float(t / reps), 4) for n, t in zip(names, tot)}
+
+
+def batched_vs_plain(lobe, torch, wl, sets, st, batched_ms, reps=5, batched_stages=None):
     """The batched graph step (already timed) against the plain path on the same batch: one
     view per call sequence, eager, same tile shape, pixels per lane, persistent choice and
     staging batch; and against the
@@ -820,6 +867,7 @@ def batched_vs_plain(lobe, torch, wl, sets, st, batched_ms, reps=5):
     for p in plain.steps:
         p.dL.copy_(torch.randn(p.dL.shape, generator=gen, device="cuda"))
     plain_ms = _time(plain.run, reps, torch.cuda.current_stream())
+    plain_stages = plain_stage_ms(torch, plain, reps)
     del plain
     torch.cuda.empty_cache()
     params = [[getattr(s, k).clone().requires_grad_(True) for k in lobe.PARAM_KEYS] for s in sets]
@@ -845,6 +893,8 @@ def batched_vs_plain(lobe, torch, wl, sets, st, batched_ms, reps=5):
             "staging_batch": list(st.batch_size), "batched_ms": round(batched_ms, 3), "plain_ms": round(plain_ms, 3),
             "batched_mpix_s": round(pixels / batched_ms / 1e3, 1), "plain_mpix_s": round(pixels / plain_ms / 1e3, 1),
             "ratio": round(plain_ms / batched_ms, 3),
+            "plain_stages_ms": plain_stages,
+            "batched_stages_ms": {k: v["ms"] for k, v in (batched_stages or {}).items()},
             "autograd_per_view_ms": round(autograd_ms, 3), "ratio_vs_autograd_per_view": round(autograd_ms / batched_ms, 3),
             "note": "ratio: against the eager one-view-per-call library path (no host synchronisation); "
                     "ratio_vs_autograd_per_view: against the autograd.Function called view by view (host-timed)"}
@@ -865,6 +915,7 @@ def single_view_extra(lobe, torch, args, rank, flush, hbm_peak, fp32_peak, K=10)
     stages, dom = stage_table(stage_ms, work, hbm_peak, fp32_peak)
     return {"workload": wl.name, "value": round(st.batch.n_pixels / float(ms.mean()) / 1e3, 3), "unit": UNIT,
             "ms_per_step": round(float(ms.mean()), 4), "tile": list(st.tile), "px_per_lane": list(st.px),
+            "persistent": st.persistent, "staging_batch": list(st.batch_size), "staging_batch_ms": st.batch_times,
             "tuning_ms": {k: round(v, 4) for k, v in (tuning or {}).items()}, "stages": stages, **counts}, st
 
 
@@ -962,8 +1013,10 @@ def main():
         cpu = cpu_baseline(wl, sampler)
         sampler.close()
     if world == 1 and not args.no_extras:
-        extras["batched_vs_plain"] = batched_vs_plain(lobe, torch, wl, sets, st, float(np.median(step_ms)))
+        extras["batched_vs_plain"] = batched_vs_plain(lobe, torch, wl, sets, st, float(np.median(step_ms)),
+                                                      batched_stages=stages)
     graph_tile, graph_px, graph_persistent, graph_batch = st.tile, st.px, st.persistent, st.batch_size
+    graph_batch_times = st.batch_times
     del st
     torch.cuda.empty_cache()
     if world == 1 and not args.no_extras and args.workload != "medium":
@@ -988,7 +1041,8 @@ def main():
                        "tile": list(graph_tile), "px_per_lane": {"fwd": graph_px[0] or "default",
                                                                   "bwd": graph_px[1] or "default"},
                        "persistent_compositing": graph_persistent,
-                       "staging_batch": {"fwd": graph_batch[0] or 32, "bwd": graph_batch[1] or 32},
+                       "staging_batch": {"fwd": graph_batch[0] or 32, "bwd": graph_batch[1] or 32,
+                                         "tuning_ms": graph_batch_times},
                        "tuning_ms": ({k: round(v, 4) for k, v in tuning.items()} if tuning else None),
                        "sh_degree": 3, **counts,
                        "step": "one CUDA graph replay: projection (each set once for all its views), binning of "

@@ -50,6 +50,7 @@ class BatchedStep:
                              px_fwd=px[0], px_bwd=px[1], persistent=persistent, batch=batch)
         self.px = px
         self.batch_size = batch
+        self.batch_times = None
         self.persistent = bool(persistent)
         self.batch = R.Batch(sets, cameras, items, blocks)
         self.tile = tuple(tile)
@@ -104,6 +105,7 @@ class BatchedStep:
         skipped. Returns (fwd, bwd)."""
         c, b = self.ctx, self.batch
         best = {"f": (float("inf"), 32), "b": (float("inf"), 32)}
+        self.batch_times = {"fwd": {}, "bwd": {}}  # ms of the composite / adjoint per staging batch
 
         def settable(batch):
             old = c.batch
@@ -119,11 +121,13 @@ class BatchedStep:
             for n in options:
                 if settable((n, 32)):
                     fwd = _time(lambda: R.render_fwd(c, b, self.proj, self.bins, self.image), reps, self.stream)
+                    self.batch_times["fwd"][n] = round(fwd, 4)
                     if fwd < best["f"][0]:
                         best["f"] = (fwd, n)
                 if settable((32, n)):
                     bwd = _time(lambda: R.render_bwd(c, b, self.proj, self.bins, self.image, self.dL, self.grad2d),
                                 reps, self.stream)
+                    self.batch_times["bwd"][n] = round(bwd, 4)
                     if bwd < best["b"][0]:
                         best["b"] = (bwd, n)
         self.set_batch((best["f"][1], best["b"][1]))

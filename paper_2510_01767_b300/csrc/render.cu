@@ -627,21 +627,23 @@ __global__ void __launch_bounds__(32 * Slab<TW, TH, PX>::WARPS)
 
 // Register cap of the paired adjoint per pixels a lane (occupancy: the kernel is latency- as
 // much as issue-bound), and the lanes below which a splat skips the warp reduction. Measured on
-// B300 (16 views of a 6.5M-Gaussian city): one pixel pair a lane at 64 registers and two at 96
-// run faster than at the compiler's choice (92-114 registers); four pairs keep 128 (lower caps
-// spill). The direct path for splats that at most 8 lanes use saves ~10% where splats are
-// small, and costs where they are large (four pairs a lane are chosen for large ones). Together:
-// the city batch's adjoint 11.1 -> 8.9-9.3 ms.
+// B300 (16 views of a 6.5M-Gaussian city): one pixel pair a lane at 64 registers runs faster
+// than at the compiler's choice; two pairs ask for 104, which one-warp blocks (16x8 tiles) get
+// as 96 at 5 warps a scheduler (8.52 -> 8.12 ms against 80 registers at 6 warps; 128 at 4:
+// 8.87 ms); four pairs keep 128 (lower caps spill). The direct path for splats that few lanes
+// use saves ~10% where splats are small, and costs where they are large (four pairs a lane are
+// chosen for large ones): up to 4 lanes with two pairs (8.61 -> 8.53 ms against 8; 16 lanes:
+// 12.4 ms), 8 with one. Together: the city batch's adjoint 11.1 -> 8.1 ms.
 #ifdef LOBE_BWD_REGS
 constexpr int bwd_regs_for(int, int = 1) { return LOBE_BWD_REGS; }
 #else
 // 64-splat staging rounds keep a second prefetched splat per lane: 16 more registers
-constexpr int bwd_regs_for(int px, int nb = 1) { return (px >= 8 ? 128 : (px >= 4 ? 96 : 64)) + 16 * (nb - 1); }
+constexpr int bwd_regs_for(int px, int nb = 1) { return (px >= 8 ? 128 : (px >= 4 ? 104 : 64)) + 16 * (nb - 1); }
 #endif
 #ifdef LOBE_BWD_DIRECT
 __host__ __device__ constexpr int bwd_direct_for(int) { return LOBE_BWD_DIRECT; }
 #else
-__host__ __device__ constexpr int bwd_direct_for(int px) { return px >= 8 ? 0 : 8; }
+__host__ __device__ constexpr int bwd_direct_for(int px) { return px >= 8 ? 0 : (px >= 4 ? 4 : 8); }
 #endif
 // Per-splat sums of the warp reduction, through shared memory (LOBE_BWD_SLOTS, default on):
 // each lane writes its nine values for a splat into a row of the warp's next slot; after

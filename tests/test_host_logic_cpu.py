@@ -27,3 +27,35 @@ def test_autotune_configuration_names():
     assert set(batched.BATCH_OPTIONS) == {32, 64}
     for tile, pxs in batched.PX_OPTIONS.items():
         assert tile in batched.TILES and len(pxs) >= 2
+
+
+def test_traffic_files_track_their_kernel_sources(tmp_path, monkeypatch):
+    """bench.py quotes a stage's DRAM traffic only while the kernel sources it was captured
+    from are unchanged: every committed traffic file names its sources, and a changed source
+    makes traffic_of return None."""
+    import importlib.util
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    prof = os.path.join(root, "profiles")
+    names = [f for f in os.listdir(prof) if f.startswith("traffic_") and f.endswith(".json")]
+    assert names
+    for f in names:
+        t = json.load(open(os.path.join(prof, f)))
+        assert t["sources"] and all(os.path.exists(os.path.join(root, p)) for p in t["sources"]), f
+        assert len(t["source_sha1"]) == 16 and t["bytes_per_launch"] > 0, f
+    # a copy of the tree with one source edited: the same file reads as stale
+    fake = tmp_path / "repo"
+    (fake / "profiles").mkdir(parents=True)
+    src = fake / "k.cu"
+    src.write_text("kernel A")
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    rec = {"bytes_per_launch": 123, "sources": ["k.cu"], "source_sha1": bench.source_digest(["k.cu"])}
+    (fake / "profiles" / "traffic_render_bwd_w.json").write_text(json.dumps(rec))
+    assert bench.traffic_of("render_bwd", "w")["bytes_per_launch"] == 123
+    src.write_text("kernel B")
+    assert bench.traffic_of("render_bwd", "w") is None
+    assert bench.traffic_of("render_fwd", "w") is None  # absent
