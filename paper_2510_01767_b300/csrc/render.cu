@@ -290,6 +290,20 @@ __device__ __forceinline__ void forward_sweep(const float4 *__restrict__ splat, 
                     float ta, tb;
                     upk(mul2(T2, sub2(pk(1.0f, 1.0f), pk(aa, ab))), ta, tb);  // next_T of both pixels
                     const bool sa = ua && ta < T_MIN, sb = ub && tb < T_MIN;
+                    if (!__any_sync(0xffffffffu, sa || sb)) {
+                        // no pixel of the warp stops here (the common case: a pixel stops once):
+                        // an unused pixel has alpha 0, so T (1 - 0) = T and its weight is 0 exactly
+                        const f2 w2 = mul2(pk(aa, ab), T2);
+                        upk(fma2(pk(q1.z, q1.z), w2, pk(C0[k], C0[k + 1])), C0[k], C0[k + 1]);
+                        upk(fma2(pk(q1.w, q1.w), w2, pk(C1[k], C1[k + 1])), C1[k], C1[k + 1]);
+                        upk(fma2(pk(cb, cb), w2, pk(C2[k], C2[k + 1])), C2[k], C2[k + 1]);
+                        if (DEPTH) upk(fma2(pk(dj, dj), w2, pk(D[k], D[k + 1])), D[k], D[k + 1]);
+                        T[k] = ta;
+                        T[k + 1] = tb;
+                        last[k] = ua ? base - start + j + 1 : last[k];
+                        last[k + 1] = ub ? base - start + j + 1 : last[k + 1];
+                        continue;
+                    }
                     const bool wa = ua && !sa, wb = ub && !sb;
                     live[k] = live[k] && !sa;
                     live[k + 1] = live[k + 1] && !sb;
