@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -465,13 +466,18 @@ def stage_table(stage_ms, work, hbm_peak, fp32_peak):
     return stages, names[int(np.argmax(mean_ms))]
 
 
+_COMMENT = re.compile(r"//[^\n]*|/\*.*?\*/", re.S)
+
+
 def source_digest(paths):
-    """sha1 (16 hex digits) of the given package source files, in order: the traffic files
-    record it for the kernels they were captured from."""
+    """sha1 (16 hex digits) of the code of the given package source files, in order, with
+    comments and whitespace removed (an edit of a comment does not change a kernel): the
+    traffic files record it for the kernels they were captured from."""
     h = hashlib.sha1()
     for rel in paths:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            code = _COMMENT.sub(" ", f.read())
+        h.update("".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

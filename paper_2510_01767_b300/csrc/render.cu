@@ -18,14 +18,16 @@
 // or re-derived by a forward sweep inside the kernel ("recompute").
 //
 // Work decomposition (B300): one warp walks one slab of a tile -- 32 lanes x PX pixels,
-// each lane owning PX pixels of one column -- through the tile's list in batches of 32
-// splats staged in warp-private shared memory (the next batch is prefetched into registers
-// while the current one is composited). Per splat a lane loads the splat once and applies
-// it to its PX pixels, sharing the column terms of the exponent. The adjoint sums each
-// splat's 9 gradient values over the lane's pixels in registers, then over the warp with a
-// reduce-scatter butterfly that leaves each total in its own lane, and nine lanes add them to
-// global memory in one instruction: one update per splat per warp (128 pixels) instead of one
-// per pixel. Warps need no block barriers.
+// each lane owning PX pixels of one column -- through the tile's list in batches of 32 (or
+// 64) splats staged in warp-private shared memory (the next batch is prefetched into
+// registers while the current one is composited). Per splat a lane loads the splat once and
+// applies it to its PX pixels, sharing the column terms of the exponent. The adjoint sums
+// each splat's 9 gradient values over the lane's pixels in registers, then over the warp --
+// through rows of a shared-memory slot summed column by column (the paired kernel), or a
+// reduce-scatter butterfly of shuffles (one pixel a lane) -- so that one update per splat and
+// warp (up to 256 pixels) reaches global memory instead of one per pixel; splats that only a
+// few lanes reach skip the warp sum and those lanes add their own values. Warps need no block
+// barriers.
 #include <map>
 #include <mutex>
 

@@ -56,6 +56,8 @@ def test_traffic_files_track_their_kernel_sources(tmp_path, monkeypatch):
     rec = {"bytes_per_launch": 123, "sources": ["k.cu"], "source_sha1": bench.source_digest(["k.cu"])}
     (fake / "profiles" / "traffic_render_bwd_w.json").write_text(json.dumps(rec))
     assert bench.traffic_of("render_bwd", "w")["bytes_per_launch"] == 123
+    src.write_text("kernel A // a comment\n/* and another */")  # comments do not change the code
+    assert bench.traffic_of("render_bwd", "w")["bytes_per_launch"] == 123
     src.write_text("kernel B")
     assert bench.traffic_of("render_bwd", "w") is None
     assert bench.traffic_of("render_fwd", "w") is None  # absent
