@@ -70,7 +70,7 @@ def test_project_matches_oracle(small, posed):
     check_projection_admissible(p, rad, s, proj.tiles.cpu().numpy(), cam, wl.tile)
 
 
-def check_projection_admissible(p, rad, s, tiles, cam, tile):
+def check_projection_admissible(p, rad, s, tiles, cam, tile, min_visible=500):
     """Radius, culling and tile count of every Gaussian: the oracle's, or (where its radius,
     rectangle or guard decision is marginal) a radius within one of it or culled; the splat
     values of every Gaussian the GPU keeps; the tile count of the GPU's own exact rectangle."""
@@ -79,7 +79,7 @@ def check_projection_admissible(p, rad, s, tiles, cam, tile):
     alt_ok = (rad == p.radius) | (rad == 0) | (np.abs(rad - p.radius_all) <= 1)
     assert np.all(alt_ok[marg]), "a marginal Gaussian's radius is outside the admissible set"
     vis = rad > 0
-    assert vis.sum() > 500
+    assert vis.sum() > min_visible
     np.testing.assert_allclose(s[vis, 0:2], p.mean2d[vis], rtol=1e-5, atol=2e-4)
     np.testing.assert_allclose(s[vis, 2:5], p.conic[vis], rtol=2e-4, atol=1e-7)
     np.testing.assert_allclose(s[vis, 5], p.opacity[vis], rtol=1e-5, atol=1e-7)
@@ -90,6 +90,38 @@ def check_projection_admissible(p, rad, s, tiles, cam, tile):
     ok = ~marg
     np.testing.assert_array_equal(tiles[ok], np.where(p.radius[ok] > 0, (p.rect[ok, 2] - p.rect[ok, 0]) *
                                                       (p.rect[ok, 3] - p.rect[ok, 1]), 0))
+
+
+def test_project_multi_set_matches_oracle():
+    """A batch of three sets whose sizes are not multiples of 32 (so warps span two sets and
+    take the per-thread copies of their SH rows), one of them visibility-cropped, each seen by
+    one or two views: every item's projection matches the oracle's as in the single-set case."""
+    rng = np.random.default_rng(17)
+    sets = [scenes.uniform_gaussians(rng, n, 1.0, 2.0, 6.0) for n in (1001, 777, 1500)]
+    cams = [scenes.pinhole(128, 128, 128.0, cx=64.0, cy=64.0),
+            scenes.pinhole(128, 128, 128.0, cx=64.0, cy=64.0,
+                           viewmat=scenes.look_at((0.6, -0.4, -0.3), (0.0, 0.0, 4.0), up=(0, -1, 0)))]
+    items = [(0, 0, -1), (0, 1, -1), (1, 0, -1), (2, 1, -1), (2, 0, -1)]
+    crop = (rng.random(1500) < 0.6).astype(np.uint8)  # set 2: 40% cropped away
+    wl = scenes.Workload("multi_set", sets, cams, [], items, (16, 16))
+    gsets = [lobe.GaussianSet.from_numpy(x) for x in sets]
+    gsets[2].crop_mask = dev(crop, torch.uint8)
+    batch = lobe.Batch(gsets, wl.cameras, items, [])
+    ctx = ctx_for(wl)
+    proj = lobe.project(ctx, batch)
+    torch.cuda.synchronize()
+    rad_all = proj.radius.cpu().numpy()
+    s_all = proj.splat.cpu().numpy().astype(np.float64)
+    t_all = proj.tiles.cpu().numpy()
+    for i, (si, ci, _) in enumerate(items):
+        cam = cams[ci].as_dict()
+        p = oracle.project(oracle.set_dict(sets[si]), cam, wl.tile, crop=crop if si == 2 else None,
+                           margins=oracle.MARGINS_E2E)
+        e0, n = batch.entry_off[i], sets[si].n
+        rad, s, t = rad_all[e0:e0 + n], s_all[e0:e0 + n], t_all[e0:e0 + n]
+        if si == 2:
+            assert np.all(rad[crop == 0] == 0) and np.all(t[crop == 0] == 0)
+        check_projection_admissible(p, rad, s, t, cam, wl.tile, min_visible=400)
 
 
 @pytest.mark.parametrize("deg", [0, 1, 2])
