@@ -161,22 +161,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_count(const uint32_t *__re
     long long lo, hi;
     chunk_of(*n_dev, blockIdx.x, gridDim.x, lo, hi);
     const uint32_t mask = (1u << nbits) - 1u;
-    for (long long base = lo + warp * 32; base < hi; base += RS_THREADS * 4) {
-        uint32_t k[4];
+    // counts only (no ranks): one shared-memory atomic a key into the warp's own histogram,
+    // eight independent loads a thread in flight
+    for (long long base = lo + warp * 32; base < hi; base += RS_THREADS * 8) {
+        uint32_t k[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            long long i = base + j * RS_THREADS + lane;
+        for (int j = 0; j < 8; ++j) {
+            const long long i = base + j * RS_THREADS + lane;
             k[j] = i < hi ? keys[i] : 0u;
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            long long i = base + j * RS_THREADS + lane;
-            unsigned valid = __ballot_sync(0xffffffffu, i < hi);
-            uint32_t d = (k[j] >> shift) & mask;
-            unsigned peers = warp_peers(d, nbits, valid);
-            if (i < hi && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
-            __syncwarp();
-        }
+        for (int j = 0; j < 8; ++j)
+            if (base + j * RS_THREADS + lane < hi) atomicAdd(&h[warp][(k[j] >> shift) & mask], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < DIG; d += RS_THREADS) {
