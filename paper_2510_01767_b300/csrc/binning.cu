@@ -393,9 +393,14 @@ __global__ void __launch_bounds__(256) k_clear_on_overflow(const uint32_t *n_use
 
 // ------------------------------------------------------------------ orchestration
 
+// Grid of the persistent chunk kernels: 16 blocks for every SM of the current device (two
+// rounds of the 8 resident 256-thread blocks an SM holds), or fewer for fewer work items.
 static unsigned persistent_grid(long long work_max)
 {
-    const long long cap = 148LL * 16;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    const long long cap = (long long)sms * 16;
     return (unsigned)(work_max < 1 ? 1 : (work_max < cap ? work_max : cap));
 }
 

@@ -993,7 +993,11 @@ cudaError_t launch_tile_order(const int *ts, int n_tiles, int *order, unsigned *
 {
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * ORDER_CTL, st);
     if (e != cudaSuccess || n_tiles == 0) return e;
-    const unsigned blocks = (unsigned)((n_tiles + 255) / 256 < 2 * 148 ? (n_tiles + 255) / 256 : 2 * 148);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    const unsigned cap = 2u * (unsigned)sms;  // two 256-thread blocks an SM: a grid-stride pass over the tiles
+    const unsigned blocks = (unsigned)(n_tiles + 255) / 256 < cap ? (unsigned)(n_tiles + 255) / 256 : cap;
     count_launch(2);
     launch_pdl(k_order_count, dim3(blocks), dim3(256), 0, st, ts, n_tiles, ctl);
     launch_pdl(k_order_place, dim3(blocks), dim3(256), 0, st, ts, n_tiles, ctl, order);

@@ -18,6 +18,8 @@ if torch.cuda.is_available():
     from paper_2510_01767_b300.losses import l1_ssim_loss
 
 KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+# GPU against GPU on the same inputs, the same terms summed in another float32 order
+ORDER_RTOL = 5e-4
 
 
 def params_of(gs, requires_grad=True):
@@ -59,7 +61,7 @@ def test_autograd_matches_oracle_finite_differences_64():
 def test_store_and_recompute_backward_agree():
     wl = scenes.small_scene()
     cam = wl.cameras[0].as_dict()
-    dL = torch.randn(3, 128, 128, device="cuda")
+    dL = torch.randn(3, 128, 128, device="cuda", generator=torch.Generator(device="cuda").manual_seed(11))
     grads = []
     for rec in (False, True):
         raster = lobe.Rasterizer(1000, tile=wl.tile, recompute_T=rec)
@@ -67,18 +69,19 @@ def test_store_and_recompute_backward_agree():
         img = lobe.rasterize(*ps, cam, raster)
         (img * dL).sum().backward()
         grads.append([p.grad.cpu().numpy() for p in ps])
-    # the two runs differ only by the order of the float32 atomic additions of the per-splat 2D
-    # gradients (a few ulps of sums over up to thousands of pixels); relative to the 1e-3 floor
-    # of the smallest elements that reaches ~1e-4, so allow 3e-4 (a third of the parity bar)
+    # the two runs differ only by the order of the float32 additions of the same terms (the
+    # per-splat atomics over pixels); relative to the 1e-3 floor of the smallest elements that
+    # reaches ~1e-4, and the quaternion gradient's normalisation (dq - q (q . dq)) subtracts
+    # nearly equal terms, so allow ORDER_RTOL = 5e-4 (half the 1e-3 gradient parity bar)
     for a, b, k in zip(grads[0], grads[1], KEYS):
-        assert grad_rel_err(a, b) <= 3e-4, k
+        assert grad_rel_err(a, b) <= ORDER_RTOL, k
 
 
 def test_multi_view_gradient_is_sum_of_single_views():
     wl = scenes.small_scene(n=500)
     c0 = wl.cameras[0].as_dict()
     cams = [c0, dict(c0, viewmat=scenes.look_at((0.4, -0.3, -0.2), (0.0, 0.0, 4.0), up=(0, -1, 0)))]
-    dL = torch.randn(2, 3, 128, 128, device="cuda")
+    dL = torch.randn(2, 3, 128, 128, device="cuda", generator=torch.Generator(device="cuda").manual_seed(12))
     raster = lobe.Rasterizer(500, tile=wl.tile)
     ps = params_of(wl.sets[0])
     (lobe.rasterize(*ps, cams, raster) * dL).sum().backward()
@@ -89,8 +92,8 @@ def test_multi_view_gradient_is_sum_of_single_views():
         (lobe.rasterize(*qs, c, lobe.Rasterizer(500, tile=wl.tile)) * dL[i]).sum().backward()
         for a, q in zip(acc, qs):
             a += q.grad
-    for a, b, k in zip(both, acc, KEYS):  # float32 atomic order, as in the store/recompute test
-        assert grad_rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 3e-4, k
+    for a, b, k in zip(both, acc, KEYS):  # float32 summation order, as in the store/recompute test
+        assert grad_rel_err(a.cpu().numpy(), b.cpu().numpy()) <= ORDER_RTOL, k
 
 
 def test_sd_statistics_only_inside_block():
