@@ -30,8 +30,8 @@
  *  - Errors found on the device (intersection count above capacity) are latched in a
  *    device status word; lobe_get_status() reads and clears it.
  *  - All floating-point data is float32, little-endian, C-contiguous.
- *  - The calls are safe to capture in a CUDA graph when no host output pointer is passed
- *    and lobe_ctx_reserve() was called beforehand.
+ *  - The calls that take a context are safe to capture in a CUDA graph when no host
+ *    output pointer is passed and lobe_ctx_reserve() was called beforehand.
  *  - A context is not thread safe; use one context per host thread.
  */
 #ifndef LOBE_H
@@ -270,8 +270,8 @@ lobe_status lobe_bin_sort(lobe_ctx *ctx, const lobe_batch *batch, const lobe_pro
  * in *n_isect_host (nullable); more pairs than bins->capacity gives LOBE_ERR_CAPACITY and
  * bins describing empty tiles.
  * The first call on a device (and the first after that device's context was destroyed and
- * created again) looks up the array's device address (and may load the library's kernels);
- * make that first call before any stream capture. All calls share the one array: calls
+ * created again) looks up the array's device address (and may load the library's kernels).
+ * All calls share the one array: calls
  * whose work overlaps on the GPU (other threads, other streams) race and must be serialised
  * by the caller. At each of its two synchronisations the call also reads the status word
  * that the kernels latch in the array (cleared at the start of every call):
