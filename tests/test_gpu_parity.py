@@ -208,6 +208,79 @@ def test_bin_sort_bit_exact_multi_item_large_tile_count():
     np.testing.assert_array_equal(bins.tile_start.cpu().numpy(), np.concatenate(want_ts))
 
 
+def test_bin_sort_and_composite_at_the_batch_limits():
+    """The largest batch one call takes: 16 views of 4096x4096 with 8x8 tiles, i.e. 2^22 tiles
+    (the length of the tile scan) in 2^16 blocks of 64x64 pixels (the 16 bits of a super-tile
+    id). Stage inputs (the oracle's float32 splats of 800 Gaussians a view): every item's lists
+    bit-exact against the oracle's, and on four 32x32 windows of every view (one around its
+    longest list) every pixel of the composite matches an admissible result. One more block is
+    an argument error, with nothing enqueued: the context then bins the limit batch again."""
+    rng = np.random.default_rng(21)
+    g = scenes.uniform_gaussians(rng, 800, 1.0, 2.0, 6.0)
+    cams = [scenes.pinhole(4096, 4096, 2600.0 + 120.0 * i) for i in range(16)]
+    tile = (8, 8)
+    wl = scenes.Workload("limits", [g], cams, [scenes.AABB()], [(0, i, 0) for i in range(16)], tile)
+    ctx = ctx_for(wl)
+    batch = make_batch(wl)
+    n_tiles, toffs = batch.tiles(tile)
+    assert n_tiles == 1 << 22
+    gd = oracle.set_dict(g)
+    parts, ids_view, ts_view, want_ids, want_ts = [], [], [], [], []
+    total = 0
+    for i, cam in enumerate(cams):
+        p = oracle.project(gd, cam.as_dict(), tile).rounded()
+        ids, ts = oracle.bin_sort(p, cam.as_dict(), tile)
+        parts.append(p)
+        ids_view.append(ids)
+        ts_view.append(ts)
+        want_ids.append(ids + i * g.n)
+        want_ts.append(ts[:-1] + total)
+        total += len(ids)
+    want_ts.append(np.array([total]))
+    splat = np.concatenate([splat_array(p) for p in parts])
+    rad = np.concatenate([p.radius for p in parts])
+    tl = np.concatenate([rect_tiles(p.mean2d, p.radius, c, tile) for p, c in zip(parts, cams)])
+    gp = lobe.Projection(dev(splat), dev(rad, torch.int32), dev(tl, torch.int32))
+    bins = lobe.bin_sort(ctx, batch, gp)
+    assert bins.count == total
+    np.testing.assert_array_equal(bins.ids().cpu().numpy(), np.concatenate(want_ids))
+    np.testing.assert_array_equal(bins.tile_start.cpu().numpy(), np.concatenate(want_ts))
+    out = lobe.render_fwd(ctx, batch, gp, bins)
+    rgbs = batch.image_views(out.rgb)
+    Ts = batch.image_views(out.T_final, channels=1)
+    ncs = batch.image_views(out.n_contrib, channels=1)
+    win_rng = np.random.default_rng(22)
+    for i, cam in enumerate(cams):
+        c = cam.as_dict()
+        gx = -(-c["width"] // tile[0])
+        t = int(np.argmax(np.diff(ts_view[i])))
+        starts = [((t % gx) * tile[0] // 32 * 32, (t // gx) * tile[1] // 32 * 32)]
+        starts += [(int(x) * 32, int(y) * 32) for x, y in win_rng.integers(0, 4096 // 32, (3, 2))]
+        eb = oracle.ExtBins(ids_view[i], np.zeros(len(ids_view[i]), np.uint8), ts_view[i])
+        rgb = rgbs[i].view(3, 4096, 4096)
+        T = Ts[i].view(4096, 4096)
+        nc = ncs[i].view(4096, 4096)
+        for x0, y0 in starts:
+            w = (x0, y0, x0 + 32, y0 + 32)
+            lv = oracle.render_leaves(parts[i], eb, c, tile, margins=oracle.MARGINS_STAGE, win=w, certain=True)
+            match_image(lv, rgb[:, y0:y0 + 32, x0:x0 + 32].cpu().numpy(), T[y0:y0 + 32, x0:x0 + 32].cpu().numpy(),
+                        nc[y0:y0 + 32, x0:x0 + 32].cpu().numpy(), f"image view {i} at the batch limits (stage)")
+    # one more 64x64-pixel block: rejected before anything is enqueued
+    cams2 = cams + [scenes.pinhole(64, 64, 64.0)]
+    wl2 = scenes.Workload("limits+1", [g], cams2, [scenes.AABB()], [(0, i, 0) for i in range(17)], tile)
+    batch2 = make_batch(wl2)
+    p17 = oracle.project(gd, cams2[16].as_dict(), tile).rounded()
+    gp2 = lobe.Projection(dev(np.concatenate([splat, splat_array(p17)])),
+                          dev(np.concatenate([rad, p17.radius]), torch.int32),
+                          dev(np.concatenate([tl, rect_tiles(p17.mean2d, p17.radius, cams2[16], tile)]), torch.int32))
+    with pytest.raises(lobe._abi.LobeError) as e:
+        lobe.bin_sort(ctx, batch2, gp2)
+    assert e.value.code == lobe._abi.ERR_ARG
+    again = lobe.bin_sort(ctx, batch, gp)
+    assert again.count == total
+    np.testing.assert_array_equal(again.tile_start.cpu().numpy(), np.concatenate(want_ts))
+
+
 # ----------------------------------------------------------------------------- render
 
 def stage_inputs(wl, g, cam):
