@@ -64,7 +64,8 @@ typedef struct lobe_ctx lobe_ctx;
  * Parameterisation (Sec. 3.2 "opacity determined by covariance and opacity"): log-scales,
  * a quaternion (w,x,y,z) that need not be normalised, an opacity logit and real SH
  * coefficients (band-major, DC first, 16 x RGB). crop_mask (nullable) is the visibility
- * crop of Sec. 3.3: a Gaussian with crop_mask[g] == 0 is culled. */
+ * crop of Sec. 3.3: a Gaussian with crop_mask[g] == 0 is culled. Every value must be finite
+ * and every quaternion nonzero; other inputs give unspecified splats for those Gaussians. */
 typedef struct {
     const float *means;          /* [n][3] */
     const float *log_scales;     /* [n][3] */
