@@ -212,9 +212,10 @@ def test_bin_sort_and_composite_at_the_batch_limits():
     """The largest batch one call takes: 16 views of 4096x4096 with 8x8 tiles, i.e. 2^22 tiles
     (the length of the tile scan) in 2^16 blocks of 64x64 pixels (the 16 bits of a super-tile
     id). Stage inputs (the oracle's float32 splats of 800 Gaussians a view): every item's lists
-    bit-exact against the oracle's, and on four 32x32 windows of every view (one around its
-    longest list) every pixel of the composite matches an admissible result. One more block is
-    an argument error, with nothing enqueued: the context then bins the limit batch again."""
+    bit-exact against the oracle's; on four 32x32 windows of every view (one around its
+    longest list) every pixel of the composite matches an admissible result; the adjoint of a
+    loss on the windows of the first and the last view in the oracle's envelope. One more block
+    is an argument error, with nothing enqueued: the context then bins the limit batch again."""
     rng = np.random.default_rng(21)
     g = scenes.uniform_gaussians(rng, 800, 1.0, 2.0, 6.0)
     cams = [scenes.pinhole(4096, 4096, 2600.0 + 120.0 * i) for i in range(16)]
@@ -250,21 +251,55 @@ def test_bin_sort_and_composite_at_the_batch_limits():
     Ts = batch.image_views(out.T_final, channels=1)
     ncs = batch.image_views(out.n_contrib, channels=1)
     win_rng = np.random.default_rng(22)
+    ebs, wins, adms = [], [], []
     for i, cam in enumerate(cams):
         c = cam.as_dict()
         gx = -(-c["width"] // tile[0])
         t = int(np.argmax(np.diff(ts_view[i])))
         starts = [((t % gx) * tile[0] // 32 * 32, (t // gx) * tile[1] // 32 * 32)]
-        starts += [(int(x) * 32, int(y) * 32) for x, y in win_rng.integers(0, 4096 // 32, (3, 2))]
+        while len(starts) < 4:  # disjoint 32x32 windows on a 32-pixel grid
+            x, y = (int(v) * 32 for v in win_rng.integers(0, 4096 // 32, 2))
+            if (x, y) not in starts:
+                starts.append((x, y))
         eb = oracle.ExtBins(ids_view[i], np.zeros(len(ids_view[i]), np.uint8), ts_view[i])
         rgb = rgbs[i].view(3, 4096, 4096)
         T = Ts[i].view(4096, 4096)
         nc = ncs[i].view(4096, 4096)
-        for x0, y0 in starts:
-            w = (x0, y0, x0 + 32, y0 + 32)
+        ebs.append(eb)
+        wins.append([(x0, y0, x0 + 32, y0 + 32) for x0, y0 in starts])
+        adms.append([])
+        for w in wins[i]:
+            x0, y0, x1, y1 = w
             lv = oracle.render_leaves(parts[i], eb, c, tile, margins=oracle.MARGINS_STAGE, win=w, certain=True)
-            match_image(lv, rgb[:, y0:y0 + 32, x0:x0 + 32].cpu().numpy(), T[y0:y0 + 32, x0:x0 + 32].cpu().numpy(),
-                        nc[y0:y0 + 32, x0:x0 + 32].cpu().numpy(), f"image view {i} at the batch limits (stage)")
+            adms[i].append(match_image(lv, rgb[:, y0:y1, x0:x1].cpu().numpy(), T[y0:y1, x0:x1].cpu().numpy(),
+                                       nc[y0:y1, x0:x1].cpu().numpy(), f"image view {i} at the batch limits (stage)"))
+    # the adjoint with dL/dC nonzero on the windows of the first and the last view only: their
+    # splats' 2D gradients in the oracle's envelope, every other entry's exactly zero
+    dL = torch.zeros(3 * batch.n_pixels, dtype=torch.float32, device="cuda")
+    dls = batch.image_views(dL)
+    dl_rng = np.random.default_rng(23)
+    dl64 = {}
+    for i in (0, 15):
+        d = np.zeros((3, 4096, 4096), np.float32)
+        for x0, y0, x1, y1 in wins[i]:
+            d[:, y0:y1, x0:x1] = dl_rng.standard_normal((3, y1 - y0, x1 - x0))
+        dls[i].copy_(torch.as_tensor(d).reshape(dls[i].shape))
+        dl64[i] = d.astype(np.float64)
+    g2d = lobe.render_bwd(ctx, batch, gp, bins, out, dL).cpu().numpy()
+    for i in (0, 15):
+        lo = np.zeros((g.n, 12))
+        hi = np.zeros((g.n, 12))
+        for w, adm in zip(wins[i], adms[i]):
+            l, h, _ = oracle.render_bwd_envelope(parts[i], ebs[i], cams[i].as_dict(), dl64[i], adm, tile,
+                                                 margins=oracle.MARGINS_STAGE, win=w, certain=True)
+            lo += l
+            hi += h
+        rows = g2d[i * g.n:(i + 1) * g.n]
+        vis = parts[i].radius > 0
+        for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                           ("color", slice(6, 9))]:
+            assert_envelope(rows[vis, cols], lo[vis, cols], hi[vis, cols], f"grad2d {name} view {i} at the batch limits")
+    assert np.all(g2d[g.n:15 * g.n] == 0)
     # one more 64x64-pixel block: rejected before anything is enqueued
     cams2 = cams + [scenes.pinhole(64, 64, 64.0)]
     wl2 = scenes.Workload("limits+1", [g], cams2, [scenes.AABB()], [(0, i, 0) for i in range(17)], tile)
