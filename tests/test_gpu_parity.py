@@ -650,6 +650,70 @@ def test_crop_mask_culls():
 
 # ----------------------------------------------------------------------------- edge cases
 
+@pytest.mark.parametrize("tile, px, persistent", [((16, 16), 0, False), ((16, 8), 4, True), ((32, 16), 8, False),
+                                                  ((8, 8), 1, True)])
+def test_views_smaller_than_a_tile(tile, px, persistent):
+    """One batch of views smaller than a tile, or one pixel wide or high (1x1, 3x2, 15x9, 17x1,
+    1x33, 40x7), every one with deep lists (300 Gaussians of about two pixels): lists bit-exact,
+    every pixel of every view's composite, and the adjoint's 2D gradients against the oracle
+    (stage inputs)."""
+    rng = np.random.default_rng(31)
+    g = scenes.uniform_gaussians(rng, 300, 1.0, 2.0, 6.0)
+    sizes = [(1, 1), (3, 2), (15, 9), (17, 1), (1, 33), (40, 7)]
+    cams = [scenes.pinhole(w, h, float(w), float(h)) for w, h in sizes]  # a field of view of about 53 degrees
+    bg = (0.1, 0.2, 0.3)
+    wl = scenes.Workload("tiny", [g], cams, [scenes.AABB()], [(0, i, 0) for i in range(len(cams))], tile)
+    ctx = ctx_for(wl, bg=bg, px_fwd=px, px_bwd=px, persistent=persistent)
+    batch = make_batch(wl)
+    gd = oracle.set_dict(g)
+    parts, ebs, want_ids, want_ts = [], [], [], []
+    total = 0
+    for i, cam in enumerate(cams):
+        p = oracle.project(gd, cam.as_dict(), tile).rounded()
+        ids, ts = oracle.bin_sort(p, cam.as_dict(), tile)
+        parts.append(p)
+        ebs.append(oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts))
+        want_ids.append(ids + i * g.n)
+        want_ts.append(ts[:-1] + total)
+        total += len(ids)
+    want_ts.append(np.array([total]))
+    assert min(np.diff(eb.tile_start).max() for eb in ebs) >= 20  # every view has a deep list
+    gp = lobe.Projection(dev(np.concatenate([splat_array(p) for p in parts])),
+                         dev(np.concatenate([p.radius for p in parts]), torch.int32),
+                         dev(np.concatenate([rect_tiles(p.mean2d, p.radius, c, tile) for p, c in zip(parts, cams)]),
+                             torch.int32))
+    bins = lobe.bin_sort(ctx, batch, gp)
+    assert bins.count == total
+    np.testing.assert_array_equal(bins.ids().cpu().numpy(), np.concatenate(want_ids))
+    np.testing.assert_array_equal(bins.tile_start.cpu().numpy(), np.concatenate(want_ts))
+    out = lobe.render_fwd(ctx, batch, gp, bins)
+    rgbs, Ts = batch.image_views(out.rgb), batch.image_views(out.T_final, channels=1)
+    ncs = batch.image_views(out.n_contrib, channels=1)
+    dl_rng = np.random.default_rng(32)
+    dL = torch.zeros(3 * batch.n_pixels, dtype=torch.float32, device="cuda")
+    dls, dl64, adms = batch.image_views(dL), [], []
+    for i, cam in enumerate(cams):
+        c = cam.as_dict()
+        lv = oracle.render_leaves(parts[i], ebs[i], c, tile, bg, oracle.MARGINS_STAGE, certain=True)
+        adms.append(match_image(lv, rgbs[i].cpu().numpy(), Ts[i].cpu().numpy(), ncs[i].cpu().numpy(),
+                                f"image {c['width']}x{c['height']} (stage, tile {tile[0]}x{tile[1]})"))
+        d = dl_rng.standard_normal((3, c["height"], c["width"])).astype(np.float32)
+        dls[i].copy_(torch.as_tensor(d))
+        dl64.append(d.astype(np.float64))
+    g2d = lobe.render_bwd(ctx, batch, gp, bins, out, dL).cpu().numpy()
+    for i, cam in enumerate(cams):
+        c = cam.as_dict()
+        lo, hi, _ = oracle.render_bwd_envelope(parts[i], ebs[i], c, dl64[i], adms[i], tile, bg, oracle.MARGINS_STAGE,
+                                               certain=True)
+        rows = g2d[i * g.n:(i + 1) * g.n]
+        vis = parts[i].radius > 0
+        for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                           ("color", slice(6, 9))]:
+            assert_envelope(rows[vis, cols], lo[vis, cols], hi[vis, cols],
+                            f"grad2d {name} {c['width']}x{c['height']} (stage, tile {tile[0]}x{tile[1]})")
+        assert np.all(rows[:, 9:] == 0)
+
+
 def test_empty_set_and_all_culled():
     empty = scenes.uniform_gaussians(np.random.default_rng(0), 0, 1.0, 2.0, 6.0)
     behind = scenes.uniform_gaussians(np.random.default_rng(1), 200, 1.0, -6.0, -2.0)
