@@ -85,6 +85,46 @@ def test_graph_follows_parameter_updates(workload):
     torch.testing.assert_close(st.image.rgb, eager.image.rgb, rtol=0, atol=0)
 
 
+def test_graph_replay_past_its_pair_capacity(workload):
+    """Gaussians that grow after capture (every scale e times larger) need more (splat, tile)
+    pairs than the captured step reserved: the replay latches LOBE_ERR_CAPACITY, its bins then
+    describe empty tiles (every pixel the background, T = 1, no 2D gradient), the context stays
+    usable, and a step built for the grown Gaussians matches the eager path again."""
+    wl = workload
+    sets = [lobe.GaussianSet.from_numpy(s) for s in wl.sets]
+    cams = [c.as_dict() for c in wl.cameras]
+    bg = (0.25, 0.5, 0.75)
+    st = BatchedStep(sets, cams, wl.items, wl.blocks, tile=(16, 16), bg=bg, slack=1.0).capture()
+    fill_dL(st)
+    st.replay()
+    st.stream.synchronize()
+    st.ctx.status()  # within capacity
+    with torch.no_grad():
+        for s in sets:
+            s.log_scales += 1.0
+    st.replay()
+    st.stream.synchronize()
+    with pytest.raises(lobe._abi.LobeError) as e:
+        st.ctx.status()
+    assert e.value.code == lobe._abi.ERR_CAPACITY
+    assert int(st.bins.tile_start.abs().max().item()) == 0
+    for v in st.images():
+        for ch in range(3):
+            assert torch.all(v[ch] == bg[ch])
+    assert torch.all(st.image.T_final == 1.0)
+    assert torch.all(st.grad2d == 0)
+    st.ctx.status()  # read and cleared
+    grown = BatchedStep(sets, cams, wl.items, wl.blocks, tile=(16, 16), bg=bg).capture()
+    assert grown.n_isect > st.bins.capacity
+    grown.replay()
+    grown.stream.synchronize()
+    grown.ctx.status()
+    eager = BatchedStep(sets, cams, wl.items, wl.blocks, tile=(16, 16), bg=bg)
+    eager.run()
+    eager.stream.synchronize()
+    torch.testing.assert_close(grown.image.rgb, eager.image.rgb, rtol=0, atol=0)
+
+
 @pytest.mark.parametrize("tile", [(8, 8), (16, 8), (32, 16)])
 def test_batched_other_tiles_match_16(workload, tile):
     wl = workload
