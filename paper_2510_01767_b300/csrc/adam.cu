@@ -9,6 +9,7 @@
 // floats of a Gaussian's 48 are its degree-0 band). In the sparse modes a chunk none of whose
 // rows is selected is skipped without touching its parameters.
 
+#include <atomic>
 #include "lobe_internal.cuh"
 
 namespace lobe {
@@ -119,20 +120,19 @@ cudaError_t launch_adam(long long n, const AdamSet &s, const float *const grad[5
     void (*kern)(AdamArrays, const uint8_t *, AdamK) = mode == 0 ? k_adam<0> : mode == 1 ? k_adam<1> : k_adam<2>;
     // one wave of resident blocks (grid-stride), or fewer when the set is small; the
     // largest array (SH, 12 chunks a row) sets the size
-    static int sms = 0, resident[3] = {0, 0, 0};
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    if (resident[mode] == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, AD_THREADS, 0) != cudaSuccess || b <= 0) b = 1;
-        resident[mode] = b;
+    // (the occupancy is a property of the kernel, looked up once; host threads with their own
+    // contexts may get here at the same time, hence the atomic)
+    static std::atomic<int> resident[3] = {0, 0, 0};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    int res = resident[mode].load(std::memory_order_relaxed);
+    if (res == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, kern, AD_THREADS, 0) != cudaSuccess || res <= 0) res = 1;
+        resident[mode].store(res, std::memory_order_relaxed);
     }
     long long blocks = (12 * n + AD_THREADS - 1) / AD_THREADS;
-    const long long cap = (long long)sms * resident[mode];
+    const long long cap = (long long)sms * res;
     if (blocks > cap) blocks = cap;
     count_launch(1);
     launch_pdl(kern, dim3((unsigned)blocks), dim3(AD_THREADS), 0, st, X, rows, k);

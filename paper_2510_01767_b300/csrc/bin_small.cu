@@ -12,6 +12,7 @@
 //   6. per tile again, the covering splats' ids are written in order (ranks from the ballots).
 // A pair count above the bins' capacity latches the capacity status, stores the count and
 // leaves every tile empty, as the general path does.
+#include <atomic>
 #include "lookback.cuh"
 
 namespace lobe {
@@ -163,12 +164,14 @@ cudaError_t launch_bin_small(const BatchParams &P, const float *splat, const int
                              int *gauss_ids, int *tile_start, long long *n_isect, long long capacity, int *status,
                              cudaStream_t st)
 {
-    static bool configured = false;
-    if (!configured) {
+    // the kernel's shared-memory limit, raised once per process (idempotent: host threads with
+    // their own contexts may both get here first)
+    static std::atomic<bool> configured{false};
+    if (!configured.load(std::memory_order_acquire)) {
         const cudaError_t e = cudaFuncSetAttribute(k_bin_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)sizeof(BinSmallSmem));
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.store(true, std::memory_order_release);
     }
     count_launch();
     cudaLaunchConfig_t cfg = {};

@@ -17,8 +17,8 @@ import torch
 import oracle
 import scenes
 from tests.helpers import (IMG_ATOL, add_envelopes, assert_envelope, assert_grad_close, assert_params_in_envelope,
-                           check_lists_admissible, match_image, oracle_grad2d_array, param_envelope, rect_of,
-                           rect_tiles, splat_array)
+                           check_lists_admissible, grad_rel_err, match_image, oracle_grad2d_array, param_envelope,
+                           rect_of, rect_tiles, splat_array)
 
 pytestmark = pytest.mark.gpu
 
@@ -712,6 +712,67 @@ def test_views_smaller_than_a_tile(tile, px, persistent):
             assert_envelope(rows[vis, cols], lo[vis, cols], hi[vis, cols],
                             f"grad2d {name} {c['width']}x{c['height']} (stage, tile {tile[0]}x{tile[1]})")
         assert np.all(rows[:, 9:] == 0)
+
+
+def test_contexts_on_concurrent_threads_and_streams():
+    """Three host threads, each with its own context on its own stream, run projection,
+    binning (two of them the general path: look-back scans and the onesweep depth sort; one
+    the one-CTA path of small batches), the composite and its adjoint on different batches ten
+    times at the same time. Contexts share nothing (look-back counters, status words,
+    scratch), so every image equals a lone run's bit for bit (the composite is deterministic)
+    and the 2D gradients agree within the float32 atomic-order bound."""
+    import threading
+
+    def workload(seed, n, w, h):
+        wl = scenes.small_scene(seed=seed, n=n)
+        cam = scenes.pinhole(w, h, 0.9 * w)
+        return scenes.Workload(wl.name, wl.sets, [cam], wl.blocks, wl.items, (16, 16))
+
+    wls = [workload(0, 20000, 512, 384), workload(1, 30000, 320, 240), workload(2, 1000, 128, 96)]
+    general = [True, True, False]
+
+    def run(i, stream, reps, out):
+        wl = wls[i]
+        with torch.cuda.stream(stream):
+            ctx = lobe.Context(tile=wl.tile, stream=stream, bin_general=general[i])
+            batch = make_batch(wl)
+            g = torch.Generator(device="cuda").manual_seed(5)
+            dL = torch.randn(3 * batch.n_pixels, generator=g, device="cuda")
+            res = []
+            for _ in range(reps):
+                proj, bins, img = lobe.forward(ctx, batch)
+                g2d = lobe.render_bwd(ctx, batch, proj, bins, img, dL)
+                res.append((img.rgb.clone(), img.T_final.clone(), img.n_contrib.clone(), g2d.clone()))
+            stream.synchronize()
+            ctx.status()
+            out.extend(res)
+
+    alone = []
+    for i in range(len(wls)):
+        r = []
+        run(i, torch.cuda.Stream(), 1, r)
+        alone.append(r[0])
+    outs = [[] for _ in wls]
+    errs = []
+
+    def worker(i):
+        try:
+            run(i, torch.cuda.Stream(), 10, outs[i])
+        except Exception as ex:  # reported below, in the main thread
+            errs.append(ex)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(wls))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not any(t.is_alive() for t in threads) and not errs, errs
+    for i in range(len(wls)):
+        rgb0, T0, nc0, g0 = alone[i]
+        assert len(outs[i]) == 10
+        for rgb, T, nc, g2d in outs[i]:
+            assert torch.equal(rgb, rgb0) and torch.equal(T, T0) and torch.equal(nc, nc0)
+            assert grad_rel_err(g2d.cpu().numpy(), g0.cpu().numpy()) <= 1e-4
 
 
 def test_empty_set_and_all_culled():
