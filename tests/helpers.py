@@ -214,8 +214,13 @@ def assert_envelope(gpu, lo, hi, name, abs_sum=None, rtol=GRAD_RTOL):
 # times that sum. E2E_TERM_REL is the relative float32 error of an end-to-end alpha that the
 # branch margins already assume (MARGINS_E2E); the largest seen on the full-size batched views
 # was 4e-4 of the sum. The stage tests, on identical float32 splats, keep the tight
-# float32-summation floor.
+# float32-summation floor, except where a test makes the terms cancel on purpose: there the
+# per-pixel terms still differ by the float32 renderer's own alpha and T error (the stage
+# margin MARGINS_STAGE, 2e-5: the adjoint's transmittance, recovered by division back
+# through the list, drifts about an ulp a splat), and the envelope widens by STAGE_TERM_REL
+# times the sum of the terms' magnitudes.
 E2E_TERM_REL = float(oracle.MARGINS_E2E[0])
+STAGE_TERM_REL = float(oracle.MARGINS_STAGE[0])
 
 
 def split2d(a):

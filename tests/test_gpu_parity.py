@@ -16,9 +16,9 @@ import torch
 
 import oracle
 import scenes
-from tests.helpers import (IMG_ATOL, add_envelopes, assert_envelope, assert_grad_close, assert_params_in_envelope,
-                           check_lists_admissible, grad_rel_err, match_image, oracle_grad2d_array, param_envelope,
-                           rect_of, rect_tiles, splat_array)
+from tests.helpers import (IMG_ATOL, STAGE_TERM_REL, add_envelopes, assert_envelope, assert_grad_close,
+                           assert_params_in_envelope, check_lists_admissible, grad_rel_err, match_image,
+                           oracle_grad2d_array, param_envelope, rect_of, rect_tiles, splat_array)
 
 pytestmark = pytest.mark.gpu
 
@@ -712,6 +712,48 @@ def test_views_smaller_than_a_tile(tile, px, persistent):
             assert_envelope(rows[vis, cols], lo[vis, cols], hi[vis, cols],
                             f"grad2d {name} {c['width']}x{c['height']} (stage, tile {tile[0]}x{tile[1]})")
         assert np.all(rows[:, 9:] == 0)
+
+
+@pytest.mark.parametrize("tile, px", [((16, 16), 0), ((16, 8), 4), ((32, 16), 8), ((8, 8), 1), ((16, 16), 2)])
+def test_needle_gaussians_match_oracle(tile, px):
+    """Needle-like Gaussians (two log-scales at -6.5, one in [-2, -1], random orientations:
+    thin splats at every angle, a median axis ratio of 11.5, radii up to 77 px) whose 3-sigma
+    squares hold many pixels far from the ellipse: the slab test that lets a warp skip a splat
+    must never skip one that reaches a pixel. Every pixel of the composite and the adjoint's
+    2D gradients against the oracle (stage inputs). A needle's conic gradient sums per-pixel
+    terms that cancel (their magnitudes add up to 3000 times the result), so the envelope is
+    widened by the stage margin of the float32 terms (STAGE_TERM_REL of that sum)."""
+    rng = np.random.default_rng(41)
+    n = 400
+    g = scenes.uniform_gaussians(rng, n, 1.2, 2.0, 6.0)
+    ls = np.full((n, 3), -6.5, np.float32)
+    ls[np.arange(n), rng.integers(0, 3, n)] = rng.uniform(-2.0, -1.0, n)
+    g = scenes.GaussianSet(g.means, ls, g.quats, (g.opacity_logits + 1.5).astype(np.float32), g.sh)
+    cam = scenes.pinhole(160, 120, 140.0)
+    wl = scenes.Workload("needles", [g], [cam], [scenes.AABB()], [(0, 0, 0)], tile)
+    c = cam.as_dict()
+    p, ids, ts = stage_inputs(wl, oracle.set_dict(g), c)
+    bg = (0.1, 0.2, 0.3)
+    eb = oracle.ExtBins(ids, np.zeros(len(ids), np.uint8), ts)
+    lv = oracle.render_leaves(p, eb, c, tile, bg, oracle.MARGINS_STAGE, certain=True)
+    ctx = ctx_for(wl, bg=bg, px_fwd=px, px_bwd=px)
+    batch = make_batch(wl)
+    gp = gpu_projection_from_oracle(p, c, tile)
+    bins = lobe.bin_sort(ctx, batch, gp)
+    np.testing.assert_array_equal(bins.ids().cpu().numpy(), ids)
+    out = lobe.render_fwd(ctx, batch, gp, bins)
+    adm = match_image(lv, out.rgb.view(3, 120, 160).cpu().numpy(), out.T_final.view(120, 160).cpu().numpy(),
+                      out.n_contrib.view(120, 160).cpu().numpy(), f"image needles (stage, tile {tile[0]}x{tile[1]})")
+    dL = np.random.default_rng(42).standard_normal((3, 120, 160)).astype(np.float32).astype(np.float64)
+    lo, hi, ab = oracle.render_bwd_envelope(p, eb, c, dL, adm, tile, bg, oracle.MARGINS_STAGE, certain=True)
+    lo -= STAGE_TERM_REL * ab
+    hi += STAGE_TERM_REL * ab
+    g2d = lobe.render_bwd(ctx, batch, gp, bins, out, dev(dL).reshape(-1)).cpu().numpy()
+    vis = p.radius > 0
+    for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                       ("color", slice(6, 9))]:
+        assert_envelope(g2d[vis, cols], lo[vis, cols], hi[vis, cols],
+                        f"grad2d {name} needles (stage, tile {tile[0]}x{tile[1]})")
 
 
 def test_contexts_on_concurrent_threads_and_streams():
