@@ -396,6 +396,142 @@ def test_render_backward_colour_gradient_is_blend_weight():
         np.testing.assert_allclose(g2d.color[i, 1], (im2.rgb[1] - f.image.rgb[1]).sum(), rtol=1e-12, atol=1e-12)
 
 
+# ----------------------------------------------------------------------------- threshold rules
+
+Y00 = 0.5 / math.sqrt(math.pi)  # the degree-0 real SH constant, 1 / (2 sqrt(pi))
+CAM_AXIS = dict(CAM128, cx=64.5, cy=64.5)  # pixel (64, 64) has its centre on the optical axis
+
+
+def on_axis_stack(logits, dc, z0=2.0, dz=0.5):
+    """Gaussians on the optical axis at increasing depths, degree-0 colours dc [n, 3]."""
+    n = len(logits)
+    sh = np.zeros((n, 16, 3))
+    sh[:, 0, :] = dc
+    return dict(means=np.stack([np.zeros(n), np.zeros(n), z0 + dz * np.arange(n)], 1),
+                log_scales=np.full((n, 3), -4.0), quats=np.tile([1.0, 0, 0, 0], (n, 1)),
+                opacity_logits=np.asarray(logits, float), sh=sh)
+
+
+def test_stop_rule_on_a_stack_closed_form():
+    """Twenty Gaussians of opacity 1/2 centred on one pixel centre at increasing depths: each
+    has sigma = 0 and alpha = 1/2 there, so T after k of them is 2^-k. The 3DGS stop rule
+    (appendix "3DGS Training"; read as: stop before blending a Gaussian when T (1 - alpha) <
+    1e-4, that Gaussian excluded) blends exactly 13, since 2^-14 < 1e-4 <= 2^-13: n_contrib = 13,
+    T_final = 2^-13, C = sum_{k<13} c_k 2^-(k+1) + T_final bg (the blending equation, Sec. 3.2)."""
+    n = 20
+    dc = np.linspace(-1.0, 1.0, n)[:, None] * np.array([1.0, 0.5, -0.5])
+    g = on_axis_stack(np.zeros(n), dc)
+    bg = (0.2, 0.3, 0.4)
+    f = oracle.forward(g, CAM_AXIS, bg=bg)
+    assert f.image.n_contrib[64, 64] == 13
+    assert f.image.T_final[64, 64] == 2.0 ** -13
+    col = np.maximum(dc * Y00 + 0.5, 0.0)
+    want = (col[:13] * 0.5 ** np.arange(1, 14)[:, None]).sum(0) + 2.0 ** -13 * np.array(bg)
+    np.testing.assert_allclose(f.image.rgb[:, 64, 64], want, rtol=1e-12, atol=0)
+
+
+def test_alpha_clamp_and_one_pixel_adjoint_closed_form():
+    """One Gaussian centred on a pixel centre (G = 1 there). Opacity sigmoid(6) = 0.9975: alpha
+    is clamped to 0.99 (the 3DGS clamp of appendix "3DGS Training"), so C = 0.99 c + 0.01 bg and
+    T = 0.01, and since alpha no longer depends on the opacity past the clamp, that pixel's
+    adjoint is dL/do = 0, dL/dc = 0.99 dL/dC. Opacity 1/2: dL/dc = alpha T dL/dC = dL/dC / 2 and
+    dL/do = G T (c - bg) . dL/dC (the colour behind the Gaussian is the background)."""
+    dc = np.array([[0.8, -0.3, 0.4]])
+    col = np.maximum(dc[0] * Y00 + 0.5, 0.0)
+    bg = np.array([0.2, 0.3, 0.4])
+    w = np.zeros((3, 128, 128))
+    w[:, 64, 64] = (0.7, -1.1, 0.5)
+    for logit, alpha, clamped in [(6.0, 0.99, True), (0.0, 0.5, False)]:
+        g = on_axis_stack([logit], dc)
+        f = oracle.forward(g, CAM_AXIS, bg=tuple(bg))
+        np.testing.assert_allclose(f.image.rgb[:, 64, 64], alpha * col + (1 - alpha) * bg, rtol=1e-12)
+        assert f.image.T_final[64, 64] == 1.0 - alpha
+        g2d = oracle.render_bwd(f.proj, f.ids, f.tile_start, CAM_AXIS, w, bg=tuple(bg))
+        np.testing.assert_allclose(g2d.color[0], alpha * w[:, 64, 64], rtol=1e-12)
+        want_do = 0.0 if clamped else float(np.dot(col - bg, w[:, 64, 64]))
+        np.testing.assert_allclose(g2d.opacity[0], want_do, rtol=1e-12, atol=1e-15)
+
+
+def test_negative_colour_is_clamped_and_passes_no_gradient():
+    """The colour is max(0, SH + 1/2) per channel (the 3DGS colour of appendix "3DGS
+    Training"): a Gaussian whose degree-0 colour is negative in the green channel composites 0
+    there (C = T bg), and the projection adjoint gives that channel's SH coefficients no
+    gradient, while the other channels' DC coefficient gets Y00 dL/dc."""
+    dc = np.array([[0.8, -3.0, 0.4]])
+    g = on_axis_stack([0.0], dc)
+    bg = (0.2, 0.3, 0.4)
+    f = oracle.forward(g, CAM_AXIS, bg=bg)
+    assert f.image.rgb[1, 64, 64] == 0.5 * bg[1]
+    g2d = oracle.Grad2D(np.zeros((1, 2)), np.zeros((1, 3)), np.array([[0.3, 0.9, -0.6]]), np.zeros(1))
+    pg = oracle.project_bwd(g, CAM_AXIS, g2d)
+    np.testing.assert_allclose(pg.sh[0, 0], [Y00 * 0.3, 0.0, Y00 * -0.6], rtol=1e-12)
+    assert np.all(pg.sh[0, :, 1] == 0.0)
+
+
+def test_fov_guard_is_1_3_times_the_half_field_of_view():
+    """The culling guard (frustum culling during rasterization, Sec. 3.3; the 3DGS 1.3 x
+    half-field-of-view reading): a Gaussian large enough that its footprint reaches the image
+    is kept at |x/z| = 1.29 W / (2 fx) and culled at 1.31 W / (2 fx); likewise in y with H, fy
+    (a 160 x 96 camera with fx != fy)."""
+    cam = dict(CAM128, width=160, height=96, fx=150.0, fy=110.0, cx=80.0, cy=48.0)
+    z = 3.0
+    hx, hy = 0.5 * 160 / 150.0, 0.5 * 96 / 110.0
+    mus = [(1.29 * hx * z, 0, z), (1.31 * hx * z, 0, z), (0, -1.29 * hy * z, z), (0, -1.31 * hy * z, z)]
+    g = dict(means=np.array(mus, float), log_scales=np.full((4, 3), -1.2), quats=np.tile([1.0, 0, 0, 0], (4, 1)),
+             opacity_logits=np.zeros(4), sh=np.zeros((4, 16, 3)))
+    p = oracle.project(g, cam)
+    assert list(p.radius > 0) == [True, False, True, False]
+    assert np.all(p.radius_all > 0)  # the culled two had footprints that reach the image
+
+
+def test_principal_point_is_the_image_of_the_optical_axis():
+    """A Gaussian on the optical axis projects to the principal point (cx, cy), here with
+    cx != cy on a non-square image."""
+    cam = dict(CAM128, width=160, height=96, cx=70.25, cy=40.75)
+    p = oracle.project(one_gaussian((0.0, 0.0, 3.0), (-3, -3, -3)), cam)
+    assert tuple(p.mean2d[0]) == (70.25, 40.75)
+
+
+def test_sort_breaks_depth_ties_by_index():
+    """Equal float32 depths in a tile are ordered by ascending Gaussian index (the tie-break
+    reading of the depth sort): 300 Gaussians on five depth planes, against np.lexsort over
+    (tile, depth key, index)."""
+    rng = np.random.default_rng(8)
+    n = 300
+    g = dict(means=np.stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.choice([2.0, 2.5, 3.0, 4.0, 5.0], n)], 1),
+             log_scales=rng.uniform(-4, -2, (n, 3)), quats=rng.standard_normal((n, 4)),
+             opacity_logits=np.zeros(n), sh=np.zeros((n, 16, 3)))
+    p = oracle.project(g, CAM128)
+    ids, ts = oracle.bin_sort(p, CAM128)
+    tiles, keys, gid = [], [], []
+    for i in np.nonzero(p.radius > 0)[0]:
+        r = p.rect[i]
+        for ty in range(r[1], r[3]):
+            for tx in range(r[0], r[2]):
+                tiles.append(ty * 8 + tx)
+                keys.append(np.float32(p.depth[i]).view(np.uint32))
+                gid.append(i)
+    tiles, keys, gid = map(np.array, (tiles, keys, gid))
+    assert len(np.unique(keys)) == 5  # every list has ties
+    order = np.lexsort((gid, keys, tiles))
+    np.testing.assert_array_equal(ids, gid[order])
+
+
+def test_sd_statistic_scales_by_half_width_and_height():
+    """The SD statistic (Sec. 3.3) of a view sums ||(dL/du W/2, dL/dv H/2)|| over the views
+    where the Gaussian is visible and inside the block: on a 160 x 96 view the two components
+    are scaled by 80 and 48."""
+    cam = dict(CAM128, width=160, height=96, cx=80.0, cy=48.0)
+    wl = scenes.small_scene(n=200)
+    g = oracle.set_dict(wl.sets[0])
+    f = oracle.forward(g, cam)
+    w = np.random.default_rng(9).standard_normal((3, 96, 160))
+    g2d, pg = oracle.backward(g, cam, f, w, aabb=scenes.AABB())
+    vis = f.proj.radius > 0
+    want = np.where(vis, np.hypot(g2d.mean2d[:, 0] * 80, g2d.mean2d[:, 1] * 48), 0.0)
+    np.testing.assert_allclose(pg.sd_acc, want, rtol=1e-14, atol=0)
+
+
 # ----------------------------------------------------------------------------- fast camera selection
 
 def test_depth_composite_on_axis_closed_form():
