@@ -1,10 +1,12 @@
 """The oracle's pins against planted mistakes (mutation check, CPU only).
 
-Each case copies ``oracle/lobe_oracle.c``, plants one plausible mistake in it -- a dropped
-term, a wrong sign, index or constant, a transposed operand, a threshold rule read the other
-way -- builds the copy and runs the pins that should catch it against that build: at least
-one of them must fail. The planted copies live in a temporary directory and never replace
-the oracle; ``oracle._lib`` is pointed at a copy for one case and restored afterwards.
+Each case copies ``oracle/lobe_oracle.c`` (or the oracle's Python module, for the parts
+written in Python: Adam, back-projection and coverage, densification, the KD partition),
+plants one plausible mistake in it -- a dropped term, a wrong sign, index or constant, a
+transposed operand, a threshold rule read the other way -- builds or loads the copy and runs
+the pins that should catch it against it: at least one of them must fail. The planted copies
+live in a temporary directory or a throwaway module and never replace the oracle; the
+``oracle`` module is pointed at a copy for one case and restored afterwards.
 Mistakes that leave every result unchanged (reordering a product of symmetric matrices) are
 not cases.
 """
@@ -12,6 +14,8 @@ import concurrent.futures
 import inspect
 import os
 import subprocess
+import sys
+import types
 
 import pytest
 
@@ -211,6 +215,109 @@ def test_pins_catch_a_planted_mistake(planted, monkeypatch, name, mistake, old, 
     monkeypatch.setattr(oracle, "_LIB", so)
     monkeypatch.setattr(oracle, "build", lambda force=False: so)
     monkeypatch.setattr(oracle, "_lib", None)
+    failed = run_catchers(catchers)
+    assert failed, f"no pin caught the planted mistake ({mistake}); ran {catchers}"
+
+
+# the same for the oracle's Python functions: (name, the mistake, text of oracle/__init__.py,
+# planted text, pins expected to catch it)
+PY_MUTANTS = [
+    ('adam_bias2', 'second-moment bias correction with t + 1',
+     'bc2 = 1.0 - beta2 ** t',
+     'bc2 = 1.0 - beta2 ** (t + 1)',
+     ['test_adam_constant_gradient_closed_form']),
+    ('adam_m', 'first moment mixed with beta2',
+     'm = beta1 * np.asarray(exp_avg[key], np.float64) + (1.0 - beta1) * g',
+     'm = beta1 * np.asarray(exp_avg[key], np.float64) + (1.0 - beta2) * g',
+     ['test_adam_constant_gradient_closed_form', 'test_adam_matches_torch_optim']),
+    ('adam_eps', 'eps inside the square root',
+     'p_new = p - rate * (m / bc1) / (np.sqrt(v / bc2) + eps)',
+     'p_new = p - rate * (m / bc1) / np.sqrt(v / bc2 + eps)',
+     ['test_adam_constant_gradient_closed_form', 'test_adam_matches_torch_optim']),
+    ('adam_sh_dc', 'SH DC at the rest rate',
+     'rate[0, :] = float(lr["sh_dc"])',
+     'rate[0, :] = float(lr["sh_rest"])',
+     ['test_adam_matches_torch_optim', 'test_adam_constant_gradient_closed_form']),
+    ('adam_sparse_moments', 'sparse step still decays the moments of unseen rows',
+     '            m = np.where(keep, np.asarray(exp_avg[key], np.float64), m)\n',
+     '',
+     ['test_adam_sparse_rows_leave_the_others_untouched']),
+    ('backproject_centre', 'pixel corner instead of centre',
+     '(px + 0.5 - c["cx"]) / c["fx"] * d',
+     '(px - c["cx"]) / c["fx"] * d',
+     ['test_backprojection_inverts_the_pinhole']),
+    ('backproject_normalize', 'normalisation by 1 - T dropped',
+     'd = D / np.where(mask, 1.0 - T, 1.0) if normalize else D',
+     'd = D',
+     ['test_backprojection_inverts_the_pinhole']),
+    ('backproject_inverse', 'world = viewmat applied, not its inverse',
+     'Vinv = np.linalg.inv(np.asarray(c["viewmat"], np.float64).reshape(4, 4))',
+     'Vinv = np.asarray(c["viewmat"], np.float64).reshape(4, 4)',
+     ['test_backprojection_inverts_the_pinhole']),
+    ('fcs_halfopen', 'boxes closed at hi',
+     'inside = mask & np.all((pts >= lo) & (pts < hi), axis=-1)',
+     'inside = mask & np.all((pts >= lo) & (pts <= hi), axis=-1)',
+     ['test_coverage_boxes_are_half_open']),
+    ('fcs_mask', 'pixels no Gaussian reached counted',
+     'inside = mask & np.all((pts >= lo) & (pts < hi), axis=-1)',
+     'inside = np.all((pts >= lo) & (pts < hi), axis=-1)',
+     ['test_coverage_of_a_wall_split_by_a_block_boundary']),
+    ('densify_threshold', 'strict gradient threshold',
+     'mean_grad >= f32(grad_threshold)',
+     'mean_grad > f32(grad_threshold)',
+     ['test_densify_thresholds_and_sd_views']),
+    ('densify_clone', 'clone test on the smallest scale',
+     'clone = dens & (ls.max(axis=1) <= f32(max_clone_log_scale))',
+     'clone = dens & (ls.min(axis=1) <= f32(max_clone_log_scale))',
+     ['test_densify_branches_and_order']),
+    ('densify_prune', 'prune at or below the logit',
+     'prune = lg < f32(prune_logit)',
+     'prune = lg <= f32(prune_logit)',
+     ['test_densify_thresholds_and_sd_views']),
+    ('densify_cnt', 'densify without SD views',
+     'dens = ~prune & (cnt > 0) & (mean_grad',
+     'dens = ~prune & (cnt >= 0) & (mean_grad',
+     ['test_densify_thresholds_and_sd_views']),
+    ('densify_shrink', 'split children grow',
+     'out["log_scales"][child] = np.asarray(params["log_scales"], np.float64)[g] - split_log_shrink',
+     'out["log_scales"][child] = np.asarray(params["log_scales"], np.float64)[g] + split_log_shrink',
+     ['test_densify_branches_and_order']),
+    ('densify_rotation', 'split offset with R transposed',
+     'np.einsum("nij,nj->ni", R, s * zk)',
+     'np.einsum("nji,nj->ni", R, s * zk)',
+     ['test_split_child_is_the_rotated_scaled_draw', 'test_split_children_follow_the_gaussian']),
+    ('densify_clone_count', 'a clone makes three',
+     'k_out = np.where(prune, 0, np.where(clone, 2, np.where(split, n_split, 1)))',
+     'k_out = np.where(prune, 0, np.where(clone, 3, np.where(split, n_split, 1)))',
+     ['test_densify_branches_and_order', 'test_densify_thresholds_and_sd_views']),
+    ('kd_tau', 'camera kept only above tau',
+     'if len(pts) and inside(pts, lo, hi).sum() / len(pts) >= tau:',
+     'if len(pts) and inside(pts, lo, hi).sum() / len(pts) > tau:',
+     ['test_kd_partition_keeps_a_camera_at_exactly_tau']),
+    ('kd_axis', 'split along the shorter extent',
+     'a = 0 if ext[0] >= ext[1] else 1',
+     'a = 1 if ext[0] >= ext[1] else 0',
+     ['test_kd_partition_bisection_closed_form', 'test_kd_partition_keeps_a_camera_at_exactly_tau']),
+    ('kd_bisect', 'bisection toward the heavier side',
+     'qhi, q = q, 0.5 * (qlo + q)',
+     'qhi, q = q, 0.5 * (qhi + q)',
+     ['test_kd_partition_bisection_closed_form']),
+    ('kd_leaf_tie', 'latest leaf first among equals',
+     '(len(leaves[i][2]) == len(leaves[best][2]) and leaves[i][3] < leaves[best][3])',
+     '(len(leaves[i][2]) == len(leaves[best][2]) and leaves[i][3] > leaves[best][3])',
+     ['test_kd_partition_splits_the_heaviest_leaf_earliest_first']),
+    ('kd_heaviest', 'lightest leaf split',
+     'if len(leaves[i][2]) > len(leaves[best][2]) or',
+     'if len(leaves[i][2]) < len(leaves[best][2]) or',
+     ['test_kd_partition_splits_the_heaviest_leaf_earliest_first']),
+    ('kd_halfopen', 'KD boxes closed at hi',
+     '        return np.all((pts >= lo) & (pts < hi), axis=-1)\n',
+     '        return np.all((pts >= lo) & (pts <= hi), axis=-1)\n',
+     ['test_kd_partition_bisection_closed_form', 'test_kd_partition_splits_the_heaviest_leaf_earliest_first']),
+]
+
+
+def run_catchers(catchers):
     failed = []
     for pin in catchers:
         fn = getattr(pins, pin)
@@ -219,4 +326,19 @@ def test_pins_catch_a_planted_mistake(planted, monkeypatch, name, mistake, old, 
             fn()
         except Exception:  # an assertion, or arithmetic the planted mistake broke
             failed.append(pin)
+    return failed
+
+
+@pytest.mark.parametrize("name, mistake, old, new, catchers", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_catch_a_planted_mistake_in_python(monkeypatch, name, mistake, old, new, catchers):
+    src = open(oracle.__file__).read()
+    assert src.count(old) == 1, f"{name}: the planted text must occur exactly once"
+    mod = types.ModuleType("oracle_planted")
+    mod.__file__ = oracle.__file__
+    monkeypatch.setitem(sys.modules, "oracle_planted", mod)  # dataclasses look their module up
+    exec(compile(src.replace(old, new), oracle.__file__, "exec"), mod.__dict__)
+    for k, v in vars(mod).items():
+        if isinstance(v, types.FunctionType):
+            monkeypatch.setattr(oracle, k, v)
+    failed = run_catchers(catchers)
     assert failed, f"no pin caught the planted mistake ({mistake}); ran {catchers}"

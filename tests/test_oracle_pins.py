@@ -609,6 +609,20 @@ def test_coverage_of_a_wall_split_by_a_block_boundary():
     assert counts.tolist() == [H * cols_left, H * (W - 5 - cols_left), 0]
 
 
+def test_coverage_boxes_are_half_open():
+    """Block boxes are half-open, lo <= p < hi (the reading of "inside the block" used by the
+    partition, Alg. 1): a wall of back-projected points at exactly z = 7 lies in the box
+    [7, inf) and not in (-inf, 7)."""
+    W, H, z = 32, 24, 7.0
+    cam = dict(viewmat=np.eye(4), fx=30.0, fy=30.0, cx=16.0, cy=12.0, width=W, height=H, near=0.01, far=1e10)
+    D = np.full((H, W), z)
+    T = np.zeros((H, W))
+    below = scenes.AABB((-math.inf, -math.inf, -math.inf), (math.inf, math.inf, z))
+    above = scenes.AABB((-math.inf, -math.inf, z), (math.inf, math.inf, math.inf))
+    counts, n, _ = oracle.fcs_coverage(D, T, cam, [below, above])
+    assert counts.tolist() == [0, W * H] and n == W * H
+
+
 # ----------------------------------------------------------------------------- densification
 
 def dens_set(n=5):
@@ -635,6 +649,24 @@ def test_densify_branches_and_order():
     np.testing.assert_allclose(out["log_scales"][2], np.float64([-1.0, -3.0, -3.0]) - math.log(1.6), rtol=1e-15)
     np.testing.assert_allclose(out["means"][2], p["means"][2], rtol=1e-15)  # z = 0: the parent's mean
     np.testing.assert_array_equal(out["sh"][5], p["sh"][4].astype(np.float64))
+
+
+def test_densify_thresholds_and_sd_views():
+    """The densification tests at their thresholds (Sec. 3.3 and the 3DGS density control of
+    appendix "3DGS Training", read as: densify when the mean SD gradient reaches the threshold,
+    prune when the opacity logit is below the limit, only Gaussians with SD views): a mean
+    gradient exactly at the threshold (2^-10 over 4 views = 2^-12) is cloned, a logit exactly at
+    the prune limit is kept, and with a zero threshold a Gaussian without SD views (cnt = 0) is
+    still only kept."""
+    p = dens_set(3)
+    p["opacity_logits"][1] = -5.0
+    acc = np.float32([2.0 ** -10, 0.0, 0.0])
+    cnt = np.int32([4, 1, 0])
+    normals = np.zeros((3, 2, 3), np.float32)
+    out, src = oracle.densify(p, acc, cnt, normals, 2.0 ** -12, math.log(0.1), -5.0, 2, math.log(1.6))
+    assert src.tolist() == [0, 0, 1, 2]
+    out, src = oracle.densify(p, acc, cnt, normals, 0.0, math.log(0.1), -6.0, 2, math.log(1.6))
+    assert src.tolist() == [0, 0, 1, 1, 2]  # cnt > 0 densifies at threshold 0; cnt = 0 does not
 
 
 def test_split_child_is_the_rotated_scaled_draw():
@@ -708,6 +740,40 @@ def test_kd_partition_invariants():
     (lo0, hi0, _), (lo1, hi1, _) = oracle.kd_partition(centers, root, 2, cams)
     assert np.isinf(hi0[1]) and np.isfinite(hi0[0]) and hi0[0] == lo1[0]
     assert np.quantile(centers[:, 0], 0.1) <= hi0[0] <= np.quantile(centers[:, 0], 0.9)
+
+
+def kd_strip():
+    """Centres on a 10 x 1 strip (x in [0, 10], median x = 5) and an unbounded root box."""
+    xs = np.linspace(0.0, 10.0, 1001)
+    centers = np.stack([xs, np.linspace(0.0, 1.0, 1001), np.zeros(1001)], 1)
+    return centers, scenes.AABB((-math.inf,) * 3, (math.inf,) * 3)
+
+
+def test_kd_partition_keeps_a_camera_at_exactly_tau():
+    """A child's camera set keeps a camera whose ratio V reaches tau (Alg. 1, V >= tau): camera
+    0 has 1 of its 10 points left of the median cut x = 5 (V = 0.1 = tau), camera 1 has 1 of 10
+    right of it; the counts tie at the median, so the cut stays there and both children keep
+    both cameras."""
+    centers, root = kd_strip()
+    cams = [np.array([[2.0, 0.5, 0.0]] + [[8.0, 0.5, 0.0]] * 9), np.array([[2.0, 0.5, 0.0]] * 9 + [[8.0, 0.5, 0.0]])]
+    (lo0, hi0, c0), (lo1, hi1, c1) = oracle.kd_partition(centers, root, 2, cams, tau=0.1)
+    assert hi0[0] == 5.0 and c0 == [0, 1] and c1 == [0, 1]
+
+
+def test_kd_partition_splits_the_heaviest_leaf_earliest_first():
+    """Alg. 1 splits the leaf with the largest workload (|C(B)|) next, the earliest created
+    among equals; one evaluated cut (steps = 1) keeps every cut at the median. One camera left
+    of x = 5 and three right of it: the right child (three cameras) is split next, at the
+    median of its centres x = 5.00 ... 10.00, 7.5. Two and two: the children tie and the left
+    one, created first, is split, at the median of x = 0.00 ... 4.99, 2.495."""
+    centers, root = kd_strip()
+    pts = lambda xs: [np.array([[x, 0.5, 0.0]]) for x in xs]
+    leaves = oracle.kd_partition(centers, root, 3, pts([2.0, 6.0, 8.0, 9.0]), steps=1)
+    assert [(lo[0], hi[0]) for lo, hi, _ in leaves] == \
+        [(-math.inf, 5.0), (5.0, pytest.approx(7.5)), (pytest.approx(7.5), math.inf)]
+    leaves = oracle.kd_partition(centers, root, 3, pts([1.0, 3.0, 7.0, 9.0]), steps=1)
+    assert [(lo[0], hi[0]) for lo, hi, _ in leaves] == \
+        [(5.0, math.inf), (-math.inf, pytest.approx(2.495)), (pytest.approx(2.495), 5.0)]
 
 
 # ----------------------------------------------------------------------------- Adam
