@@ -108,9 +108,9 @@ __device__ __forceinline__ uint32_t lb_exclusive_warp(const unsigned long long *
 // old value before taking its ticket). The last ticket holder also re-arms the counter.
 __device__ __forceinline__ void lb_take(int *ctl, int stage, bool bump, int &ticket, uint32_t &gen)
 {
-    volatile int *vctl = ctl;
-    const uint32_t g = (uint32_t)vctl[1];
-    __threadfence();
+    // an acquire load: the ticket below cannot be taken before the generation is read
+    uint32_t g;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(ctl + 1) : "memory");
     ticket = atomicAdd(ctl + 2 + stage, 1);
     gen = bump ? g + 1u : g;
     if (ticket == (int)gridDim.x - 1) {
