@@ -204,6 +204,54 @@ def test_envelope_is_min_max_over_admitted_leaves(seed):
         np.testing.assert_allclose(hi, adj.max(axis=0), rtol=1e-12, atol=1e-15)
 
 
+def test_a_marginal_stop_alone_gives_both_outcomes():
+    """Two clamped splats (alpha = 0.99, far from the clamp, sigma and 1/255 margins) bring
+    T (1 - alpha) to 1e-4 within float rounding at the second one, whose only marginal decision
+    is then the stop: the leaves are exactly the exhaustive filter's, the composite that blends
+    it (and, past it, stops before the third) and the one that stops before it; the adjoint
+    envelope over each is that list's textbook adjoint."""
+    sig, opac = [0.002, 0.002, 0.5], [0.995, 0.995, 0.5]
+    colors = np.array([[0.9, 0.1, 0.2], [0.3, 0.8, 0.5], [0.2, 0.4, 0.9]])
+    unc = [0, 0, 0]
+    p = one_pixel_projection(sig, opac, colors)
+    eb = oracle.ExtBins(np.arange(3, dtype=np.int32), np.zeros(3, np.uint8), np.array([0, 3], np.int32))
+    lv = oracle.render_leaves(p, eb, CAM1, (16, 16), margins=MARGINS)
+    n = int(lv.n[0, 0])
+    keys = [(tuple(np.round(lv.C[0, 0, l], 12)), round(float(lv.T[0, 0, l]), 12), int(lv.nc[0, 0, l]))
+            for l in range(n)]
+    want = brute_force_outcomes(sig, opac, colors, unc)
+    assert n == 2 and set(keys) == set(want)
+    assert sorted(int(lv.nc[0, 0, l]) for l in range(n)) == [1, 2]
+    gC = np.array([0.7, -1.1, 0.4])
+    for l in range(n):
+        lo, hi, _ = oracle.render_bwd_envelope(p, eb, CAM1, gC.reshape(3, 1, 1), np.array([[1 << l]], np.uint64),
+                                               (16, 16), margins=MARGINS)
+        np.testing.assert_allclose(lo, adjoint(want[keys[l]], colors, sig, gC), rtol=1e-12, atol=1e-15)
+        np.testing.assert_array_equal(lo, hi)
+
+
+def test_single_leaf_envelope_with_clamped_pairs_is_the_plain_adjoint():
+    """As below, with opacity logits raised by 6 so that most pixels composite clamped pairs
+    (alpha = 0.99, whose opacity and exponent get no gradient): one leaf per pixel, and the
+    envelope over it is exactly orc_render_bwd."""
+    wl = scenes.small_scene()
+    cam = wl.cameras[0].as_dict()
+    g = oracle.set_dict(wl.sets[0])
+    g["opacity_logits"] = g["opacity_logits"] + 6.0
+    f = oracle.forward(g, cam, wl.tile)
+    assert np.mean(f.proj.opacity[f.proj.radius > 0] >= 0.99) > 0.5
+    eb = oracle.bin_ext(f.proj, cam, wl.tile)
+    lv = oracle.render_leaves(f.proj, eb, cam, wl.tile)
+    assert np.all(lv.n == 1)
+    dL = np.random.default_rng(2).standard_normal((3, 128, 128))
+    lo, hi, _ = oracle.render_bwd_envelope(f.proj, eb, cam, dL, np.ones((128, 128), np.uint64), wl.tile)
+    want = oracle.render_bwd(f.proj, f.ids, f.tile_start, cam, dL, wl.tile)
+    np.testing.assert_array_equal(lo, hi)
+    for name, cols in [("mean2d", slice(0, 2)), ("conic", slice(2, 5)), ("opacity", slice(5, 6)),
+                       ("color", slice(6, 9))]:
+        np.testing.assert_allclose(lo[:, cols], getattr(want, name).reshape(len(lo), -1), rtol=1e-12, atol=1e-14)
+
+
 def test_single_leaf_envelope_is_the_plain_adjoint():
     """Zero margins: one leaf per pixel, equal to the plain composite, and the envelope over it
     is exactly orc_render_bwd (lo = hi)."""

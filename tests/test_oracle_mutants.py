@@ -20,6 +20,7 @@ import types
 import pytest
 
 import oracle
+import tests.test_oracle_branches as branches
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lobe_oracle.c")
@@ -186,6 +187,39 @@ MUTANTS = [
      'if (!(mu[i] >= aabb[i] && mu[i] < aabb[3 + i])) inside = 0;',
      'if (!(mu[i] >= aabb[i] || mu[i] < aabb[3 + i])) inside = 0;',
      ['test_sd_statistic_is_scaled_mean2d_gradient_norm']),
+    # the enumeration of admissible branches (the leaves of a pixel and their adjoints)
+    ('walk_skip', 'the skipped outcome of a used pair never followed',
+     '    if (order[0] != 0 && skip_ok) order[no++] = 0;\n',
+     '    if (0 && skip_ok) order[no++] = 0;\n',
+     [('branches', 'test_leaves_equal_exhaustive_filter', (0,))]),
+    ('walk_clamp', 'the other side of a marginal clamp never followed',
+     '        int clamp_ok = c == cl_fp || cl_m;\n',
+     '        int clamp_ok = c == cl_fp;\n',
+     [('branches', 'test_leaves_equal_exhaustive_filter', (0,))]),
+    ('walk_stop', 'the other side of a marginal stop never followed',
+     '    for (int b = 0; b < 1 + marg; ++b) {\n        int st = b == 0 ? stop : !stop;',
+     '    for (int b = 0; b < 1; ++b) {\n        int st = b == 0 ? stop : !stop;',
+     [('branches', 'test_leaves_equal_exhaustive_filter', (2,)), ('branches', 'test_leaves_equal_exhaustive_filter', (3,))]),
+    ('walk_plain_stop', 'a marginal stop on the plain path taken as certain',
+     '        if (fabs(Tn - 1e-4) < mg[M_REL] * 1e-4) {\n            pair_stop(w, &q, S, alpha, q.araw >= 0.99, NULL);',
+     '        if (0) {\n            pair_stop(w, &q, S, alpha, q.araw >= 0.99, NULL);',
+     [('branches', 'test_a_marginal_stop_alone_gives_both_outcomes', ())]),
+    ('walk_member', 'uncertain members never flipped',
+     '    int mem_fp = u != 1, mem_m = u != 0;',
+     '    int mem_fp = u != 1, mem_m = 0;',
+     [('branches', 'test_leaves_equal_exhaustive_filter', (3,)), ('branches', 'test_leaves_equal_exhaustive_filter', (4,))]),
+    ('walk_clamped_record', 'a clamped pair recorded as unclamped on the plain path',
+     '        r->dx = q.dx; r->dy = q.dy; r->clamped = q.araw >= 0.99;',
+     '        r->dx = q.dx; r->dy = q.dy; r->clamped = 0;',
+     [('branches', 'test_single_leaf_envelope_with_clamped_pairs_is_the_plain_adjoint', ())]),
+    ('walk_fp_first', 'leaf 0 not the FP64 outcome',
+     '    order[no++] = fp_used ? 1 + cl_fp : 0;',
+     '    order[no++] = 0;',
+     [('branches', 'test_leaves_equal_exhaustive_filter', (0,))]),
+    ('walk_sigma', 'sigma margin ignored',
+     '        int m_sig = fabs(q.sigma) < mg[M_SIG];\n',
+     '        int m_sig = 0;\n',
+     [('branches', 'test_leaves_equal_exhaustive_filter', (0,))])
 ]
 
 
@@ -318,14 +352,19 @@ PY_MUTANTS = [
 
 
 def run_catchers(catchers):
+    """Runs each catcher: a pin's name (tests/test_oracle_pins.py, no arguments) or
+    (module, name, arguments) with module "branches" (tests/test_oracle_branches.py) or
+    "pins". Returns the ones that failed."""
     failed = []
-    for pin in catchers:
-        fn = getattr(pins, pin)
-        assert not inspect.signature(fn).parameters, f"{pin} takes arguments"
+    for c in catchers:
+        mod, name, args = (pins, c, ()) if isinstance(c, str) else ({"pins": pins, "branches": branches}[c[0]], c[1],
+                                                                    tuple(c[2]))
+        fn = getattr(mod, name)
+        assert len(inspect.signature(fn).parameters) == len(args), f"{name}: wrong number of arguments"
         try:
-            fn()
+            fn(*args)
         except Exception:  # an assertion, or arithmetic the planted mistake broke
-            failed.append(pin)
+            failed.append(c)
     return failed
 
 
