@@ -187,6 +187,10 @@ MUTANTS = [
      'if (!(mu[i] >= aabb[i] && mu[i] < aabb[3 + i])) inside = 0;',
      'if (!(mu[i] >= aabb[i] || mu[i] < aabb[3 + i])) inside = 0;',
      ['test_sd_statistic_is_scaled_mean2d_gradient_norm']),
+    ('crop_overwrite', 'the visibility crop keeps only the last camera',
+     '        if (P.visible) mask[g] = 1;',
+     '        mask[g] = P.visible ? 1 : 0;',
+     ['test_visibility_crop_is_the_union_over_the_block_cameras']),
     # the enumeration of admissible branches (the leaves of a pixel and their adjoints)
     ('walk_skip', 'the skipped outcome of a used pair never followed',
      '    if (order[0] != 0 && skip_ok) order[no++] = 0;\n',
@@ -348,6 +352,10 @@ PY_MUTANTS = [
      '        return np.all((pts >= lo) & (pts < hi), axis=-1)\n',
      '        return np.all((pts >= lo) & (pts <= hi), axis=-1)\n',
      ['test_kd_partition_bisection_closed_form', 'test_kd_partition_splits_the_heaviest_leaf_earliest_first']),
+    ('depth_colour', 'the depth composite blends colours',
+     'q = Projection(p.mean2d, p.conic, np.repeat(p.depth[:, None], 3, axis=1), p.opacity,',
+     'q = Projection(p.mean2d, p.conic, p.color, p.opacity,',
+     ['test_depth_composite_on_axis_closed_form'])
 ]
 
 

@@ -195,6 +195,20 @@ def test_culling_rules():
     assert list(mask) == [0, 0, 0, 1, 1]
 
 
+def test_visibility_crop_is_the_union_over_the_block_cameras():
+    """Visibility cropping keeps a Gaussian that any camera of the block sees (Sec. 3.3): two
+    cameras looking along +z and -z from the origin each see only the Gaussians in front of
+    them, and the crop over both keeps all of them, whatever the order of the cameras."""
+    mus = [(0, 0, 3.0), (0, 0, -3.0), (0.2, 0.1, 4.0), (-0.1, 0.2, -5.0)]
+    g = dict(means=np.array(mus, float), log_scales=np.full((4, 3), -3.0), quats=np.tile([1.0, 0, 0, 0], (4, 1)),
+             opacity_logits=np.zeros(4), sh=np.zeros((4, 16, 3)))
+    back = dict(CAM128, viewmat=np.diag([1.0, -1.0, -1.0, 1.0]))  # a half turn about x: looks along -z
+    assert list(oracle.visibility_crop(g, [CAM128])) == [1, 0, 1, 0]
+    assert list(oracle.visibility_crop(g, [back])) == [0, 1, 0, 1]
+    assert list(oracle.visibility_crop(g, [CAM128, back])) == [1, 1, 1, 1]
+    assert list(oracle.visibility_crop(g, [back, CAM128])) == [1, 1, 1, 1]
+
+
 def test_depth_key_is_float32_z():
     g = one_gaussian((0.1, 0.2, 3.3), (-3, -3, -3))
     vm = scenes.look_at((1.0, -2.0, 0.5), (0.0, 0.0, 4.0), up=(0, -1, 0))
