@@ -11,6 +11,7 @@ no decision is marginal, the plain binning under each radius a marginal decision
 the plain adjoint of each branch realised by nudging the input across its threshold. CPU only.
 """
 import itertools
+import math
 
 import numpy as np
 import pytest
@@ -331,3 +332,29 @@ def test_extended_lists_cover_every_allowed_radius():
               zip(eb.ids[eb.tile_start[t]:eb.tile_start[t + 1]], eb.unc[eb.tile_start[t]:eb.tile_start[t + 1]])
               if u != 1}
     assert inside == plain
+
+
+def test_a_marginal_guard_makes_every_tile_of_the_outer_rectangle_uncertain():
+    """A Gaussian on the 1.3 x fov guard (|x/z| = 1.3 W / (2 fx) within the guard margin) may be
+    culled or kept by a float32 projection: it is an uncertain member of every tile of its
+    rectangle of radius r + 1 and a certain member of none, so the lists with it culled and
+    with it kept are both admissible."""
+    cam = dict(viewmat=np.eye(4, dtype=np.float32), fx=128.0, fy=128.0, cx=64.0, cy=64.0, width=128,
+               height=128, near=0.01, far=1e10)
+    z = 3.0
+    g = dict(means=np.array([[0.65 * z, 0.0, z], [0.0, 0.0, z]]), log_scales=np.full((2, 3), -1.0),
+             quats=np.tile([1.0, 0, 0, 0], (2, 1)), opacity_logits=np.zeros(2), sh=np.zeros((2, 16, 3)))
+    p = oracle.project(g, cam, (16, 16), margins=np.array([5e-4, 0.5, 2e-2, 2e-5, 1e-4, 2e-5]))
+    assert p.flags[0] & oracle.F_GUARD and p.radius_all[0] > 0
+    eb = oracle.bin_ext(p, cam, (16, 16))
+    gx, gy = oracle.grid(cam, (16, 16))
+    r = p.radius_all[0] + 1
+    u, v = p.mean2d[0]
+    outer = [(tx, ty) for ty in range(gy) for tx in range(gx)
+             if math.floor((u - r) / 16) <= tx < math.ceil((u + r) / 16) and math.floor((v - r) / 16) <= ty < math.ceil((v + r) / 16)]
+    assert outer
+    for tx, ty in outer:
+        t = ty * gx + tx
+        sl = slice(eb.tile_start[t], eb.tile_start[t + 1])
+        k = list(eb.ids[sl]).index(0)  # a member of the tile...
+        assert eb.unc[sl][k] != 0      # ...but never a certain one

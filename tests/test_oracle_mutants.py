@@ -223,7 +223,28 @@ MUTANTS = [
     ('walk_sigma', 'sigma margin ignored',
      '        int m_sig = fabs(q.sigma) < mg[M_SIG];\n',
      '        int m_sig = 0;\n',
-     [('branches', 'test_leaves_equal_exhaustive_filter', (0,))])
+     [('branches', 'test_leaves_equal_exhaustive_filter', (0,))]),
+    # the extended tile lists (members a marginal projection decision may add or remove)
+    ('ext_outer', 'uncertain members only up to radius r, not r + 1',
+     '    int outer[4], inner[4] = {0, 0, 0, 0};\n    tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g] + 1, tw, th, gx, gy, outer);',
+     '    int outer[4], inner[4] = {0, 0, 0, 0};\n    tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g], tw, th, gx, gy, outer);',
+     [('branches', 'test_extended_lists_cover_every_allowed_radius', ())]),
+    ('ext_inner', 'certain core of radius r instead of r - 1',
+     'radius_all[g] > 1)\n        tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g] - 1, tw, th, gx, gy, inner);\n    if (tx',
+     'radius_all[g] > 1)\n        tile_rect(mean2d[2 * g], mean2d[2 * g + 1], radius_all[g], tw, th, gx, gy, inner);\n    if (tx',
+     [('branches', 'test_extended_lists_cover_every_allowed_radius', ())]),
+    ('ext_guard', 'a marginal guard decision not uncertain',
+     '    if (flags & F_GUARD) return 1;\n',
+     '    if (flags & F_GUARD) return 0;\n',
+     [('branches', 'test_a_marginal_guard_makes_every_tile_of_the_outer_rectangle_uncertain', ())]),
+    ('ext_rect_flag', 'a marginal rectangle edge not uncertain',
+     '    return (flags & (F_RADIUS | F_RECT)) != 0;',
+     '    return (flags & F_RADIUS) != 0;',
+     [('branches', 'test_extended_lists_cover_every_allowed_radius', ())]),
+    ('ext_inside_code', 'uncertain inside / outside codes swapped',
+     '    return in_own ? 2 : 1;',
+     '    return in_own ? 1 : 2;',
+     [('branches', 'test_extended_lists_cover_every_allowed_radius', ())])
 ]
 
 
