@@ -256,7 +256,7 @@ def planted(tmp_path_factory):
 
     def build(m):
         name, _, old, new, _ = m
-        assert src.count(old) == 1, f"{name}: the planted text must occur exactly once"
+        assert name == "unchanged" or src.count(old) == 1, f"{name}: the planted text must occur exactly once"
         c = root / f"{name}.c"
         c.write_text(src.replace(old, new))
         so = root / f"lib{name}.so"
@@ -265,7 +265,7 @@ def planted(tmp_path_factory):
         return name, str(so)
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-        return dict(ex.map(build, MUTANTS))
+        return dict(ex.map(build, MUTANTS + [("unchanged", "", "", "", [])]))
 
 
 @pytest.mark.parametrize("name, mistake, old, new, catchers", MUTANTS, ids=[m[0] for m in MUTANTS])
@@ -410,3 +410,32 @@ def test_pins_catch_a_planted_mistake_in_python(monkeypatch, name, mistake, old,
             monkeypatch.setattr(oracle, k, v)
     failed = run_catchers(catchers)
     assert failed, f"no pin caught the planted mistake ({mistake}); ran {catchers}"
+
+
+def _unique(catchers):
+    seen, out = set(), []
+    for c in catchers:
+        key = c if isinstance(c, str) else (c[0], c[1], tuple(c[2]))
+        if key not in seen:
+            seen.add(key)
+            out.append(c)
+    return out
+
+
+def test_every_catcher_passes_on_an_unchanged_copy(planted, monkeypatch):
+    """The control: built from the unchanged source (and the unchanged Python module loaded
+    the same way as the planted ones), every pin named above passes, so a failure above is the
+    planted mistake's doing and not the harness's."""
+    so = planted["unchanged"]
+    monkeypatch.setattr(oracle, "_LIB", so)
+    monkeypatch.setattr(oracle, "build", lambda force=False: so)
+    monkeypatch.setattr(oracle, "_lib", None)
+    assert run_catchers(_unique([c for m in MUTANTS for c in m[4]])) == []
+    mod = types.ModuleType("oracle_planted")
+    mod.__file__ = oracle.__file__
+    monkeypatch.setitem(sys.modules, "oracle_planted", mod)
+    exec(compile(open(oracle.__file__).read(), oracle.__file__, "exec"), mod.__dict__)
+    for k, v in vars(mod).items():
+        if isinstance(v, types.FunctionType):
+            monkeypatch.setattr(oracle, k, v)
+    assert run_catchers(_unique([c for m in PY_MUTANTS for c in m[4]])) == []
