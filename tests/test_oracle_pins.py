@@ -602,7 +602,7 @@ def test_backprojection_inverts_the_pinhole():
     # normalised depth divides by the accumulated opacity
     ptsn, _ = oracle.backproject(D, T, cam, normalize=True)
     pcn = ptsn @ V[:3, :3].T + V[:3, 3]
-    np.testing.assert_allclose(pcn[..., 2][mask], (D / (1 - T))[mask], rtol=1e-12)
+    np.testing.assert_allclose(pcn[..., 2][mask], D[mask] / (1 - T[mask]), rtol=1e-12)
 
 
 def test_coverage_of_a_wall_split_by_a_block_boundary():
